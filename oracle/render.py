@@ -1,0 +1,236 @@
+"""Brute-force per-pixel renderer of sliced 4D Gaussians and its gradient.
+
+The image is the plain definition of Eq. 3 (Sec. 3.1) over the 3D Gaussians
+sliced at time t (Sec. 3.2.2): every pixel composites, front to back, every
+visible Gaussian in the global order of camera-space depth of its sliced mean
+(ties by Gaussian index). There are no tiles, no keys and no sort kernel.
+
+Per-pixel rules (the 3D Gaussian Splatting rasteriser's, which the paper
+follows; thresholds as fixed for this renderer):
+  d      = pixel centre - mean2d
+  power  = -1/2 d^T conic d
+  skip   if power > 0 or power < -4.5       (3-sigma ellipse, per pixel)
+  alpha  = min(0.99, opacity_t exp(power))
+  skip   if alpha < 1/255
+  T'     = T (1 - alpha); stop before this Gaussian if T' < 1e-4
+  C     += rgb alpha T;  T = T'
+  pixel  = C + T bg
+Gaussians are culled before the pixel loop when lambda (t - mu_t)^2 > 16
+(Sec. 3.2.2), when the sliced mean is at depth <= 0.2, or when the 2D
+covariance is not positive definite.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from .projection import camera_tensors, project
+from .rotor import rotor_normalize, rotor_to_matrix
+from .sh import sh_color
+from .slicing import covariance4, slice_at
+
+ALPHA_MIN = 1.0 / 255.0
+ALPHA_MAX = 0.99
+T_MIN = 1e-4
+POWER_CUT = -4.5
+TEMPORAL_CUT = 16.0
+NEAR = 0.2
+DILATION = 0.3
+
+PARAM_NAMES = ("mean", "rotor", "logscale", "logit", "sh")
+
+
+def to_f64(g: dict) -> dict:
+    """Upcast a dict of float32 numpy parameter arrays to float64 tensors."""
+    return {k: torch.as_tensor(np.asarray(g[k]), dtype=torch.float64).clone() for k in PARAM_NAMES}
+
+
+def _cam(cam):
+    return cam if isinstance(cam, dict) else camera_tensors(cam)
+
+
+def preprocess(scene: dict, cam, t: float, cull_temporal: bool = True, sh_degree: int = 3) -> dict:
+    """Per-Gaussian steps: activations, F_norm, F_map, Sigma4, slice, projection,
+    SH colour. Returns float64 tensors (differentiable w.r.t. ``scene``)."""
+    cam = _cam(cam)
+    scale = torch.exp(scene["logscale"])
+    opacity = torch.sigmoid(scene["logit"])
+    R = rotor_to_matrix(rotor_normalize(scene["rotor"]))
+    sigma4 = covariance4(R, scale)
+    mu3, sigma3, temporal, lam_dt2 = slice_at(scene["mean"], sigma4, t)
+    proj = project(mu3, sigma3, cam, DILATION)
+    centre = -cam["R"].T @ cam["t"]
+    dirs = mu3 - centre
+    dirs = dirs / torch.linalg.norm(dirs, dim=-1, keepdim=True)
+    rgb = sh_color(scene["sh"], dirs, sh_degree)
+    visible = (proj["z"] > NEAR) & (proj["det"] > 0)
+    if cull_temporal:
+        visible = visible & (lam_dt2 <= TEMPORAL_CUT)
+    return {
+        "visible": visible, "mean2d": proj["mean2d"], "conic": proj["conic"],
+        "cov2d": proj["cov2d"], "det": proj["det"], "z": proj["z"], "pc": proj["pc"],
+        "opacity_t": opacity * temporal, "rgb": rgb, "mu3": mu3, "sigma3": sigma3,
+        "sigma4": sigma4, "lam_dt2": lam_dt2, "R": R,
+    }
+
+
+def depth_order(rec: dict) -> torch.Tensor:
+    """Indices of the visible Gaussians in increasing depth, ties by index."""
+    vis = torch.nonzero(rec["visible"]).flatten()
+    z = rec["z"].detach()[vis]
+    _, perm = torch.sort(z, stable=True)
+    return vis[perm]
+
+
+def _composite(m2, con, o, col, z, px, py, bg):
+    """Composite a chunk of pixels (px, py: [P]) over G depth-ordered Gaussians."""
+    dx = px[:, None] - m2[None, :, 0]
+    dy = py[:, None] - m2[None, :, 1]
+    power = -0.5 * (con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy) - con[None, :, 1] * dx * dy
+    in_cut = (power <= 0.0) & (power >= POWER_CUT)
+    alpha_raw = o[None, :] * torch.exp(power)
+    alpha = torch.clamp(alpha_raw, max=ALPHA_MAX)
+    valid = in_cut & (alpha >= ALPHA_MIN)
+    a_eff = torch.where(valid, alpha, torch.zeros_like(alpha))
+    one_minus = 1.0 - a_eff
+    T_after = torch.cumprod(one_minus, dim=1)
+    ones = torch.ones_like(T_after[:, :1])
+    T_before = torch.cat([ones, T_after[:, :-1]], dim=1)
+    included = valid & (T_after >= T_MIN)
+    w = torch.where(included, a_eff * T_before, torch.zeros_like(a_eff))
+    C = w @ col  # [P,3]
+    T_final = torch.prod(torch.where(included, one_minus, torch.ones_like(one_minus)), dim=1)
+    img = C + T_final[:, None] * bg[None, :]
+    G = m2.shape[0]
+    pos = torch.arange(G)
+    last_pos = torch.where(included, pos[None, :], torch.full_like(pos[None, :], -1)).amax(dim=1) \
+        if G > 0 else torch.full((px.shape[0],), -1, dtype=torch.long)
+    # decision margins over the Gaussians the pixel reaches (T before >= 1e-4)
+    with torch.no_grad():
+        reached = T_before.detach() >= T_MIN
+        inf = torch.full_like(power, math.inf)
+        m_cut = torch.where(reached, (power.detach() - POWER_CUT).abs() / abs(POWER_CUT), inf)
+        m_alpha = torch.where(reached & in_cut, (alpha_raw.detach() - ALPHA_MIN).abs() / ALPHA_MIN, inf)
+        m_T = torch.where(reached & valid, (T_after.detach() - T_MIN).abs() / T_MIN, inf)
+        m_thr = torch.minimum(torch.minimum(m_cut, m_alpha), m_T)
+        m_thr = m_thr.amin(dim=1) if G > 0 else torch.full((px.shape[0],), math.inf, dtype=torch.float64)
+        zz = z[None, :].expand_as(power)
+        vz = torch.where(valid & reached, zz, torch.full_like(zz, -math.inf))
+        prev = torch.cummax(vz, dim=1).values
+        prev = torch.cat([torch.full_like(prev[:, :1], -math.inf), prev[:, :-1]], dim=1)
+        gap = torch.where(valid & reached & torch.isfinite(prev), (zz - prev) / zz, inf)
+        m_dep = gap.amin(dim=1) if G > 0 else torch.full((px.shape[0],), math.inf, dtype=torch.float64)
+    return img, T_final, last_pos, m_thr, m_dep
+
+
+def _pixel_grid(width: int, height: int):
+    jj, ii = torch.meshgrid(torch.arange(height), torch.arange(width), indexing="ij")
+    return ii.flatten(), jj.flatten()
+
+
+def _chunked(rec, order, cols, rows, bg, budget=4_000_000):
+    G = int(order.numel())
+    m2 = rec["mean2d"][order]
+    con = rec["conic"][order]
+    o = rec["opacity_t"][order]
+    col = rec["rgb"][order]
+    z = rec["z"].detach()[order]
+    P = cols.numel()
+    step = max(1, budget // max(G, 1))
+    outs = []
+    for s in range(0, P, step):
+        px = cols[s:s + step].to(torch.float64) + 0.5
+        py = rows[s:s + step].to(torch.float64) + 0.5
+        outs.append(_composite(m2, con, o, col, z, px, py, bg))
+    img = torch.cat([x[0] for x in outs]) if outs else torch.zeros((0, 3), dtype=torch.float64)
+    T = torch.cat([x[1] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
+    lp = torch.cat([x[2] for x in outs]) if outs else torch.zeros(0, dtype=torch.long)
+    mt = torch.cat([x[3] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
+    md = torch.cat([x[4] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
+    last = torch.where(lp >= 0, order[lp.clamp(min=0)] if G > 0 else lp, torch.full_like(lp, -1))
+    return img, T, last, mt, md
+
+
+def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool = True,
+           sh_degree: int = 3, rec: dict | None = None) -> dict:
+    """Render the full image. Returns ``image`` [3,H,W], ``T`` [H,W] (final
+    transmittance), ``last`` [H,W] (index of the last composited Gaussian, -1 if
+    none), ``margin`` [H,W] (smallest relative margin of a threshold decision),
+    ``margin_depth`` [H,W] (smallest relative depth gap between two Gaussians
+    that both contribute), and the per-Gaussian records ``rec``."""
+    cam = _cam(cam)
+    if rec is None:
+        rec = preprocess(scene, cam, t, cull_temporal, sh_degree)
+    order = depth_order(rec)
+    W, H = cam["width"], cam["height"]
+    cols, rows = _pixel_grid(W, H)
+    bg_t = torch.as_tensor(bg, dtype=torch.float64)
+    img, T, last, mt, md = _chunked(rec, order, cols, rows, bg_t)
+    return {
+        "image": img.T.reshape(3, H, W), "T": T.reshape(H, W), "last": last.reshape(H, W),
+        "margin": mt.reshape(H, W), "margin_depth": md.reshape(H, W), "rec": rec, "order": order,
+    }
+
+
+def render_pixels(scene: dict, cam, t: float, pixels, bg=(0.0, 0.0, 0.0), rec: dict | None = None,
+                  budget: int = 4_000_000) -> dict:
+    """Render only the listed pixels (int [P,2] as (column, row))."""
+    cam = _cam(cam)
+    if rec is None:
+        rec = preprocess(scene, cam, t)
+    order = depth_order(rec)
+    pix = torch.as_tensor(np.asarray(pixels), dtype=torch.long)
+    bg_t = torch.as_tensor(bg, dtype=torch.float64)
+    img, T, last, mt, md = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
+    return {"rgb": img, "T": T, "last": last, "margin": mt, "margin_depth": md}
+
+
+REC_GRAD_KEYS = ("mean2d", "conic", "opacity_t", "rgb")
+
+
+def render_grad(scene: dict, cam, t: float, grad_image, bg=(0.0, 0.0, 0.0), sh_degree: int = 3) -> dict:
+    """Gradient of L = sum(grad_image * image) w.r.t. every parameter, by
+    reverse-mode automatic differentiation of ``render`` in float64. The
+    composite is differentiated pixel chunk by pixel chunk into per-Gaussian
+    record gradients (d mean2d, d conic, d opacity_t, d rgb), which are then
+    pulled back through ``preprocess``. Returns the parameter gradients under
+    the parameter names and the record gradients under ``rec_<name>``."""
+    cam = _cam(cam)
+    leaves = {k: v.detach().clone().requires_grad_(True) for k, v in scene.items()}
+    rec = preprocess(leaves, cam, t, True, sh_degree)
+    recd = {k: (rec[k].detach().clone().requires_grad_(True) if k in REC_GRAD_KEYS else rec[k])
+            for k in rec}
+    order = depth_order(recd)
+    W, H = cam["width"], cam["height"]
+    cols, rows = _pixel_grid(W, H)
+    gi = torch.as_tensor(np.asarray(grad_image), dtype=torch.float64).reshape(3, H * W).T
+    bg_t = torch.as_tensor(bg, dtype=torch.float64)
+    G = max(int(order.numel()), 1)
+    step = max(1, 2_000_000 // G)
+    m2 = recd["mean2d"][order]
+    con = recd["conic"][order]
+    o = recd["opacity_t"][order]
+    col = recd["rgb"][order]
+    z = recd["z"].detach()[order]
+    for s in range(0, H * W, step):
+        px = cols[s:s + step].to(torch.float64) + 0.5
+        py = rows[s:s + step].to(torch.float64) + 0.5
+        img = _composite(m2, con, o, col, z, px, py, bg_t)[0]
+        (img * gi[s:s + step]).sum().backward(retain_graph=True)
+    out = {}
+    rec_grads = []
+    rec_outs = []
+    for k in REC_GRAD_KEYS:
+        g = recd[k].grad
+        if g is None:
+            g = torch.zeros_like(recd[k])
+        out["rec_" + k] = g.detach()
+        rec_grads.append(g)
+        rec_outs.append(rec[k])
+    torch.autograd.backward(rec_outs, rec_grads)
+    for k in leaves:
+        g = leaves[k].grad
+        out[k] = torch.zeros_like(leaves[k]) if g is None else g.detach()
+    return out

@@ -1,0 +1,290 @@
+"""Pins for the oracle's projection and compositing (Sec. 3.1 Eq. 3, Sec. 3.2.2):
+analytic single-Gaussian footprints (Jacobian of the projection by automatic
+differentiation, slice by textbook conditioning, rotation from closed forms),
+two-layer closed form, the transmittance stop, the spatial/temporal
+separability of Sec. 3.2.1, cull neutrality and finite-difference gradients."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle.render import PARAM_NAMES, depth_order
+
+special = pytest.importorskip("scipy.special")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rotors():
+    rows = [ln for ln in open(os.path.join(GOLDEN, "rotor_cases.txt")) if ln.strip() and not ln.startswith("#")]
+    out = []
+    for ln in rows:
+        v = np.array([float(x) for x in ln.split()])
+        out.append((v[:8], v[8:].reshape(4, 4)))
+    return out
+
+
+def _real_sh_l1(d):
+    th = math.acos(d[2])
+    ph = math.atan2(d[1], d[0])
+    out = [special.sph_harm_y(0, 0, th, ph).real]
+    Y11 = special.sph_harm_y(1, 1, th, ph)
+    out += [math.sqrt(2) * Y11.imag, special.sph_harm_y(1, 0, th, ph).real, math.sqrt(2) * Y11.real]
+    return np.array(out)
+
+
+def expected_single(mean4, Rm, s, logit, sh, cam, t, bg=np.zeros(3)):
+    """Independent footprint of one Gaussian: image [3,H,W], T [H,W]."""
+    S4 = Rm @ np.diag(s ** 2) @ Rm.T
+    dt = t - mean4[3]
+    mu3 = mean4[:3] + S4[:3, 3] / S4[3, 3] * dt
+    S3 = S4[:3, :3] - np.outer(S4[:3, 3], S4[:3, 3]) / S4[3, 3]
+    temporal = math.exp(-0.5 * dt * dt / S4[3, 3])
+    w2c = cam.world_to_cam.astype(np.float64)
+
+    def pi(x):
+        pc = torch.as_tensor(w2c[:, :3]) @ x + torch.as_tensor(w2c[:, 3])
+        return torch.stack([cam.fx * pc[0] / pc[2] + cam.cx, cam.fy * pc[1] / pc[2] + cam.cy])
+
+    x0 = torch.as_tensor(mu3)
+    J = torch.autograd.functional.jacobian(pi, x0).numpy()
+    m2 = pi(x0).numpy()
+    cov = J @ S3 @ J.T + 0.3 * np.eye(2)
+    inv = np.linalg.inv(cov)
+    d = mu3 - cam.center
+    d = d / np.linalg.norm(d)
+    Y = _real_sh_l1(d)
+    rgb = np.maximum(0.0, (Y[:, None] * sh[:4]).sum(0) + 0.5)
+    o = 1.0 / (1.0 + math.exp(-logit)) * temporal
+    H, W = cam.height, cam.width
+    img = np.zeros((3, H, W))
+    T = np.ones((H, W))
+    for j in range(H):
+        for i in range(W):
+            dd = np.array([i + 0.5, j + 0.5]) - m2
+            power = -0.5 * dd @ inv @ dd
+            if power > 0 or power < -4.5:
+                continue
+            a = min(0.99, o * math.exp(power))
+            if a < 1 / 255:
+                continue
+            img[:, j, i] = rgb * a
+            T[j, i] = 1 - a
+    img += T[None] * bg[:, None, None]
+    return img, T, m2
+
+
+def _one(mean4, rotor, ls, logit, sh):
+    return {
+        "mean": torch.as_tensor(np.asarray(mean4, np.float64)[None]),
+        "rotor": torch.as_tensor(np.asarray(rotor, np.float64)[None]),
+        "logscale": torch.as_tensor(np.asarray(ls, np.float64)[None]),
+        "logit": torch.as_tensor(np.array([logit], np.float64)),
+        "sh": torch.as_tensor(np.asarray(sh, np.float64)[None]),
+    }
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_single_gaussian_footprint(case):
+    rotor, Rm = _golden_rotors()[case]
+    cam = synth.look_at((0.3, -0.2, -4.0), (0.0, 0.0, 0.0), 64, 48)
+    rng = np.random.default_rng(case)
+    mean4 = np.array([0.1, -0.05, 0.2, 0.4])
+    ls = np.log(np.array([0.35, 0.15, 0.25, 0.5]))
+    sh = np.zeros((16, 3))
+    sh[:4] = rng.normal(0, 0.4, (4, 3))
+    sh[4:] = 0.0
+    logit = 1.2
+    t = 0.55
+    bg = np.array([0.2, 0.4, 0.8])
+    img_ref, T_ref, _ = expected_single(mean4, Rm, np.exp(ls), logit, sh, cam, t, bg)
+    out = oracle.render(_one(mean4, rotor, ls, logit, sh), cam, t, bg=tuple(bg))
+    np.testing.assert_allclose(out["image"].numpy(), img_ref, atol=1e-12)
+    np.testing.assert_allclose(out["T"].numpy(), T_ref, atol=1e-12)
+    covered = T_ref < 1
+    assert covered.sum() > 50  # the footprint spans many pixels
+    assert (out["last"].numpy()[covered] == 0).all() and (out["last"].numpy()[~covered] == -1).all()
+
+
+def test_two_layers_closed_form():
+    """C = c1 a1 + c2 a2 (1 - a1) with Gaussian 1 nearer (Eq. 3)."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 40, 40)
+    ident = np.zeros(8)
+    ident[0] = 1
+    g = []
+    for mean4, col in (((0.05, 0.0, 0.5, 0.5), 0.3), ((-0.05, 0.02, -0.5, 0.5), -0.2)):
+        sh = np.zeros((16, 3))
+        sh[0] = col
+        g.append((np.array(mean4), sh))
+    ls = np.log(np.array([0.3, 0.25, 0.2, 1.0]))
+    scene = {k: torch.cat([_one(m, ident, ls, 0.8, sh)[k] for m, sh in g]) for k in PARAM_NAMES}
+    out = oracle.render(scene, cam, 0.5)
+    # Gaussian 1 has the larger z so it is behind; the nearer one is index 1
+    i1, T1, _ = expected_single(g[1][0], np.eye(4), np.exp(ls), 0.8, g[1][1], cam, 0.5)
+    i0, T0, _ = expected_single(g[0][0], np.eye(4), np.exp(ls), 0.8, g[0][1], cam, 0.5)
+    a_near, a_far = 1 - T1, 1 - T0
+    ref = i1 + i0 * (1 - a_near)[None]
+    np.testing.assert_allclose(out["image"].numpy(), ref, atol=1e-12)
+    np.testing.assert_allclose(out["T"].numpy(), (1 - a_near) * (1 - a_far), atol=1e-12)
+
+
+def test_transmittance_stop_on_opaque_stack():
+    """Five Gaussians on the optical axis, alpha = 0.95 at the centre pixel:
+    T goes 0.05, 0.0025, 1.25e-4, then 6.25e-6 < 1e-4, so the 4th is not
+    composited and the 3rd nearest is the last one."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 33, 33)  # centre pixel 16 at 16.5
+    ident = np.zeros(8)
+    ident[0] = 1
+    logit = math.log(0.95 / 0.05)
+    zs = [0.9, -0.3, 0.6, 0.0, -0.6]
+    cols = [0.1, 0.2, 0.3, 0.4, 0.5]
+    parts = []
+    for z, c in zip(zs, cols):
+        sh = np.zeros((16, 3))
+        sh[0] = c
+        parts.append(_one((0.0, 0.0, z, 0.5), ident, np.log([0.2, 0.2, 0.2, 1.0]), logit, sh))
+    scene = {k: torch.cat([p[k] for p in parts]) for k in parts[0]}
+    out = oracle.render(scene, cam, 0.5)
+    near = np.argsort(zs)  # nearest first
+    C0 = 0.5 / math.sqrt(math.pi)
+    rgb = [0.5 + C0 * cols[k] for k in near]
+    T = 1.0
+    ref = 0.0
+    for k in range(3):
+        ref += rgb[k] * 0.95 * T
+        T *= 0.05
+    assert out["last"][16, 16].item() == near[2]
+    assert abs(out["T"][16, 16].item() - 1.25e-4) < 1e-15
+    assert abs(out["image"][0, 16, 16].item() - ref) < 1e-13
+
+
+def test_temporal_cull_never_changes_the_image():
+    """lambda (t - mu_t)^2 > 16 gives alpha <= exp(-8) < 1/255 (Sec. 3.2.2)."""
+    g, cam, t = synth.small_scene(seed=7, n=600, width=64, height=64)
+    sc = oracle.to_f64(g)
+    a = oracle.render(sc, cam, t, cull_temporal=True)
+    b = oracle.render(sc, cam, t, cull_temporal=False)
+    assert int(a["rec"]["visible"].sum()) < int(b["rec"]["visible"].sum())
+    # same decisions; only the summation's rounding may differ
+    assert torch.equal(a["last"], b["last"])
+    assert (a["image"] - b["image"]).abs().max() < 1e-14 and (a["T"] - b["T"]).abs().max() < 1e-14
+
+
+def test_static_rotor_reduces_to_3d_splatting():
+    """tau = 0 (Sec. 3.2.1): the 4D render equals a 3D Gaussian splat with
+    Sigma3 = Q diag(s^2) Q^T (Q the quaternion matrix of (s, -b12, b02, -b01))
+    and opacity o exp(-1/2 (t - mu_t)^2 / s_t^2)."""
+    g, cam, t = synth.small_scene(seed=8, n=400, width=64, height=64)
+    g["rotor"][:, 4:] = 0.0
+    sc = oracle.to_f64(g)
+    out4 = oracle.render(sc, cam, t)
+    q = sc["rotor"][:, :4].numpy()
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    from test_oracle_rotor import quat_matrix
+    Q = np.stack([quat_matrix(a, -d, c, -b) for a, b, c, d in q])
+    s = np.exp(sc["logscale"].numpy())
+    S3 = Q @ (s[:, :3, None] ** 2 * np.transpose(Q, (0, 2, 1)))
+    mu3 = torch.as_tensor(sc["mean"][:, :3].numpy())
+    camt = oracle.camera_tensors(cam)
+    pr = oracle.project(mu3, torch.as_tensor(S3), camt)
+    dt = t - sc["mean"][:, 3].numpy()
+    op = 1 / (1 + np.exp(-sc["logit"].numpy())) * np.exp(-0.5 * dt * dt / s[:, 3] ** 2)
+    d = mu3 - torch.as_tensor(cam.center)
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    rec = {"visible": (pr["z"] > 0.2) & (pr["det"] > 0) & torch.as_tensor(dt * dt / s[:, 3] ** 2 <= 16),
+           "mean2d": pr["mean2d"], "conic": pr["conic"], "z": pr["z"],
+           "opacity_t": torch.as_tensor(op), "rgb": oracle.sh_color(sc["sh"], d)}
+    out3 = oracle.render(None, cam, t, rec=rec)
+    np.testing.assert_allclose(out4["image"].numpy(), out3["image"].numpy(), atol=1e-12)
+    assert torch.equal(out4["last"], out3["last"])
+
+
+def test_input_order_does_not_matter():
+    g, cam, t = synth.small_scene(seed=9, n=500, width=48, height=48)
+    sc = oracle.to_f64(g)
+    perm = torch.as_tensor(np.random.default_rng(0).permutation(500))
+    sp = {k: v[perm] for k, v in sc.items()}
+    a = oracle.render(sc, cam, t)
+    b = oracle.render(sp, cam, t)
+    np.testing.assert_allclose(a["image"].numpy(), b["image"].numpy(), atol=1e-14)
+    la, lb = a["last"], b["last"]
+    mapped = torch.where(lb >= 0, perm[lb.clamp(min=0)], lb)
+    assert torch.equal(la, mapped)
+
+
+def test_background_adds_final_transmittance():
+    g, cam, t = synth.small_scene(seed=10, n=300, width=32, height=32)
+    sc = oracle.to_f64(g)
+    a = oracle.render(sc, cam, t)
+    b = oracle.render(sc, cam, t, bg=(1.0, 0.5, 0.25))
+    bg = torch.tensor([1.0, 0.5, 0.25], dtype=torch.float64)
+    assert torch.allclose(b["image"], a["image"] + a["T"][None] * bg[:, None, None], atol=1e-15)
+
+
+def fd_scene():
+    """64 Gaussians sized to cover a 32x32 view (the finite-difference workload)."""
+    g = synth.gaussians(64, 11, ls_xyz=(-1.6, 0.3), ls_t=(-0.7, 0.3))
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 32, 32)
+    return g, cam, 0.5
+
+
+def _decisions(sc, cam, t):
+    rec = oracle.preprocess(sc, cam, t)
+    order = depth_order(rec)
+    jj, ii = torch.meshgrid(torch.arange(cam.height), torch.arange(cam.width), indexing="ij")
+    px = ii.flatten().double() + 0.5
+    py = jj.flatten().double() + 0.5
+    m2, con = rec["mean2d"][order], rec["conic"][order]
+    dx = px[:, None] - m2[None, :, 0]
+    dy = py[:, None] - m2[None, :, 1]
+    power = -0.5 * (con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy) - con[None, :, 1] * dx * dy
+    alpha = torch.clamp(rec["opacity_t"][order][None] * torch.exp(power), max=0.99)
+    valid = (power <= 0) & (power >= -4.5) & (alpha >= 1 / 255)
+    T = torch.cumprod(1 - torch.where(valid, alpha, torch.zeros_like(alpha)), 1)
+    inc = valid & (T >= 1e-4)
+    clamp = (alpha >= 0.99) & valid
+    return (tuple(order.tolist()), valid.numpy().tobytes(), inc.numpy().tobytes(), clamp.numpy().tobytes())
+
+
+def test_gradient_matches_central_differences():
+    g, cam, t = fd_scene()
+    sc = oracle.to_f64(g)
+    rng = np.random.default_rng(12)
+    wimg = rng.normal(0, 1, (3, 32, 32))
+    grads = oracle.render_grad(sc, cam, t, wimg)
+    W = torch.as_tensor(wimg)
+
+    def L(s):
+        return float((oracle.render(s, cam, t)["image"] * W).sum())
+
+    base = _decisions(sc, cam, t)
+    checked = 0
+    for name in PARAM_NAMES:
+        flat = sc[name].reshape(-1)
+        idx = rng.choice(flat.numel(), size=min(60, flat.numel()), replace=False)
+        for k in idx:
+            x = flat[k].item()
+            h = 1e-6 * max(1.0, abs(x))
+            vals = []
+            ok = True
+            for sgn in (1, -1):
+                s2 = {kk: vv.clone() for kk, vv in sc.items()}
+                s2[name].reshape(-1)[k] = x + sgn * h
+                if _decisions(s2, cam, t) != base:
+                    ok = False
+                    break
+                vals.append(L(s2))
+            if not ok:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grads[name].reshape(-1)[k].item()
+            scale = grads[name].abs().max().item()
+            assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-3 * scale) + 1e-9, (name, int(k), fd, an)
+            checked += 1
+    assert checked >= 200
+    # every parameter group receives gradient
+    for name in ("mean", "rotor", "logscale", "logit", "sh"):
+        assert grads[name].abs().max() > 0
