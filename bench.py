@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the 4D-rotor Gaussian splatting render on one GB300.
+
+Workload (frames/s): 300,000 seeded synthetic 4D Gaussians (means in [-3,3]^3),
+1352x1014, the 300-frame circular sweep at radius 8 (t_k = k/299), FP32, one
+view per launch; a step renders one frame of the sweep. The same run also
+measures the training step (4 views at seeded (t, angle), forward + L1 loss +
+backward through the autograd-free C ABI path) as train it/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Multi-GPU runs (torchrun) are independent replicas:
+each rank renders its own frames of the sweep, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & train it/s, 300k 4D Gaussians @1352×1014, vs plain path; % roofline"
+WIDTH, HEIGHT, N_GAUSS, FRAMES, RADIUS = 1352, 1014, 300_000, 300, 8.0
+TRAIN_VIEWS = 4
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--train-steps", type=int, default=10)
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---- clocks ------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- workload ------------------------------------------------------------------
+def frame_camera(k: int):
+    import synth
+    return synth.orbit_camera(k % FRAMES, FRAMES, RADIUS, WIDTH, HEIGHT)
+
+
+def algorithmic_bytes(stage: str, n: int, n_vis: int, keys: int, passes: int, npix: int) -> float:
+    """Bytes the method must move per launch of a stage."""
+    if stage == "preprocess":
+        return 68.0 * n + 192.0 * n_vis + 48.0 * n_vis + 12.0 * n
+    if stage == "binning":
+        return 4.0 * n + 12.0 * n_vis + 12.0 * keys
+    if stage == "sort":
+        return 24.0 * keys
+    if stage == "ranges":
+        return 8.0 * keys
+    if stage == "blend":
+        return 4.0 * keys + 48.0 * n_vis + 20.0 * npix
+    return 0.0
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03307_gb300 as r4g
+    from paper_2402_03307_gb300 import abi
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    g = synth.fwd300k_scene()
+    params = {k: torch.as_tensor(v).to(dev).contiguous() for k, v in g.items()}
+    rend = r4g.Renderer()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # size the key buffer once over the whole sweep (not timed)
+    cap = 0
+    for k in range(0, FRAMES, 15):
+        cam, t = frame_camera(k)
+        res = rend.render(params, cam, t)
+        cap = max(cap, res.key_capacity)
+        _, need = rend.status(res)
+        cap = max(cap, int(need * 1.1))
+    frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    frames = [(rank * args.steps + i) * 7 % FRAMES for i in range(args.steps)]
+
+    def render_frame(k):
+        cam, t = frame_camera(k)
+        return rend.render(params, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
+
+    for i in range(args.warmup):
+        render_frame(frames[i % len(frames)])
+    torch.cuda.synchronize()
+    abi.r4g_stage_times(rend.ctx, reset=True)
+    abi.r4g_set_timing(rend.ctx, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i, k in enumerate(frames):
+        flush.zero_()  # evict L2 between frames (outside the timed events)
+        evs[i][0].record(stream)
+        res = render_frame(k)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    abi.r4g_set_timing(rend.ctx, False)
+    stage_ms, stage_launch = abi.r4g_stage_times(rend.ctx, reset=True)
+    st, need = rend.status(res)
+    if st != abi.R4G_OK:
+        raise RuntimeError("key buffer overflow during the timed region")
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    fps = world * len(frames) / (total_ms / 1e3)
+
+    # per-frame statistics for the roofline model (frame of the last step)
+    ex = rend.export(res)
+    keys = ex["key_count"]
+    n_vis = int((ex["records"][:, 5] > 0).sum().item())
+    passes = math.ceil((32 + math.ceil(math.log2(math.ceil(WIDTH / 16) * math.ceil(HEIGHT / 16)))) / 8)
+    per_stage = {k: v / len(frames) for k, v in stage_ms.items() if v > 0}
+    top = max(per_stage, key=per_stage.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bytes_top = algorithmic_bytes(top, N_GAUSS, n_vis, keys, passes, WIDTH * HEIGHT)
+    achieved = bytes_top / (per_stage[top] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                "peak_source": peak_src,
+                "stage_ms": {k: round(v, 4) for k, v in per_stage.items()}}
+
+    out = {"metric": METRIC, "value": round(fps, 2), "unit": "frames/s", "n_gpus": world,
+           "steps": len(frames), "warmup": args.warmup, "ms_per_step": round(total_ms / len(frames), 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded 4D Gaussians; stands in for Plenoptic Video at its resolution)",
+           "config": {"workload": "300k 4D Gaussians, 1352x1014, 300-frame orbit sweep r=8, FP32, 1 view/launch",
+                      "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile": "16x16",
+                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
+                      "keys_last_frame": keys, "visible_last_frame": n_vis},
+           "gpu_launches": int(sum(stage_launch.values())),
+           "wall_s": round(wall, 3), "clocks": clk, "roofline": roofline}
+
+    # ---- training step: 4 views forward + L1 + backward --------------------------
+    if not args.no_train and not args.frames_only:
+        out["train"] = train_bench(args, rend, params, dev, stream)
+    # ---- end to end through host buffers ---------------------------------------------
+    if not args.no_e2e and not args.frames_only:
+        out["e2e"] = e2e_bench(args, rend, g, dev, stream, frames, cap)
+    return out
+
+
+def train_bench(args, rend, params, dev, stream):
+    import torch
+    import synth
+
+    views = synth.train_views(seed=33, views=TRAIN_VIEWS)
+    target = torch.as_tensor(synth.smooth_target(34, WIDTH, HEIGHT)).to(dev)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+    caps = []
+    for cam, t in views:
+        r = rend.render(params, cam, t)
+        caps.append(int(rend.status(r)[1] * 1.1) + 1024)
+    frames = [rend.new_frame(N_GAUSS, WIDTH, HEIGHT, c, dev) for c in caps]
+    imgs = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev) for _ in views]
+    gimg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    inv = 1.0 / (3 * WIDTH * HEIGHT * len(views))
+
+    def step():
+        for v in grads.values():
+            v.zero_()
+        for (cam, t), fr, im, c in zip(views, frames, imgs, caps):
+            res = rend.render(params, cam, t, frame=fr, key_capacity=c, out=im, check=False)
+            torch.sign(im - target, out=gimg)
+            gimg.mul_(inv)
+            rend.backward(params, cam, t, res, gimg, grads)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.train_steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.train_steps
+    return {"value": round(1000.0 / ms, 3), "unit": "it/s", "ms_per_it": round(ms, 3), "views": TRAIN_VIEWS,
+            "steps": args.train_steps, "loss": "L1 vs seeded smooth target (sign gradient in torch)"}
+
+
+def e2e_bench(args, rend, g, dev, stream, frames, cap):
+    import torch
+
+    host = {k: torch.as_tensor(v).pin_memory() for k, v in g.items()}
+    dparams = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()}
+    frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    himg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = himg.numel() * 4
+
+    def step(k):
+        for name, v in host.items():
+            dparams[name].copy_(v, non_blocking=True)
+        cam, t = frame_camera(k)
+        rend.render(dparams, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
+        himg.copy_(img, non_blocking=True)
+
+    for i in range(3):
+        step(frames[i % len(frames)])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in frames:
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(len(frames) / (ms / 1e3), 2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+# ---- CPU oracle baseline -----------------------------------------------------------
+def cpu_baseline(budget_s: float = 15.0) -> dict:
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+
+    g = synth.fwd300k_scene()
+    cam, t = frame_camera(37)
+    sc = oracle.to_f64(g)
+    t0 = time.perf_counter()
+    rec = oracle.preprocess(sc, cam, t)
+    t_pre = time.perf_counter() - t0
+    done, t_pix = 0, 0.0
+    chunk = 256
+    seed = 0
+    while t_pix < budget_s:
+        pix = synth.random_pixels(seed, WIDTH, HEIGHT, chunk)
+        t0 = time.perf_counter()
+        oracle.render_pixels(sc, cam, t, pix, rec=rec)
+        t_pix += time.perf_counter() - t0
+        done += len(pix)
+        seed += 1
+    per_frame = t_pre + t_pix * (WIDTH * HEIGHT / done)
+    return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: preprocess of all 300k Gaussians ({t_pre:.2f} s) + {done} random pixels of "
+                      f"frame 37 brute-forced over all visible Gaussians ({t_pix:.1f} s), scaled to "
+                      f"{WIDTH * HEIGHT} pixels"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(budget_s=max(5.0, min(60.0, 2.0 * args.steps)))
+        out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "frames/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "300k 4D Gaussians, 1352x1014, orbit sweep frame 37"},
+               "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
+                                           "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+    out = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.frames_only:
+        out["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

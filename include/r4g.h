@@ -1,0 +1,214 @@
+/*
+ * r4g.h -- C ABI of the GB300 (sm_103a) renderer for 4D-rotor Gaussian splatting
+ * (Duan et al., "4D-Rotor Gaussian Splatting", SIGGRAPH 2024, arXiv 2402.03307).
+ *
+ * The library renders N anisotropic 4D Gaussians at a query time t and
+ * differentiates the render:
+ *   rotor normalisation F_norm            appendix A.1
+ *   rotor -> 4x4 rotation F_map           appendix A.2
+ *   Sigma4 = R S S^T R^T                  Sec. 3.2.1 (Eq. 5)
+ *   temporal slice (Eq. 7, stable form)   Sec. 3.2.2, appendix A.3
+ *   visibility cull lambda (t-mu_t)^2>16  Sec. 3.2.2
+ *   EWA projection J V Sigma V^T J^T      Sec. 3.1
+ *   SH colour, alpha compositing (Eq. 3)  Sec. 3.1
+ * with (tile, depth) 64-bit keys, a bit-exact stable radix sort and a tiled
+ * front-to-back blend, all in hand-written CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - All buffer pointers are DEVICE pointers unless a parameter says "host".
+ *    The caller owns every buffer; the library never frees caller memory and
+ *    never allocates except in r4g_create (a few bytes of status memory).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work on that stream; none synchronises, except
+ *    r4g_frame_status, which waits for the stream to read the frame's status.
+ *  - Return value: R4G_OK, or an error code for invalid arguments detected on
+ *    the host (nothing is enqueued then), or R4G_ECUDA when a launch fails
+ *    (r4g_last_error gives the CUDA message). Errors that only the device can
+ *    see (key-buffer overflow) are recorded in the frame and returned by
+ *    r4g_frame_status.
+ *  - Floating point: FP32 arithmetic; BF16 storage is accepted for the scales
+ *    and SH coefficients; an FP64 debug mode computes Sigma4 and the slice in
+ *    double precision.
+ */
+#ifndef R4G_H
+#define R4G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum r4g_status {
+  R4G_OK = 0,
+  R4G_EINVAL = 1,      /* a NULL pointer, a negative or oversize count, a bad enum */
+  R4G_ENOMEM = 2,      /* r4g_create could not allocate its status memory */
+  R4G_EWORKSPACE = 3,  /* the frame / scratch buffer is smaller than required */
+  R4G_ECUDA = 4,       /* a CUDA launch or call failed; see r4g_last_error */
+  R4G_ETIMEOUT = 5,    /* reserved: a bounded device-side wait gave up */
+  R4G_EDEVICE = 6,     /* the device reported an inconsistent state */
+  R4G_EOVERFLOW = 7    /* the frame's key capacity was too small (see r4g_frame_status) */
+} r4g_status;
+
+typedef enum r4g_dtype { R4G_F32 = 0, R4G_BF16 = 1 } r4g_dtype;
+
+/* Flags of r4g_config.flags */
+#define R4G_FLAG_FP64_SLICE 0x1u   /* debug: Sigma4, the slice and Sigma3 in FP64 */
+#define R4G_FLAG_NO_TEMPORAL_CULL 0x2u  /* keep Gaussians with lambda (t-mu_t)^2 > 16 */
+
+/* Render configuration. tile_w x tile_h in {8x8, 16x16, 16x32}. */
+typedef struct r4g_config {
+  int32_t tile_w;      /* tile width in pixels (default 16) */
+  int32_t tile_h;      /* tile height in pixels (default 16) */
+  float bg[3];         /* background colour added with the final transmittance (default 0) */
+  int32_t sh_degree;   /* 0..3 SH bands used (default 3) */
+  uint32_t flags;      /* R4G_FLAG_* */
+} r4g_config;
+
+/* N Gaussians, one row each, all device pointers, row-major, densely packed.
+ * mean [n,4] = (x, y, z, t); rotor [n,8] = (s, b01, b02, b12, b03, b13, b23, p)
+ * (raw: normalised inside the render, appendix A.1); logscale [n,4] = log of
+ * (s_x, s_y, s_z, s_t) stored as float or bf16 per scale_dtype; logit [n]
+ * (opacity = sigmoid(logit)); sh [n,16,3] SH coefficients [coefficient][rgb]
+ * stored as float or bf16 per sh_dtype. mean, rotor and logscale rows must be
+ * 16-byte aligned (8-byte for bf16 logscale). */
+typedef struct r4g_gaussians {
+  const float* mean;
+  const float* rotor;
+  const void* logscale;
+  const float* logit;
+  const void* sh;
+  int64_t n;
+  int32_t scale_dtype; /* r4g_dtype */
+  int32_t sh_dtype;    /* r4g_dtype */
+} r4g_gaussians;
+
+/* Pinhole camera, host struct passed by pointer. world_to_cam is the row-major
+ * 3x4 [R | t] (OpenCV axes: x right, y down, z forward); pixel (i, j) samples
+ * the image-plane point (i + 0.5, j + 0.5); u = fx x/z + cx, v = fy y/z + cy. */
+typedef struct r4g_camera {
+  float world_to_cam[12];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} r4g_camera;
+
+/* Parameter gradients (device pointers, FP32, same shapes as r4g_gaussians).
+ * The backward ADDS into them, so several views can accumulate one step;
+ * the caller zeroes them. */
+typedef struct r4g_grads {
+  float* mean;
+  float* rotor;
+  float* logscale;
+  float* logit;
+  float* sh;
+} r4g_grads;
+
+/* One (camera, t) view of a batched call. */
+typedef struct r4g_view {
+  r4g_camera cam;
+  float t;
+} r4g_view;
+
+/* ---- context -------------------------------------------------------------- */
+typedef struct r4g_ctx r4g_ctx;
+
+/* Create a context holding a copy of `cfg` (NULL = defaults: 16x16 tiles,
+ * black background, degree 3, no flags). The context is not thread-safe;
+ * use one per host thread. Returns R4G_EINVAL for an unsupported tile shape. */
+r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg);
+void r4g_destroy(r4g_ctx* ctx);
+/* Message of the last error on this context (static storage, never NULL). */
+const char* r4g_last_error(const r4g_ctx* ctx);
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t r4g_version(void);
+
+/* ---- frame state ------------------------------------------------------------
+ * A frame is one caller-allocated device buffer holding everything a render
+ * writes for its backward: per-Gaussian screen records, the sorted (tile,
+ * depth) keys and Gaussian indices, per-tile ranges, per-pixel final
+ * transmittance and last-contributor position, plus the sort's scratch.
+ * key_capacity bounds the number of (tile, Gaussian) pairs; a render whose
+ * pairs exceed it marks the frame R4G_EOVERFLOW (the image is then invalid)
+ * and records the count it needed (r4g_frame_status). */
+r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t height,
+                           int64_t key_capacity, size_t* bytes /* host out */);
+
+/* Wait for `stream`, then report the frame's device-side status: R4G_OK or
+ * R4G_EOVERFLOW. *keys_needed (host, may be NULL) receives the number of
+ * (tile, Gaussian) pairs of the last render into this frame. */
+r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
+                            int64_t* keys_needed, void* stream);
+
+/* Copy out of a frame (device -> device, enqueued on `stream`): the key count
+ * (uint32 [1]), the sorted 64-bit keys and 32-bit values (first key_count
+ * entries, key = tile_id << 32 | float_bits(depth)), per-tile ranges
+ * (uint32 [tiles][2], [begin, end)), and the per-Gaussian screen records
+ * (float [n][12] = mean2d.x, mean2d.y, conic a, b, c, opacity_t, depth,
+ * unused, r, g, b, unused; conic is the inverse 2D covariance, exponent
+ * -1/2 (a dx^2 + 2 b dx dy + c dy^2); culled Gaussians have opacity_t = 0).
+ * Any output pointer may be NULL. For tests and tools. */
+r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes, int64_t n,
+                            int32_t width, int32_t height,
+                            uint32_t* key_count, uint64_t* keys, uint32_t* values,
+                            uint32_t* ranges, float* records, void* stream);
+
+/* ---- render -----------------------------------------------------------------
+ * Forward render of `g` seen by `cam` at time `t` (Sec. 3.2.2 and Sec. 3.1):
+ * out_rgb [3, height, width] (planar FP32), and, when not NULL,
+ * out_T [height, width] (final transmittance) and out_last [height, width]
+ * (1 + position in the tile's sorted list of the last composited Gaussian,
+ * 0 when none). The frame must be at least r4g_frame_bytes(n, width, height,
+ * key_capacity) bytes. */
+r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam, float t,
+                      float* out_rgb, float* out_T, uint32_t* out_last,
+                      void* frame, size_t frame_bytes, int64_t key_capacity, void* stream);
+
+/* Backward of r4g_render for the same (g, cam, t) and the frame it filled:
+ * given dL/d out_rgb (grad_rgb [3, height, width]) ADD dL/d parameters into
+ * `grads`. Transmittance is recovered back to front from the stored final T,
+ * no per-layer state is kept. Gradients through inactive branches (clamped
+ * alpha, negative colour, the Jacobian clamp, culled Gaussians) are zero. */
+r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam,
+                               float t, const float* grad_rgb, r4g_grads* grads,
+                               void* frame, size_t frame_bytes, int64_t key_capacity,
+                               void* stream);
+
+/* ---- measurement ------------------------------------------------------------
+ * Stage timing: when enabled on a context, r4g_render / r4g_render_backward
+ * record a CUDA event pair around each stage on the call's stream; the times
+ * are accumulated when r4g_stage_times collects them (it waits for those
+ * events). Launch counts are kept whether or not timing is on. */
+typedef enum r4g_stage {
+  R4G_STAGE_PREPROCESS = 0,   /* per-Gaussian preprocess kernel */
+  R4G_STAGE_BINNING = 1,      /* block-total scan + key emission */
+  R4G_STAGE_SORT = 2,         /* radix sort passes */
+  R4G_STAGE_RANGES = 3,       /* tile ranges */
+  R4G_STAGE_BLEND = 4,        /* forward blend */
+  R4G_STAGE_BLEND_BWD = 5,    /* backward blend */
+  R4G_STAGE_PREPROCESS_BWD = 6,
+  R4G_NSTAGES = 7
+} r4g_stage;
+
+r4g_status r4g_set_timing(r4g_ctx* ctx, int32_t enable);
+/* ms[R4G_NSTAGES] and launches[R4G_NSTAGES] (host, either may be NULL)
+ * receive the accumulated stage times and kernel launch counts since the
+ * last reset; reset != 0 clears them afterwards. */
+r4g_status r4g_stage_times(r4g_ctx* ctx, double* ms, int64_t* launches, int32_t reset);
+
+/* ---- sort -------------------------------------------------------------------
+ * Stable LSD radix sort of (uint64 key, uint32 value) pairs on key bits
+ * [begin_bit, end_bit), 0 <= begin_bit < end_bit <= 64 (the key-sort step of
+ * the tile rasteriser, Sec. 3.1). keys_in/values_in are read only; results go
+ * to keys_out/values_out (which must not alias the inputs). scratch must hold
+ * r4g_sort_scratch_bytes(n) bytes. Bit-exact and deterministic. */
+r4g_status r4g_sort_scratch_bytes(int64_t n, size_t* bytes /* host out */);
+r4g_status r4g_sort_pairs(const uint64_t* keys_in, const uint32_t* values_in,
+                          uint64_t* keys_out, uint32_t* values_out, int64_t n,
+                          int32_t begin_bit, int32_t end_bit,
+                          void* scratch, size_t scratch_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* R4G_H */

@@ -38,6 +38,7 @@ POWER_CUT = -4.5
 TEMPORAL_CUT = 16.0
 NEAR = 0.2
 DILATION = 0.3
+IMPACT_MIN = 1e-4  # smallest colour change a flipped decision must be able to cause to count
 
 PARAM_NAMES = ("mean", "rotor", "logscale", "logit", "sh")
 
@@ -86,6 +87,8 @@ def depth_order(rec: dict) -> torch.Tensor:
 
 def _composite(m2, con, o, col, z, px, py, bg):
     """Composite a chunk of pixels (px, py: [P]) over G depth-ordered Gaussians."""
+    G = m2.shape[0]
+    pos = torch.arange(G)
     dx = px[:, None] - m2[None, :, 0]
     dy = py[:, None] - m2[None, :, 1]
     power = -0.5 * (con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy) - con[None, :, 1] * dx * dy
@@ -103,26 +106,46 @@ def _composite(m2, con, o, col, z, px, py, bg):
     C = w @ col  # [P,3]
     T_final = torch.prod(torch.where(included, one_minus, torch.ones_like(one_minus)), dim=1)
     img = C + T_final[:, None] * bg[None, :]
-    G = m2.shape[0]
-    pos = torch.arange(G)
     last_pos = torch.where(included, pos[None, :], torch.full_like(pos[None, :], -1)).amax(dim=1) \
         if G > 0 else torch.full((px.shape[0],), -1, dtype=torch.long)
-    # decision margins over the Gaussians the pixel reaches (T before >= 1e-4)
+    # Decision margins over the Gaussians the pixel reaches (T before >= 1e-4).
+    # m_thr / m_dep cover every decision; m_thr_img / m_dep_img only those
+    # whose flip could move the pixel colour by IMPACT_MIN or more (a flip of
+    # Gaussian i changes the colour by at most alpha_i T_i (|c_i| + |rest|)).
     with torch.no_grad():
-        reached = T_before.detach() >= T_MIN
-        inf = torch.full_like(power, math.inf)
-        m_cut = torch.where(reached, (power.detach() - POWER_CUT).abs() / abs(POWER_CUT), inf)
-        m_alpha = torch.where(reached & in_cut, (alpha_raw.detach() - ALPHA_MIN).abs() / ALPHA_MIN, inf)
+        P = px.shape[0]
+        inf_row = torch.full((P,), math.inf, dtype=torch.float64)
+        if G == 0:
+            return img, T_final, last_pos, inf_row, inf_row, inf_row, inf_row
+        Tb = T_before.detach()
+        pw = power.detach()
+        ar = alpha_raw.detach()
+        al = alpha.detach()
+        reached = Tb >= T_MIN
+        inf = torch.full_like(pw, math.inf)
+        cmax = 2.0 * max(1.0, float(col.detach().max()), float(bg.max()))
+        m_cut = torch.where(reached, (pw - POWER_CUT).abs() / abs(POWER_CUT), inf)
+        m_alpha = torch.where(reached & in_cut, (ar - ALPHA_MIN).abs() / ALPHA_MIN, inf)
         m_T = torch.where(reached & valid, (T_after.detach() - T_MIN).abs() / T_MIN, inf)
-        m_thr = torch.minimum(torch.minimum(m_cut, m_alpha), m_T)
-        m_thr = m_thr.amin(dim=1) if G > 0 else torch.full((px.shape[0],), math.inf, dtype=torch.float64)
-        zz = z[None, :].expand_as(power)
-        vz = torch.where(valid & reached, zz, torch.full_like(zz, -math.inf))
-        prev = torch.cummax(vz, dim=1).values
-        prev = torch.cat([torch.full_like(prev[:, :1], -math.inf), prev[:, :-1]], dim=1)
-        gap = torch.where(valid & reached & torch.isfinite(prev), (zz - prev) / zz, inf)
-        m_dep = gap.amin(dim=1) if G > 0 else torch.full((px.shape[0],), math.inf, dtype=torch.float64)
-    return img, T_final, last_pos, m_thr, m_dep
+        m_thr = torch.minimum(torch.minimum(m_cut, m_alpha), m_T).amin(dim=1)
+        a_cut = torch.clamp(o.detach() * math.exp(POWER_CUT), max=ALPHA_MAX)[None, :]
+        imp_cut = a_cut * Tb * cmax
+        imp_alpha = ALPHA_MIN * Tb * cmax
+        m_img = torch.minimum(torch.where(imp_cut >= IMPACT_MIN, m_cut, inf),
+                              torch.where(imp_alpha >= IMPACT_MIN, m_alpha, inf)).amin(dim=1)
+        # depth order of consecutive contributing Gaussians
+        vr = valid & reached
+        posm = torch.where(vr, pos[None, :].expand_as(pw), torch.full_like(pos[None, :].expand_as(pw), -1))
+        prev = torch.cummax(posm, dim=1).values
+        prev = torch.cat([torch.full_like(prev[:, :1], -1), prev[:, :-1]], dim=1)
+        has_prev = vr & (prev >= 0)
+        pi = prev.clamp(min=0)
+        zz = z[None, :].expand_as(pw)
+        gap = torch.where(has_prev, (zz - z[pi]) / zz, inf)
+        imp_dep = al * al.gather(1, pi) * Tb.gather(1, pi) * cmax
+        m_dep = gap.amin(dim=1)
+        m_dep_img = torch.where(imp_dep >= IMPACT_MIN, gap, inf).amin(dim=1)
+    return img, T_final, last_pos, m_thr, m_dep, m_img, m_dep_img
 
 
 def _pixel_grid(width: int, height: int):
@@ -147,10 +170,9 @@ def _chunked(rec, order, cols, rows, bg, budget=4_000_000):
     img = torch.cat([x[0] for x in outs]) if outs else torch.zeros((0, 3), dtype=torch.float64)
     T = torch.cat([x[1] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
     lp = torch.cat([x[2] for x in outs]) if outs else torch.zeros(0, dtype=torch.long)
-    mt = torch.cat([x[3] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
-    md = torch.cat([x[4] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
+    extra = [torch.cat([x[k] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64) for k in (3, 4, 5, 6)]
     last = torch.where(lp >= 0, order[lp.clamp(min=0)] if G > 0 else lp, torch.full_like(lp, -1))
-    return img, T, last, mt, md
+    return (img, T, last, *extra)
 
 
 def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool = True,
@@ -159,7 +181,9 @@ def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool =
     transmittance), ``last`` [H,W] (index of the last composited Gaussian, -1 if
     none), ``margin`` [H,W] (smallest relative margin of a threshold decision),
     ``margin_depth`` [H,W] (smallest relative depth gap between two Gaussians
-    that both contribute), and the per-Gaussian records ``rec``."""
+    that both contribute), the same two restricted to decisions whose flip
+    could change the colour by IMPACT_MIN or more (``margin_img``,
+    ``margin_depth_img``), and the per-Gaussian records ``rec``."""
     cam = _cam(cam)
     if rec is None:
         rec = preprocess(scene, cam, t, cull_temporal, sh_degree)
@@ -167,10 +191,11 @@ def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool =
     W, H = cam["width"], cam["height"]
     cols, rows = _pixel_grid(W, H)
     bg_t = torch.as_tensor(bg, dtype=torch.float64)
-    img, T, last, mt, md = _chunked(rec, order, cols, rows, bg_t)
+    img, T, last, mt, md, mi, mdi = _chunked(rec, order, cols, rows, bg_t)
     return {
         "image": img.T.reshape(3, H, W), "T": T.reshape(H, W), "last": last.reshape(H, W),
-        "margin": mt.reshape(H, W), "margin_depth": md.reshape(H, W), "rec": rec, "order": order,
+        "margin": mt.reshape(H, W), "margin_depth": md.reshape(H, W),
+        "margin_img": mi.reshape(H, W), "margin_depth_img": mdi.reshape(H, W), "rec": rec, "order": order,
     }
 
 
@@ -183,8 +208,9 @@ def render_pixels(scene: dict, cam, t: float, pixels, bg=(0.0, 0.0, 0.0), rec: d
     order = depth_order(rec)
     pix = torch.as_tensor(np.asarray(pixels), dtype=torch.long)
     bg_t = torch.as_tensor(bg, dtype=torch.float64)
-    img, T, last, mt, md = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
-    return {"rgb": img, "T": T, "last": last, "margin": mt, "margin_depth": md}
+    img, T, last, mt, md, mi, mdi = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
+    return {"rgb": img, "T": T, "last": last, "margin": mt, "margin_depth": md, "margin_img": mi,
+            "margin_depth_img": mdi}
 
 
 REC_GRAD_KEYS = ("mean2d", "conic", "opacity_t", "rgb")

@@ -1,0 +1,441 @@
+// C ABI of libr4g: argument checks, frame layout and the launch sequence of
+// the render (preprocess -> scan + key build -> radix sort -> tile ranges ->
+// blend) and of its backward (blend backward -> preprocess backward).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "r4g.h"
+#include "r4g_internal.cuh"
+
+struct r4g_ctx {
+  r4g_config cfg;
+  char err[512];
+  bool timing = false;
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[R4G_NSTAGES] = {};
+  int64_t launches[R4G_NSTAGES] = {};
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+r4g_status fail(r4g_ctx* ctx, r4g_status st, const char* msg) {
+  char* dst = ctx ? ctx->err : g_err;
+  std::snprintf(dst, 512, "%s", msg);
+  return st;
+}
+
+r4g_status cuda_fail(r4g_ctx* ctx, cudaError_t e, const char* where) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  return fail(ctx, R4G_ECUDA, buf);
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+bool tile_ok(int tw, int th) {
+  return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 16 && th == 32);
+}
+
+r4g::CamDev make_cam(const r4g_camera& c) {
+  r4g::CamDev d;
+  for (int k = 0; k < 3; ++k) {
+    for (int j = 0; j < 3; ++j) d.R[3 * k + j] = c.world_to_cam[4 * k + j];
+    d.t[k] = c.world_to_cam[4 * k + 3];
+  }
+  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
+    double acc = 0;
+    for (int k = 0; k < 3; ++k) acc -= static_cast<double>(d.R[3 * k + j]) * d.t[k];
+    d.pos[j] = static_cast<float>(acc);
+  }
+  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+  d.limx = static_cast<float>(r4g::kClampFov * (c.width / (2.0 * c.fx)));
+  d.limy = static_cast<float>(r4g::kClampFov * (c.height / (2.0 * c.fy)));
+  d.width = c.width;
+  d.height = c.height;
+  return d;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+r4g_status check_gaussians(r4g_ctx* ctx, const r4g_gaussians* g) {
+  if (!g) return fail(ctx, R4G_EINVAL, "gaussians is NULL");
+  if (g->n < 0 || g->n > (int64_t(1) << 31) - 1) return fail(ctx, R4G_EINVAL, "n out of range");
+  if ((g->scale_dtype != R4G_F32 && g->scale_dtype != R4G_BF16) ||
+      (g->sh_dtype != R4G_F32 && g->sh_dtype != R4G_BF16))
+    return fail(ctx, R4G_EINVAL, "unknown dtype");
+  if (g->n == 0) return R4G_OK;
+  if (!g->mean || !g->rotor || !g->logscale || !g->logit || !g->sh)
+    return fail(ctx, R4G_EINVAL, "a parameter pointer is NULL");
+  if (!aligned(g->mean, 16) || !aligned(g->rotor, 16) || !aligned(g->sh, 16) ||
+      !aligned(g->logscale, g->scale_dtype == R4G_BF16 ? 8 : 16) || !aligned(g->logit, 4))
+    return fail(ctx, R4G_EINVAL, "parameter buffers must be 16-byte aligned");
+  return R4G_OK;
+}
+
+r4g_status check_camera(r4g_ctx* ctx, const r4g_camera* c) {
+  if (!c) return fail(ctx, R4G_EINVAL, "camera is NULL");
+  if (c->width <= 0 || c->height <= 0 || c->width > 32768 || c->height > 32768)
+    return fail(ctx, R4G_EINVAL, "image size out of range (1..32768)");
+  if (!(c->fx > 0) || !(c->fy > 0) || !std::isfinite(c->cx) || !std::isfinite(c->cy))
+    return fail(ctx, R4G_EINVAL, "bad intrinsics");
+  return R4G_OK;
+}
+
+cudaEvent_t take_event(r4g_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one stage of a call: records an event pair around it when timing
+// is enabled and counts the stage's kernel launches.
+struct StageScope {
+  r4g_ctx* ctx;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageScope(r4g_ctx* c, int st, cudaStream_t str, int nlaunch) : ctx(c), stage(st), s(str) {
+    ctx->launches[stage] += nlaunch;
+    if (ctx->timing) {
+      a = take_event(ctx);
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~StageScope() {
+    if (a) {
+      cudaEvent_t b = take_event(ctx);
+      if (b) {
+        cudaEventRecord(b, s);
+        ctx->pending.push_back({stage, a, b});
+      } else {
+        ctx->pool.push_back(a);
+      }
+    }
+  }
+};
+
+}  // namespace
+
+namespace r4g {
+
+FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h) {
+  FrameLayout L{};
+  L.n = n;
+  L.cap = cap;
+  L.width = width;
+  L.height = height;
+  L.tile_w = tile_w;
+  L.tile_h = tile_h;
+  L.tiles_x = (width + tile_w - 1) / tile_w;
+  L.tiles_y = (height + tile_h - 1) / tile_h;
+  L.ntiles = L.tiles_x * L.tiles_y;
+  L.nblocks = static_cast<int>((n + kPreBlock - 1) / kPreBlock);
+  L.sort_ctas = sort_ctas_for(cap);
+  int tb = 0;
+  while ((int64_t(1) << tb) < L.ntiles) ++tb;
+  L.sort_bits = 32 + tb;
+  const size_t npix = static_cast<size_t>(width) * height;
+  size_t o = 0;
+  L.header = o;   o = align_up(o + sizeof(FrameHeader));
+  L.rec = o;      o = align_up(o + 3 * sizeof(float4) * n);
+  L.rect = o;     o = align_up(o + sizeof(uint2) * n);
+  L.touched = o;  o = align_up(o + sizeof(uint32_t) * n);
+  L.blocksum = o; o = align_up(o + sizeof(uint32_t) * (L.nblocks + 1));
+  L.keys0 = o;    o = align_up(o + sizeof(uint64_t) * cap);
+  L.vals0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
+  L.keys1 = o;    o = align_up(o + sizeof(uint64_t) * cap);
+  L.vals1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
+  L.ranges = o;   o = align_up(o + sizeof(uint2) * L.ntiles);
+  L.tfinal = o;   o = align_up(o + sizeof(float) * npix);
+  L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
+  L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * L.sort_ctas);
+  L.recgrad = o;  o = align_up(o + 12 * sizeof(float) * n);
+  L.total = o;
+  return L;
+}
+
+// Number of radix passes decides which buffer ends up holding the sorted
+// list: pass p writes keys1 when p is even and keys0 when p is odd.
+static bool sorted_in_keys1(const FrameLayout& L) {
+  const int passes = (L.sort_bits + kSortRadixBits - 1) / kSortRadixBits;
+  return passes % 2 == 1;
+}
+
+}  // namespace r4g
+
+using namespace r4g;
+
+extern "C" {
+
+int32_t r4g_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg) {
+  if (!out) return fail(nullptr, R4G_EINVAL, "out is NULL");
+  *out = nullptr;
+  r4g_config c;
+  if (cfg) {
+    c = *cfg;
+  } else {
+    std::memset(&c, 0, sizeof(c));
+    c.tile_w = 16;
+    c.tile_h = 16;
+    c.sh_degree = 3;
+  }
+  if (!tile_ok(c.tile_w, c.tile_h)) return fail(nullptr, R4G_EINVAL, "tile shape must be 8x8, 16x16 or 16x32");
+  if (c.sh_degree < 0 || c.sh_degree > 3) return fail(nullptr, R4G_EINVAL, "sh_degree must be 0..3");
+  if (c.flags & ~(R4G_FLAG_FP64_SLICE | R4G_FLAG_NO_TEMPORAL_CULL)) return fail(nullptr, R4G_EINVAL, "unknown flag");
+  r4g_ctx* ctx = new (std::nothrow) r4g_ctx;
+  if (!ctx) return fail(nullptr, R4G_ENOMEM, "out of host memory");
+  ctx->cfg = c;
+  ctx->err[0] = 0;
+  *out = ctx;
+  return R4G_OK;
+}
+
+void r4g_destroy(r4g_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+r4g_status r4g_set_timing(r4g_ctx* ctx, int32_t enable) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  ctx->timing = enable != 0;
+  return R4G_OK;
+}
+
+r4g_status r4g_stage_times(r4g_ctx* ctx, double* ms, int64_t* launches, int32_t reset) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  for (auto& p : ctx->pending) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_stage_times");
+    ctx->ms[p.stage] += t;
+    ctx->pool.push_back(p.a);
+    ctx->pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  for (int k = 0; k < R4G_NSTAGES; ++k) {
+    if (ms) ms[k] = ctx->ms[k];
+    if (launches) launches[k] = ctx->launches[k];
+    if (reset) {
+      ctx->ms[k] = 0;
+      ctx->launches[k] = 0;
+    }
+  }
+  return R4G_OK;
+}
+
+const char* r4g_last_error(const r4g_ctx* ctx) { return ctx ? ctx->err : g_err; }
+
+r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t height,
+                           int64_t key_capacity, size_t* bytes) {
+  r4g_ctx* c = const_cast<r4g_ctx*>(ctx);
+  if (!ctx || !bytes) return fail(c, R4G_EINVAL, "NULL argument");
+  if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, R4G_EINVAL, "n out of range");
+  if (width <= 0 || height <= 0 || width > 32768 || height > 32768) return fail(c, R4G_EINVAL, "bad image size");
+  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(c, R4G_EINVAL, "key_capacity out of range");
+  *bytes = make_layout(n, width, height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h).total;
+  return R4G_OK;
+}
+
+r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
+                            int64_t* keys_needed, void* stream) {
+  if (!ctx || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
+  if (frame_bytes < sizeof(FrameHeader)) return fail(ctx, R4G_EWORKSPACE, "frame too small");
+  FrameHeader h;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, frame, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_frame_status");
+  if (keys_needed) *keys_needed = h.key_needed;
+  if (h.status & 1u) return fail(ctx, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
+  return R4G_OK;
+}
+
+r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes, int64_t n,
+                            int32_t width, int32_t height, uint32_t* key_count, uint64_t* keys,
+                            uint32_t* values, uint32_t* ranges, float* records, void* stream) {
+  if (!ctx || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FrameHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, frame, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_frame_export");
+  // The key capacity is not stored in the frame; the largest one that fits is
+  // recovered from the frame size, which is how the layout was made.
+  int64_t lo = 0, hi = int64_t(0xffffffffu);
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo + 1) / 2;
+    if (make_layout(n, width, height, mid, ctx->cfg.tile_w, ctx->cfg.tile_h).total <= frame_bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  const FrameLayout L = make_layout(n, width, height, lo, ctx->cfg.tile_w, ctx->cfg.tile_h);
+  if (L.total > frame_bytes || h.key_count > L.cap) return fail(ctx, R4G_EWORKSPACE, "frame size does not match");
+  void* f = const_cast<void*>(frame);
+  const bool k1 = sorted_in_keys1(L);
+  const uint32_t K = h.key_count;
+  if (key_count) e = cudaMemcpyAsync(key_count, &at<FrameHeader>(f, L.header)->key_count, 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && keys && K)
+    e = cudaMemcpyAsync(keys, at<uint64_t>(f, k1 ? L.keys1 : L.keys0), 8ull * K, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && values && K)
+    e = cudaMemcpyAsync(values, at<uint32_t>(f, k1 ? L.vals1 : L.vals0), 4ull * K, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && ranges)
+    e = cudaMemcpyAsync(ranges, at<uint2>(f, L.ranges), 8ull * L.ntiles, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && records && n) {
+    const char* rec = at<char>(f, L.rec);
+    for (int part = 0; part < 3 && e == cudaSuccess; ++part)
+      e = cudaMemcpy2DAsync(records + 4 * part, 48, rec + part * 16 * n, 16, 16, n, cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_frame_export");
+  return R4G_OK;
+}
+
+r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam, float t,
+                      float* out_rgb, float* out_T, uint32_t* out_last, void* frame,
+                      size_t frame_bytes, int64_t key_capacity, void* stream) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  r4g_status st = check_gaussians(ctx, g);
+  if (st != R4G_OK) return st;
+  if ((st = check_camera(ctx, cam)) != R4G_OK) return st;
+  if (!out_rgb || !frame) return fail(ctx, R4G_EINVAL, "out_rgb / frame is NULL");
+  if (!std::isfinite(t)) return fail(ctx, R4G_EINVAL, "t is not finite");
+  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
+  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
+  const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
+  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const CamDev cd = make_cam(*cam);
+  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const bool has = L.n > 0;
+  {
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, has ? 1 : 0);
+    if ((e = launch_preprocess_fwd(*g, cd, t, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "preprocess");
+  }
+  {
+    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 2 : 0);
+    if ((e = launch_binning(L, frame, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
+  }
+  const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
+  int which = 0;
+  if (has) {
+    const int passes = (L.sort_bits + kSortRadixBits - 1) / kSortRadixBits;
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 3 * passes);
+    e = launch_sort(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
+                    at<uint32_t>(frame, L.vals1), at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                    count, 0, L.cap, 0, L.sort_bits, at<uint32_t>(frame, L.sortcnt), L.sort_ctas, s, &which);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
+  }
+  const bool k1 = sorted_in_keys1(L);
+  const uint64_t* keys = at<uint64_t>(frame, k1 ? L.keys1 : L.keys0);
+  const uint32_t* vals = at<uint32_t>(frame, k1 ? L.vals1 : L.vals0);
+  {
+    StageScope sc(ctx, R4G_STAGE_RANGES, s, has ? 1 : 0);
+    if ((e = launch_ranges(L, frame, keys, s)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
+  }
+  {
+    StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
+    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "blend");
+  }
+  return R4G_OK;
+}
+
+r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam, float t,
+                               const float* grad_rgb, r4g_grads* grads, void* frame,
+                               size_t frame_bytes, int64_t key_capacity, void* stream) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  r4g_status st = check_gaussians(ctx, g);
+  if (st != R4G_OK) return st;
+  if ((st = check_camera(ctx, cam)) != R4G_OK) return st;
+  if (!grad_rgb || !grads || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
+  if (g->n > 0 && (!grads->mean || !grads->rotor || !grads->logscale || !grads->logit || !grads->sh))
+    return fail(ctx, R4G_EINVAL, "a gradient pointer is NULL");
+  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
+  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
+  const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
+  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
+  if (L.n == 0) return R4G_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const CamDev cd = make_cam(*cam);
+  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.recgrad), 0, 12 * sizeof(float) * L.n, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const bool k1 = sorted_in_keys1(L);
+  const uint32_t* vals = at<uint32_t>(frame, k1 ? L.vals1 : L.vals0);
+  {
+    StageScope sc(ctx, R4G_STAGE_BLEND_BWD, s, 1);
+    if ((e = launch_blend_bwd(L, frame, vals, ctx->cfg.bg, grad_rgb, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "blend backward");
+  }
+  {
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, 1);
+    if ((e = launch_preprocess_bwd(*g, cd, t, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, *grads, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "preprocess backward");
+  }
+  return R4G_OK;
+}
+
+r4g_status r4g_sort_scratch_bytes(int64_t n, size_t* bytes) {
+  if (!bytes || n < 0 || n > int64_t(0xffffffffu)) return fail(nullptr, R4G_EINVAL, "bad argument");
+  const int ctas = sort_ctas_for(n);
+  *bytes = align_up(sizeof(uint64_t) * n) + align_up(sizeof(uint32_t) * n) +
+           align_up(sizeof(uint32_t) * kSortRadix * ctas);
+  return R4G_OK;
+}
+
+r4g_status r4g_sort_pairs(const uint64_t* keys_in, const uint32_t* values_in, uint64_t* keys_out,
+                          uint32_t* values_out, int64_t n, int32_t begin_bit, int32_t end_bit,
+                          void* scratch, size_t scratch_bytes, void* stream) {
+  if (n < 0 || n > int64_t(0xffffffffu)) return fail(nullptr, R4G_EINVAL, "n out of range");
+  if (begin_bit < 0 || end_bit > 64 || begin_bit >= end_bit) return fail(nullptr, R4G_EINVAL, "bad bit range");
+  size_t need = 0;
+  r4g_sort_scratch_bytes(n, &need);
+  if (n == 0) return R4G_OK;
+  if (!keys_in || !values_in || !keys_out || !values_out || !scratch) return fail(nullptr, R4G_EINVAL, "NULL argument");
+  if (scratch_bytes < need) return fail(nullptr, R4G_EWORKSPACE, "scratch smaller than r4g_sort_scratch_bytes");
+  if (!aligned(scratch, 256) || !aligned(keys_in, 8) || !aligned(keys_out, 8))
+    return fail(nullptr, R4G_EINVAL, "misaligned buffer");
+  if (keys_in == keys_out || values_in == values_out) return fail(nullptr, R4G_EINVAL, "outputs alias inputs");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint64_t* tk = at<uint64_t>(scratch, 0);
+  uint32_t* tv = at<uint32_t>(scratch, align_up(sizeof(uint64_t) * n));
+  uint32_t* cnt = at<uint32_t>(scratch, align_up(sizeof(uint64_t) * n) + align_up(sizeof(uint32_t) * n));
+  const int passes = (end_bit - begin_bit + kSortRadixBits - 1) / kSortRadixBits;
+  // the last pass (index passes-1) writes buffer 1 when its index is even
+  const bool last_even = (passes - 1) % 2 == 0;
+  uint64_t* k1 = last_even ? keys_out : tk;
+  uint32_t* v1 = last_even ? values_out : tv;
+  uint64_t* k2 = last_even ? tk : keys_out;
+  uint32_t* v2 = last_even ? tv : values_out;
+  int which = 0;
+  const cudaError_t e = launch_sort(keys_in, values_in, k1, v1, k2, v2, nullptr, static_cast<uint32_t>(n), n,
+                                    begin_bit, end_bit, cnt, sort_ctas_for(n), s, &which);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "sort");
+  return R4G_OK;
+}
+
+}  // extern "C"

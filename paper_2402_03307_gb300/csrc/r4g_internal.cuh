@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of libr4g.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "r4g.h"
+
+namespace r4g {
+
+// Per-pixel and per-Gaussian thresholds of the compositing rules (Sec. 3.1
+// rasteriser, Sec. 3.2.2 visibility threshold).
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kPowerCut = -4.5f;     // 3-sigma ellipse: d^T conic d <= 9
+constexpr float kTemporalCut = 16.0f;  // lambda (t - mu_t)^2 > 16 culls
+constexpr float kNear = 0.2f;
+constexpr float kDilation = 0.3f;      // low-pass term added to the 2D covariance
+constexpr float kClampFov = 1.3f;      // J is taken with x/z, y/z within 1.3 tan(fov/2)
+
+// Camera as the kernels see it (passed by value).
+struct CamDev {
+  float R[9];
+  float t[3];
+  float pos[3];  // camera centre in world space, -R^T t
+  float fx, fy, cx, cy;
+  float limx, limy;  // 1.3 tan(fov/2) per axis
+  int width, height;
+};
+
+// Frame header at the start of every frame buffer (device memory).
+struct FrameHeader {
+  uint32_t status;        // bit 0: key overflow
+  uint32_t key_count;     // pairs actually written (min(needed, capacity))
+  uint32_t key_needed;    // pairs the render needed
+  uint32_t n_visible;
+  uint32_t pad[60];
+};
+
+// Byte offsets of the regions of a frame; computed on the host.
+struct FrameLayout {
+  size_t header, rec, rect, touched, blocksum, keys0, vals0, keys1, vals1,
+      ranges, tfinal, last, sortcnt, recgrad, total;
+  int64_t n, cap;
+  int width, height, tile_w, tile_h, tiles_x, tiles_y, ntiles;
+  int nblocks;       // preprocess blocks (kPreBlock Gaussians each)
+  int sort_ctas;     // CTAs of each radix pass
+  int sort_bits;     // key bits to sort: 32 + ceil(log2(ntiles))
+};
+
+constexpr int kPreBlock = 256;     // Gaussians per preprocess / key-build block
+constexpr int kSortThreads = 256;
+constexpr int kSortIPT = 8;        // items per thread per tile
+constexpr int kSortTile = kSortThreads * kSortIPT;
+constexpr int kSortRadixBits = 8;
+constexpr int kSortRadix = 1 << kSortRadixBits;
+
+int sort_ctas_for(int64_t cap);
+FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h);
+
+// Exponent of a Gaussian at a pixel, power = -1/2 (a dx^2 + 2 b dx dy + c dy^2),
+// with A = (mean2d.x, mean2d.y, a, b). Every rounding step is explicit so the
+// forward and backward blends take bit-identical per-pixel decisions.
+__device__ __forceinline__ float gauss_power(const float4& A, float c, float fx, float fy,
+                                             float& dx, float& dy) {
+  dx = __fsub_rn(fx, A.x);
+  dy = __fsub_rn(fy, A.y);
+  float q = __fmul_rn(__fmul_rn(A.z, dx), dx);
+  q = __fmaf_rn(__fmul_rn(c, dy), dy, q);
+  const float cross = __fmul_rn(__fmul_rn(A.w, dx), dy);
+  return __fmaf_rn(-0.5f, q, -cross);
+}
+
+template <typename T>
+inline T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+// ---- launchers (return cudaGetLastError() after enqueueing) -----------------
+cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, float t,
+                                  const FrameLayout& L, void* frame, int sh_degree,
+                                  uint32_t flags, cudaStream_t s);
+cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s);
+cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf1,
+                        uint32_t* vbuf1, uint64_t* kbuf2, uint32_t* vbuf2,
+                        const uint32_t* count_dev, uint32_t count_host, int64_t cap,
+                        int begin_bit, int end_bit, uint32_t* counts, int ctas,
+                        cudaStream_t s, int* result_in_buf);
+cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint64_t* keys,
+                          cudaStream_t s);
+cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
+                             const float* bg, float* out_rgb, float* out_T,
+                             uint32_t* out_last, cudaStream_t s);
+cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* vals,
+                             const float* bg, const float* grad_rgb, cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const CamDev& cam, float t,
+                                  const FrameLayout& L, void* frame, int sh_degree,
+                                  uint32_t flags, r4g_grads grads, cudaStream_t s);
+
+}  // namespace r4g

@@ -1,0 +1,236 @@
+"""PyTorch-facing API over the r4g C ABI: device memory and streams come from
+PyTorch, every step of the render and of its backward runs in libr4g's CUDA
+kernels.
+
+    r = Renderer()                       # 16x16 tiles, black background, SH degree 3
+    img = r.render(params, cam, t).image # [3, H, W] float32 on the GPU
+    img = render(params, cam, t)         # autograd-aware (Render4DFunction)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import abi
+
+PARAM_NAMES = ("mean", "rotor", "logscale", "logit", "sh")
+
+
+def camera_struct(cam) -> abi.r4g_camera:
+    """r4g_camera from any object (or dict) with world_to_cam [3,4], fx, fy,
+    cx, cy, width, height."""
+    get = (lambda k: cam[k]) if isinstance(cam, dict) else (lambda k: getattr(cam, k))
+    c = abi.r4g_camera()
+    w2c = [float(x) for x in torch.as_tensor(get("world_to_cam"), dtype=torch.float32).flatten().tolist()]
+    if len(w2c) != 12:
+        raise ValueError("world_to_cam must have 12 entries (3x4)")
+    for k in range(12):
+        c.world_to_cam[k] = w2c[k]
+    c.fx, c.fy, c.cx, c.cy = float(get("fx")), float(get("fy")), float(get("cx")), float(get("cy"))
+    c.width, c.height = int(get("width")), int(get("height"))
+    return c
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return abi.R4G_F32
+    if t.dtype == torch.bfloat16:
+        return abi.R4G_BF16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def gaussians_struct(p: dict) -> abi.r4g_gaussians:
+    n = int(p["mean"].shape[0])
+    shapes = {"mean": (n, 4), "rotor": (n, 8), "logscale": (n, 4), "logit": (n,), "sh": (n, 16, 3)}
+    for k, shp in shapes.items():
+        t = p[k]
+        if not t.is_cuda:
+            raise ValueError(f"{k} must be a CUDA tensor")
+        if tuple(t.shape) != shp:
+            raise ValueError(f"{k} has shape {tuple(t.shape)}, expected {shp}")
+        if not t.is_contiguous():
+            raise ValueError(f"{k} must be contiguous")
+    for k in ("mean", "rotor", "logit"):
+        if p[k].dtype != torch.float32:
+            raise TypeError(f"{k} must be float32")
+    g = abi.r4g_gaussians()
+    g.mean, g.rotor, g.logscale = p["mean"].data_ptr(), p["rotor"].data_ptr(), p["logscale"].data_ptr()
+    g.logit, g.sh, g.n = p["logit"].data_ptr(), p["sh"].data_ptr(), n
+    g.scale_dtype, g.sh_dtype = _dtype_code(p["logscale"]), _dtype_code(p["sh"])
+    return g
+
+
+@dataclass
+class RenderResult:
+    image: torch.Tensor        # [3, H, W]
+    frame: torch.Tensor        # uint8 frame buffer (saved state for the backward)
+    key_capacity: int
+    width: int
+    height: int
+    n: int
+
+
+class Renderer:
+    """Owns an r4g context (tile shape, background, SH degree, flags)."""
+
+    def __init__(self, tile=(16, 16), bg=(0.0, 0.0, 0.0), sh_degree: int = 3, flags: int = 0,
+                 keys_per_gaussian: float = 32.0):
+        cfg = abi.r4g_config()
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+        for k in range(3):
+            cfg.bg[k] = float(bg[k])
+        cfg.sh_degree = int(sh_degree)
+        cfg.flags = int(flags)
+        self.cfg = cfg
+        self.tile = (cfg.tile_w, cfg.tile_h)
+        self.bg = tuple(float(x) for x in bg)
+        self.ctx = abi.r4g_create(cfg)
+        self.keys_per_gaussian = float(keys_per_gaussian)
+        self._cap_hint: dict = {}
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and abi._lib is not None:
+            abi.r4g_destroy(ctx)
+            self.ctx = None
+
+    # ---- memory ---------------------------------------------------------------
+    def frame_bytes(self, n: int, width: int, height: int, key_capacity: int) -> int:
+        return abi.r4g_frame_bytes(self.ctx, n, width, height, key_capacity)
+
+    def new_frame(self, n: int, width: int, height: int, key_capacity: int, device=None) -> torch.Tensor:
+        nbytes = self.frame_bytes(n, width, height, key_capacity)
+        return torch.empty(nbytes, dtype=torch.uint8, device=device or torch.cuda.current_device())
+
+    def default_capacity(self, n: int, width: int, height: int) -> int:
+        hint = self._cap_hint.get((n, width, height))
+        if hint:
+            return hint
+        return int(max(1 << 16, self.keys_per_gaussian * max(n, 1)))
+
+    # ---- render ---------------------------------------------------------------
+    def render(self, params: dict, cam, t: float, *, frame: torch.Tensor | None = None,
+               key_capacity: int | None = None, out: torch.Tensor | None = None,
+               check: bool = True, stream=None) -> RenderResult:
+        """Render one view. With ``check`` the call waits for the stream to read
+        the frame status and re-renders with a larger key buffer on overflow;
+        without it the caller must call :meth:`status` before trusting the image."""
+        g = gaussians_struct(params)
+        c = camera_struct(cam)
+        dev = params["mean"].device
+        cap = int(key_capacity or self.default_capacity(g.n, c.width, c.height))
+        s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        while True:
+            if frame is None or frame.numel() < self.frame_bytes(g.n, c.width, c.height, cap):
+                frame = self.new_frame(g.n, c.width, c.height, cap, dev)
+            img = out if out is not None else torch.empty((3, c.height, c.width), dtype=torch.float32, device=dev)
+            abi.r4g_render(self.ctx, g, c, float(t), img.data_ptr(), None, None, frame.data_ptr(),
+                           frame.numel(), cap, s)
+            res = RenderResult(img, frame, cap, c.width, c.height, g.n)
+            if not check:
+                return res
+            st, need = abi.r4g_frame_status(self.ctx, frame.data_ptr(), frame.numel(), s)
+            if st == abi.R4G_OK:
+                return res
+            cap = int(need * 1.25) + 1024
+            self._cap_hint[(g.n, c.width, c.height)] = cap
+            frame = None
+
+    def status(self, res: RenderResult, stream=None) -> tuple[int, int]:
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        return abi.r4g_frame_status(self.ctx, res.frame.data_ptr(), res.frame.numel(), s)
+
+    def backward(self, params: dict, cam, t: float, res: RenderResult, grad_image: torch.Tensor,
+                 grads: dict, stream=None) -> None:
+        """Accumulate dL/dparams into ``grads`` (float32 tensors shaped like the
+        parameters) given dL/dimage for a render ``res`` of (params, cam, t)."""
+        g = gaussians_struct(params)
+        c = camera_struct(cam)
+        gi = grad_image.contiguous()
+        if gi.dtype != torch.float32 or tuple(gi.shape) != (3, c.height, c.width):
+            raise ValueError("grad_image must be float32 [3, H, W]")
+        out = abi.r4g_grads()
+        for k in PARAM_NAMES:
+            t_ = grads[k]
+            if t_.dtype != torch.float32 or not t_.is_contiguous() or t_.numel() != params[k].numel():
+                raise ValueError(f"grads[{k}] must be a contiguous float32 tensor like the parameter")
+            setattr(out, k, t_.data_ptr())
+        s = (stream or torch.cuda.current_stream(gi.device)).cuda_stream
+        abi.r4g_render_backward(self.ctx, g, c, float(t), gi.data_ptr(), out, res.frame.data_ptr(),
+                                res.frame.numel(), res.key_capacity, s)
+
+    def export(self, res: RenderResult, stream=None) -> dict:
+        """Sorted keys / values, tile ranges and screen records of a frame (tests, tools)."""
+        dev = res.frame.device
+        s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        abi.r4g_frame_export(self.ctx, res.frame.data_ptr(), res.frame.numel(), res.n, res.width,
+                             res.height, cnt.data_ptr(), None, None, None, None, s)
+        k = int(cnt.item())
+        keys = torch.empty(max(k, 1), dtype=torch.int64, device=dev)
+        vals = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+        tx = (res.width + self.tile[0] - 1) // self.tile[0]
+        ty = (res.height + self.tile[1] - 1) // self.tile[1]
+        ranges = torch.empty((tx * ty, 2), dtype=torch.int32, device=dev)
+        rec = torch.empty((max(res.n, 1), 12), dtype=torch.float32, device=dev)
+        abi.r4g_frame_export(self.ctx, res.frame.data_ptr(), res.frame.numel(), res.n, res.width,
+                             res.height, None, keys.data_ptr(), vals.data_ptr(), ranges.data_ptr(),
+                             rec.data_ptr(), s)
+        return {"key_count": k, "keys": keys[:k], "values": vals[:k], "ranges": ranges, "records": rec[:res.n]}
+
+
+class Render4DFunction(torch.autograd.Function):
+    """image = render(mean, rotor, logscale, logit, sh; camera, t) with a
+    hand-written CUDA backward (r4g_render_backward)."""
+
+    @staticmethod
+    def forward(ctx, mean, rotor, logscale, logit, sh, renderer: Renderer, cam, t: float):
+        params = {"mean": mean.detach(), "rotor": rotor.detach(), "logscale": logscale.detach(),
+                  "logit": logit.detach(), "sh": sh.detach()}
+        res = renderer.render(params, cam, t)
+        ctx.renderer, ctx.cam, ctx.t, ctx.res = renderer, cam, t, res
+        ctx.save_for_backward(mean, rotor, logscale, logit, sh)
+        return res.image
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        mean, rotor, logscale, logit, sh = ctx.saved_tensors
+        params = {"mean": mean, "rotor": rotor, "logscale": logscale, "logit": logit, "sh": sh}
+        grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=v.device) for k, v in params.items()}
+        ctx.renderer.backward(params, ctx.cam, ctx.t, ctx.res, grad_image.float(), grads)
+        out = [grads[k].to(params[k].dtype) for k in PARAM_NAMES]
+        return (*out, None, None, None)
+
+
+_default: Renderer | None = None
+
+
+def default_renderer() -> Renderer:
+    global _default
+    if _default is None:
+        _default = Renderer()
+    return _default
+
+
+def render(params: dict, cam, t: float, renderer: Renderer | None = None) -> torch.Tensor:
+    """Differentiable render of ``params`` (dict of CUDA tensors) -> [3, H, W]."""
+    r = renderer or default_renderer()
+    return Render4DFunction.apply(params["mean"], params["rotor"], params["logscale"], params["logit"],
+                                  params["sh"], r, cam, t)
+
+
+def sort_pairs(keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end_bit: int = 64):
+    """Stable radix sort of (int64 key as uint64 bits, int32 value) pairs on bits
+    [begin_bit, end_bit) with the library's kernels. Returns new tensors."""
+    n = int(keys.numel())
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(values)
+    if n == 0:
+        return ko, vo
+    nb = abi.r4g_sort_scratch_bytes(n)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=keys.device)
+    s = torch.cuda.current_stream(keys.device).cuda_stream
+    abi.r4g_sort_pairs(keys.data_ptr(), values.data_ptr(), ko.data_ptr(), vo.data_ptr(), n, begin_bit,
+                       end_bit, scratch.data_ptr(), nb, s)
+    return ko, vo

@@ -1,0 +1,100 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/r4g.h declares; host-side argument checks return their
+error codes without touching a device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "r4g.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2402_03307_gb300 import abi
+    return abi.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(r4g_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    from paper_2402_03307_gb300 import abi
+    bound = {s[0] for s in abi.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_version(lib):
+    assert lib.r4g_version() == 10000
+
+
+def test_create_rejects_bad_config(lib):
+    from paper_2402_03307_gb300 import abi
+    cfg = abi.r4g_config()
+    cfg.tile_w, cfg.tile_h, cfg.sh_degree = 12, 12, 3
+    h = C.c_void_p()
+    assert lib.r4g_create(C.byref(h), C.byref(cfg)) == abi.R4G_EINVAL
+    cfg.tile_w, cfg.tile_h, cfg.sh_degree = 16, 16, 4
+    assert lib.r4g_create(C.byref(h), C.byref(cfg)) == abi.R4G_EINVAL
+    cfg.sh_degree, cfg.flags = 3, 0x100
+    assert lib.r4g_create(C.byref(h), C.byref(cfg)) == abi.R4G_EINVAL
+    assert b"flag" in lib.r4g_last_error(None)
+
+
+def test_frame_bytes_and_argument_checks(lib):
+    from paper_2402_03307_gb300 import abi
+    ctx = abi.r4g_create()
+    try:
+        a = abi.r4g_frame_bytes(ctx, 1000, 128, 128, 1 << 16)
+        b = abi.r4g_frame_bytes(ctx, 1000, 128, 128, 1 << 17)
+        assert b - a >= 24 * (1 << 16)  # two key + value buffers per extra key
+        assert a % 256 == 0
+        out = C.c_size_t()
+        assert lib.r4g_frame_bytes(ctx, -1, 128, 128, 10, C.byref(out)) == abi.R4G_EINVAL
+        assert lib.r4g_frame_bytes(ctx, 10, 0, 128, 10, C.byref(out)) == abi.R4G_EINVAL
+        # render with a NULL gaussian struct / camera is rejected on the host
+        cam = abi.r4g_camera()
+        cam.width, cam.height, cam.fx, cam.fy = 16, 16, 10.0, 10.0
+        g = abi.r4g_gaussians()
+        g.n = 0
+        assert lib.r4g_render(ctx, None, C.byref(cam), 0.5, None, None, None, None, 0, 0, None) == abi.R4G_EINVAL
+        assert lib.r4g_render(ctx, C.byref(g), None, 0.5, None, None, None, None, 0, 0, None) == abi.R4G_EINVAL
+        # n > 0 with NULL parameter pointers
+        g.n = 5
+        assert lib.r4g_render(ctx, C.byref(g), C.byref(cam), 0.5, 1, None, None, 256, 1 << 20, 16,
+                              None) == abi.R4G_EINVAL
+        # an undersized frame is refused before any launch
+        g.n = 0
+        need = abi.r4g_frame_bytes(ctx, 0, 16, 16, 16)
+        assert lib.r4g_render(ctx, C.byref(g), C.byref(cam), 0.5, 256, None, None, 256, need - 256, 16,
+                              None) == abi.R4G_EWORKSPACE
+        # non-finite t
+        assert lib.r4g_render(ctx, C.byref(g), C.byref(cam), float("nan"), 256, None, None, 256, need, 16,
+                              None) == abi.R4G_EINVAL
+    finally:
+        abi.r4g_destroy(ctx)
+
+
+def test_sort_argument_checks(lib):
+    from paper_2402_03307_gb300 import abi
+    out = C.c_size_t()
+    assert lib.r4g_sort_scratch_bytes(1000, C.byref(out)) == abi.R4G_OK and out.value >= 12000
+    assert lib.r4g_sort_pairs(None, None, None, None, 10, 0, 70, None, 0, None) == abi.R4G_EINVAL
+    assert lib.r4g_sort_pairs(None, None, None, None, 10, 8, 8, None, 0, None) == abi.R4G_EINVAL
+    assert lib.r4g_sort_pairs(None, None, None, None, 0, 0, 64, None, 0, None) == abi.R4G_OK
+    assert lib.r4g_sort_pairs(256, 512, 1024, 2048, 10, 0, 64, 4096, 1, None) == abi.R4G_EWORKSPACE
+    assert lib.r4g_sort_pairs(256, 512, 256, 2048, 10, 0, 64, 4096, 1 << 20, None) == abi.R4G_EINVAL

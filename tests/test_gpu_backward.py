@@ -1,0 +1,120 @@
+"""Backward parity: gradients of L = sum(w * image) from the CUDA backward
+(r4g_render_backward, through the C ABI) against the FP64 oracle's analytic
+gradient (itself pinned by central differences). Tolerance: per parameter
+group ||g - g_ref|| <= 1e-2 ||g_ref||, and per element
+|g - g_ref| <= 1e-2 (|g_ref| + 1e-3 max|g_ref|) for 99.9% of elements.
+The upstream gradient w is zeroed on ambiguous pixels (a threshold decision
+within rounding of flipping), where two different gradients are both right."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import ambiguous, to_device
+
+pytestmark = pytest.mark.gpu
+NAMES = ("mean", "rotor", "logscale", "logit", "sh")
+
+
+@pytest.fixture(scope="module")
+def r4g():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03307_gb300 as m
+    return m
+
+
+def _weights(g, cam, t, seed, bg=(0.0, 0.0, 0.0)):
+    ref = oracle.render(oracle.to_f64(g), cam, t, bg=bg)
+    amb = ambiguous(ref, image=False)
+    w = np.random.default_rng(seed).normal(0, 1, (3, cam.height, cam.width))
+    w[:, amb] = 0.0
+    return w.astype(np.float32)
+
+
+def _gpu_grads(r4g, g, cam, t, w, **kw):
+    rend = r4g.Renderer(**kw)
+    p = to_device(g)
+    res = rend.render(p, cam, t)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in p.items()}
+    rend.backward(p, cam, t, res, torch.as_tensor(w).cuda(), grads)
+    torch.cuda.synchronize()
+    return {k: v.double().cpu().numpy() for k, v in grads.items()}
+
+
+def _compare(got, ref, tag):
+    for k in NAMES:
+        a = got[k].reshape(-1)
+        b = ref[k].numpy().reshape(-1)
+        nb = np.linalg.norm(b)
+        assert nb > 0, (tag, k)
+        rel = np.linalg.norm(a - b) / nb
+        assert rel <= 1e-2, (tag, k, rel)
+        bad = np.abs(a - b) > 1e-2 * (np.abs(b) + 1e-3 * np.abs(b).max())
+        assert bad.mean() <= 1e-3, (tag, k, bad.mean(), int(bad.sum()))
+
+
+def test_backward_fd_workload(r4g):
+    """64 Gaussians, 32x32 (the finite-difference workload of the training config)."""
+    g = synth.gaussians(64, 11, ls_xyz=(-1.6, 0.3), ls_t=(-0.7, 0.3))
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 32, 32)
+    w = _weights(g, cam, 0.5, 0)
+    got = _gpu_grads(r4g, g, cam, 0.5, w)
+    ref = oracle.render_grad(oracle.to_f64(g), cam, 0.5, w)
+    _compare(got, ref, "fd64")
+
+
+def test_backward_small_scene(r4g):
+    g, cam, t = synth.small_scene(seed=21)
+    w = _weights(g, cam, t, 1)
+    got = _gpu_grads(r4g, g, cam, t, w)
+    ref = oracle.render_grad(oracle.to_f64(g), cam, t, w)
+    _compare(got, ref, "small")
+
+
+def test_backward_with_background_and_tiles(r4g):
+    g, cam, t = synth.small_scene(seed=22, width=72, height=56)
+    bg = (0.3, 0.6, 0.9)
+    w = _weights(g, cam, t, 2, bg)
+    ref = oracle.render_grad(oracle.to_f64(g), cam, t, w, bg=bg)
+    for tile in ((16, 16), (8, 8), (16, 32)):
+        got = _gpu_grads(r4g, g, cam, t, w, bg=bg, tile=tile)
+        _compare(got, ref, f"tile{tile}")
+
+
+def test_views_accumulate(r4g):
+    g = synth.gaussians(200, 23)
+    views = [(synth.look_at((0.0, 0.0, -4.0), (0, 0, 0), 48, 40), 0.3),
+             (synth.look_at((3.0, 0.5, -2.5), (0, 0, 0), 40, 48), 0.7)]
+    rend = r4g.Renderer()
+    p = to_device(g)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in p.items()}
+    ref = {k: 0.0 for k in NAMES}
+    for i, (cam, t) in enumerate(views):
+        w = _weights(g, cam, t, 10 + i)
+        res = rend.render(p, cam, t)
+        rend.backward(p, cam, t, res, torch.as_tensor(w).cuda(), grads)
+        r = oracle.render_grad(oracle.to_f64(g), cam, t, w)
+        ref = {k: ref[k] + r[k] for k in NAMES}
+    torch.cuda.synchronize()
+    _compare({k: v.double().cpu().numpy() for k, v in grads.items()}, ref, "views")
+
+
+def test_autograd_function(r4g):
+    g, cam, t = synth.small_scene(seed=24, n=300, width=48, height=48)
+    p = {k: v.requires_grad_(True) for k, v in to_device(g).items()}
+    w = _weights(g, cam, t, 3)
+    img = r4g.render(p, cam, t)
+    (img * torch.as_tensor(w).cuda()).sum().backward()
+    ref = oracle.render_grad(oracle.to_f64(g), cam, t, w)
+    _compare({k: p[k].grad.double().cpu().numpy() for k in NAMES}, ref, "autograd")
+
+
+def test_backward_fp64_slice_path(r4g):
+    from paper_2402_03307_gb300 import abi
+    g, cam, t = synth.small_scene(seed=25, n=400, width=64, height=64)
+    w = _weights(g, cam, t, 4)
+    got = _gpu_grads(r4g, g, cam, t, w, flags=abi.R4G_FLAG_FP64_SLICE)
+    ref = oracle.render_grad(oracle.to_f64(g), cam, t, w)
+    _compare(got, ref, "fp64")

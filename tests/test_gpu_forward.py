@@ -1,0 +1,210 @@
+"""Forward render parity: the CUDA path through the C ABI against the FP64
+oracle on the same seeded inputs -- image (max-abs 2e-3 on unambiguous
+pixels, PSNR > 60 dB), final transmittance, last contributor, per-Gaussian
+screen records, the sorted key list, and the edge cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import MAX_ABS, MIN_PSNR, ambiguous, gpu_last_ids, image_report, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def r4g():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03307_gb300 as m
+    return m
+
+
+def _render(r4g, g, cam, t, **kw):
+    rend = r4g.Renderer(**kw)
+    res = rend.render(to_device(g), cam, t)
+    torch.cuda.synchronize()
+    return rend, res
+
+
+def _check_image(img, ref, tag=""):
+    rep = image_report(img, ref)
+    assert rep["ambiguous"] < 1e-4 or rep["ambiguous"] * img.shape[1] * img.shape[2] <= 2, (tag, rep["ambiguous"])
+    assert rep["max_abs"] <= MAX_ABS, (tag, rep["max_abs"])
+    assert rep["psnr"] > MIN_PSNR, (tag, rep["psnr"])
+    return rep
+
+
+def test_small_scene_image_T_and_last(r4g):
+    g, cam, t = synth.small_scene(seed=1)
+    rend, res = _render(r4g, g, cam, t)
+    ref = oracle.render(oracle.to_f64(g), cam, t)
+    img = res.image.cpu().numpy()
+    rep = _check_image(img, ref, "small")
+    ex = rend.export(res)
+    T_gpu = res.frame  # T lives in the frame; read it through a second render with outputs
+    out_T = torch.empty((cam.height, cam.width), device="cuda")
+    out_last = torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda")
+    from paper_2402_03307_gb300 import abi
+    s = torch.cuda.current_stream().cuda_stream
+    abi.r4g_render(rend.ctx, r4g.gaussians_struct(to_device(g)), r4g.camera_struct(cam), t,
+                   res.image.data_ptr(), out_T.data_ptr(), out_last.data_ptr(), res.frame.data_ptr(),
+                   res.frame.numel(), res.key_capacity, s)
+    torch.cuda.synchronize()
+    del T_gpu
+    amb = ambiguous(ref, image=False)
+    assert amb.mean() < 0.01
+    T = out_T.cpu().numpy()
+    assert np.abs(T - ref["T"].numpy())[~amb].max() < 1e-4
+    ids = gpu_last_ids(out_last.cpu().numpy(), ex["values"].cpu().numpy(), ex["ranges"].cpu().numpy(), (16, 16))
+    assert np.array_equal(ids[~amb], ref["last"].numpy()[~amb])
+    assert (ref["last"].numpy() >= 0).mean() > 0.3  # the scene covers much of the view
+
+
+def test_records_match_oracle(r4g):
+    g, cam, t = synth.small_scene(seed=3)
+    rend, res = _render(r4g, g, cam, t)
+    rec = rend.export(res)["records"].cpu().numpy().astype(np.float64)
+    o = oracle.preprocess(oracle.to_f64(g), cam, t)
+    vis_o = o["visible"].numpy() & (o["opacity_t"].numpy() >= 1 / 255)
+    vis_g = rec[:, 5] > 0
+    # visibility agrees except within rounding of a cull threshold
+    near = np.abs(o["opacity_t"].numpy() * 255 - 1) < 1e-4
+    assert np.array_equal(vis_o[~near], vis_g[~near])
+    v = vis_o & vis_g
+    assert v.sum() > 300
+    np.testing.assert_allclose(rec[v, 0:2], o["mean2d"].numpy()[v], rtol=0, atol=2e-3)
+    con = o["conic"].numpy()[v]
+    scale = np.abs(con).max(axis=1, keepdims=True)
+    assert (np.abs(rec[v][:, [2, 3, 4]] - con) / scale).max() < 1e-3
+    np.testing.assert_allclose(rec[v, 5], o["opacity_t"].numpy()[v], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(rec[v, 6], o["z"].numpy()[v], rtol=1e-6)
+    np.testing.assert_allclose(rec[v][:, 8:11], o["rgb"].numpy()[v], rtol=0, atol=1e-5)
+
+
+def test_sorted_keys_are_consistent(r4g):
+    g, cam, t = synth.small_scene(seed=4)
+    rend, res = _render(r4g, g, cam, t)
+    ex = rend.export(res)
+    keys = ex["keys"].cpu().numpy().view(np.uint64)
+    vals = ex["values"].cpu().numpy().view(np.uint32)
+    rec = ex["records"].cpu().numpy()
+    ranges = ex["ranges"].cpu().numpy()
+    assert len(keys) > 1000
+    assert np.all(keys[1:] >= keys[:-1])  # sorted
+    # depth bits of each key are the record depth of its Gaussian
+    assert np.array_equal((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32), rec[vals, 6].view(np.uint32))
+    # equal keys keep increasing Gaussian index (stable sort of index-ordered emission)
+    same = keys[1:] == keys[:-1]
+    assert np.all(vals[1:][same] > vals[:-1][same])
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    for tid in np.unique(tiles):
+        b, e = ranges[tid]
+        assert np.all(tiles[b:e] == tid) and (e - b) == np.sum(tiles == tid)
+    # every (tile, Gaussian) pair appears once
+    pairs = tiles * (1 << 32) + vals.astype(np.int64)
+    assert len(np.unique(pairs)) == len(pairs)
+
+
+def test_image_does_not_depend_on_tile_shape(r4g):
+    g, cam, t = synth.small_scene(seed=5, width=120, height=88)
+    imgs = []
+    for tile in ((16, 16), (8, 8), (16, 32)):
+        _, res = _render(r4g, g, cam, t, tile=tile)
+        imgs.append(res.image.cpu().numpy())
+    assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
+
+
+@pytest.mark.parametrize("size", [(37, 29), (1, 1), (200, 17), (64, 64)])
+def test_ragged_image_sizes(r4g, size):
+    w, h = size
+    g = synth.gaussians(500, 6)
+    cam = synth.look_at((0.5, 0.3, -3.5), (0.0, 0.0, 0.0), w, h)
+    _, res = _render(r4g, g, cam, 0.4)
+    ref = oracle.render(oracle.to_f64(g), cam, 0.4)
+    _check_image(res.image.cpu().numpy(), ref, str(size))
+
+
+def test_background_and_sh_degree(r4g):
+    g, cam, t = synth.small_scene(seed=7, width=96, height=72)
+    for deg in (0, 1, 2, 3):
+        bg = (0.25, 0.5, 1.0)
+        _, res = _render(r4g, g, cam, t, bg=bg, sh_degree=deg)
+        ref = oracle.render(oracle.to_f64(g), cam, t, bg=bg, sh_degree=deg)
+        _check_image(res.image.cpu().numpy(), ref, f"deg{deg}")
+
+
+def test_empty_and_fully_culled_scenes(r4g):
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 40, 30)
+    g0 = {k: v[:0] for k, v in synth.gaussians(4, 0).items()}
+    _, res = _render(r4g, g0, cam, 0.5, bg=(0.1, 0.2, 0.3))
+    img = res.image.cpu().numpy()
+    assert np.allclose(img[0], 0.1) and np.allclose(img[1], 0.2) and np.allclose(img[2], 0.3)
+    g = synth.gaussians(300, 1)
+    g["mean"][:, 2] = -10.0  # all behind the camera
+    _, res = _render(r4g, g, cam, 0.5)
+    assert np.all(res.image.cpu().numpy() == 0.0)
+
+
+def test_key_overflow_is_reported_and_recovered(r4g):
+    g, cam, t = synth.small_scene(seed=8)
+    rend = r4g.Renderer()
+    p = to_device(g)
+    small = rend.render(p, cam, t, key_capacity=64, check=False)
+    st, need = rend.status(small)
+    from paper_2402_03307_gb300 import abi
+    assert st == abi.R4G_EOVERFLOW and need > 64
+    full = rend.render(p, cam, t, key_capacity=need)
+    st2, need2 = rend.status(full)
+    assert st2 == abi.R4G_OK and need2 == need
+    auto = rend.render(p, cam, t, key_capacity=64)  # check=True grows the buffer
+    assert torch.equal(auto.image, full.image)
+
+
+def test_temporal_cull_flag_is_output_neutral(r4g):
+    from paper_2402_03307_gb300 import abi
+    g, cam, t = synth.small_scene(seed=9)
+    _, a = _render(r4g, g, cam, t)
+    _, b = _render(r4g, g, cam, t, flags=abi.R4G_FLAG_NO_TEMPORAL_CULL)
+    assert torch.equal(a.image, b.image)
+
+
+def test_fp64_slice_debug_path(r4g):
+    from paper_2402_03307_gb300 import abi
+    g, cam, t = synth.small_scene(seed=10)
+    g["logscale"][:, 3] -= 4.0  # near-degenerate temporal scales
+    _, res = _render(r4g, g, cam, t, flags=abi.R4G_FLAG_FP64_SLICE)
+    ref = oracle.render(oracle.to_f64(g), cam, t)
+    _check_image(res.image.cpu().numpy(), ref, "fp64")
+
+
+def test_bf16_storage_of_scales_and_sh(r4g):
+    g, cam, t = synth.small_scene(seed=11)
+    p = to_device(g, dtypes={"logscale": torch.bfloat16, "sh": torch.bfloat16})
+    rend = r4g.Renderer()
+    res = rend.render(p, cam, t)
+    g_round = dict(g)
+    g_round["logscale"] = p["logscale"].float().cpu().numpy()
+    g_round["sh"] = p["sh"].float().cpu().numpy()
+    ref = oracle.render(oracle.to_f64(g_round), cam, t)
+    _check_image(res.image.cpu().numpy(), ref, "bf16")
+
+
+def test_full_size_frame_sampled_pixels(r4g):
+    """300k Gaussians at 1352x1014 (sweep frame 37): 1500 sampled pixels against
+    the oracle, computed one by one over all Gaussians; the rest by properties."""
+    g = synth.fwd300k_scene()
+    cam, t = synth.orbit_camera(37, 300, 8.0, 1352, 1014)
+    rend = r4g.Renderer()
+    res = rend.render(to_device(g), cam, t)
+    img = res.image.cpu().numpy()
+    assert np.isfinite(img).all() and img.min() >= 0
+    pix = synth.random_pixels(5, 1352, 1014, 1500)
+    ref = oracle.render_pixels(oracle.to_f64(g), cam, t, pix)
+    amb = ambiguous(ref, image=True)
+    got = img[:, pix[:, 1], pix[:, 0]].T
+    err = np.abs(got - ref["rgb"].numpy())
+    assert amb.mean() < 0.02
+    assert err[~amb].max() <= MAX_ABS, err[~amb].max()
+    assert (ref["rgb"].numpy().sum(1) > 0).mean() > 0.5
