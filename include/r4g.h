@@ -17,7 +17,8 @@
  * Conventions shared by every entry point:
  *  - All buffer pointers are DEVICE pointers unless a parameter says "host".
  *    The caller owns every buffer; the library never frees caller memory and
- *    never allocates except in r4g_create (a few bytes of status memory).
+ *    allocates no device memory (it creates CUDA events only when stage
+ *    timing is enabled).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call only enqueues work on that stream; none synchronises, except
  *    r4g_frame_status, which waits for the stream to read the frame's status.
@@ -207,6 +208,27 @@ r4g_status r4g_sort_pairs(const uint64_t* keys_in, const uint32_t* values_in,
                           uint64_t* keys_out, uint32_t* values_out, int64_t n,
                           int32_t begin_bit, int32_t end_bit,
                           void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---- sort without allocation -------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory and therefore cannot pass the scratch buffer
+ * r4g_sort_pairs needs (a plug-in inside a host application that owns the GPU
+ * memory budget, a real-time loop that must not call an allocator). Same
+ * result as r4g_sort_pairs, bit for bit, for n <= R4G_SORT_NOALLOC_MAX_PAIRS;
+ * larger n returns R4G_EINVAL with nothing enqueued. It allocates nothing:
+ * its scratch is one file-scope device array of R4G_SORT_NOALLOC_SCRATCH_BYTES
+ * bytes that each GPU loading the library holds until the process exits.
+ * All calls on a device share that array and it keeps the last call's
+ * contents, so calls that may overlap on the GPU (unordered streams) race and
+ * corrupt each other; order them on one stream or with events. The first call
+ * on each device looks up the array's device address with that device current
+ * and caches it; make that first call before starting any stream capture.
+ * Error messages are returned by r4g_last_error(NULL). */
+#define R4G_SORT_NOALLOC_MAX_PAIRS 1048576
+#define R4G_SORT_NOALLOC_SCRATCH_BYTES 12894208
+r4g_status r4g_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* values_in,
+                                  uint64_t* keys_out, uint32_t* values_out, int64_t n,
+                                  int32_t begin_bit, int32_t end_bit, void* stream);
 
 #ifdef __cplusplus
 }

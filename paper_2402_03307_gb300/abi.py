@@ -64,6 +64,8 @@ SIGNATURES = [
     ("r4g_sort_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
     ("r4g_sort_pairs", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                  C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("r4g_sort_pairs_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.c_int32, C.c_int32, C.c_void_p]),
 ]
 
 

@@ -135,6 +135,8 @@ struct StageScope {
 
 namespace r4g {
 
+void set_last_error(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h) {
   FrameLayout L{};
   L.n = n;

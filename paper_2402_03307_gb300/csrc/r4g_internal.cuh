@@ -57,6 +57,8 @@ constexpr int kSortRadixBits = 8;
 constexpr int kSortRadix = 1 << kSortRadixBits;
 
 int sort_ctas_for(int64_t cap);
+// Sets the message r4g_last_error(NULL) returns on this host thread.
+void set_last_error(const char* msg);
 FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h);
 
 // Exponent of a Gaussian at a pixel, power = -1/2 (a dx^2 + 2 b dx dy + c dy^2),
