@@ -47,7 +47,7 @@ typedef enum r4g_status {
   R4G_ENOMEM = 2,      /* r4g_create could not allocate its status memory */
   R4G_EWORKSPACE = 3,  /* the frame / scratch buffer is smaller than required */
   R4G_ECUDA = 4,       /* a CUDA launch or call failed; see r4g_last_error */
-  R4G_ETIMEOUT = 5,    /* reserved: a bounded device-side wait gave up */
+  R4G_ETIMEOUT = 5,    /* a bounded device-side wait gave up (see r4g_frame_status) */
   R4G_EDEVICE = 6,     /* the device reported an inconsistent state */
   R4G_EOVERFLOW = 7    /* the frame's key capacity was too small (see r4g_frame_status) */
 } r4g_status;
@@ -135,8 +135,9 @@ int32_t r4g_version(void);
 r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t height,
                            int64_t key_capacity, size_t* bytes /* host out */);
 
-/* Wait for `stream`, then report the frame's device-side status: R4G_OK or
- * R4G_EOVERFLOW. *keys_needed (host, may be NULL) receives the number of
+/* Wait for `stream`, then report the frame's device-side status: R4G_OK,
+ * R4G_EOVERFLOW, or R4G_ETIMEOUT when a radix-sort look-back wait reached its
+ * iteration limit (the image of that render is then invalid). *keys_needed (host, may be NULL) receives the number of
  * (tile, Gaussian) pairs of the last render into this frame. */
 r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
                             int64_t* keys_needed, void* stream);

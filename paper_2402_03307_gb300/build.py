@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libr4g.so")
-SOURCES = ["preprocess.cu", "binning.cu", "sort.cu", "sort_noalloc.cu", "blend.cu", "api.cu"]
+SOURCES = ["preprocess.cu", "binning.cu", "sort.cu", "sort_noalloc.cu", "onesweep.cu", "blend.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -150,34 +150,52 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
   L.ntiles = L.tiles_x * L.tiles_y;
   L.nblocks = static_cast<int>((n + kPreBlock - 1) / kPreBlock);
   L.sort_ctas = sort_ctas_for(cap);
+  L.depth_ctas = sort_ctas_for(n);
   int tb = 0;
   while ((int64_t(1) << tb) < L.ntiles) ++tb;
-  L.sort_bits = 32 + tb;
+  L.tile_bits = tb;
+  const int dpasses = 32 / kSortRadixBits;
+  const int tpasses = (tb + kSortRadixBits - 1) / kSortRadixBits;
+  L.order_in_1 = dpasses % 2 == 1;
+  L.keys_in_1 = tpasses % 2 == 1;
+  const int cnt_ctas = L.sort_ctas > L.depth_ctas ? L.sort_ctas : L.depth_ctas;
   const size_t npix = static_cast<size_t>(width) * height;
   size_t o = 0;
   L.header = o;   o = align_up(o + sizeof(FrameHeader));
   L.rec = o;      o = align_up(o + 3 * sizeof(float4) * n);
   L.rect = o;     o = align_up(o + sizeof(uint2) * n);
   L.touched = o;  o = align_up(o + sizeof(uint32_t) * n);
+  L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * n);
+  L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * n);
+  L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * n);
+  L.ord1 = o;     o = align_up(o + sizeof(uint32_t) * n);
+  L.offs = o;     o = align_up(o + sizeof(uint32_t) * (n + 1));
+  L.srect = o;    o = align_up(o + sizeof(uint2) * n);
   L.blocksum = o; o = align_up(o + sizeof(uint32_t) * (L.nblocks + 1));
-  L.keys0 = o;    o = align_up(o + sizeof(uint64_t) * cap);
+  L.keys0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.vals0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
-  L.keys1 = o;    o = align_up(o + sizeof(uint64_t) * cap);
+  L.keys1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.vals1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.ranges = o;   o = align_up(o + sizeof(uint2) * L.ntiles);
   L.tfinal = o;   o = align_up(o + sizeof(float) * npix);
   L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
-  L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * L.sort_ctas);
+  L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);
+  {
+    const size_t a = onesweep_scratch_bytes(n, 32), b = onesweep_scratch_bytes(cap, tb);
+    L.onesweep = o; o = align_up(o + (a > b ? a : b));
+  }
   L.recgrad = o;  o = align_up(o + 12 * sizeof(float) * n);
   L.total = o;
   return L;
 }
 
-// Number of radix passes decides which buffer ends up holding the sorted
-// list: pass p writes keys1 when p is even and keys0 when p is odd.
-static bool sorted_in_keys1(const FrameLayout& L) {
-  const int passes = (L.sort_bits + kSortRadixBits - 1) / kSortRadixBits;
-  return passes % 2 == 1;
+// Sorted tile keys / values of a frame (which buffer depends on the number
+// of radix passes: pass p writes buffer 1 when p is even, buffer 0 when odd).
+static const uint32_t* sorted_tile_keys(const FrameLayout& L, void* f) {
+  return at<uint32_t>(f, L.keys_in_1 ? L.keys1 : L.keys0);
+}
+static const uint32_t* sorted_vals(const FrameLayout& L, void* f) {
+  return at<uint32_t>(f, L.keys_in_1 ? L.vals1 : L.vals0);
 }
 
 }  // namespace r4g
@@ -274,6 +292,7 @@ r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_frame_status");
   if (keys_needed) *keys_needed = h.key_needed;
   if (h.status & 1u) return fail(ctx, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
+  if (h.status & 2u) return fail(ctx, R4G_ETIMEOUT, "a radix-sort look-back wait hit its iteration limit");
   return R4G_OK;
 }
 
@@ -297,13 +316,11 @@ r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   const FrameLayout L = make_layout(n, width, height, lo, ctx->cfg.tile_w, ctx->cfg.tile_h);
   if (L.total > frame_bytes || h.key_count > L.cap) return fail(ctx, R4G_EWORKSPACE, "frame size does not match");
   void* f = const_cast<void*>(frame);
-  const bool k1 = sorted_in_keys1(L);
   const uint32_t K = h.key_count;
   if (key_count) e = cudaMemcpyAsync(key_count, &at<FrameHeader>(f, L.header)->key_count, 4, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && keys && K)
-    e = cudaMemcpyAsync(keys, at<uint64_t>(f, k1 ? L.keys1 : L.keys0), 8ull * K, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && keys && K) e = launch_export_keys(L, f, sorted_tile_keys(L, f), sorted_vals(L, f), keys, s);
   if (e == cudaSuccess && values && K)
-    e = cudaMemcpyAsync(values, at<uint32_t>(f, k1 ? L.vals1 : L.vals0), 4ull * K, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyAsync(values, sorted_vals(L, f), 4ull * K, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && ranges)
     e = cudaMemcpyAsync(ranges, at<uint2>(f, L.ranges), 8ull * L.ntiles, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && records && n) {
@@ -324,7 +341,7 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
   if ((st = check_camera(ctx, cam)) != R4G_OK) return st;
   if (!out_rgb || !frame) return fail(ctx, R4G_EINVAL, "out_rgb / frame is NULL");
   if (!std::isfinite(t)) return fail(ctx, R4G_EINVAL, "t is not finite");
-  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
+  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(ctx, R4G_EINVAL, "key_capacity out of range (< 2^30)");
   if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
   const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
   if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
@@ -333,31 +350,42 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
   cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const bool has = L.n > 0;
+  const int dpasses = 32 / kSortRadixBits;
+  const int tpasses = (L.tile_bits + kSortRadixBits - 1) / kSortRadixBits;
   {
     StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, has ? 1 : 0);
     if ((e = launch_preprocess_fwd(*g, cd, t, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, s)) != cudaSuccess)
       return cuda_fail(ctx, e, "preprocess");
   }
-  {
-    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 2 : 0);
-    if ((e = launch_binning(L, frame, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
-  }
-  const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
+  uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
   int which = 0;
   if (has) {
-    const int passes = (L.sort_bits + kSortRadixBits - 1) / kSortRadixBits;
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 3 * passes);
-    e = launch_sort(at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint64_t>(frame, L.keys1),
-                    at<uint32_t>(frame, L.vals1), at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                    count, 0, L.cap, 0, L.sort_bits, at<uint32_t>(frame, L.sortcnt), L.sort_ctas, s, &which);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "sort");
+    // depth order of the Gaussians: stable sort of the depth bits, values = index
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);
+    e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
+                        at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
+                        nullptr, static_cast<uint32_t>(L.n), L.n, 32, at<void>(frame, L.onesweep), err, s, &which);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
   }
-  const bool k1 = sorted_in_keys1(L);
-  const uint64_t* keys = at<uint64_t>(frame, k1 ? L.keys1 : L.keys0);
-  const uint32_t* vals = at<uint32_t>(frame, k1 ? L.vals1 : L.vals0);
+  const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
+  {
+    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 4 : 0);
+    if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
+  }
+  const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
+  if (has && tpasses > 0) {
+    // stable sort of the depth-ordered pairs by tile id
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + tpasses);
+    e = launch_onesweep(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint32_t>(frame, L.keys1),
+                        at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
+  }
+  const uint32_t* tkeys = sorted_tile_keys(L, frame);
+  const uint32_t* vals = sorted_vals(L, frame);
   {
     StageScope sc(ctx, R4G_STAGE_RANGES, s, has ? 1 : 0);
-    if ((e = launch_ranges(L, frame, keys, s)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
+    if ((e = launch_ranges(L, frame, tkeys, s)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
   }
   {
     StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
@@ -386,8 +414,7 @@ r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_c
   const CamDev cd = make_cam(*cam);
   cudaError_t e = cudaMemsetAsync(at<char>(frame, L.recgrad), 0, 12 * sizeof(float) * L.n, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  const bool k1 = sorted_in_keys1(L);
-  const uint32_t* vals = at<uint32_t>(frame, k1 ? L.vals1 : L.vals0);
+  const uint32_t* vals = sorted_vals(L, frame);
   {
     StageScope sc(ctx, R4G_STAGE_BLEND_BWD, s, 1);
     if ((e = launch_blend_bwd(L, frame, vals, ctx->cfg.bg, grad_rgb, s)) != cudaSuccess)

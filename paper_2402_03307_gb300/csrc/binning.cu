@@ -1,8 +1,13 @@
-// Tile binning of the rasteriser (Sec. 3.1): the exclusive scan of the
-// per-Gaussian tile counts, the emission of one 64-bit key per (tile,
-// Gaussian) pair -- key = tile_id << 32 | float_bits(depth), value = Gaussian
-// index, in Gaussian-index order and row-major tile order within a Gaussian --
-// and the per-tile [begin, end) ranges of the sorted key list.
+// Tile binning of the rasteriser (Sec. 3.1). The Gaussians are first put in
+// depth order (a stable radix sort of their depth bits, ties by index), then
+// one (tile, Gaussian) pair is emitted per tile a Gaussian's box covers, in
+// that order and row-major within a Gaussian. A stable sort of the pairs by
+// tile id then gives, bit for bit, the order of a stable sort of 64-bit keys
+// tile_id << 32 | float_bits(depth) emitted in Gaussian-index order.
+// This file holds: the per-block totals of tile counts in depth order, their
+// exclusive scan, per-Gaussian offsets, the emission balanced over the output
+// pairs, the per-tile [begin, end)
+// ranges of the sorted list, and the export of the equivalent 64-bit keys.
 #include <cuda_runtime.h>
 
 #include "r4g_internal.cuh"
@@ -11,8 +16,26 @@ namespace r4g {
 
 constexpr int kScanThreads = 1024;
 
-// Exclusive scan of the per-block tile totals in place (one CTA); writes the
-// pair count and the overflow flag into the frame header.
+// blocksum[b] = sum of touched[order[j]] over the block's depth positions.
+__global__ void __launch_bounds__(kPreBlock)
+    depth_blocksum_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, int n,
+                          uint32_t* __restrict__ blocksum) {
+  __shared__ uint32_t s_sum[kPreBlock / 32];
+  const int j = blockIdx.x * kPreBlock + threadIdx.x;
+  const uint32_t c = j < n ? touched[order[j]] : 0u;
+  const uint32_t ws = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t a = 0;
+#pragma unroll
+    for (int w = 0; w < kPreBlock / 32; ++w) a += s_sum[w];
+    blocksum[blockIdx.x] = a;
+  }
+}
+
+// Exclusive scan of the per-block totals in place (one CTA); writes the pair
+// count and the overflow flag into the frame header.
 __global__ void __launch_bounds__(kScanThreads)
     scan_blocksums_kernel(uint32_t* blocksum, int nblocks, FrameHeader* hdr, uint32_t cap) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -56,19 +79,18 @@ __global__ void __launch_bounds__(kScanThreads)
   }
 }
 
-// One thread per Gaussian (same blocking as the preprocess); each warp emits
-// the keys of its 32 Gaussians cooperatively, 32 consecutive keys per step,
-// so the writes are coalesced and a Gaussian with many tiles does not stall
-// one lane.
+// Exclusive offset of every Gaussian's first pair, in depth order, and its
+// tile rectangle gathered into depth order (same blocking as
+// depth_blocksum_kernel; blockoff holds the scanned block totals).
 __global__ void __launch_bounds__(kPreBlock)
-    keybuild_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ blockoff,
-                    const uint2* __restrict__ rect, const float4* __restrict__ recB, int n,
-                    int tiles_x, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                    uint32_t cap) {
+    depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
+                         const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect, int n,
+                         uint32_t* __restrict__ offs, uint2* __restrict__ srect) {
   __shared__ uint32_t s_warp[kPreBlock / 32];
-  const int i = blockIdx.x * kPreBlock + threadIdx.x;
+  const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t cnt = i < n ? touched[i] : 0u;
+  const uint32_t g = j < n ? order[j] : 0u;
+  const uint32_t cnt = j < n ? touched[g] : 0u;
   uint32_t x = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -77,72 +99,128 @@ __global__ void __launch_bounds__(kPreBlock)
   }
   if (lane == 31) s_warp[warp] = x;
   __syncthreads();
-  uint32_t wbase = blockoff[blockIdx.x];
-  for (int w = 0; w < warp; ++w) wbase += s_warp[w];
-  const uint32_t excl = x - cnt;  // within the warp
-  const uint32_t wtotal = __shfl_sync(0xffffffffu, x, 31);
-  uint2 r = make_uint2(0u, 0u);
-  uint32_t zb = 0;
-  if (cnt) {
-    r = rect[i];
-    zb = __float_as_uint(recB[i].z);
+  uint32_t base = blockoff[blockIdx.x];
+  for (int w = 0; w < warp; ++w) base += s_warp[w];
+  if (j < n) {
+    offs[j] = base + x - cnt;
+    srect[j] = cnt ? rect[g] : make_uint2(0u, 0u);
   }
-  for (uint32_t j0 = 0; j0 < wtotal; j0 += 32) {
-    const uint32_t j = j0 + lane;
-    // owner = the last lane whose exclusive offset is <= j
-    int own = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const uint32_t e = __shfl_sync(0xffffffffu, excl, own + step);
-      if (e <= j) own += step;
+}
+
+// Pair emission balanced over the output: CTA c writes pairs
+// [c E, (c + 1) E) of the depth-ordered list. Gaussians with pairs are at the
+// front of the depth order (a Gaussian without tiles has the largest key), so
+// their offsets increase strictly and a chunk of E pairs involves at most
+// E + 1 of them: their offsets are loaded into shared memory and each pair
+// finds its Gaussian by binary search there. Pair q of Gaussian j covers tile
+// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j].
+constexpr int kEmitChunk = 2048;
+__global__ void __launch_bounds__(kPreBlock)
+    emit_kernel(const uint32_t* __restrict__ offs, const uint2* __restrict__ srect,
+                const uint32_t* __restrict__ order, int n, int tiles_x, const FrameHeader* hdr,
+                uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
+  __shared__ uint32_t s_off[kEmitChunk + 1];
+  __shared__ uint32_t s_jlo;
+  const uint32_t K = hdr->key_count;
+  const uint32_t q0 = blockIdx.x * kEmitChunk;
+  if (q0 >= K) return;  // CTA-uniform: the grid is sized for the capacity
+  if (threadIdx.x == 0) {
+    // last j with offs[j] <= q0
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (offs[mid] <= q0) lo = mid;
+      else hi = mid - 1;
     }
-    const uint32_t oex = __shfl_sync(0xffffffffu, excl, own);
-    const uint32_t orx = __shfl_sync(0xffffffffu, r.x, own);
-    const uint32_t ory = __shfl_sync(0xffffffffu, r.y, own);
-    const uint32_t oz = __shfl_sync(0xffffffffu, zb, own);
-    if (j < wtotal) {
-      const uint32_t local = j - oex;
-      const uint32_t x0 = orx & 0xffffu, y0 = orx >> 16, x1 = ory & 0xffffu;
-      const uint32_t w = x1 - x0;
-      const uint32_t ty = y0 + local / w, tx = x0 + local % w;
-      const uint32_t pos = wbase + j;
-      if (pos < cap) {
-        keys[pos] = (static_cast<uint64_t>(ty * static_cast<uint32_t>(tiles_x) + tx) << 32) | oz;
-        vals[pos] = static_cast<uint32_t>(blockIdx.x * kPreBlock + warp * 32 + own);
+    s_jlo = static_cast<uint32_t>(lo);
+  }
+  __syncthreads();
+  const int jlo = static_cast<int>(s_jlo);
+  const int m = min(kEmitChunk + 1, n - jlo);  // window of Gaussians
+  for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
+  __syncthreads();
+  const uint32_t qend = min(K, q0 + kEmitChunk);
+  for (uint32_t q = q0 + threadIdx.x; q < qend; q += kPreBlock) {
+    int lo = 0, hi = m - 1;  // last i with s_off[i] <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= q) lo = mid;
+      else hi = mid - 1;
+    }
+    const int j = jlo + lo;
+    const uint32_t local = q - s_off[lo];
+    const uint2 r = srect[j];
+    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+    const uint32_t w = x1 - x0;
+    const uint32_t ty = y0 + local / w, tx = x0 + local % w;
+    tkeys[q] = ty * static_cast<uint32_t>(tiles_x) + tx;
+    vals[q] = order[j];
+  }
+}
+
+// ranges[tile] = [first, last+1) of the tile's entries in the sorted list;
+// four consecutive entries per thread.
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const FrameHeader* hdr,
+                              uint2* __restrict__ ranges) {
+  const uint32_t n = hdr->key_count;
+  const uint32_t stride = gridDim.x * blockDim.x * 4;
+  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) * 4; b < n; b += stride) {
+    uint32_t k[6];
+    k[0] = b > 0 ? keys[b - 1] : 0xffffffffu;
+#pragma unroll
+    for (int u = 0; u < 5; ++u) k[u + 1] = (b + u < n) ? keys[b + u] : 0xffffffffu;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = b + u;
+      if (i < n) {
+        const uint32_t tile = k[u + 1];
+        if (k[u] != tile) ranges[tile].x = i;
+        if (k[u + 2] != tile) ranges[tile].y = i + 1;
       }
     }
   }
 }
 
-// ranges[tile] = [first, last+1) of the tile's keys in the sorted list.
-__global__ void ranges_kernel(const uint64_t* __restrict__ keys, const FrameHeader* hdr,
-                              uint2* __restrict__ ranges) {
+__global__ void export_keys_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
+                                   const float4* __restrict__ recB, const FrameHeader* hdr,
+                                   uint64_t* __restrict__ out) {
   const uint32_t n = hdr->key_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t tile = static_cast<uint32_t>(keys[i] >> 32);
-    if (i == 0 || static_cast<uint32_t>(keys[i - 1] >> 32) != tile) ranges[tile].x = i;
-    if (i == n - 1 || static_cast<uint32_t>(keys[i + 1] >> 32) != tile) ranges[tile].y = i + 1;
-  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | __float_as_uint(recB[vals[i]].z);
 }
 
-cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s) {
+cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   uint32_t* bs = at<uint32_t>(frame, L.blocksum);
+  const uint32_t* touched = at<uint32_t>(frame, L.touched);
+  const int n = static_cast<int>(L.n);
+  uint32_t* offs = at<uint32_t>(frame, L.offs);
+  uint2* srect = at<uint2>(frame, L.srect);
+  depth_blocksum_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, n, bs);
   scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
-  const float4* recB = at<float4>(frame, L.rec) + L.n;
-  keybuild_kernel<<<L.nblocks, kPreBlock, 0, s>>>(
-      at<uint32_t>(frame, L.touched), bs, at<uint2>(frame, L.rect), recB, static_cast<int>(L.n),
-      L.tiles_x, at<uint64_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-      static_cast<uint32_t>(L.cap));
+  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect), n, offs, srect);
+  const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
+  if (chunks > 0)
+    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, n, L.tiles_x, hdr,
+                                                                     at<uint32_t>(frame, L.keys0),
+                                                                     at<uint32_t>(frame, L.vals0));
   return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint64_t* keys, cudaStream_t s) {
+cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* tile_keys, cudaStream_t s) {
   uint2* ranges = at<uint2>(frame, L.ranges);
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.ntiles, s);
   if (L.n == 0) return cudaGetLastError();
-  ranges_kernel<<<4 * 152, 256, 0, s>>>(keys, at<FrameHeader>(frame, L.header), ranges);
+  ranges_kernel<<<2 * 152, 256, 0, s>>>(tile_keys, at<FrameHeader>(frame, L.header), ranges);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
+                               const uint32_t* vals, uint64_t* out, cudaStream_t s) {
+  if (L.n == 0) return cudaSuccess;
+  const float4* recB = at<float4>(frame, L.rec) + L.n;
+  export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, recB, at<FrameHeader>(frame, L.header), out);
   return cudaGetLastError();
 }
 

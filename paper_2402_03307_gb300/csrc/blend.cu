@@ -1,82 +1,385 @@
-// Tiled front-to-back alpha compositing (Sec. 3.1, Eq. 3) over the sorted
-// per-tile Gaussian lists. One CTA per tile, one thread per pixel. Batches
-// of CTA-size screen records are staged in shared memory; every pixel walks
-// the batch applying the per-pixel rules
+// Tiled front-to-back alpha compositing (Sec. 3.1, Eq. 3) and its backward.
+//
+// One CTA per tile; each thread owns two horizontally adjacent pixels and
+// evaluates them together with Blackwell's packed FP32x2 instructions. Each
+// warp owns a 64-pixel block of the tile (16x4 for 16-wide tiles, 8x8 for
+// 8x8 tiles). Batches of screen records are staged in shared memory with
+// every operand already duplicated into the (x, x) pairs the packed
+// instructions take. While staging, each Gaussian gets one bit per warp
+// telling whether its contributing ellipse can reach a pixel centre of that
+// warp's block; a warp then walks only the set bits of a 32-entry ballot, so
+// Gaussians that cannot touch it cost nothing. Every pixel applies the exact
+// rules of the rasteriser:
 //   power = -1/2 d^T conic d, skip if power > 0 or power < -4.5,
 //   alpha = min(0.99, opacity_t exp(power)), skip if alpha < 1/255,
-//   stop before a Gaussian that would take T below 1e-4,
-// and the CTA leaves as soon as every pixel has stopped (block-wide vote).
+//   stop before a Gaussian that would take T below 1e-4.
+// The exponent is evaluated in base 2 (power' = log2(e) power, alpha =
+// opacity_t 2^power'). The cutoff and the 1/255 rule form one window
+// pmin <= power' <= 0, pmin = max(-4.5 log2 e, -log2(255 opacity_t)),
+// tested as |(power' - mid) / half| <= 1. A pixel that stops moves to
+// infinity, so no later Gaussian reaches it; a warp whose pixels have all
+// stopped leaves the batch, a CTA whose pixels have all stopped leaves the
+// tile. The forward and the backward call the same evaluator, so they take
+// bit-identical decisions. The frame keeps, per pixel, the number of list
+// entries it considered (the stop position); the backward walks back from it.
 #include <cuda_runtime.h>
 
 #include "r4g_internal.cuh"
 
 namespace r4g {
 
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+constexpr float kCut2 = kPowerCut * kLog2e;  // cutoff on power'
+constexpr uint32_t kClampBit = 1u << 31;     // opacity_t > 0.99: alpha may need the clamp
+constexpr float kFar = 3.0e38f;              // where a stopped pixel moves
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH)
+struct Blend {
+  static constexpr int NT = TW * TH / 2;     // threads per CTA
+  static constexpr int NW = NT / 32;         // warps per CTA
+  static constexpr int PCOLS = TW / 2;       // thread columns
+  static constexpr int WROWS = 32 / PCOLS;   // pixel rows per warp block
+  static_assert(NT % 32 == 0 && 32 % PCOLS == 0 && NW <= 16, "tile shape");
+};
+
+// A staged Gaussian (96 bytes), operands duplicated for the packed pairs:
+//   p0 = (-mx, -mx, -my, -my)     p1 = (A', A', B', B')
+//   p2 = (C', C', o, o)           p3 = (r, r, g, g)
+//   p4 = (b, b, ih, ih)           p5 = (nm, nm, mask bits, 0)
+// with power' = A' dx^2 + B' dx dy + C' dy^2, ih = 1 / half, nm = -mid / half.
+struct __align__(16) StagedG {
+  float4 p0, p1, p2, p3, p4, p5;
+};
+
+// Can the Gaussian's contributing region {q <= min(9, 2 ln(255 o))}, q = d^T conic d,
+// contain a pixel centre of the rectangle [x0, x1] x [y0, y1]? Exact minimum of
+// q over the rectangle (inside, or on one of the four edges), compared with a
+// relative and an absolute slack so the answer is conservative under FP32.
+__device__ __forceinline__ bool ellipse_meets_rect(const float4 A, float c, float o, float x0, float x1,
+                                                   float y0, float y1) {
+  const float mx = A.x, my = A.y, a = A.z, b = A.w;
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+  const float k2 = fminf(9.0f, 2.0f * __logf(255.0f * o));
+  const float thr = k2 * 1.001f + 1e-3f;
+  float qmin = 3.4e38f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {  // vertical edges: minimise over dy
+    const float dx = (e ? x1 : x0) - mx;
+    float dy = -b * dx / c;
+    dy = fminf(fmaxf(dy, y0 - my), y1 - my);
+    qmin = fminf(qmin, a * dx * dx + 2.0f * b * dx * dy + c * dy * dy);
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {  // horizontal edges: minimise over dx
+    const float dy = (e ? y1 : y0) - my;
+    float dx = -b * dy / a;
+    dx = fminf(fmaxf(dx, x0 - mx), x1 - mx);
+    qmin = fminf(qmin, a * dx * dx + 2.0f * b * dx * dy + c * dy * dy);
+  }
+  return qmin <= thr;
+}
+
+// Stage one batch entry: record -> shared memory, plus the warp-block bits.
+template <int TW, int TH>
+__device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, const float4* __restrict__ recB,
+                                            const float4* __restrict__ recC, uint32_t gid, int tx, int ty,
+                                            StagedG* sg) {
+  using B = Blend<TW, TH>;
+  const float4 A = recA[gid], Bv = recB[gid], C = recC[gid];
+  const float Ap = -0.5f * kLog2e * A.z, Bp = -kLog2e * A.w, Cp = -0.5f * kLog2e * Bv.x, o = Bv.y;
+  const float pmin = fmaxf(kCut2, -log2f(255.0f * o));
+  const float mid = 0.5f * pmin, half = fmaxf(-0.5f * pmin, 1e-6f);
+  const float ih = 1.0f / half, nm = -mid * ih;
+  uint32_t m = o > kAlphaMax ? kClampBit : 0u;
+  const float x0 = tx * TW + 0.5f, x1 = tx * TW + TW - 0.5f;
+#pragma unroll
+  for (int w = 0; w < B::NW; ++w) {
+    const float y0 = ty * TH + w * B::WROWS + 0.5f;
+    const float y1 = y0 + B::WROWS - 1.0f;
+    if (ellipse_meets_rect(A, Bv.x, o, x0, x1, y0, y1)) m |= 1u << w;
+  }
+  sg->p0 = make_float4(-A.x, -A.x, -A.y, -A.y);
+  sg->p1 = make_float4(Ap, Ap, Bp, Bp);
+  sg->p2 = make_float4(Cp, Cp, o, o);
+  sg->p3 = make_float4(C.x, C.x, C.y, C.y);
+  sg->p4 = make_float4(C.z, C.z, ih, ih);
+  sg->p5 = make_float4(nm, nm, __uint_as_float(m), 0.0f);
+}
+
+// Evaluation of one staged Gaussian at the pixel pair (px, py), (px + 1, py):
+// power', 2^power', opacity_t 2^power' and whether the window takes it, every
+// rounding explicit.
+struct PairEval {
+  float2 p, e, araw, dx, dy;
+  bool v0, v1;
+};
+
+__device__ __forceinline__ PairEval eval_pair(const StagedG& g, float2 PX, float2 PY) {
+  PairEval r;
+  const float4 p0 = g.p0, p1 = g.p1, p2 = g.p2, p4 = g.p4, p5 = g.p5;
+  r.dx = __fadd2_rn(PX, make_float2(p0.x, p0.y));
+  r.dy = __fadd2_rn(PY, make_float2(p0.z, p0.w));
+  const float2 bdy = __fmul2_rn(make_float2(p1.z, p1.w), r.dy);
+  const float2 t = __ffma2_rn(make_float2(p1.x, p1.y), r.dx, bdy);
+  const float2 u = __fmul2_rn(__fmul2_rn(make_float2(p2.x, p2.y), r.dy), r.dy);
+  r.p = __ffma2_rn(r.dx, t, u);
+  r.e = make_float2(ex2_approx(r.p.x), ex2_approx(r.p.y));
+  r.araw = __fmul2_rn(make_float2(p2.z, p2.w), r.e);
+  const float2 q = __ffma2_rn(r.p, make_float2(p4.z, p4.w), make_float2(p5.x, p5.y));
+  r.v0 = fabsf(q.x) <= 1.0f;
+  r.v1 = fabsf(q.y) <= 1.0f;
+  return r;
+}
+
+template <int TW, int TH, bool kLast>
+__global__ void __launch_bounds__(Blend<TW, TH>::NT)
     blend_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
                      const float4* __restrict__ recC, int width, int height, int tiles_x,
                      float bg0, float bg1, float bg2, float* __restrict__ out_rgb,
-                     float* __restrict__ out_T, uint32_t* __restrict__ out_last) {
-  constexpr int BS = TW * TH;
-  __shared__ float4 sA[BS];
-  __shared__ float4 sB[BS];
-  __shared__ float4 sC[BS];
+                     float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
+                     uint32_t* __restrict__ out_last) {
+  using B = Blend<TW, TH>;
+  constexpr int BS = B::NT;
+  __shared__ StagedG sg[BS];
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int px = tx * TW + static_cast<int>(threadIdx.x) % TW;
-  const int py = ty * TH + static_cast<int>(threadIdx.x) / TW;
-  const bool inside = px < width && py < height;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int px = tx * TW + 2 * (lane % B::PCOLS);
+  const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
+  const bool in0 = px < width && py < height;
+  const bool in1 = px + 1 < width && py < height;
+  float2 PX = make_float2(in0 ? px + 0.5f : kFar, in1 ? px + 1.5f : kFar);
+  const float2 PY = make_float2(py + 0.5f, py + 0.5f);
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
-  float T = 1.0f, c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
-  uint32_t last = 0;
-  bool done = !inside;
+  float2 T = make_float2(1.0f, 1.0f);
+  float2 cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
+  uint32_t stop0 = static_cast<uint32_t>(n), stop1 = static_cast<uint32_t>(n);
+  uint32_t last0 = 0, last1 = 0;
+  bool done0 = !in0, done1 = !in1;
+  const uint32_t wbit = 1u << warp;
   for (int b = 0; b < n; b += BS) {
-    if (__syncthreads_count(done) == BS) break;
+    if (__syncthreads_count(done0 && done1) == BS) break;
     const int idx = b + static_cast<int>(threadIdx.x);
-    if (idx < n) {
-      const uint32_t gid = vals[rg.x + idx];
-      sA[threadIdx.x] = recA[gid];
-      sB[threadIdx.x] = recB[gid];
-      sC[threadIdx.x] = recC[gid];
-    }
+    if (idx < n) stage_entry<TW, TH>(recA, recB, recC, vals[rg.x + idx], tx, ty, &sg[threadIdx.x]);
     __syncthreads();
     const int cnt = min(BS, n - b);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        const float4 A = sA[j];
-        const float4 B = sB[j];
-        float dx, dy;
-        const float power = gauss_power(A, B.x, fx, fy, dx, dy);
-        if (power > 0.0f || power < kPowerCut) continue;
-        const float alpha = fminf(kAlphaMax, __fmul_rn(B.y, __expf(power)));
-        if (alpha < kAlphaMin) continue;
-        const float Tn = T * (1.0f - alpha);
-        if (Tn < kTMin) {
-          done = true;
-          break;
+    bool wdone = __all_sync(0xffffffffu, done0 && done1);
+    for (int j0 = 0; j0 < cnt && !wdone; j0 += 32) {
+      const uint32_t m = (j0 + lane < cnt) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
+      uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
+      const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
+      while (bits) {
+        const int jj = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const StagedG& g = sg[j0 + jj];
+        const PairEval ev = eval_pair(g, PX, PY);
+        bool v0 = ev.v0, v1 = ev.v1;
+        float2 a = make_float2(v0 ? ev.araw.x : 0.0f, v1 ? ev.araw.y : 0.0f);
+        if ((cbits >> jj) & 1u) a = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
+        float2 Tn = __ffma2_rn(make_float2(-T.x, -T.y), a, T);  // T (1 - alpha)
+        const bool st0 = Tn.x < kTMin, st1 = Tn.y < kTMin;      // only a taken Gaussian can stop
+        if (__any_sync(0xffffffffu, st0 || st1)) {
+          // stop before this Gaussian: it is not composited; the pixel is done
+          const uint32_t pos = static_cast<uint32_t>(b + j0 + jj);
+          if (st0) { a.x = 0.0f; Tn.x = T.x; PX.x = kFar; v0 = false; done0 = true; stop0 = pos; }
+          if (st1) { a.y = 0.0f; Tn.y = T.y; PX.y = kFar; v1 = false; done1 = true; stop1 = pos; }
+          wdone = __all_sync(0xffffffffu, done0 && done1);
         }
-        const float4 Cc = sC[j];
-        const float w = alpha * T;
-        c0 += Cc.x * w;
-        c1 += Cc.y * w;
-        c2 += Cc.z * w;
+        const float4 p3 = g.p3, p4 = g.p4;
+        const float2 w = __fmul2_rn(a, T);
+        cr = __ffma2_rn(make_float2(p3.x, p3.y), w, cr);
+        cg = __ffma2_rn(make_float2(p3.z, p3.w), w, cg);
+        cb = __ffma2_rn(make_float2(p4.x, p4.y), w, cb);
         T = Tn;
-        last = static_cast<uint32_t>(b + j + 1);
+        if constexpr (kLast) {
+          const uint32_t pos1 = static_cast<uint32_t>(b + j0 + jj + 1);
+          last0 = v0 ? pos1 : last0;
+          last1 = v1 ? pos1 : last1;
+        }
+        if (wdone) break;
       }
     }
   }
-  if (inside) {
+  const size_t plane = static_cast<size_t>(width) * height;
+  if (in0) {
     const size_t pix = static_cast<size_t>(py) * width + px;
-    const size_t plane = static_cast<size_t>(width) * height;
-    out_rgb[pix] = c0 + T * bg0;
-    out_rgb[plane + pix] = c1 + T * bg1;
-    out_rgb[2 * plane + pix] = c2 + T * bg2;
-    out_T[pix] = T;
-    out_last[pix] = last;
+    out_rgb[pix] = cr.x + T.x * bg0;
+    out_rgb[plane + pix] = cg.x + T.x * bg1;
+    out_rgb[2 * plane + pix] = cb.x + T.x * bg2;
+    out_T[pix] = T.x;
+    out_stop[pix] = stop0;
+    if constexpr (kLast) out_last[pix] = last0;
+  }
+  if (in1) {
+    const size_t pix = static_cast<size_t>(py) * width + px + 1;
+    out_rgb[pix] = cr.y + T.y * bg0;
+    out_rgb[plane + pix] = cg.y + T.y * bg1;
+    out_rgb[2 * plane + pix] = cb.y + T.y * bg2;
+    out_T[pix] = T.y;
+    out_stop[pix] = stop1;
+    if constexpr (kLast) out_last[pix] = last1;
+  }
+}
+
+// Backward of the blend. Each pixel re-walks its list back to front from its
+// stop position and the stored final transmittance T_N: T_i = T_{i+1} / (1 - a_i),
+// the colour already accumulated behind i is carried along, and per-Gaussian
+// gradients (d mean2d, d conic, d opacity_t, d rgb) are summed over the two
+// pixels of a thread, then over the warp with a transpose reduction (14
+// shuffles for 9 values) before one atomic add per value and warp.
+template <int TW, int TH>
+__global__ void __launch_bounds__(Blend<TW, TH>::NT)
+    blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                     const float4* __restrict__ recA, const float4* __restrict__ recB,
+                     const float4* __restrict__ recC, int width, int height, int tiles_x,
+                     float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
+                     const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
+                     float* __restrict__ rgrad) {
+  using B = Blend<TW, TH>;
+  constexpr int BS = B::NT;
+  __shared__ StagedG sg[BS];
+  __shared__ uint32_t sG[BS];
+  __shared__ uint32_t s_max;
+  const int tile = blockIdx.x;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int px = tx * TW + 2 * (lane % B::PCOLS);
+  const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
+  const bool in0 = px < width && py < height;
+  const bool in1 = px + 1 < width && py < height;
+  const float2 PX = make_float2(px + 0.5f, px + 1.5f);
+  const float2 PY = make_float2(py + 0.5f, py + 0.5f);
+  const uint2 rg = ranges[tile];
+  const int n = static_cast<int>(rg.y - rg.x);
+  const size_t plane = static_cast<size_t>(width) * height;
+  float T[2] = {1.f, 1.f}, S[2] = {0.f, 0.f}, bgg[2] = {0.f, 0.f};
+  float g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  uint32_t L[2] = {0u, 0u};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (k == 0 ? in0 : in1) {
+      const size_t pix = static_cast<size_t>(py) * width + px + k;
+      T[k] = Tfinal[pix];
+      L[k] = stoppos[pix];
+      g[k][0] = grad_rgb[pix];
+      g[k][1] = grad_rgb[plane + pix];
+      g[k][2] = grad_rgb[2 * plane + pix];
+      bgg[k] = T[k] * (bg0 * g[k][0] + bg1 * g[k][1] + bg2 * g[k][2]);  // (d out / d T_N) . g, times T_N
+    }
+  }
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  const uint32_t mine = L[0] > L[1] ? L[0] : L[1];
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+  if (lane == 0 && wmax) atomicMax(&s_max, wmax);
+  __syncthreads();
+  const int maxL = static_cast<int>(s_max);
+  const uint32_t wbit = 1u << warp;
+  for (int b0 = ((maxL - 1) / BS) * BS; maxL > 0 && b0 >= 0; b0 -= BS) {
+    const int idx = b0 + static_cast<int>(threadIdx.x);
+    __syncthreads();
+    if (idx < n) {
+      const uint32_t gid = vals[rg.x + idx];
+      sG[threadIdx.x] = gid;
+      stage_entry<TW, TH>(recA, recB, recC, gid, tx, ty, &sg[threadIdx.x]);
+    }
+    __syncthreads();
+    const int cnt = min(BS, n - b0);
+    for (int j0 = ((cnt - 1) / 32) * 32; j0 >= 0; j0 -= 32) {
+      const uint32_t m = (j0 + lane < cnt && b0 + j0 + lane < maxL) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
+      uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
+      const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
+      while (bits) {
+        const int jj = 31 - __clz(bits);
+        bits &= ~(1u << jj);
+        const uint32_t p = static_cast<uint32_t>(b0 + j0 + jj);
+        const StagedG& gs = sg[j0 + jj];
+        const PairEval ev = eval_pair(gs, PX, PY);
+        const bool clamp = (cbits >> jj) & 1u;
+        const float4 p1 = gs.p1, p2 = gs.p2, p3 = gs.p3, p4 = gs.p4;
+        const float araw[2] = {ev.araw.x, ev.araw.y};
+        const float ee[2] = {ev.e.x, ev.e.y};
+        const float dxs[2] = {ev.dx.x, ev.dx.y};
+        const bool vv[2] = {ev.v0, ev.v1};
+        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (p < L[k] && vv[k]) {
+            any = true;
+            const float alpha = clamp ? fminf(kAlphaMax, araw[k]) : araw[k];
+            const float om = 1.0f - alpha;
+            const float Ti = T[k] / om;
+            const float w = alpha * Ti;
+            v[6] += g[k][0] * w;
+            v[7] += g[k][1] * w;
+            v[8] += g[k][2] * w;
+            const float gc = g[k][0] * p3.x + g[k][1] * p3.z + g[k][2] * p4.x;
+            const float dalpha = gc * Ti - (S[k] + bgg[k]) / om;
+            S[k] += gc * w;
+            T[k] = Ti;
+            const float da = (clamp && araw[k] > kAlphaMax) ? 0.0f : dalpha;
+            // alpha = o 2^power'; d alpha / d power' = alpha ln 2
+            const float dpp = da * araw[k] * kLn2;
+            const float dx = dxs[k], dy = ev.dy.x;
+            v[5] += da * ee[k];                                  // d opacity_t
+            v[0] -= dpp * (2.0f * p1.x * dx + p1.z * dy);        // d mean2d.x
+            v[1] -= dpp * (p1.z * dx + 2.0f * p2.x * dy);        // d mean2d.y
+            v[2] += dpp * dx * dx;                               // d A'
+            v[3] += dpp * dx * dy;                               // d B'
+            v[4] += dpp * dy * dy;                               // d C'
+          }
+        }
+        if (__any_sync(0xffffffffu, any)) {
+          // transpose reduction: values 0..7 end one per group of 4 lanes
+          {
+            const bool up = lane & 16;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float send = up ? v[k] : v[k + 4];
+              const float keep = up ? v[k + 4] : v[k];
+              v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+          }
+          {
+            const bool up = lane & 8;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const float send = up ? v[k] : v[k + 2];
+              const float keep = up ? v[k + 2] : v[k];
+              v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+          }
+          {
+            const bool up = lane & 4;
+            const float send = up ? v[0] : v[1];
+            const float keep = up ? v[1] : v[0];
+            v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+          }
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v[8] += __shfl_xor_sync(0xffffffffu, v[8], o);
+          float* dst = rgrad + static_cast<size_t>(sG[j0 + jj]) * 12;
+          if ((lane & 3) == 0) {
+            const int id = lane >> 2;  // value index 0..7
+            // A', B', C' -> conic a, b, c: A' = -L a / 2, B' = -L b, C' = -L c / 2
+            const float scale = (id == 2 || id == 4) ? -0.5f * kLog2e : (id == 3 ? -kLog2e : 1.0f);
+            atomicAdd(dst + (id < 6 ? id : id + 2), v[0] * scale);
+          }
+          if (lane == 1) atomicAdd(dst + 10, v[8]);
+        }
+      }
+    }
   }
 }
 
@@ -87,170 +390,27 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   const float4* recB = recA + L.n;
   const float4* recC = recB + L.n;
   const uint2* ranges = at<uint2>(frame, L.ranges);
-  // the frame always keeps T and the last position for the backward
+  // the frame always keeps T and the stop positions for the backward
   float* T = at<float>(frame, L.tfinal);
-  uint32_t* last = at<uint32_t>(frame, L.last);
+  uint32_t* stop = at<uint32_t>(frame, L.last);
   const size_t npix = static_cast<size_t>(L.width) * L.height;
-#define R4G_BLEND(TW_, TH_)                                                                   \
-  blend_fwd_kernel<TW_, TH_><<<L.ntiles, TW_ * TH_, 0, s>>>(ranges, vals, recA, recB, recC,   \
-                                                             L.width, L.height, L.tiles_x,    \
-                                                             bg[0], bg[1], bg[2], out_rgb, T, \
-                                                             last)
-  if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND(16, 16);
-  else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND(8, 8);
-  else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND(16, 32);
-  else return cudaErrorInvalidValue;
+#define R4G_BLEND(TW_, TH_, LAST_)                                                                \
+  blend_fwd_kernel<TW_, TH_, LAST_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                     \
+      ranges, vals, recA, recB, recC, L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], out_rgb, \
+      T, stop, out_last)
+  const bool lst = out_last != nullptr;
+  if (L.tile_w == 16 && L.tile_h == 16) {
+    if (lst) R4G_BLEND(16, 16, true); else R4G_BLEND(16, 16, false);
+  } else if (L.tile_w == 8 && L.tile_h == 8) {
+    if (lst) R4G_BLEND(8, 8, true); else R4G_BLEND(8, 8, false);
+  } else if (L.tile_w == 16 && L.tile_h == 32) {
+    if (lst) R4G_BLEND(16, 32, true); else R4G_BLEND(16, 32, false);
+  } else {
+    return cudaErrorInvalidValue;
+  }
 #undef R4G_BLEND
   if (out_T) cudaMemcpyAsync(out_T, T, npix * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  if (out_last)
-    cudaMemcpyAsync(out_last, last, npix * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError();
-}
-
-
-// Backward of the blend. Each pixel re-walks its list back to front from the
-// stored final transmittance T_N and last position: T_i = T_{i+1} / (1 - a_i),
-// the colour already accumulated behind i is carried along, and per-Gaussian
-// gradients (d mean2d, d conic, d opacity_t, d rgb) are summed over the warp
-// with a transpose reduction (14 shuffles for 9 values) before one atomic add
-// per value and warp. Decisions (cutoff, 1/255) are recomputed with the same
-// code as the forward so the composited set is identical.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH)
-    blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                     const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, int width, int height, int tiles_x,
-                     float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
-                     const uint32_t* __restrict__ lastpos, const float* __restrict__ grad_rgb,
-                     float* __restrict__ rgrad) {
-  constexpr int BS = TW * TH;
-  __shared__ float4 sA[BS];
-  __shared__ float4 sB[BS];
-  __shared__ float4 sC[BS];
-  __shared__ uint32_t sG[BS];
-  __shared__ uint32_t s_max;
-  const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int px = tx * TW + static_cast<int>(threadIdx.x) % TW;
-  const int py = ty * TH + static_cast<int>(threadIdx.x) / TW;
-  const bool inside = px < width && py < height;
-  const float fx = px + 0.5f, fy = py + 0.5f;
-  const int lane = threadIdx.x & 31;
-  const uint2 rg = ranges[tile];
-  const int n = static_cast<int>(rg.y - rg.x);
-  float T = 1.0f, Tf = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  uint32_t L = 0;
-  if (inside) {
-    const size_t pix = static_cast<size_t>(py) * width + px;
-    const size_t plane = static_cast<size_t>(width) * height;
-    T = Tfinal[pix];
-    Tf = T;
-    L = lastpos[pix];
-    g0 = grad_rgb[pix];
-    g1 = grad_rgb[plane + pix];
-    g2 = grad_rgb[2 * plane + pix];
-  }
-  const float bgg = Tf * (bg0 * g0 + bg1 * g1 + bg2 * g2);  // d out / d(T_final) . g
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, L);
-  if (lane == 0 && wmax) atomicMax(&s_max, wmax);
-  __syncthreads();
-  const int maxL = static_cast<int>(s_max);
-  float S = 0.0f;  // sum over Gaussians behind i of g . c_k a_k T_k
-  for (int b0 = ((maxL - 1) / BS) * BS; maxL > 0 && b0 >= 0; b0 -= BS) {
-    const int idx = b0 + static_cast<int>(threadIdx.x);
-    __syncthreads();
-    if (idx < n) {
-      const uint32_t gid = vals[rg.x + idx];
-      sG[threadIdx.x] = gid;
-      sA[threadIdx.x] = recA[gid];
-      sB[threadIdx.x] = recB[gid];
-      sC[threadIdx.x] = recC[gid];
-    }
-    __syncthreads();
-    const int cnt = min(BS, n - b0);
-    for (int j = cnt - 1; j >= 0; --j) {
-      const int p = b0 + j;
-      float v[9];
-      bool contrib = false;
-      if (p < static_cast<int>(L)) {
-        const float4 A = sA[j];
-        const float4 B = sB[j];
-        float dx, dy;
-        const float power = gauss_power(A, B.x, fx, fy, dx, dy);
-        if (!(power > 0.0f || power < kPowerCut)) {
-          const float e = __expf(power);
-          const float araw = __fmul_rn(B.y, e);
-          const float alpha = fminf(kAlphaMax, araw);
-          if (!(alpha < kAlphaMin)) {
-            contrib = true;
-            const float4 Cc = sC[j];
-            const float om = 1.0f - alpha;
-            const float Ti = T / om;
-            const float w = alpha * Ti;
-            v[6] = g0 * w;
-            v[7] = g1 * w;
-            v[8] = g2 * w;
-            const float gc = g0 * Cc.x + g1 * Cc.y + g2 * Cc.z;
-            const float dalpha = gc * Ti - (S + bgg) / om;
-            S += gc * w;
-            T = Ti;
-            const float da = (araw > kAlphaMax) ? 0.0f : dalpha;
-            const float dpow = da * araw;
-            v[5] = da * e;  // d opacity_t
-            v[2] = -0.5f * dpow * dx * dx;
-            v[3] = -dpow * dx * dy;
-            v[4] = -0.5f * dpow * dy * dy;
-            v[0] = dpow * (A.z * dx + A.w * dy);
-            v[1] = dpow * (A.w * dx + B.x * dy);
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-        if (!contrib) {
-#pragma unroll
-          for (int k = 0; k < 9; ++k) v[k] = 0.0f;
-        }
-        // transpose reduction: values 0..7 end one per group of 4 lanes
-        {
-          const bool up = lane & 16;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float send = up ? v[k] : v[k + 4];
-            const float keep = up ? v[k + 4] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-          }
-        }
-        {
-          const bool up = lane & 8;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const float send = up ? v[k] : v[k + 2];
-            const float keep = up ? v[k + 2] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-          }
-        }
-        {
-          const bool up = lane & 4;
-          const float send = up ? v[0] : v[1];
-          const float keep = up ? v[1] : v[0];
-          v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[8] += __shfl_xor_sync(0xffffffffu, v[8], o);
-        const uint32_t gid = sG[j];
-        float* dst = rgrad + static_cast<size_t>(gid) * 12;
-        if ((lane & 3) == 0) {
-          const int id = lane >> 2;  // value index 0..7
-          atomicAdd(dst + (id < 6 ? id : id + 2), v[0]);
-        }
-        if (lane == 1) atomicAdd(dst + 10, v[8]);
-      }
-    }
-  }
 }
 
 cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* vals,
@@ -260,13 +420,12 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   const float4* recC = recB + L.n;
   const uint2* ranges = at<uint2>(frame, L.ranges);
   const float* T = at<float>(frame, L.tfinal);
-  const uint32_t* last = at<uint32_t>(frame, L.last);
+  const uint32_t* stop = at<uint32_t>(frame, L.last);
   float* rgrad = at<float>(frame, L.recgrad);
-#define R4G_BLEND_BWD(TW_, TH_)                                                               \
-  blend_bwd_kernel<TW_, TH_><<<L.ntiles, TW_ * TH_, 0, s>>>(ranges, vals, recA, recB, recC,   \
-                                                             L.width, L.height, L.tiles_x,    \
-                                                             bg[0], bg[1], bg[2], T, last,    \
-                                                             grad_rgb, rgrad)
+#define R4G_BLEND_BWD(TW_, TH_)                                                                   \
+  blend_bwd_kernel<TW_, TH_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                            \
+      ranges, vals, recA, recB, recC, L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], T, stop, \
+      grad_rgb, rgrad)
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16);
   else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8);
   else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND_BWD(16, 32);

@@ -1,0 +1,276 @@
+// Single-kernel-per-pass stable LSD radix sort of (uint32 key, uint32 value)
+// pairs for the render's two sorts (Gaussian depth keys, tile ids), after the
+// "Onesweep" scheme: one histogram kernel counts the digits of every pass at
+// once; each pass is then a single kernel in which a CTA
+//   1. takes the next tile of 2048 items from an atomic ticket (so every tile
+//      before it belongs to a CTA that is already running),
+//   2. ranks its items stably by the pass's digit (warp match + per-warp
+//      histograms), publishes its per-digit counts,
+//   3. looks back over the tiles before it, summing their published counts
+//      until it meets a tile that has published its inclusive prefix, and
+//      publishes its own prefix,
+//   4. scatters its items, staged in shared memory in digit order, to
+//      digit start + prefix + local rank.
+// The look-back only waits on tiles that publish their counts before they
+// wait themselves; each wait is bounded by an iteration limit after which the
+// CTA sets an error bit in the frame header, treats the tile as empty and
+// carries on (the image is then wrong and the status reports it, but nothing
+// hangs). Counts and values are limited to 2^30.
+#include <cuda_runtime.h>
+
+#include "r4g_internal.cuh"
+
+namespace r4g {
+
+constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
+constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix published
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void store_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Digit histograms of every pass: hist[p * 256 + d] for digits of bits
+// [8 p, 8 p + 8) of the keys, limited to `bits` bits in total.
+__global__ void __launch_bounds__(kSortThreads)
+    onesweep_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
+                         int passes, int bits, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_h[4][kSortRadix];
+  for (int k = threadIdx.x; k < 4 * kSortRadix; k += kSortThreads) (&s_h[0][0])[k] = 0;
+  __syncthreads();
+  const uint32_t n = count_dev ? *count_dev : count_host;
+  const int lane = threadIdx.x & 31;
+  constexpr int ILP = 8;
+  // eight independent loads in flight per thread before any is used
+  for (uint32_t base = blockIdx.x * kSortThreads * ILP; base < n; base += gridDim.x * kSortThreads * ILP) {
+    uint32_t key[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const uint32_t i = base + u * kSortThreads + threadIdx.x;
+      key[u] = i < n ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const bool ok = base + u * kSortThreads + threadIdx.x < n;
+      const uint32_t act = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        for (int p = 0; p < passes; ++p) {
+          const int sh = p * kSortRadixBits;
+          const int nb = min(kSortRadixBits, bits - sh);
+          const uint32_t d = (key[u] >> sh) & ((1u << nb) - 1u);
+          const uint32_t peers = __match_any_sync(act, d);
+          if (lane == __ffs(peers) - 1) atomicAdd(&s_h[p][d], __popc(peers));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p)
+    for (int d = threadIdx.x; d < kSortRadix; d += kSortThreads) {
+      const uint32_t c = s_h[p][d];
+      if (c) atomicAdd(&hist[p * kSortRadix + d], c);
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+    onesweep_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* count_dev,
+                         uint32_t count_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
+                         uint32_t* status, uint32_t* ticket, uint32_t* err) {
+  constexpr int NW = kSortThreads / 32;
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_dstart[kSortRadix];   // global start of each digit + tile prefix
+  __shared__ uint32_t s_tstart[kSortRadix];   // tile-local start of each digit
+  __shared__ uint32_t s_tcount[kSortRadix];
+  __shared__ uint32_t s_whist[NW][kSortRadix];
+  __shared__ uint32_t s_scan[NW];
+  __shared__ uint32_t s_k[kSortTile];
+  __shared__ uint32_t s_v[kSortTile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int k = threadIdx.x; k < NW * kSortRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t n = count_dev ? *count_dev : count_host;
+  const uint64_t tb64 = static_cast<uint64_t>(t) * kSortTile;
+  if (tb64 >= n) return;  // grid sized for the capacity; CTA-uniform exit
+  const uint32_t tb = static_cast<uint32_t>(tb64);
+  const uint32_t tn = min(static_cast<uint32_t>(kSortTile), n - tb);
+
+  // ---- load and rank the tile (stable: warp w holds items [w*256, w*256+256))
+  uint32_t k[kSortIPT], v[kSortIPT], d[kSortIPT], rk[kSortIPT];
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    const uint32_t li = warp * (32 * kSortIPT) + j * 32 + lane;
+    if (li < tn) {
+      k[j] = kin[tb + li];
+      v[j] = vin ? vin[tb + li] : tb + li;
+      d[j] = (k[j] >> shift) & mask;
+    } else {
+      k[j] = 0;
+      v[j] = 0;
+      d[j] = 0xffffffffu;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    const bool ok = d[j] != 0xffffffffu;
+    const uint32_t act = __ballot_sync(0xffffffffu, ok);
+    rk[j] = 0;
+    if (ok) {
+      const uint32_t peers = __match_any_sync(act, d[j]);
+      const uint32_t base = s_whist[warp][d[j]];
+      __syncwarp(act);
+      if (lane == __ffs(peers) - 1) s_whist[warp][d[j]] = base + __popc(peers);
+      rk[j] = base + __popc(peers & lt_mask);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit (thread = digit): exclusive over warps, tile count
+  const int dd = threadIdx.x;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t c = s_whist[w][dd];
+    s_whist[w][dd] = cnt;
+    cnt += c;
+  }
+  s_tcount[dd] = cnt;
+  // ---- publish the tile's count, then look back for its exclusive prefix
+  uint32_t* st = status + static_cast<size_t>(t) * kSortRadix;
+  if (t == 0) {
+    store_relaxed(st + dd, kFlagPrefix | cnt);
+  } else {
+    store_relaxed(st + dd, kFlagAgg | cnt);
+  }
+  // Look-back, eight predecessors per round (their statuses are read in
+  // parallel): add published counts newest first until a published prefix;
+  // a round that makes no progress counts against the spin limit.
+  uint32_t excl = 0;
+  if (t > 0) {
+    constexpr int WIN = 8;
+    int64_t kt = static_cast<int64_t>(t) - 1;
+    uint32_t idle = 0;
+    bool found = false;
+    while (!found && kt >= 0) {
+      uint32_t sv[WIN];
+#pragma unroll
+      for (int w = 0; w < WIN; ++w)
+        sv[w] = (kt - w >= 0) ? load_volatile(status + static_cast<size_t>(kt - w) * kSortRadix + dd) : kFlagPrefix;
+      int used = 0;
+#pragma unroll
+      for (int w = 0; w < WIN; ++w) {
+        if (found || used < w) continue;           // stopped earlier in this window
+        if ((sv[w] & ~kValMask) == 0u) continue;   // not ready: retry from here
+        if (kt - w >= 0) excl += sv[w] & kValMask;
+        ++used;
+        if (sv[w] & kFlagPrefix) found = true;
+      }
+      kt -= used;
+      if (used == 0 && ++idle >= kSpinLimit) {  // gave up: record it and go on
+        atomicOr(err, 2u);
+        break;
+      }
+    }
+    store_relaxed(st + dd, kFlagPrefix | (excl + cnt));
+  }
+  // global digit start: exclusive scan of this pass's histogram (+ tile prefix)
+  {
+    const uint32_t h = hist[dd];
+    uint32_t x = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_scan[w];
+    s_dstart[dd] = pre + x - h + excl;
+    __syncthreads();
+    // tile-local digit starts: exclusive scan of the tile counts
+    x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    pre = 0;
+    for (int w = 0; w < warp; ++w) pre += s_scan[w];
+    s_tstart[dd] = pre + x - cnt;
+  }
+  __syncthreads();
+  // ---- stage in digit order, then write each digit's run contiguously
+#pragma unroll
+  for (int j = 0; j < kSortIPT; ++j) {
+    if (d[j] != 0xffffffffu) {
+      const uint32_t pos = s_tstart[d[j]] + s_whist[warp][d[j]] + rk[j];
+      s_k[pos] = k[j];
+      s_v[pos] = v[j];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < tn; i += kSortThreads) {
+    const uint32_t key = s_k[i];
+    const uint32_t dg = (key >> shift) & mask;
+    const uint32_t o = s_dstart[dg] + i - s_tstart[dg];
+    kout[o] = key;
+    vout[o] = s_v[i];
+  }
+}
+
+size_t onesweep_scratch_bytes(int64_t cap, int bits) {
+  const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+  const int64_t tiles = (cap + kSortTile - 1) / kSortTile;
+  return sizeof(uint32_t) * (static_cast<size_t>(passes) * kSortRadix       // histograms
+                             + 32                                           // tickets
+                             + static_cast<size_t>(passes) * tiles * kSortRadix);  // status
+}
+
+cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
+                            uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
+                            int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
+                            int* result_in_buf) {
+  const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+  *result_in_buf = 0;
+  if (passes == 0 || cap == 0) return cudaSuccess;
+  const int64_t tiles = (cap + kSortTile - 1) / kSortTile;
+  uint32_t* hist = static_cast<uint32_t*>(scratch);
+  uint32_t* tickets = hist + passes * kSortRadix;
+  uint32_t* status = tickets + 32;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, onesweep_scratch_bytes(cap, bits), s);
+  if (e != cudaSuccess) return e;
+  const int hist_ctas = static_cast<int>(tiles < 2 * 152 ? tiles : 2 * 152);
+  onesweep_hist_kernel<<<hist_ctas, kSortThreads, 0, s>>>(kin, count_dev, count_host, passes, bits, hist);
+  const uint32_t* ki = kin;
+  const uint32_t* vi = vin;
+  int which = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * kSortRadixBits;
+    const int nb = min(kSortRadixBits, bits - shift);
+    uint32_t* ko = (which == 1) ? kbuf2 : kbuf1;
+    uint32_t* vo = (which == 1) ? vbuf2 : vbuf1;
+    onesweep_pass_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
+        ki, vi, ko, vo, count_dev, count_host, shift, (1u << nb) - 1u, hist + p * kSortRadix,
+        status + static_cast<size_t>(p) * tiles * kSortRadix, tickets + p, err);
+    ki = ko;
+    vi = vo;
+    which = (which == 1) ? 2 : 1;
+  }
+  *result_in_buf = which;
+  return cudaGetLastError();
+}
+
+}  // namespace r4g

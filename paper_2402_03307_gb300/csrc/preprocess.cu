@@ -17,6 +17,7 @@ struct PreOut {
   float4* recC;  // (r, g, b, 0)
   uint2* rect;   // tile rect: (x0 | y0 << 16, x1 | y1 << 16), [x0, x1) x [y0, y1)
   uint32_t* touched;
+  uint32_t* dkey;  // float bits of the depth for Gaussians with tiles, else 0xffffffff
   uint32_t* blocksum;
   FrameHeader* header;
   int tile_w, tile_h, tiles_x, tiles_y;
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(kPreBlock)
       out.rect[i] = make_uint2(0u, 0u);
     }
     out.touched[i] = ntiles;
+    out.dkey[i] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
   }
   // per-block totals of the tile counts and of the visible Gaussians
   __shared__ uint32_t s_sum[kPreBlock / 32], s_vis[kPreBlock / 32];
@@ -268,6 +270,7 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, flo
   o.recC = o.recB + L.n;
   o.rect = at<uint2>(frame, L.rect);
   o.touched = at<uint32_t>(frame, L.touched);
+  o.dkey = at<uint32_t>(frame, L.dkey0);
   o.blocksum = at<uint32_t>(frame, L.blocksum);
   o.header = at<FrameHeader>(frame, L.header);
   o.tile_w = L.tile_w; o.tile_h = L.tile_h; o.tiles_x = L.tiles_x; o.tiles_y = L.tiles_y;

@@ -31,7 +31,7 @@ struct CamDev {
 
 // Frame header at the start of every frame buffer (device memory).
 struct FrameHeader {
-  uint32_t status;        // bit 0: key overflow
+  uint32_t status;        // bit 0: key overflow, bit 1: a sort look-back gave up waiting
   uint32_t key_count;     // pairs actually written (min(needed, capacity))
   uint32_t key_needed;    // pairs the render needed
   uint32_t n_visible;
@@ -40,13 +40,16 @@ struct FrameHeader {
 
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
-  size_t header, rec, rect, touched, blocksum, keys0, vals0, keys1, vals1,
-      ranges, tfinal, last, sortcnt, recgrad, total;
+  size_t header, rec, rect, touched, dkey0, dkey1, ord0, ord1, offs, srect, blocksum, keys0, vals0, keys1, vals1,
+      ranges, tfinal, last, sortcnt, onesweep, recgrad, total;
   int64_t n, cap;
   int width, height, tile_w, tile_h, tiles_x, tiles_y, ntiles;
   int nblocks;       // preprocess blocks (kPreBlock Gaussians each)
-  int sort_ctas;     // CTAs of each radix pass
-  int sort_bits;     // key bits to sort: 32 + ceil(log2(ntiles))
+  int sort_ctas;     // CTAs of each radix pass over the keys
+  int depth_ctas;    // CTAs of each radix pass over the N depth keys
+  int tile_bits;     // ceil(log2(ntiles)): bits of the tile sort
+  bool order_in_1;   // the depth order ends in ord1 (else ord0)
+  bool keys_in_1;    // the tile-sorted values end in vals1 (else vals0)
 };
 
 constexpr int kPreBlock = 256;     // Gaussians per preprocess / key-build block
@@ -55,6 +58,7 @@ constexpr int kSortIPT = 8;        // items per thread per tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
 constexpr int kSortRadixBits = 8;
 constexpr int kSortRadix = 1 << kSortRadixBits;
+constexpr int kSortMaxCtas = 2 * 152;  // two CTAs per SM of a GB300; a multiple of 16
 
 int sort_ctas_for(int64_t cap);
 // Sets the message r4g_last_error(NULL) returns on this host thread.
@@ -83,14 +87,29 @@ inline T* at(void* base, size_t off) {
 cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, float t,
                                   const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, cudaStream_t s);
-cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s);
+// scan of the tile counts in depth order and key emission (tile key, index)
+cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s);
 cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf1,
                         uint32_t* vbuf1, uint64_t* kbuf2, uint32_t* vbuf2,
                         const uint32_t* count_dev, uint32_t count_host, int64_t cap,
                         int begin_bit, int end_bit, uint32_t* counts, int ctas,
                         cudaStream_t s, int* result_in_buf);
-cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint64_t* keys,
+cudaError_t launch_sort_u32(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
+                            uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
+                            int begin_bit, int end_bit, uint32_t* counts, int ctas, cudaStream_t s,
+                            int* result_in_buf);
+// One-kernel-per-pass radix sort of (uint32 key, uint32 value) on key bits
+// [0, bits) (see onesweep.cu); scratch holds onesweep_scratch_bytes(cap, bits).
+size_t onesweep_scratch_bytes(int64_t cap, int bits);
+cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
+                            uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
+                            int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
+                            int* result_in_buf);
+cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                           cudaStream_t s);
+// 64-bit (tile << 32 | depth bits) keys of the sorted list, for export
+cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
+                               const uint32_t* vals, uint64_t* out, cudaStream_t s);
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, float* out_rgb, float* out_T,
                              uint32_t* out_last, cudaStream_t s);

@@ -34,7 +34,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t al(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr int64_t kMaxPairs = R4G_SORT_NOALLOC_MAX_PAIRS;
-constexpr int kMaxCtas = 2 * 152;  // upper bound of sort_ctas_for()
+constexpr int kMaxCtas = kSortMaxCtas;  // upper bound of sort_ctas_for()
 constexpr size_t kKeysOff = 0;
 constexpr size_t kValsOff = al(sizeof(uint64_t) * kMaxPairs);
 constexpr size_t kCntOff = kValsOff + al(sizeof(uint32_t) * kMaxPairs);
