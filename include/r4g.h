@@ -161,7 +161,8 @@ r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
  * out_T [height, width] (final transmittance) and out_last [height, width]
  * (1 + position in the tile's sorted list of the last composited Gaussian,
  * 0 when none). The frame must be at least r4g_frame_bytes(n, width, height,
- * key_capacity) bytes. */
+ * key_capacity) bytes. An image may have at most 51,200 tiles (e.g. 3840x2160
+ * with 16x16 tiles); larger ones return R4G_EINVAL. */
 r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam, float t,
                       float* out_rgb, float* out_T, uint32_t* out_last,
                       void* frame, size_t frame_bytes, int64_t key_capacity, void* stream);

@@ -165,12 +165,14 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
   L.rec = o;      o = align_up(o + 3 * sizeof(float4) * n);
   L.rect = o;     o = align_up(o + sizeof(uint2) * n);
   L.touched = o;  o = align_up(o + sizeof(uint32_t) * n);
+  L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * (L.tiles_x + 1) * (L.tiles_y + 1));
   L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * n);
   L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * n);
   L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * n);
   L.ord1 = o;     o = align_up(o + sizeof(uint32_t) * n);
   L.offs = o;     o = align_up(o + sizeof(uint32_t) * (n + 1));
   L.srect = o;    o = align_up(o + sizeof(uint2) * n);
+  L.chunks = o;   o = align_up(o + sizeof(uint32_t) * ((cap + 2047) / 2048 + 1));
   L.blocksum = o; o = align_up(o + sizeof(uint32_t) * (L.nblocks + 1));
   L.keys0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.vals0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
@@ -344,10 +346,13 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
   if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(ctx, R4G_EINVAL, "key_capacity out of range (< 2^30)");
   if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
   const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
+  if (L.ntiles > kMaxTiles) return fail(ctx, R4G_EINVAL, "too many tiles (> 51200) for this image and tile shape");
   if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const CamDev cd = make_cam(*cam);
   cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, sizeof(uint32_t) * (L.tiles_x + 1) * (L.tiles_y + 1), s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const bool has = L.n > 0;
   const int dpasses = 32 / kSortRadixBits;
@@ -373,20 +378,21 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
     if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
   }
   const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
+  {
+    // per-tile counts -> tile ranges and the tile sort's digit histograms
+    StageScope sc(ctx, R4G_STAGE_RANGES, s, 1);
+    if ((e = launch_tile_counts(L, frame, at<uint32_t>(frame, L.onesweep), tpasses, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "tile counts");
+  }
   if (has && tpasses > 0) {
     // stable sort of the depth-ordered pairs by tile id
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + tpasses);
+    StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
     e = launch_onesweep(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint32_t>(frame, L.keys1),
                         at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which);
+                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
   }
-  const uint32_t* tkeys = sorted_tile_keys(L, frame);
   const uint32_t* vals = sorted_vals(L, frame);
-  {
-    StageScope sc(ctx, R4G_STAGE_RANGES, s, has ? 1 : 0);
-    if ((e = launch_ranges(L, frame, tkeys, s)) != cudaSuccess) return cuda_fail(ctx, e, "ranges");
-  }
   {
     StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
     if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last, s)) != cudaSuccess)

@@ -15,6 +15,7 @@
 namespace r4g {
 
 constexpr int kScanThreads = 1024;
+constexpr int kTileCountsMaxSmem = kMaxTiles * 4;
 
 // blocksum[b] = sum of touched[order[j]] over the block's depth positions.
 __global__ void __launch_bounds__(kPreBlock)
@@ -82,10 +83,13 @@ __global__ void __launch_bounds__(kScanThreads)
 // Exclusive offset of every Gaussian's first pair, in depth order, and its
 // tile rectangle gathered into depth order (same blocking as
 // depth_blocksum_kernel; blockoff holds the scanned block totals).
+constexpr int kEmitChunk = 2048;
+
 __global__ void __launch_bounds__(kPreBlock)
     depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
                          const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect, int n,
-                         uint32_t* __restrict__ offs, uint2* __restrict__ srect) {
+                         uint32_t* __restrict__ offs, uint2* __restrict__ srect,
+                         uint32_t* __restrict__ chunk_start, uint32_t nchunks) {
   __shared__ uint32_t s_warp[kPreBlock / 32];
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -102,8 +106,12 @@ __global__ void __launch_bounds__(kPreBlock)
   uint32_t base = blockoff[blockIdx.x];
   for (int w = 0; w < warp; ++w) base += s_warp[w];
   if (j < n) {
-    offs[j] = base + x - cnt;
+    const uint32_t o = base + x - cnt;
+    offs[j] = o;
     srect[j] = cnt ? rect[g] : make_uint2(0u, 0u);
+    // this Gaussian owns the first pair of every emission chunk starting in [o, o + cnt)
+    for (uint32_t c = (o + kEmitChunk - 1) / kEmitChunk; cnt && c * kEmitChunk < o + cnt && c < nchunks; ++c)
+      chunk_start[c] = static_cast<uint32_t>(j);
   }
 }
 
@@ -113,29 +121,17 @@ __global__ void __launch_bounds__(kPreBlock)
 // their offsets increase strictly and a chunk of E pairs involves at most
 // E + 1 of them: their offsets are loaded into shared memory and each pair
 // finds its Gaussian by binary search there. Pair q of Gaussian j covers tile
-// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j].
-constexpr int kEmitChunk = 2048;
+// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j]. The
+// Gaussian holding the chunk's first pair comes from depth_offsets_kernel.
 __global__ void __launch_bounds__(kPreBlock)
     emit_kernel(const uint32_t* __restrict__ offs, const uint2* __restrict__ srect,
-                const uint32_t* __restrict__ order, int n, int tiles_x, const FrameHeader* hdr,
-                uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
+                const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
+                int tiles_x, const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
-  __shared__ uint32_t s_jlo;
   const uint32_t K = hdr->key_count;
   const uint32_t q0 = blockIdx.x * kEmitChunk;
   if (q0 >= K) return;  // CTA-uniform: the grid is sized for the capacity
-  if (threadIdx.x == 0) {
-    // last j with offs[j] <= q0
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (offs[mid] <= q0) lo = mid;
-      else hi = mid - 1;
-    }
-    s_jlo = static_cast<uint32_t>(lo);
-  }
-  __syncthreads();
-  const int jlo = static_cast<int>(s_jlo);
+  const int jlo = static_cast<int>(chunk_start[blockIdx.x]);
   const int m = min(kEmitChunk + 1, n - jlo);  // window of Gaussians
   for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
   __syncthreads();
@@ -156,6 +152,86 @@ __global__ void __launch_bounds__(kPreBlock)
     tkeys[q] = ty * static_cast<uint32_t>(tiles_x) + tx;
     vals[q] = order[j];
   }
+}
+
+// Per-tile pair counts from the 2D difference array the preprocess filled
+// (prefix sums along x, then along y, in shared memory with warp scans), their
+// exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
+// list, and the digit histograms of the tile sort's radix passes. One CTA;
+// the difference array is copied into dynamic shared memory.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(1024)
+    tile_counts_kernel(const uint32_t* __restrict__ tdiff, int tiles_x, int tiles_y, uint32_t cap,
+                       const FrameHeader* hdr, uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
+                       int passes) {
+  extern __shared__ uint32_t s_c[];  // tiles_y x tiles_x counts
+  __shared__ uint32_t s_h[4][kSortRadix];
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const int st = tiles_x + 1;
+  const int ntiles = tiles_x * tiles_y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int k = threadIdx.x; k < 4 * kSortRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_c[t] = tdiff[(t / tiles_x) * st + (t % tiles_x)];
+  __syncthreads();
+  for (int y = warp; y < tiles_y; y += nwarp) {  // each warp: running sums along its rows
+    uint32_t carry = 0;
+    for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+      const int x = x0 + lane;
+      const uint32_t v = x < tiles_x ? s_c[y * tiles_x + x] : 0u;
+      const uint32_t inc = warp_incl_scan(v, lane) + carry;
+      if (x < tiles_x) s_c[y * tiles_x + x] = inc;
+      carry = __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  __syncthreads();
+  for (int x = warp; x < tiles_x; x += nwarp) {  // each warp: running sums down its columns
+    uint32_t carry = 0;
+    for (int y0 = 0; y0 < tiles_y; y0 += 32) {
+      const int y = y0 + lane;
+      const uint32_t v = y < tiles_y ? s_c[y * tiles_x + x] : 0u;
+      const uint32_t inc = warp_incl_scan(v, lane) + carry;
+      if (y < tiles_y) s_c[y * tiles_x + x] = inc;
+      carry = __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  // after a key-capacity overflow the list is incomplete: every tile gets an
+  // empty range so nothing downstream reads it (the frame reports the overflow)
+  const bool overflow = hdr->key_needed > cap;
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const uint32_t c = t < ntiles ? s_c[t] : 0u;
+    const uint32_t x = warp_incl_scan(c, lane);
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = warp_incl_scan(lane < nwarp ? s_warp[lane] : 0u, lane);
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t start = s_carry + (warp ? s_warp[warp - 1] : 0u) + x - c;
+    if (t < ntiles) {
+      ranges[t] = overflow ? make_uint2(0u, 0u) : make_uint2(start, start + c);
+      if (c) {
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(t >> (8 * p)) & 0xff], c);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = start + c;
+    __syncthreads();
+  }
+  for (int p = 0; p < passes; ++p)
+    for (int d = threadIdx.x; d < kSortRadix; d += blockDim.x) hist[p * kSortRadix + d] = s_h[p][d];
 }
 
 // ranges[tile] = [first, last+1) of the tile's entries in the sorted list;
@@ -182,11 +258,13 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const FrameHead
 }
 
 __global__ void export_keys_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                                   const float4* __restrict__ recB, const FrameHeader* hdr,
+                                   const float4* __restrict__ recB, const FrameHeader* hdr, uint32_t ng,
                                    uint64_t* __restrict__ out) {
   const uint32_t n = hdr->key_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    out[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | __float_as_uint(recB[vals[i]].z);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = vals[i];  // out of range only in an overflowed (invalid) frame
+    out[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | (g < ng ? __float_as_uint(recB[g].z) : 0u);
+  }
 }
 
 cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s) {
@@ -197,14 +275,27 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   const int n = static_cast<int>(L.n);
   uint32_t* offs = at<uint32_t>(frame, L.offs);
   uint2* srect = at<uint2>(frame, L.srect);
+  uint32_t* cstart = at<uint32_t>(frame, L.chunks);
+  const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
   depth_blocksum_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, n, bs);
   scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
-  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect), n, offs, srect);
-  const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
+  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect), n, offs,
+                                                        srect, cstart, static_cast<uint32_t>(chunks));
   if (chunks > 0)
-    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, n, L.tiles_x, hdr,
+    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, cstart, n, L.tiles_x, hdr,
                                                                      at<uint32_t>(frame, L.keys0),
                                                                      at<uint32_t>(frame, L.vals0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s) {
+  const size_t smem = sizeof(uint32_t) * static_cast<size_t>(L.ntiles);
+  if (smem > kTileCountsMaxSmem) return cudaErrorInvalidValue;
+  // opt in to large dynamic shared memory (a per-device function attribute)
+  cudaFuncSetAttribute(tile_counts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileCountsMaxSmem);
+  tile_counts_kernel<<<1, 1024, smem, s>>>(at<uint32_t>(frame, L.tdiff), L.tiles_x, L.tiles_y,
+                                        static_cast<uint32_t>(L.cap), at<FrameHeader>(frame, L.header),
+                                        at<uint2>(frame, L.ranges), hist, passes);
   return cudaGetLastError();
 }
 
@@ -220,7 +311,8 @@ cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t
                                const uint32_t* vals, uint64_t* out, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
   const float4* recB = at<float4>(frame, L.rec) + L.n;
-  export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, recB, at<FrameHeader>(frame, L.header), out);
+  export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, recB, at<FrameHeader>(frame, L.header),
+                                             static_cast<uint32_t>(L.n), out);
   return cudaGetLastError();
 }
 

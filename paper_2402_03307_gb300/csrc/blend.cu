@@ -49,13 +49,14 @@ struct Blend {
   static_assert(NT % 32 == 0 && 32 % PCOLS == 0 && NW <= 16, "tile shape");
 };
 
-// A staged Gaussian (96 bytes), operands duplicated for the packed pairs:
+// A staged Gaussian (128-byte slot), operands duplicated for the packed pairs:
 //   p0 = (-mx, -mx, -my, -my)     p1 = (A', A', B', B')
 //   p2 = (C', C', o, o)           p3 = (r, r, g, g)
 //   p4 = (b, b, ih, ih)           p5 = (nm, nm, mask bits, 0)
 // with power' = A' dx^2 + B' dx dy + C' dy^2, ih = 1 / half, nm = -mid / half.
-struct __align__(16) StagedG {
+struct __align__(128) StagedG {
   float4 p0, p1, p2, p3, p4, p5;
+  float4 pad0, pad1;  // 128-byte stride: the entry address is a shift
 };
 
 // Can the Gaussian's contributing region {q <= min(9, 2 ln(255 o))}, q = d^T conic d,
@@ -89,9 +90,13 @@ __device__ __forceinline__ bool ellipse_meets_rect(const float4 A, float c, floa
 // Stage one batch entry: record -> shared memory, plus the warp-block bits.
 template <int TW, int TH>
 __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, const float4* __restrict__ recB,
-                                            const float4* __restrict__ recC, uint32_t gid, int tx, int ty,
-                                            StagedG* sg) {
+                                            const float4* __restrict__ recC, uint32_t gid, uint32_t ng, int tx,
+                                            int ty, StagedG* sg) {
   using B = Blend<TW, TH>;
+  if (gid >= ng) {  // defensive: an entry that reaches no pixel
+    sg->p5 = make_float4(0.0f, 0.0f, __uint_as_float(0u), 0.0f);
+    return;
+  }
   const float4 A = recA[gid], Bv = recB[gid], C = recC[gid];
   const float Ap = -0.5f * kLog2e * A.z, Bp = -kLog2e * A.w, Cp = -0.5f * kLog2e * Bv.x, o = Bv.y;
   const float pmin = fmaxf(kCut2, -log2f(255.0f * o));
@@ -138,11 +143,53 @@ __device__ __forceinline__ PairEval eval_pair(const StagedG& g, float2 PX, float
   return r;
 }
 
+// Per-thread state of the forward walk over a tile list.
+struct FwdState {
+  float2 PX, T, cr, cg, cb;
+  uint32_t stop0, stop1, last0, last1;
+  bool done0, done1;
+};
+
+// One staged Gaussian composited into the thread's two pixels. kClamp: the
+// Gaussian's opacity_t exceeds 0.99 so alpha is clamped; kLast: track the
+// last composited position. Returns true when every pixel of the warp has
+// stopped.
+template <bool kClamp, bool kLast>
+__device__ __forceinline__ bool fwd_step(FwdState& S, const StagedG& g, float2 PY, uint32_t pos) {
+  const PairEval ev = eval_pair(g, S.PX, PY);
+  bool v0 = ev.v0, v1 = ev.v1;
+  float2 a = make_float2(v0 ? ev.araw.x : 0.0f, v1 ? ev.araw.y : 0.0f);
+  if constexpr (kClamp) a = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
+  float2 Tn = __ffma2_rn(make_float2(-S.T.x, -S.T.y), a, S.T);  // T (1 - alpha)
+  const bool st0 = Tn.x < kTMin, st1 = Tn.y < kTMin;            // only a taken Gaussian can stop
+  bool wdone = false;
+  if (__any_sync(0xffffffffu, st0 || st1)) {
+    // stop before this Gaussian: it is not composited; the pixel is done
+    if (st0) { a.x = 0.0f; Tn.x = S.T.x; S.PX.x = kFar; v0 = false; S.done0 = true; S.stop0 = pos; }
+    if (st1) { a.y = 0.0f; Tn.y = S.T.y; S.PX.y = kFar; v1 = false; S.done1 = true; S.stop1 = pos; }
+    wdone = __all_sync(0xffffffffu, S.done0 && S.done1);
+  }
+  const float4 p3 = g.p3, p4 = g.p4;
+  const float2 w = __fmul2_rn(a, S.T);
+  S.cr = __ffma2_rn(make_float2(p3.x, p3.y), w, S.cr);
+  S.cg = __ffma2_rn(make_float2(p3.z, p3.w), w, S.cg);
+  S.cb = __ffma2_rn(make_float2(p4.x, p4.y), w, S.cb);
+  S.T = Tn;
+  if constexpr (kLast) {
+    S.last0 = v0 ? pos + 1 : S.last0;
+    S.last1 = v1 ? pos + 1 : S.last1;
+  }
+  return wdone;
+}
+
+template <int TW, int TH>
+constexpr int fwd_min_blocks() { return Blend<TW, TH>::NT <= 128 ? 8 : 4; }
+
 template <int TW, int TH, bool kLast>
-__global__ void __launch_bounds__(Blend<TW, TH>::NT)
+__global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
     blend_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, int width, int height, int tiles_x,
+                     const float4* __restrict__ recC, uint32_t ng, int width, int height, int tiles_x,
                      float bg0, float bg1, float bg2, float* __restrict__ out_rgb,
                      float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
                      uint32_t* __restrict__ out_last) {
@@ -156,77 +203,67 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
   const bool in0 = px < width && py < height;
   const bool in1 = px + 1 < width && py < height;
-  float2 PX = make_float2(in0 ? px + 0.5f : kFar, in1 ? px + 1.5f : kFar);
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
-  float2 T = make_float2(1.0f, 1.0f);
-  float2 cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
-  uint32_t stop0 = static_cast<uint32_t>(n), stop1 = static_cast<uint32_t>(n);
-  uint32_t last0 = 0, last1 = 0;
-  bool done0 = !in0, done1 = !in1;
+  FwdState S;
+  S.PX = make_float2(in0 ? px + 0.5f : kFar, in1 ? px + 1.5f : kFar);
+  S.T = make_float2(1.0f, 1.0f);
+  S.cr = S.cg = S.cb = make_float2(0.f, 0.f);
+  S.stop0 = S.stop1 = static_cast<uint32_t>(n);
+  S.last0 = S.last1 = 0;
+  S.done0 = !in0;
+  S.done1 = !in1;
   const uint32_t wbit = 1u << warp;
   for (int b = 0; b < n; b += BS) {
-    if (__syncthreads_count(done0 && done1) == BS) break;
+    if (__syncthreads_count(S.done0 && S.done1) == BS) break;
     const int idx = b + static_cast<int>(threadIdx.x);
-    if (idx < n) stage_entry<TW, TH>(recA, recB, recC, vals[rg.x + idx], tx, ty, &sg[threadIdx.x]);
+    if (idx < n) stage_entry<TW, TH>(recA, recB, recC, vals[rg.x + idx], ng, tx, ty, &sg[threadIdx.x]);
     __syncthreads();
     const int cnt = min(BS, n - b);
-    bool wdone = __all_sync(0xffffffffu, done0 && done1);
+    bool wdone = __all_sync(0xffffffffu, S.done0 && S.done1);
     for (int j0 = 0; j0 < cnt && !wdone; j0 += 32) {
       const uint32_t m = (j0 + lane < cnt) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
       uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
       const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
-      while (bits) {
-        const int jj = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const StagedG& g = sg[j0 + jj];
-        const PairEval ev = eval_pair(g, PX, PY);
-        bool v0 = ev.v0, v1 = ev.v1;
-        float2 a = make_float2(v0 ? ev.araw.x : 0.0f, v1 ? ev.araw.y : 0.0f);
-        if ((cbits >> jj) & 1u) a = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
-        float2 Tn = __ffma2_rn(make_float2(-T.x, -T.y), a, T);  // T (1 - alpha)
-        const bool st0 = Tn.x < kTMin, st1 = Tn.y < kTMin;      // only a taken Gaussian can stop
-        if (__any_sync(0xffffffffu, st0 || st1)) {
-          // stop before this Gaussian: it is not composited; the pixel is done
-          const uint32_t pos = static_cast<uint32_t>(b + j0 + jj);
-          if (st0) { a.x = 0.0f; Tn.x = T.x; PX.x = kFar; v0 = false; done0 = true; stop0 = pos; }
-          if (st1) { a.y = 0.0f; Tn.y = T.y; PX.y = kFar; v1 = false; done1 = true; stop1 = pos; }
-          wdone = __all_sync(0xffffffffu, done0 && done1);
+      const StagedG* grp = sg + j0;
+      const uint32_t pos0 = static_cast<uint32_t>(b + j0);
+      if (cbits == 0u) {  // no Gaussian of this group needs the alpha clamp
+        while (bits) {
+          const int jj = __ffs(bits) - 1;
+          bits &= bits - 1;
+          if (fwd_step<false, kLast>(S, grp[jj], PY, pos0 + jj)) { wdone = true; break; }
         }
-        const float4 p3 = g.p3, p4 = g.p4;
-        const float2 w = __fmul2_rn(a, T);
-        cr = __ffma2_rn(make_float2(p3.x, p3.y), w, cr);
-        cg = __ffma2_rn(make_float2(p3.z, p3.w), w, cg);
-        cb = __ffma2_rn(make_float2(p4.x, p4.y), w, cb);
-        T = Tn;
-        if constexpr (kLast) {
-          const uint32_t pos1 = static_cast<uint32_t>(b + j0 + jj + 1);
-          last0 = v0 ? pos1 : last0;
-          last1 = v1 ? pos1 : last1;
+      } else {
+        while (bits) {
+          const int jj = __ffs(bits) - 1;
+          bits &= bits - 1;
+          const bool c = (cbits >> jj) & 1u;
+          const bool d = c ? fwd_step<true, kLast>(S, grp[jj], PY, pos0 + jj)
+                           : fwd_step<false, kLast>(S, grp[jj], PY, pos0 + jj);
+          if (d) { wdone = true; break; }
         }
-        if (wdone) break;
       }
     }
   }
   const size_t plane = static_cast<size_t>(width) * height;
   if (in0) {
     const size_t pix = static_cast<size_t>(py) * width + px;
-    out_rgb[pix] = cr.x + T.x * bg0;
-    out_rgb[plane + pix] = cg.x + T.x * bg1;
-    out_rgb[2 * plane + pix] = cb.x + T.x * bg2;
-    out_T[pix] = T.x;
-    out_stop[pix] = stop0;
-    if constexpr (kLast) out_last[pix] = last0;
+    out_rgb[pix] = S.cr.x + S.T.x * bg0;
+    out_rgb[plane + pix] = S.cg.x + S.T.x * bg1;
+    out_rgb[2 * plane + pix] = S.cb.x + S.T.x * bg2;
+    out_T[pix] = S.T.x;
+    out_stop[pix] = S.stop0;
+    if constexpr (kLast) out_last[pix] = S.last0;
   }
   if (in1) {
     const size_t pix = static_cast<size_t>(py) * width + px + 1;
-    out_rgb[pix] = cr.y + T.y * bg0;
-    out_rgb[plane + pix] = cg.y + T.y * bg1;
-    out_rgb[2 * plane + pix] = cb.y + T.y * bg2;
-    out_T[pix] = T.y;
-    out_stop[pix] = stop1;
-    if constexpr (kLast) out_last[pix] = last1;
+    out_rgb[pix] = S.cr.y + S.T.y * bg0;
+    out_rgb[plane + pix] = S.cg.y + S.T.y * bg1;
+    out_rgb[2 * plane + pix] = S.cb.y + S.T.y * bg2;
+    out_T[pix] = S.T.y;
+    out_stop[pix] = S.stop1;
+    if constexpr (kLast) out_last[pix] = S.last1;
   }
 }
 
@@ -240,7 +277,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(Blend<TW, TH>::NT)
     blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, int width, int height, int tiles_x,
+                     const float4* __restrict__ recC, uint32_t ng, int width, int height, int tiles_x,
                      float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
                      const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
                      float* __restrict__ rgrad) {
@@ -290,7 +327,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
     if (idx < n) {
       const uint32_t gid = vals[rg.x + idx];
       sG[threadIdx.x] = gid;
-      stage_entry<TW, TH>(recA, recB, recC, gid, tx, ty, &sg[threadIdx.x]);
+      stage_entry<TW, TH>(recA, recB, recC, gid, ng, tx, ty, &sg[threadIdx.x]);
     }
     __syncthreads();
     const int cnt = min(BS, n - b0);
@@ -396,8 +433,8 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   const size_t npix = static_cast<size_t>(L.width) * L.height;
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                \
   blend_fwd_kernel<TW_, TH_, LAST_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                     \
-      ranges, vals, recA, recB, recC, L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], out_rgb, \
-      T, stop, out_last)
+      ranges, vals, recA, recB, recC, static_cast<uint32_t>(L.n), L.width, L.height, L.tiles_x, bg[0], \
+      bg[1], bg[2], out_rgb, T, stop, out_last)
   const bool lst = out_last != nullptr;
   if (L.tile_w == 16 && L.tile_h == 16) {
     if (lst) R4G_BLEND(16, 16, true); else R4G_BLEND(16, 16, false);
@@ -424,8 +461,8 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   float* rgrad = at<float>(frame, L.recgrad);
 #define R4G_BLEND_BWD(TW_, TH_)                                                                   \
   blend_bwd_kernel<TW_, TH_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                            \
-      ranges, vals, recA, recB, recC, L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], T, stop, \
-      grad_rgb, rgrad)
+      ranges, vals, recA, recB, recC, static_cast<uint32_t>(L.n), L.width, L.height, L.tiles_x, bg[0], \
+      bg[1], bg[2], T, stop, grad_rgb, rgrad)
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16);
   else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8);
   else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND_BWD(16, 32);

@@ -26,6 +26,10 @@ constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
 constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix published
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kOsIPT = 8;                           // items per thread
+constexpr int kOsTile = kSortThreads * kOsIPT;      // 2048 items per tile
+constexpr int kOsWin = 8;                           // predecessors read per look-back round
+constexpr int kOsHistCtas = 2 * 152;
 
 __device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) {
   uint32_t v;
@@ -38,17 +42,19 @@ __device__ __forceinline__ void store_relaxed(uint32_t* p, uint32_t v) {
 }
 
 // Digit histograms of every pass: hist[p * 256 + d] for digits of bits
-// [8 p, 8 p + 8) of the keys, limited to `bits` bits in total.
+// [8 p, 8 p + 8) of the keys, limited to `bits` bits in total (at most four
+// passes). Shared-memory atomics into one sub-histogram per pair of warps,
+// eight loads in flight per thread.
 __global__ void __launch_bounds__(kSortThreads)
     onesweep_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
                          int passes, int bits, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_h[4][kSortRadix];
-  for (int k = threadIdx.x; k < 4 * kSortRadix; k += kSortThreads) (&s_h[0][0])[k] = 0;
+  constexpr int NS = kSortThreads / 64;  // sub-histograms
+  __shared__ uint32_t s_h[NS][4][kSortRadix];
+  for (int k = threadIdx.x; k < NS * 4 * kSortRadix; k += kSortThreads) (&s_h[0][0][0])[k] = 0;
   __syncthreads();
   const uint32_t n = count_dev ? *count_dev : count_host;
-  const int lane = threadIdx.x & 31;
+  const int sub = threadIdx.x / 64;
   constexpr int ILP = 8;
-  // eight independent loads in flight per thread before any is used
   for (uint32_t base = blockIdx.x * kSortThreads * ILP; base < n; base += gridDim.x * kSortThreads * ILP) {
     uint32_t key[ILP];
 #pragma unroll
@@ -58,15 +64,11 @@ __global__ void __launch_bounds__(kSortThreads)
     }
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      const bool ok = base + u * kSortThreads + threadIdx.x < n;
-      const uint32_t act = __ballot_sync(0xffffffffu, ok);
-      if (ok) {
+      if (base + u * kSortThreads + threadIdx.x < n) {
         for (int p = 0; p < passes; ++p) {
           const int sh = p * kSortRadixBits;
           const int nb = min(kSortRadixBits, bits - sh);
-          const uint32_t d = (key[u] >> sh) & ((1u << nb) - 1u);
-          const uint32_t peers = __match_any_sync(act, d);
-          if (lane == __ffs(peers) - 1) atomicAdd(&s_h[p][d], __popc(peers));
+          atomicAdd(&s_h[sub][p][(key[u] >> sh) & ((1u << nb) - 1u)], 1u);
         }
       }
     }
@@ -74,7 +76,9 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   for (int p = 0; p < passes; ++p)
     for (int d = threadIdx.x; d < kSortRadix; d += kSortThreads) {
-      const uint32_t c = s_h[p][d];
+      uint32_t c = 0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) c += s_h[q][p][d];
       if (c) atomicAdd(&hist[p * kSortRadix + d], c);
     }
 }
@@ -91,8 +95,8 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ uint32_t s_tcount[kSortRadix];
   __shared__ uint32_t s_whist[NW][kSortRadix];
   __shared__ uint32_t s_scan[NW];
-  __shared__ uint32_t s_k[kSortTile];
-  __shared__ uint32_t s_v[kSortTile];
+  __shared__ uint32_t s_k[kOsTile];
+  __shared__ uint32_t s_v[kOsTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
@@ -100,16 +104,16 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   const uint32_t t = s_tile;
   const uint32_t n = count_dev ? *count_dev : count_host;
-  const uint64_t tb64 = static_cast<uint64_t>(t) * kSortTile;
+  const uint64_t tb64 = static_cast<uint64_t>(t) * kOsTile;
   if (tb64 >= n) return;  // grid sized for the capacity; CTA-uniform exit
   const uint32_t tb = static_cast<uint32_t>(tb64);
-  const uint32_t tn = min(static_cast<uint32_t>(kSortTile), n - tb);
+  const uint32_t tn = min(static_cast<uint32_t>(kOsTile), n - tb);
 
   // ---- load and rank the tile (stable: warp w holds items [w*256, w*256+256))
-  uint32_t k[kSortIPT], v[kSortIPT], d[kSortIPT], rk[kSortIPT];
+  uint32_t k[kOsIPT], v[kOsIPT], d[kOsIPT], rk[kOsIPT];
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
-    const uint32_t li = warp * (32 * kSortIPT) + j * 32 + lane;
+  for (int j = 0; j < kOsIPT; ++j) {
+    const uint32_t li = warp * (32 * kOsIPT) + j * 32 + lane;
     if (li < tn) {
       k[j] = kin[tb + li];
       v[j] = vin ? vin[tb + li] : tb + li;
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(kSortThreads)
     }
   }
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < kOsIPT; ++j) {
     const bool ok = d[j] != 0xffffffffu;
     const uint32_t act = __ballot_sync(0xffffffffu, ok);
     rk[j] = 0;
@@ -152,12 +156,12 @@ __global__ void __launch_bounds__(kSortThreads)
   } else {
     store_relaxed(st + dd, kFlagAgg | cnt);
   }
-  // Look-back, eight predecessors per round (their statuses are read in
+  // Look-back, kOsWin predecessors per round (their statuses are read in
   // parallel): add published counts newest first until a published prefix;
   // a round that makes no progress counts against the spin limit.
   uint32_t excl = 0;
   if (t > 0) {
-    constexpr int WIN = 8;
+    constexpr int WIN = kOsWin;
     int64_t kt = static_cast<int64_t>(t) - 1;
     uint32_t idle = 0;
     bool found = false;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kSortThreads)
   __syncthreads();
   // ---- stage in digit order, then write each digit's run contiguously
 #pragma unroll
-  for (int j = 0; j < kSortIPT; ++j) {
+  for (int j = 0; j < kOsIPT; ++j) {
     if (d[j] != 0xffffffffu) {
       const uint32_t pos = s_tstart[d[j]] + s_whist[warp][d[j]] + rk[j];
       s_k[pos] = k[j];
@@ -226,14 +230,16 @@ __global__ void __launch_bounds__(kSortThreads)
     const uint32_t key = s_k[i];
     const uint32_t dg = (key >> shift) & mask;
     const uint32_t o = s_dstart[dg] + i - s_tstart[dg];
-    kout[o] = key;
-    vout[o] = s_v[i];
+    if (o < n) {  // only false after a key-capacity overflow, whose result is discarded
+      kout[o] = key;
+      vout[o] = s_v[i];
+    }
   }
 }
 
 size_t onesweep_scratch_bytes(int64_t cap, int bits) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
-  const int64_t tiles = (cap + kSortTile - 1) / kSortTile;
+  const int64_t tiles = (cap + kOsTile - 1) / kOsTile;
   return sizeof(uint32_t) * (static_cast<size_t>(passes) * kSortRadix       // histograms
                              + 32                                           // tickets
                              + static_cast<size_t>(passes) * tiles * kSortRadix);  // status
@@ -242,18 +248,24 @@ size_t onesweep_scratch_bytes(int64_t cap, int bits) {
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf) {
+                            int* result_in_buf, bool hist_ready) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   *result_in_buf = 0;
   if (passes == 0 || cap == 0) return cudaSuccess;
-  const int64_t tiles = (cap + kSortTile - 1) / kSortTile;
+  const int64_t tiles = (cap + kOsTile - 1) / kOsTile;
   uint32_t* hist = static_cast<uint32_t*>(scratch);
   uint32_t* tickets = hist + passes * kSortRadix;
   uint32_t* status = tickets + 32;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, onesweep_scratch_bytes(cap, bits), s);
+  // the histograms either come ready (filled by the caller's kernels) or are
+  // counted here; tickets and statuses always start at zero
+  const size_t hbytes = sizeof(uint32_t) * passes * kSortRadix;
+  cudaError_t e = hist_ready ? cudaMemsetAsync(tickets, 0, onesweep_scratch_bytes(cap, bits) - hbytes, s)
+                             : cudaMemsetAsync(scratch, 0, onesweep_scratch_bytes(cap, bits), s);
   if (e != cudaSuccess) return e;
-  const int hist_ctas = static_cast<int>(tiles < 2 * 152 ? tiles : 2 * 152);
-  onesweep_hist_kernel<<<hist_ctas, kSortThreads, 0, s>>>(kin, count_dev, count_host, passes, bits, hist);
+  if (!hist_ready) {
+    const int hist_ctas = static_cast<int>(tiles < kOsHistCtas ? tiles : kOsHistCtas);
+    onesweep_hist_kernel<<<hist_ctas, kSortThreads, 0, s>>>(kin, count_dev, count_host, passes, bits, hist);
+  }
   const uint32_t* ki = kin;
   const uint32_t* vi = vin;
   int which = 0;

@@ -18,6 +18,7 @@ struct PreOut {
   uint2* rect;   // tile rect: (x0 | y0 << 16, x1 | y1 << 16), [x0, x1) x [y0, y1)
   uint32_t* touched;
   uint32_t* dkey;  // float bits of the depth for Gaussians with tiles, else 0xffffffff
+  uint32_t* tdiff; // 2D difference array of the tile counts, (tiles_y + 1) x (tiles_x + 1)
   uint32_t* blocksum;
   FrameHeader* header;
   int tile_w, tile_h, tiles_x, tiles_y;
@@ -224,6 +225,12 @@ __global__ void __launch_bounds__(kPreBlock)
       out.recC[i] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
       out.rect[i] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
+      // +1 on every tile of the rectangle, as four corner updates
+      const int st = out.tiles_x + 1;
+      atomicAdd(out.tdiff + y0 * st + x0, 1u);
+      atomicAdd(out.tdiff + y0 * st + x1, 0xffffffffu);
+      atomicAdd(out.tdiff + y1 * st + x0, 0xffffffffu);
+      atomicAdd(out.tdiff + y1 * st + x1, 1u);
     } else {
       out.recA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       out.recB[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -271,6 +278,7 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, flo
   o.rect = at<uint2>(frame, L.rect);
   o.touched = at<uint32_t>(frame, L.touched);
   o.dkey = at<uint32_t>(frame, L.dkey0);
+  o.tdiff = at<uint32_t>(frame, L.tdiff);
   o.blocksum = at<uint32_t>(frame, L.blocksum);
   o.header = at<FrameHeader>(frame, L.header);
   o.tile_w = L.tile_w; o.tile_h = L.tile_h; o.tiles_x = L.tiles_x; o.tiles_y = L.tiles_y;

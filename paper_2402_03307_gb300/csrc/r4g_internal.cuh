@@ -40,7 +40,8 @@ struct FrameHeader {
 
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
-  size_t header, rec, rect, touched, dkey0, dkey1, ord0, ord1, offs, srect, blocksum, keys0, vals0, keys1, vals1,
+  size_t header, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, srect, chunks, blocksum, keys0, vals0,
+      keys1, vals1,
       ranges, tfinal, last, sortcnt, onesweep, recgrad, total;
   int64_t n, cap;
   int width, height, tile_w, tile_h, tiles_x, tiles_y, ntiles;
@@ -52,7 +53,8 @@ struct FrameLayout {
   bool keys_in_1;    // the tile-sorted values end in vals1 (else vals0)
 };
 
-constexpr int kPreBlock = 256;     // Gaussians per preprocess / key-build block
+constexpr int kPreBlock = 256;
+constexpr int kMaxTiles = 51200;   // tiles per image (the tile-count kernel keeps them in shared memory)     // Gaussians per preprocess / key-build block
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;        // items per thread per tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
@@ -104,7 +106,9 @@ size_t onesweep_scratch_bytes(int64_t cap, int bits);
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf);
+                            int* result_in_buf, bool hist_ready = false);
+// per-tile counts -> ranges and the tile sort's digit histograms (hist[p][256])
+cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s);
 cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                           cudaStream_t s);
 // 64-bit (tile << 32 | depth bits) keys of the sorted list, for export
