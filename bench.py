@@ -111,16 +111,24 @@ def frame_camera(k: int):
     return synth.orbit_camera(k % FRAMES, FRAMES, RADIUS, WIDTH, HEIGHT)
 
 
-def algorithmic_bytes(stage: str, n: int, n_vis: int, keys: int, passes: int, npix: int) -> float:
-    """Bytes the method must move per launch of a stage."""
+SMS, FP32_LANES = 152, 128
+# FP32 operations (an FMA counts once) the compositing rule of Eq. 3 needs per
+# composited (pixel, Gaussian) pair: d (2), -1/2 d^T conic d (9), alpha =
+# o e^power (1), the 0.99 clamp (1), T (1 - alpha) (2), w = alpha T (1),
+# C += c w (3); the exponential itself runs on the MUFU unit.
+FP32_OPS_PER_PAIR = 19
+
+
+def algorithmic_bytes(stage: str, n: int, n_vis: int, keys: int, npix: int) -> float:
+    """Bytes a stage must move per launch (the per-unit figures of the design doc)."""
     if stage == "preprocess":
         return 68.0 * n + 192.0 * n_vis + 48.0 * n_vis + 12.0 * n
     if stage == "binning":
-        return 4.0 * n + 12.0 * n_vis + 12.0 * keys
-    if stage == "sort":
-        return 24.0 * keys
+        return 4.0 * n + 12.0 * n_vis + 8.0 * keys
+    if stage == "sort":  # depth sort of N (key, index) pairs + tile sort of the pairs, one read + one write
+        return 16.0 * n + 16.0 * keys
     if stage == "ranges":
-        return 8.0 * keys
+        return 8.0 * 5440
     if stage == "blend":
         return 4.0 * keys + 48.0 * n_vis + 20.0 * npix
     return 0.0
@@ -202,11 +210,19 @@ def run_ours(args, rank, world, local):
         total_ms = float(tt.item())
     fps = world * len(frames) / (total_ms / 1e3)
 
-    # per-frame statistics for the roofline model (frame of the last step)
-    ex = rend.export(res)
-    keys = ex["key_count"]
-    n_vis = int((ex["records"][:, 5] > 0).sum().item())
-    passes = math.ceil((32 + math.ceil(math.log2(math.ceil(WIDTH / 16) * math.ceil(HEIGHT / 16)))) / 8)
+    # per-frame work of the timed frames, counted in an untimed instrumented pass
+    counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
+    cframe = counter.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    work = {"keys": 0, "n_visible": 0, "pairs": 0}
+    for k in frames:
+        cam, t = frame_camera(k)
+        r = counter.render(params, cam, t, frame=cframe, key_capacity=cap, out=img, check=False)
+        st_ = counter.stats(r)
+        work["keys"] += st_["key_count"]
+        work["n_visible"] += st_["n_visible"]
+        work["pairs"] += st_["composited_pairs"]
+    work = {k: v / len(frames) for k, v in work.items()}
+    keys, n_vis = work["keys"], work["n_visible"]
     per_stage = {k: v / len(frames) for k, v in stage_ms.items() if v > 0}
     top = max(per_stage, key=per_stage.get)
     peaks = {}
@@ -215,13 +231,28 @@ def run_ours(args, rank, world, local):
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    bytes_top = algorithmic_bytes(top, N_GAUSS, n_vis, keys, passes, WIDTH * HEIGHT)
-    achieved = bytes_top / (per_stage[top] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm_peak,
-                "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": None,
-                "peak_source": peak_src,
-                "stage_ms": {k: round(v, 4) for k, v in per_stage.items()}}
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    alu_peak = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12  # FP32 lane-operations, T/s
+
+    def stage_roof(stage):
+        sec = per_stage[stage] / 1e3
+        if stage == "blend":
+            ach = work["pairs"] * FP32_OPS_PER_PAIR / sec / 1e12
+            return {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                    "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4)}
+        ach = algorithmic_bytes(stage, N_GAUSS, n_vis, keys, WIDTH * HEIGHT) / sec / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4)}
+
+    roofline = dict(stage_roof(top))
+    roofline.update({"kernel": top, "traffic": None,
+                     "peak_source": (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
+                                     f"MEASURED_PEAKS.json)") if top == "blend" else f"{src} hbm_gbs",
+                     "work_per_frame": {"composited_pairs": round(work["pairs"]), "keys": round(keys),
+                                        "visible": round(n_vis), "fp32_ops_per_pair": FP32_OPS_PER_PAIR},
+                     "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+                     "stages": {k: stage_roof(k) for k in per_stage}})
 
     out = {"metric": METRIC, "value": round(fps, 2), "unit": "frames/s", "n_gpus": world,
            "steps": len(frames), "warmup": args.warmup, "ms_per_step": round(total_ms / len(frames), 4),
@@ -229,8 +260,7 @@ def run_ours(args, rank, world, local):
            "data": "synthetic (seeded 4D Gaussians; stands in for Plenoptic Video at its resolution)",
            "config": {"workload": "300k 4D Gaussians, 1352x1014, 300-frame orbit sweep r=8, FP32, 1 view/launch",
                       "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile": "16x16",
-                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
-                      "keys_last_frame": keys, "visible_last_frame": n_vis},
+                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
            "gpu_launches": int(sum(stage_launch.values())),
            "wall_s": round(wall, 3), "clocks": clk, "roofline": roofline}
 

@@ -57,6 +57,8 @@ typedef enum r4g_dtype { R4G_F32 = 0, R4G_BF16 = 1 } r4g_dtype;
 /* Flags of r4g_config.flags */
 #define R4G_FLAG_FP64_SLICE 0x1u   /* debug: Sigma4, the slice and Sigma3 in FP64 */
 #define R4G_FLAG_NO_TEMPORAL_CULL 0x2u  /* keep Gaussians with lambda (t-mu_t)^2 > 16 */
+#define R4G_FLAG_COUNT_PAIRS 0x4u  /* measurement: count composited (pixel, Gaussian) pairs
+                                     (a slower, instrumented blend; see r4g_frame_stats) */
 
 /* Render configuration. tile_w x tile_h in {8x8, 16x16, 16x32}. */
 typedef struct r4g_config {
@@ -141,6 +143,19 @@ r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t
  * (tile, Gaussian) pairs of the last render into this frame. */
 r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
                             int64_t* keys_needed, void* stream);
+
+/* Statistics of the last render into a frame (waits for `stream`). */
+typedef struct r4g_frame_info {
+  int64_t n_visible;         /* Gaussians with at least one tile */
+  int64_t key_count;         /* (tile, Gaussian) pairs in the sorted list */
+  int64_t key_needed;        /* pairs the render needed (> key_count after an overflow) */
+  int64_t composited_pairs;  /* (pixel, Gaussian) pairs composited; -1 unless the context
+                                has R4G_FLAG_COUNT_PAIRS */
+  int32_t status;            /* R4G_OK, R4G_EOVERFLOW or R4G_ETIMEOUT */
+  int32_t reserved;
+} r4g_frame_info;
+r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, r4g_frame_info* out,
+                           void* stream);
 
 /* Copy out of a frame (device -> device, enqueued on `stream`): the key count
  * (uint32 [1]), the sorted 64-bit keys and 32-bit values (first key_count

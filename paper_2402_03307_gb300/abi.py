@@ -13,6 +13,7 @@ R4G_OK, R4G_EINVAL, R4G_ENOMEM, R4G_EWORKSPACE, R4G_ECUDA, R4G_ETIMEOUT, R4G_EDE
 R4G_F32, R4G_BF16 = 0, 1
 R4G_FLAG_FP64_SLICE = 0x1
 R4G_FLAG_NO_TEMPORAL_CULL = 0x2
+R4G_FLAG_COUNT_PAIRS = 0x4
 STATUS_NAMES = {0: "R4G_OK", 1: "R4G_EINVAL", 2: "R4G_ENOMEM", 3: "R4G_EWORKSPACE", 4: "R4G_ECUDA",
                 5: "R4G_ETIMEOUT", 6: "R4G_EDEVICE", 7: "R4G_EOVERFLOW"}
 
@@ -38,6 +39,11 @@ class r4g_grads(C.Structure):
                 ("logit", C.c_void_p), ("sh", C.c_void_p)]
 
 
+class r4g_frame_info(C.Structure):
+    _fields_ = [("n_visible", C.c_int64), ("key_count", C.c_int64), ("key_needed", C.c_int64),
+                ("composited_pairs", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
 class r4g_view(C.Structure):
     _fields_ = [("cam", r4g_camera), ("t", C.c_float)]
 
@@ -51,6 +57,7 @@ SIGNATURES = [
     ("r4g_frame_bytes", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int64,
                                   C.POINTER(C.c_size_t)]),
     ("r4g_frame_status", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64), C.c_void_p]),
+    ("r4g_frame_stats", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(r4g_frame_info), C.c_void_p]),
     ("r4g_frame_export", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64, C.c_int32, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("r4g_render", C.c_int, [C.c_void_p, C.POINTER(r4g_gaussians), C.POINTER(r4g_camera), C.c_float,
@@ -133,6 +140,12 @@ def r4g_frame_status(ctx, frame: int, frame_bytes: int, stream: int) -> tuple[in
     if st not in (R4G_OK, R4G_EOVERFLOW):
         check(st, ctx)
     return st, need.value
+
+
+def r4g_frame_stats(ctx, frame: int, frame_bytes: int, stream: int) -> dict:
+    info = r4g_frame_info()
+    check(lib().r4g_frame_stats(ctx, frame, frame_bytes, C.byref(info), stream), ctx)
+    return {k: getattr(info, k) for k, _ in r4g_frame_info._fields_ if k != "reserved"}
 
 
 def r4g_frame_export(ctx, frame, frame_bytes, n, width, height, key_count, keys, values, ranges,

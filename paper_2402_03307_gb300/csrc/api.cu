@@ -222,7 +222,8 @@ r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg) {
   }
   if (!tile_ok(c.tile_w, c.tile_h)) return fail(nullptr, R4G_EINVAL, "tile shape must be 8x8, 16x16 or 16x32");
   if (c.sh_degree < 0 || c.sh_degree > 3) return fail(nullptr, R4G_EINVAL, "sh_degree must be 0..3");
-  if (c.flags & ~(R4G_FLAG_FP64_SLICE | R4G_FLAG_NO_TEMPORAL_CULL)) return fail(nullptr, R4G_EINVAL, "unknown flag");
+  if (c.flags & ~(R4G_FLAG_FP64_SLICE | R4G_FLAG_NO_TEMPORAL_CULL | R4G_FLAG_COUNT_PAIRS))
+    return fail(nullptr, R4G_EINVAL, "unknown flag");
   r4g_ctx* ctx = new (std::nothrow) r4g_ctx;
   if (!ctx) return fail(nullptr, R4G_ENOMEM, "out of host memory");
   ctx->cfg = c;
@@ -295,6 +296,24 @@ r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   if (keys_needed) *keys_needed = h.key_needed;
   if (h.status & 1u) return fail(ctx, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
   if (h.status & 2u) return fail(ctx, R4G_ETIMEOUT, "a radix-sort look-back wait hit its iteration limit");
+  return R4G_OK;
+}
+
+r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, r4g_frame_info* out,
+                           void* stream) {
+  if (!ctx || !frame || !out) return fail(ctx, R4G_EINVAL, "NULL argument");
+  if (frame_bytes < sizeof(FrameHeader)) return fail(ctx, R4G_EWORKSPACE, "frame too small");
+  FrameHeader h;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h, frame, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "r4g_frame_stats");
+  out->n_visible = h.n_visible;
+  out->key_count = h.key_count;
+  out->key_needed = h.key_needed;
+  out->composited_pairs = (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) ? static_cast<int64_t>(h.composited) : -1;
+  out->status = (h.status & 1u) ? R4G_EOVERFLOW : ((h.status & 2u) ? R4G_ETIMEOUT : R4G_OK);
+  out->reserved = 0;
   return R4G_OK;
 }
 
@@ -395,7 +414,8 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
   const uint32_t* vals = sorted_vals(L, frame);
   {
     StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
-    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last, s)) != cudaSuccess)
+    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last,
+                              (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) != 0, s)) != cudaSuccess)
       return cuda_fail(ctx, e, "blend");
   }
   return R4G_OK;

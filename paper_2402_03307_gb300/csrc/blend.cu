@@ -146,17 +146,16 @@ __device__ __forceinline__ PairEval eval_pair(const StagedG& g, float2 PX, float
 // Per-thread state of the forward walk over a tile list.
 struct FwdState {
   float2 PX, T, cr, cg, cb;
-  uint32_t stop0, stop1, last0, last1;
+  uint32_t stop0, stop1, last0, last1, pairs;
   bool done0, done1;
 };
 
-// One staged Gaussian composited into the thread's two pixels. kClamp: the
+// Composite one evaluated Gaussian into the thread's two pixels. kClamp: the
 // Gaussian's opacity_t exceeds 0.99 so alpha is clamped; kLast: track the
 // last composited position. Returns true when every pixel of the warp has
 // stopped.
 template <bool kClamp, bool kLast>
-__device__ __forceinline__ bool fwd_step(FwdState& S, const StagedG& g, float2 PY, uint32_t pos) {
-  const PairEval ev = eval_pair(g, S.PX, PY);
+__device__ __forceinline__ bool fwd_apply(FwdState& S, const PairEval& ev, const StagedG& g, uint32_t pos) {
   bool v0 = ev.v0, v1 = ev.v1;
   float2 a = make_float2(v0 ? ev.araw.x : 0.0f, v1 ? ev.araw.y : 0.0f);
   if constexpr (kClamp) a = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
@@ -175,11 +174,45 @@ __device__ __forceinline__ bool fwd_step(FwdState& S, const StagedG& g, float2 P
   S.cg = __ffma2_rn(make_float2(p3.z, p3.w), w, S.cg);
   S.cb = __ffma2_rn(make_float2(p4.x, p4.y), w, S.cb);
   S.T = Tn;
-  if constexpr (kLast) {
+  if constexpr (kLast) {  // instrumented variant: last composited position and a pair count
     S.last0 = v0 ? pos + 1 : S.last0;
     S.last1 = v1 ? pos + 1 : S.last1;
+    S.pairs += (v0 ? 1u : 0u) + (v1 ? 1u : 0u);
   }
   return wdone;
+}
+
+// Walk the set bits of one 32-entry group, two Gaussians per iteration: the
+// two evaluations are independent and overlap; the composites stay in order.
+// A pixel that stops inside an iteration has moved to infinity before the
+// second composite only through its done flag: the second evaluation saw the
+// old position, so its result is discarded for that pixel.
+template <bool kClamp, bool kLast>
+__device__ __forceinline__ bool fwd_group(FwdState& S, const StagedG* grp, uint32_t bits, uint32_t cbits,
+                                          float2 PY, uint32_t pos0) {
+  while (bits) {
+    const int j0 = __ffs(bits) - 1;
+    bits &= bits - 1;
+    if (bits) {
+      const int j1 = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const PairEval e0 = eval_pair(grp[j0], S.PX, PY);
+      PairEval e1 = eval_pair(grp[j1], S.PX, PY);
+      const bool c0 = kClamp && ((cbits >> j0) & 1u), c1 = kClamp && ((cbits >> j1) & 1u);
+      if (c0 ? fwd_apply<true, kLast>(S, e0, grp[j0], pos0 + j0) : fwd_apply<false, kLast>(S, e0, grp[j0], pos0 + j0))
+        return true;
+      e1.v0 = e1.v0 && !S.done0;
+      e1.v1 = e1.v1 && !S.done1;
+      if (c1 ? fwd_apply<true, kLast>(S, e1, grp[j1], pos0 + j1) : fwd_apply<false, kLast>(S, e1, grp[j1], pos0 + j1))
+        return true;
+    } else {
+      const PairEval e0 = eval_pair(grp[j0], S.PX, PY);
+      const bool c0 = kClamp && ((cbits >> j0) & 1u);
+      if (c0 ? fwd_apply<true, kLast>(S, e0, grp[j0], pos0 + j0) : fwd_apply<false, kLast>(S, e0, grp[j0], pos0 + j0))
+        return true;
+    }
+  }
+  return false;
 }
 
 template <int TW, int TH>
@@ -192,7 +225,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
                      const float4* __restrict__ recC, uint32_t ng, int width, int height, int tiles_x,
                      float bg0, float bg1, float bg2, float* __restrict__ out_rgb,
                      float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
-                     uint32_t* __restrict__ out_last) {
+                     uint32_t* __restrict__ out_last, unsigned long long* __restrict__ pair_count) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT;
   __shared__ StagedG sg[BS];
@@ -212,6 +245,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
   S.cr = S.cg = S.cb = make_float2(0.f, 0.f);
   S.stop0 = S.stop1 = static_cast<uint32_t>(n);
   S.last0 = S.last1 = 0;
+  S.pairs = 0;
   S.done0 = !in0;
   S.done1 = !in1;
   const uint32_t wbit = 1u << warp;
@@ -228,22 +262,9 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
       const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
       const StagedG* grp = sg + j0;
       const uint32_t pos0 = static_cast<uint32_t>(b + j0);
-      if (cbits == 0u) {  // no Gaussian of this group needs the alpha clamp
-        while (bits) {
-          const int jj = __ffs(bits) - 1;
-          bits &= bits - 1;
-          if (fwd_step<false, kLast>(S, grp[jj], PY, pos0 + jj)) { wdone = true; break; }
-        }
-      } else {
-        while (bits) {
-          const int jj = __ffs(bits) - 1;
-          bits &= bits - 1;
-          const bool c = (cbits >> jj) & 1u;
-          const bool d = c ? fwd_step<true, kLast>(S, grp[jj], PY, pos0 + jj)
-                           : fwd_step<false, kLast>(S, grp[jj], PY, pos0 + jj);
-          if (d) { wdone = true; break; }
-        }
-      }
+      // no Gaussian of this group needs the alpha clamp: the common path
+      wdone = cbits == 0u ? fwd_group<false, kLast>(S, grp, bits, cbits, PY, pos0)
+                          : fwd_group<true, kLast>(S, grp, bits, cbits, PY, pos0);
     }
   }
   const size_t plane = static_cast<size_t>(width) * height;
@@ -254,7 +275,9 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
     out_rgb[2 * plane + pix] = S.cb.x + S.T.x * bg2;
     out_T[pix] = S.T.x;
     out_stop[pix] = S.stop0;
-    if constexpr (kLast) out_last[pix] = S.last0;
+    if constexpr (kLast) {
+      if (out_last) out_last[pix] = S.last0;
+    }
   }
   if (in1) {
     const size_t pix = static_cast<size_t>(py) * width + px + 1;
@@ -263,7 +286,13 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
     out_rgb[2 * plane + pix] = S.cb.y + S.T.y * bg2;
     out_T[pix] = S.T.y;
     out_stop[pix] = S.stop1;
-    if constexpr (kLast) out_last[pix] = S.last1;
+    if constexpr (kLast) {
+      if (out_last) out_last[pix] = S.last1;
+    }
+  }
+  if constexpr (kLast) {
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, S.pairs);
+    if (lane == 0 && wsum) atomicAdd(pair_count, static_cast<unsigned long long>(wsum));
   }
 }
 
@@ -421,7 +450,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
 }
 
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
-                             const float* bg, float* out_rgb, float* out_T, uint32_t* out_last,
+                             const float* bg, float* out_rgb, float* out_T, uint32_t* out_last, bool count,
                              cudaStream_t s) {
   const float4* recA = at<float4>(frame, L.rec);
   const float4* recB = recA + L.n;
@@ -434,8 +463,10 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                \
   blend_fwd_kernel<TW_, TH_, LAST_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                     \
       ranges, vals, recA, recB, recC, static_cast<uint32_t>(L.n), L.width, L.height, L.tiles_x, bg[0], \
-      bg[1], bg[2], out_rgb, T, stop, out_last)
-  const bool lst = out_last != nullptr;
+      bg[1], bg[2], out_rgb, T, stop, out_last, pairs)
+  // the instrumented variant serves both the last-contributor output and the pair count
+  const bool lst = out_last != nullptr || count;
+  unsigned long long* pairs = &at<FrameHeader>(frame, L.header)->composited;
   if (L.tile_w == 16 && L.tile_h == 16) {
     if (lst) R4G_BLEND(16, 16, true); else R4G_BLEND(16, 16, false);
   } else if (L.tile_w == 8 && L.tile_h == 8) {

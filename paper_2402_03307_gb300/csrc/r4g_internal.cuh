@@ -35,7 +35,8 @@ struct FrameHeader {
   uint32_t key_count;     // pairs actually written (min(needed, capacity))
   uint32_t key_needed;    // pairs the render needed
   uint32_t n_visible;
-  uint32_t pad[60];
+  unsigned long long composited;  // composited (pixel, Gaussian) pairs, counted on request
+  uint32_t pad[58];
 };
 
 // Byte offsets of the regions of a frame; computed on the host.
@@ -116,7 +117,7 @@ cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t
                                const uint32_t* vals, uint64_t* out, cudaStream_t s);
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, float* out_rgb, float* out_T,
-                             uint32_t* out_last, cudaStream_t s);
+                             uint32_t* out_last, bool count, cudaStream_t s);
 cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, const float* grad_rgb, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const CamDev& cam, float t,

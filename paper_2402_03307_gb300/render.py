@@ -137,6 +137,12 @@ class Renderer:
             self._cap_hint[(g.n, c.width, c.height)] = cap
             frame = None
 
+    def stats(self, res: RenderResult, stream=None) -> dict:
+        """n_visible, key_count, key_needed, composited_pairs (-1 unless the
+        renderer was made with flags including R4G_FLAG_COUNT_PAIRS), status."""
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        return abi.r4g_frame_stats(self.ctx, res.frame.data_ptr(), res.frame.numel(), s)
+
     def status(self, res: RenderResult, stream=None) -> tuple[int, int]:
         s = (stream or torch.cuda.current_stream()).cuda_stream
         return abi.r4g_frame_status(self.ctx, res.frame.data_ptr(), res.frame.numel(), s)
