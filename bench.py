@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--train-steps", type=int, default=10)
@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
+    ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
     return ap.parse_args()
 
 
@@ -71,7 +72,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
 
@@ -154,6 +155,8 @@ def run_ours(args, rank, world, local):
     rend = r4g.Renderer()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if args.train_only:
+        return {"train": train_bench(args, rend, params, dev, stream)}
 
     def barrier():
         if world > 1:
@@ -391,7 +394,7 @@ def main():
         print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.frames_only:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.frames_only or args.train_only):
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(out))

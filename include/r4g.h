@@ -96,9 +96,9 @@ typedef struct r4g_camera {
   int32_t width, height;
 } r4g_camera;
 
-/* Parameter gradients (device pointers, FP32, same shapes as r4g_gaussians).
- * The backward ADDS into them, so several views can accumulate one step;
- * the caller zeroes them. */
+/* Parameter gradients (device pointers, FP32, same shapes as r4g_gaussians,
+ * 16-byte aligned rows). The backward ADDS into them, so several views can
+ * accumulate one step; the caller zeroes them. */
 typedef struct r4g_grads {
   float* mean;
   float* rotor;
@@ -186,7 +186,10 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
  * given dL/d out_rgb (grad_rgb [3, height, width]) ADD dL/d parameters into
  * `grads`. Transmittance is recovered back to front from the stored final T,
  * no per-layer state is kept. Gradients through inactive branches (clamped
- * alpha, negative colour, the Jacobian clamp, culled Gaussians) are zero. */
+ * alpha, negative colour, the Jacobian clamp, culled Gaussians) are zero.
+ * A frame whose key buffer overflowed adds nothing (its image was invalid;
+ * r4g_frame_status reports it). Deterministic: the same inputs add the same
+ * bits (no floating-point atomics). */
 r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam,
                                float t, const float* grad_rgb, r4g_grads* grads,
                                void* frame, size_t frame_bytes, int64_t key_capacity,

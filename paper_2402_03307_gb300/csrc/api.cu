@@ -178,6 +178,8 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
   L.vals0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.keys1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.vals1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
+  L.egid = o;     o = align_up(o + sizeof(uint32_t) * cap);
+  L.gbuf = o;     o = align_up(o + 12 * sizeof(float) * cap);
   L.ranges = o;   o = align_up(o + sizeof(uint2) * L.ntiles);
   L.tfinal = o;   o = align_up(o + sizeof(float) * npix);
   L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
@@ -186,7 +188,6 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
     const size_t a = onesweep_scratch_bytes(n, 32), b = onesweep_scratch_bytes(cap, tb);
     L.onesweep = o; o = align_up(o + (a > b ? a : b));
   }
-  L.recgrad = o;  o = align_up(o + 12 * sizeof(float) * n);
   L.total = o;
   return L;
 }
@@ -340,8 +341,7 @@ r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   const uint32_t K = h.key_count;
   if (key_count) e = cudaMemcpyAsync(key_count, &at<FrameHeader>(f, L.header)->key_count, 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && keys && K) e = launch_export_keys(L, f, sorted_tile_keys(L, f), sorted_vals(L, f), keys, s);
-  if (e == cudaSuccess && values && K)
-    e = cudaMemcpyAsync(values, sorted_vals(L, f), 4ull * K, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && values && K) e = launch_export_values(L, f, sorted_vals(L, f), values, s);
   if (e == cudaSuccess && ranges)
     e = cudaMemcpyAsync(ranges, at<uint2>(f, L.ranges), 8ull * L.ntiles, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && records && n) {
@@ -406,7 +406,8 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
   if (has && tpasses > 0) {
     // stable sort of the depth-ordered pairs by tile id
     StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
-    e = launch_onesweep(at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), at<uint32_t>(frame, L.keys1),
+    // values: the emission index of each pair, generated by the first pass
+    e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
                         at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
                         count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
@@ -431,6 +432,9 @@ r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_c
   if (!grad_rgb || !grads || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
   if (g->n > 0 && (!grads->mean || !grads->rotor || !grads->logscale || !grads->logit || !grads->sh))
     return fail(ctx, R4G_EINVAL, "a gradient pointer is NULL");
+  if (g->n > 0 && (!aligned(grads->mean, 16) || !aligned(grads->rotor, 16) || !aligned(grads->logscale, 16) ||
+                   !aligned(grads->sh, 16) || !aligned(grads->logit, 4)))
+    return fail(ctx, R4G_EINVAL, "gradient buffers must be 16-byte aligned");
   if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
   if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
   const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
@@ -438,8 +442,7 @@ r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_c
   if (L.n == 0) return R4G_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const CamDev cd = make_cam(*cam);
-  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.recgrad), 0, 12 * sizeof(float) * L.n, s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  cudaError_t e = cudaSuccess;
   const uint32_t* vals = sorted_vals(L, frame);
   {
     StageScope sc(ctx, R4G_STAGE_BLEND_BWD, s, 1);

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kPreBlock)
 __global__ void __launch_bounds__(kPreBlock)
     emit_kernel(const uint32_t* __restrict__ offs, const uint2* __restrict__ srect,
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
-                int tiles_x, const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ vals) {
+                int tiles_x, const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
+                uint32_t* __restrict__ ident) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   const uint32_t K = hdr->key_count;
   const uint32_t q0 = blockIdx.x * kEmitChunk;
@@ -150,7 +151,8 @@ __global__ void __launch_bounds__(kPreBlock)
     const uint32_t w = x1 - x0;
     const uint32_t ty = y0 + local / w, tx = x0 + local % w;
     tkeys[q] = ty * static_cast<uint32_t>(tiles_x) + tx;
-    vals[q] = order[j];
+    egid[q] = order[j];
+    if (ident) ident[q] = q;  // a single-tile image has no tile sort to generate the values
   }
 }
 
@@ -257,15 +259,27 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, const FrameHead
   }
 }
 
+// The sort carries each pair's emission index e; egid[e] is its Gaussian.
 __global__ void export_keys_kernel(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                                   const float4* __restrict__ recB, const FrameHeader* hdr, uint32_t ng,
-                                   uint64_t* __restrict__ out) {
+                                   const uint32_t* __restrict__ egid, const float4* __restrict__ recB,
+                                   const FrameHeader* hdr, uint32_t ng, uint32_t cap, uint64_t* __restrict__ out) {
   const uint32_t n = hdr->key_count;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t g = vals[i];  // out of range only in an overflowed (invalid) frame
+    const uint32_t e = vals[i];  // out of range only in an overflowed (invalid) frame
+    const uint32_t g = e < cap ? egid[e] : ng;
     out[i] = (static_cast<uint64_t>(tkeys[i]) << 32) | (g < ng ? __float_as_uint(recB[g].z) : 0u);
   }
 }
+
+__global__ void export_values_kernel(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ egid,
+                                     const FrameHeader* hdr, uint32_t cap, uint32_t* __restrict__ out) {
+  const uint32_t n = hdr->key_count;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t e = vals[i];
+    out[i] = e < cap ? egid[e] : 0xffffffffu;
+  }
+}
+
 
 cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
@@ -284,7 +298,9 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   if (chunks > 0)
     emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, cstart, n, L.tiles_x, hdr,
                                                                      at<uint32_t>(frame, L.keys0),
-                                                                     at<uint32_t>(frame, L.vals0));
+                                                                     at<uint32_t>(frame, L.egid),
+                                                                     L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0)
+                                                                                      : nullptr);
   return cudaGetLastError();
 }
 
@@ -311,9 +327,19 @@ cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t
                                const uint32_t* vals, uint64_t* out, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
   const float4* recB = at<float4>(frame, L.rec) + L.n;
-  export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, recB, at<FrameHeader>(frame, L.header),
-                                             static_cast<uint32_t>(L.n), out);
+  export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, at<uint32_t>(frame, L.egid), recB,
+                                             at<FrameHeader>(frame, L.header), static_cast<uint32_t>(L.n),
+                                             static_cast<uint32_t>(L.cap), out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_export_values(const FrameLayout& L, void* frame, const uint32_t* vals, uint32_t* out,
+                                 cudaStream_t s) {
+  if (L.n == 0) return cudaSuccess;
+  export_values_kernel<<<4 * 152, 256, 0, s>>>(vals, at<uint32_t>(frame, L.egid), at<FrameHeader>(frame, L.header),
+                                               static_cast<uint32_t>(L.cap), out);
+  return cudaGetLastError();
+}
+
 
 }  // namespace r4g

@@ -222,9 +222,9 @@ template <int TW, int TH, bool kLast>
 __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
     blend_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, uint32_t ng, int width, int height, int tiles_x,
-                     float bg0, float bg1, float bg2, float* __restrict__ out_rgb,
-                     float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
+                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
+                     uint32_t cap, int width, int height, int tiles_x, float bg0, float bg1, float bg2,
+                     float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
                      uint32_t* __restrict__ out_last, unsigned long long* __restrict__ pair_count) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT;
@@ -252,7 +252,10 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
   for (int b = 0; b < n; b += BS) {
     if (__syncthreads_count(S.done0 && S.done1) == BS) break;
     const int idx = b + static_cast<int>(threadIdx.x);
-    if (idx < n) stage_entry<TW, TH>(recA, recB, recC, vals[rg.x + idx], ng, tx, ty, &sg[threadIdx.x]);
+    if (idx < n) {
+      const uint32_t e = vals[rg.x + idx];  // emission index of the pair
+      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, &sg[threadIdx.x]);
+    }
     __syncthreads();
     const int cnt = min(BS, n - b);
     bool wdone = __all_sync(0xffffffffu, S.done0 && S.done1);
@@ -301,20 +304,25 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
 // the colour already accumulated behind i is carried along, and per-Gaussian
 // gradients (d mean2d, d conic, d opacity_t, d rgb) are summed over the two
 // pixels of a thread, then over the warp with a transpose reduction (14
-// shuffles for 9 values) before one atomic add per value and warp.
+// shuffles for 9 values), then over the CTA's warps in a fixed order in
+// shared memory, and written once per (tile, Gaussian) pair into the
+// per-pair buffer (indexed by the pair's emission index); a gather kernel
+// then sums each Gaussian's pairs. No float atomics: the gradient is
+// deterministic.
 template <int TW, int TH>
 __global__ void __launch_bounds__(Blend<TW, TH>::NT)
     blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, uint32_t ng, int width, int height, int tiles_x,
-                     float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
-                     const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
-                     float* __restrict__ rgrad) {
+                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
+                     uint32_t cap, int width, int height, int tiles_x, float bg0, float bg1, float bg2,
+                     const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
+                     const float* __restrict__ grad_rgb, float4* __restrict__ gbuf) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT;
   __shared__ StagedG sg[BS];
-  __shared__ uint32_t sG[BS];
+  __shared__ uint32_t sE[BS];
   __shared__ uint32_t s_max;
+  extern __shared__ float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -345,7 +353,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
   const uint32_t mine = L[0] > L[1] ? L[0] : L[1];
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);  // this warp's walk ends here
   if (lane == 0 && wmax) atomicMax(&s_max, wmax);
   __syncthreads();
   const int maxL = static_cast<int>(s_max);
@@ -353,15 +361,18 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   for (int b0 = ((maxL - 1) / BS) * BS; maxL > 0 && b0 >= 0; b0 -= BS) {
     const int idx = b0 + static_cast<int>(threadIdx.x);
     __syncthreads();
+    for (int k = threadIdx.x; k < B::NW * BS * 9 / 4; k += BS)
+      reinterpret_cast<float4*>(s_slab)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (idx < n) {
-      const uint32_t gid = vals[rg.x + idx];
-      sG[threadIdx.x] = gid;
-      stage_entry<TW, TH>(recA, recB, recC, gid, ng, tx, ty, &sg[threadIdx.x]);
+      const uint32_t e = vals[rg.x + idx];
+      sE[threadIdx.x] = e;
+      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, &sg[threadIdx.x]);
     }
     __syncthreads();
     const int cnt = min(BS, n - b0);
     for (int j0 = ((cnt - 1) / 32) * 32; j0 >= 0; j0 -= 32) {
-      const uint32_t m = (j0 + lane < cnt && b0 + j0 + lane < maxL) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
+      const uint32_t m = (j0 + lane < cnt && static_cast<uint32_t>(b0 + j0 + lane) < wmax)
+                             ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
       uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
       const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
       while (bits) {
@@ -383,14 +394,14 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
           if (p < L[k] && vv[k]) {
             any = true;
             const float alpha = clamp ? fminf(kAlphaMax, araw[k]) : araw[k];
-            const float om = 1.0f - alpha;
-            const float Ti = T[k] / om;
+            const float iom = 1.0f / (1.0f - alpha);  // alpha <= 0.99
+            const float Ti = T[k] * iom;
             const float w = alpha * Ti;
             v[6] += g[k][0] * w;
             v[7] += g[k][1] * w;
             v[8] += g[k][2] * w;
             const float gc = g[k][0] * p3.x + g[k][1] * p3.z + g[k][2] * p4.x;
-            const float dalpha = gc * Ti - (S[k] + bgg[k]) / om;
+            const float dalpha = gc * Ti - (S[k] + bgg[k]) * iom;
             S[k] += gc * w;
             T[k] = Ti;
             const float da = (clamp && araw[k] > kAlphaMax) ? 0.0f : dalpha;
@@ -435,16 +446,44 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
           v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v[8] += __shfl_xor_sync(0xffffffffu, v[8], o);
-          float* dst = rgrad + static_cast<size_t>(sG[j0 + jj]) * 12;
+          float* dst = s_slab + (warp * BS + j0 + jj) * 9;
           if ((lane & 3) == 0) {
             const int id = lane >> 2;  // value index 0..7
             // A', B', C' -> conic a, b, c: A' = -L a / 2, B' = -L b, C' = -L c / 2
             const float scale = (id == 2 || id == 4) ? -0.5f * kLog2e : (id == 3 ? -kLog2e : 1.0f);
-            atomicAdd(dst + (id < 6 ? id : id + 2), v[0] * scale);
+            dst[id] = v[0] * scale;
           }
-          if (lane == 1) atomicAdd(dst + 10, v[8]);
+          if (lane == 1) dst[8] = v[8];
         }
       }
+    }
+    __syncthreads();
+    // each entry of the batch: sum over the warps (fixed order), one write
+    if (idx < n) {
+      float acc[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+#pragma unroll
+      for (int w = 0; w < B::NW; ++w) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += s_slab[(w * BS + threadIdx.x) * 9 + k];
+      }
+      const uint32_t e = sE[threadIdx.x];
+      if (e < cap) {
+        float4* d = gbuf + 3 * static_cast<size_t>(e);
+        d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        d[1] = make_float4(acc[4], acc[5], 0.0f, 0.0f);
+        d[2] = make_float4(acc[6], acc[7], acc[8], 0.0f);
+      }
+    }
+  }
+  // list entries no pixel of the tile reached: zero gradient
+  const int start = maxL > 0 ? ((maxL - 1) / BS) * BS + BS : 0;
+  for (int i = start + static_cast<int>(threadIdx.x); i < n; i += BS) {
+    const uint32_t e = vals[rg.x + i];
+    if (e < cap) {
+      float4* d = gbuf + 3 * static_cast<size_t>(e);
+      d[0] = d[1] = d[2] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -462,8 +501,9 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   const size_t npix = static_cast<size_t>(L.width) * L.height;
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                \
   blend_fwd_kernel<TW_, TH_, LAST_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                     \
-      ranges, vals, recA, recB, recC, static_cast<uint32_t>(L.n), L.width, L.height, L.tiles_x, bg[0], \
-      bg[1], bg[2], out_rgb, T, stop, out_last, pairs)
+      ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.n), static_cast<uint32_t>(L.cap),     \
+      L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], out_rgb, T, stop, out_last, pairs)
+  const uint32_t* egid = at<uint32_t>(frame, L.egid);
   // the instrumented variant serves both the last-contributor output and the pair count
   const bool lst = out_last != nullptr || count;
   unsigned long long* pairs = &at<FrameHeader>(frame, L.header)->composited;
@@ -489,14 +529,20 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   const uint2* ranges = at<uint2>(frame, L.ranges);
   const float* T = at<float>(frame, L.tfinal);
   const uint32_t* stop = at<uint32_t>(frame, L.last);
-  float* rgrad = at<float>(frame, L.recgrad);
-#define R4G_BLEND_BWD(TW_, TH_)                                                                   \
-  blend_bwd_kernel<TW_, TH_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                            \
-      ranges, vals, recA, recB, recC, static_cast<uint32_t>(L.n), L.width, L.height, L.tiles_x, bg[0], \
-      bg[1], bg[2], T, stop, grad_rgb, rgrad)
-  if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16);
-  else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8);
-  else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND_BWD(16, 32);
+  const uint32_t* egid = at<uint32_t>(frame, L.egid);
+  float4* gbuf = at<float4>(frame, L.gbuf);
+#define R4G_BLEND_BWD(TW_, TH_)                                                                    \
+  {                                                                                                \
+    const size_t slab = sizeof(float) * 9 * Blend<TW_, TH_>::NW * Blend<TW_, TH_>::NT;            \
+    cudaFuncSetAttribute(blend_bwd_kernel<TW_, TH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                         static_cast<int>(slab));                                                  \
+    blend_bwd_kernel<TW_, TH_><<<L.ntiles, Blend<TW_, TH_>::NT, slab, s>>>(                        \
+        ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.n), static_cast<uint32_t>(L.cap), \
+        L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], T, stop, grad_rgb, gbuf);              \
+  }
+  if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16)
+  else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8)
+  else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND_BWD(16, 32)
   else return cudaErrorInvalidValue;
 #undef R4G_BLEND_BWD
   return cudaGetLastError();

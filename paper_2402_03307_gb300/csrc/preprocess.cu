@@ -398,17 +398,60 @@ __device__ __forceinline__ void rotor_normalize_bwd(const float rin[8], const Ro
     gr[k] = g1[k] + rn.delta * Pg[k] + gdot * (dd_de * Pr[k] + dd_dl2 * S(2) * r[k]);
 }
 
+constexpr int kBwdBlock = 128;
+
+// The backward runs over the depth order, whose first n_visible entries are
+// the Gaussians with tiles, so every warp is full. Each warp first sums, for
+// each of its 32 Gaussians in turn, the per-pair gradients the blend
+// backward wrote (a Gaussian's pairs are contiguous, [offs[j], offs[j] + cnt)),
+// reading them coalesced; then every thread runs its Gaussian's chain rule.
 template <typename S, bool kScaleBF16, bool kShBF16>
-__global__ void __launch_bounds__(kPreBlock)
-    preprocess_bwd_kernel(r4g_gaussians g, CamDev cam, float t, const uint32_t* __restrict__ touched,
-                          const float* __restrict__ rgrad, int sh_degree, bool temporal_cull,
-                          r4g_grads out) {
-  const int i = blockIdx.x * kPreBlock + threadIdx.x;
-  if (i >= g.n || touched[i] == 0) return;
-  const float4* rg4 = reinterpret_cast<const float4*>(rgrad + static_cast<size_t>(i) * 12);
-  const float4 ga = rg4[0];  // d mean2d.x, d mean2d.y, d conic a, d conic b
-  const float4 gb = rg4[1];  // d conic c, d opacity_t
-  const float4 gc = rg4[2];  // d r, d g, d b
+__global__ void __launch_bounds__(kBwdBlock, 4)
+    preprocess_bwd_kernel(r4g_gaussians g, CamDev cam, float t, const uint32_t* __restrict__ order,
+                          const uint32_t* __restrict__ offs, const uint32_t* __restrict__ touched,
+                          const float4* __restrict__ gbuf, const FrameHeader* hdr, int sh_degree,
+                          bool temporal_cull, r4g_grads out) {
+  const int j = blockIdx.x * kBwdBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int nvis = static_cast<int>(hdr->n_visible);
+  if ((hdr->status & 1u) || (j - lane) >= nvis) return;  // warp-uniform (overflowed frame: no gradient)
+  const bool mine = j < nvis;
+  const uint32_t gi = mine ? order[j] : 0u;
+  const uint32_t o = mine ? offs[j] : 0u;
+  const uint32_t cnt = mine ? touched[gi] : 0u;
+  // warp-cooperative gather of the pair gradients: lane l adds pairs l, l+32, ...
+  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+  for (int q = 0; q < 32; ++q) {
+    const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
+    if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
+    const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
+    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t k = lane; k < qc; k += 32) {
+      const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
+      const float4 x = pr[0], y = pr[1], z = pr[2];
+      v[0] += x.x; v[1] += x.y; v[2] += x.z; v[3] += x.w;
+      v[4] += y.x; v[5] += y.y;
+      v[6] += z.x; v[7] += z.y; v[8] += z.z;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], sh);
+    }
+    if (lane == q) {
+      ga = make_float4(v[0], v[1], v[2], v[3]);
+      gb = make_float4(v[4], v[5], 0.f, 0.f);
+      gc = make_float4(v[6], v[7], v[8], 0.f);
+    }
+  }
+  if (cnt == 1) {
+    const float4* pr = gbuf + 3 * static_cast<size_t>(o);
+    ga = pr[0];
+    gb = pr[1];
+    gc = pr[2];
+  }
+  if (!mine) return;
+  const int i = static_cast<int>(gi);
   Fwd f;
   Geo<S> G;
   forward_geometry<S, kScaleBF16>(g, i, cam, t, temporal_cull, f, &G);
@@ -418,14 +461,25 @@ __global__ void __launch_bounds__(kPreBlock)
   // ---- colour: rgb = max(0, sum_k Y_k(dir) c_k + 0.5)
   const float grgb[3] = {f.rgb_pos[0] ? gc.x : 0.f, f.rgb_pos[1] ? gc.y : 0.f, f.rgb_pos[2] ? gc.z : 0.f};
   const int nb = (sh_degree + 1) * (sh_degree + 1);
-  float* gsh = out.sh + static_cast<size_t>(i) * 48;
   float wk[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    wk[k] = shc[k][0] * grgb[0] + shc[k][1] * grgb[1] + shc[k][2] * grgb[2];
-    if (k < nb) {
+  for (int k = 0; k < 16; ++k) wk[k] = shc[k][0] * grgb[0] + shc[k][1] * grgb[1] + shc[k][2] * grgb[2];
+  {
+    // d c_k = Y_k d rgb, accumulated as 16-byte vectors over the 48-float row
+    float4* gsh4 = reinterpret_cast<float4*>(out.sh + static_cast<size_t>(i) * 48);
+    const int nvec = (nb * 3 + 3) / 4;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += Y[k] * grgb[ch];
+    for (int v = 0; v < 12; ++v) {
+      if (v < nvec) {
+        float4 a = gsh4[v];
+        float* ap = reinterpret_cast<float*>(&a);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int e = 4 * v + h;
+          if (e < nb * 3) ap[h] += Y[e / 3] * grgb[e % 3];
+        }
+        gsh4[v] = a;
+      }
     }
   }
   float gmu[3];
@@ -577,38 +631,60 @@ __global__ void __launch_bounds__(kPreBlock)
   rotor_normalize_bwd<S>(G.p.rot, G.rn, grh, grot);
 
   // ---- write (accumulate)
-  float* gm = out.mean + static_cast<size_t>(i) * 4;
-  gm[0] += static_cast<float>(gmxyz[0]);
-  gm[1] += static_cast<float>(gmxyz[1]);
-  gm[2] += static_cast<float>(gmxyz[2]);
-  gm[3] += static_cast<float>(-gdt);
-  float* gr = out.rotor + static_cast<size_t>(i) * 8;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) gr[k] += static_cast<float>(grot[k]);
-  float* gl = out.logscale + static_cast<size_t>(i) * 4;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) gl[k] += static_cast<float>(gsc2[k] * S(2) * G.sc2[k]);
+  // accumulate (+=) with 16-byte vector accesses
+  float4* gm = reinterpret_cast<float4*>(out.mean) + i;
+  float4 vm = *gm;
+  vm.x += static_cast<float>(gmxyz[0]);
+  vm.y += static_cast<float>(gmxyz[1]);
+  vm.z += static_cast<float>(gmxyz[2]);
+  vm.w += static_cast<float>(-gdt);
+  *gm = vm;
+  float4* gr = reinterpret_cast<float4*>(out.rotor) + 2 * static_cast<size_t>(i);
+  float4 r0 = gr[0], r1 = gr[1];
+  r0.x += static_cast<float>(grot[0]); r0.y += static_cast<float>(grot[1]);
+  r0.z += static_cast<float>(grot[2]); r0.w += static_cast<float>(grot[3]);
+  r1.x += static_cast<float>(grot[4]); r1.y += static_cast<float>(grot[5]);
+  r1.z += static_cast<float>(grot[6]); r1.w += static_cast<float>(grot[7]);
+  gr[0] = r0;
+  gr[1] = r1;
+  float4* gl = reinterpret_cast<float4*>(out.logscale) + i;
+  float4 vl = *gl;
+  vl.x += static_cast<float>(gsc2[0] * S(2) * G.sc2[0]);
+  vl.y += static_cast<float>(gsc2[1] * S(2) * G.sc2[1]);
+  vl.z += static_cast<float>(gsc2[2] * S(2) * G.sc2[2]);
+  vl.w += static_cast<float>(gsc2[3] * S(2) * G.sc2[3]);
+  *gl = vl;
   out.logit[i] += static_cast<float>(g_o) * f.opacity * (1.0f - f.opacity);
 }
 
+struct BwdIn {
+  const uint32_t *order, *offs, *touched;
+  const float4* gbuf;
+  const FrameHeader* hdr;
+};
+
 template <typename S, bool A, bool B>
-static void launch_pre_bwd_t(const r4g_gaussians& g, const CamDev& cam, float t,
-                             const uint32_t* touched, const float* rgrad, int nblocks,
+static void launch_pre_bwd_t(const r4g_gaussians& g, const CamDev& cam, float t, const BwdIn& in, int nblocks,
                              int sh_degree, bool tc, const r4g_grads& out, cudaStream_t s) {
-  preprocess_bwd_kernel<S, A, B><<<nblocks, kPreBlock, 0, s>>>(g, cam, t, touched, rgrad, sh_degree, tc, out);
+  preprocess_bwd_kernel<S, A, B><<<nblocks, kBwdBlock, 0, s>>>(g, cam, t, in.order, in.offs, in.touched, in.gbuf,
+                                                               in.hdr, sh_degree, tc, out);
 }
 
 cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const CamDev& cam, float t,
                                   const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, r4g_grads grads, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
-  const uint32_t* touched = at<uint32_t>(frame, L.touched);
-  const float* rgrad = at<float>(frame, L.recgrad);
+  BwdIn in;
+  in.order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
+  in.offs = at<uint32_t>(frame, L.offs);
+  in.touched = at<uint32_t>(frame, L.touched);
+  in.gbuf = at<float4>(frame, L.gbuf);
+  in.hdr = at<FrameHeader>(frame, L.header);
   const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
   const bool f64 = flags & R4G_FLAG_FP64_SLICE;
   const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
-  const int nb = L.nblocks;
-#define R4G_PB(S_, A_, B_) launch_pre_bwd_t<S_, A_, B_>(g, cam, t, touched, rgrad, nb, sh_degree, tc, grads, s)
+  const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
+#define R4G_PB(S_, A_, B_) launch_pre_bwd_t<S_, A_, B_>(g, cam, t, in, nb, sh_degree, tc, grads, s)
   if (f64) {
     if (sb && hb) R4G_PB(double, true, true);
     else if (sb) R4G_PB(double, true, false);

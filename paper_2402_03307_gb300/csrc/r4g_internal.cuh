@@ -42,8 +42,8 @@ struct FrameHeader {
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
   size_t header, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, srect, chunks, blocksum, keys0, vals0,
-      keys1, vals1,
-      ranges, tfinal, last, sortcnt, onesweep, recgrad, total;
+      keys1, vals1, egid, gbuf,
+      ranges, tfinal, last, sortcnt, onesweep, total;
   int64_t n, cap;
   int width, height, tile_w, tile_h, tiles_x, tiles_y, ntiles;
   int nblocks;       // preprocess blocks (kPreBlock Gaussians each)
@@ -115,6 +115,9 @@ cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* til
 // 64-bit (tile << 32 | depth bits) keys of the sorted list, for export
 cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                                const uint32_t* vals, uint64_t* out, cudaStream_t s);
+// Gaussian index of each sorted pair (the sort carries emission indices)
+cudaError_t launch_export_values(const FrameLayout& L, void* frame, const uint32_t* vals, uint32_t* out,
+                                 cudaStream_t s);
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, float* out_rgb, float* out_T,
                              uint32_t* out_last, bool count, cudaStream_t s);
