@@ -299,15 +299,111 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
   }
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-thread state of the backward walk (two pixels, packed).
+struct BwdState {
+  float2 PX, T, U, gr, gg, gb;  // T_{i+1}; U = colour-gradient behind i + T_N (g . bg); d L / d out
+  uint32_t L0, L1;              // stop positions
+};
+
+// Backward of one list entry at position p for the thread's two pixels.
+// With alpha_i = opacity_t 2^power' and the per-pixel upstream gradient g:
+//   T_i = T_{i+1} / (1 - alpha_i),
+//   dL/dalpha_i = (g . c_i) T_i - U_{i+1} / (1 - alpha_i),
+//   U_i = U_{i+1} + (g . c_i) alpha_i T_i,
+//   dL/dc_i = g alpha_i T_i.
+// The entry's geometric gradients are all linear in dq = dL/dalpha_i alpha_i
+// (dalpha/dpower = alpha), so the thread accumulates the raw moments
+//   D = sum dq, M0 = sum dq dx, M1 = sum dq dy, Qxx = sum dq dx^2,
+//   Qxy = sum dq dx dy, Qyy = sum dq dy^2
+// (the two pixels share dy) and the conversion to d mean2d, d conic and
+// d opacity_t happens once per (tile, entry). Out: v[9] = D, M0, M1, Qxx,
+// Qxy, Qyy, dr, dg, db. Returns false when no pixel of the warp takes it.
+template <bool kClamp>
+__device__ __forceinline__ bool bwd_entry(BwdState& S, const StagedG& gs, uint32_t p, float2 PY, float v[9]) {
+  const PairEval ev = eval_pair(gs, S.PX, PY);
+  const bool a0 = p < S.L0 && ev.v0, a1 = p < S.L1 && ev.v1;
+  if (!__any_sync(0xffffffffu, a0 || a1)) return false;
+  const float2 ar = make_float2(a0 ? ev.araw.x : 0.0f, a1 ? ev.araw.y : 0.0f);
+  float2 al = ar;
+  if constexpr (kClamp) al = make_float2(fminf(ar.x, kAlphaMax), fminf(ar.y, kAlphaMax));
+  const float2 om = __ffma2_rn(al, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - alpha >= 0.01
+  const float2 iom = make_float2(a0 ? rcp_approx(om.x) : 1.0f, a1 ? rcp_approx(om.y) : 1.0f);
+  const float2 Ti = __fmul2_rn(S.T, iom);
+  const float2 w = __fmul2_rn(al, Ti);
+  const float4 p3 = gs.p3, p4 = gs.p4;
+  const float2 gc = __ffma2_rn(S.gb, make_float2(p4.x, p4.y),
+                               __ffma2_rn(S.gg, make_float2(p3.z, p3.w), __fmul2_rn(S.gr, make_float2(p3.x, p3.y))));
+  float2 da = __fmul2_rn(iom, __ffma2_rn(gc, S.T, make_float2(-S.U.x, -S.U.y)));
+  S.U = __ffma2_rn(gc, w, S.U);
+  S.T = Ti;
+  if constexpr (kClamp) {  // a clamped alpha does not depend on power' or opacity_t
+    if (ar.x > kAlphaMax) da.x = 0.0f;
+    if (ar.y > kAlphaMax) da.y = 0.0f;
+  }
+  const float2 dq = __fmul2_rn(da, ar);  // zero for pixels that do not take the entry
+  const float2 t = __fmul2_rn(dq, ev.dx);
+  const float2 q = __fmul2_rn(t, ev.dx);
+  const float dy = ev.dy.x;
+  v[0] = dq.x + dq.y;
+  v[1] = t.x + t.y;
+  v[2] = dy * v[0];
+  v[3] = q.x + q.y;
+  v[4] = dy * v[1];
+  v[5] = dy * v[2];
+  const float2 cr = __fmul2_rn(S.gr, w), cg = __fmul2_rn(S.gg, w), cb = __fmul2_rn(S.gb, w);
+  v[6] = cr.x + cr.y;
+  v[7] = cg.x + cg.y;
+  v[8] = cb.x + cb.y;
+  return true;
+}
+
+// Sum v[0..8] over the warp: values 0..7 by a transpose reduction (they end
+// one per group of 4 lanes: value k in lane 4k), value 8 by a butterfly.
+__device__ __forceinline__ void warp_reduce9(float v[9], int lane) {
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float send = up ? v[k] : v[k + 4];
+      const float keep = up ? v[k + 4] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float send = up ? v[k] : v[k + 2];
+      const float keep = up ? v[k + 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {
+    const bool up = lane & 4;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v[8] += __shfl_xor_sync(0xffffffffu, v[8], o);
+}
+
 // Backward of the blend. Each pixel re-walks its list back to front from its
-// stop position and the stored final transmittance T_N: T_i = T_{i+1} / (1 - a_i),
-// the colour already accumulated behind i is carried along, and per-Gaussian
-// gradients (d mean2d, d conic, d opacity_t, d rgb) are summed over the two
-// pixels of a thread, then over the warp with a transpose reduction (14
-// shuffles for 9 values), then over the CTA's warps in a fixed order in
-// shared memory, and written once per (tile, Gaussian) pair into the
-// per-pair buffer (indexed by the pair's emission index); a gather kernel
-// then sums each Gaussian's pairs. No float atomics: the gradient is
+// stop position and the stored final transmittance T_N (bwd_entry). Per
+// (warp, entry) the raw moments are summed over the warp (warp_reduce9) into
+// the warp's shared-memory slab; at the end of each batch every entry sums
+// the warps' slabs in a fixed order, converts the moments to d mean2d,
+// d conic, d opacity_t and d rgb, and writes them once into the per-pair
+// buffer (indexed by the pair's emission index), which the preprocess
+// backward sums per Gaussian. No float atomics: the gradient is
 // deterministic.
 template <int TW, int TH>
 __global__ void __launch_bounds__(Blend<TW, TH>::NT)
@@ -330,13 +426,13 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
   const bool in0 = px < width && py < height;
   const bool in1 = px + 1 < width && py < height;
-  const float2 PX = make_float2(px + 0.5f, px + 1.5f);
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
   const size_t plane = static_cast<size_t>(width) * height;
-  float T[2] = {1.f, 1.f}, S[2] = {0.f, 0.f}, bgg[2] = {0.f, 0.f};
-  float g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  BwdState S;
+  S.PX = make_float2(px + 0.5f, px + 1.5f);
+  float T[2] = {1.f, 1.f}, U[2] = {0.f, 0.f}, g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   uint32_t L[2] = {0u, 0u};
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -347,13 +443,19 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
       g[k][0] = grad_rgb[pix];
       g[k][1] = grad_rgb[plane + pix];
       g[k][2] = grad_rgb[2 * plane + pix];
-      bgg[k] = T[k] * (bg0 * g[k][0] + bg1 * g[k][1] + bg2 * g[k][2]);  // (d out / d T_N) . g, times T_N
+      U[k] = T[k] * (bg0 * g[k][0] + bg1 * g[k][1] + bg2 * g[k][2]);  // T_N (g . bg)
     }
   }
+  S.T = make_float2(T[0], T[1]);
+  S.U = make_float2(U[0], U[1]);
+  S.gr = make_float2(g[0][0], g[1][0]);
+  S.gg = make_float2(g[0][1], g[1][1]);
+  S.gb = make_float2(g[0][2], g[1][2]);
+  S.L0 = L[0];
+  S.L1 = L[1];
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  const uint32_t mine = L[0] > L[1] ? L[0] : L[1];
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, mine);  // this warp's walk ends here
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, L[0] > L[1] ? L[0] : L[1]);  // this warp's walk ends here
   if (lane == 0 && wmax) atomicMax(&s_max, wmax);
   __syncthreads();
   const int maxL = static_cast<int>(s_max);
@@ -379,86 +481,19 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
         const int jj = 31 - __clz(bits);
         bits &= ~(1u << jj);
         const uint32_t p = static_cast<uint32_t>(b0 + j0 + jj);
-        const StagedG& gs = sg[j0 + jj];
-        const PairEval ev = eval_pair(gs, PX, PY);
-        const bool clamp = (cbits >> jj) & 1u;
-        const float4 p1 = gs.p1, p2 = gs.p2, p3 = gs.p3, p4 = gs.p4;
-        const float araw[2] = {ev.araw.x, ev.araw.y};
-        const float ee[2] = {ev.e.x, ev.e.y};
-        const float dxs[2] = {ev.dx.x, ev.dx.y};
-        const bool vv[2] = {ev.v0, ev.v1};
-        float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (p < L[k] && vv[k]) {
-            any = true;
-            const float alpha = clamp ? fminf(kAlphaMax, araw[k]) : araw[k];
-            const float iom = 1.0f / (1.0f - alpha);  // alpha <= 0.99
-            const float Ti = T[k] * iom;
-            const float w = alpha * Ti;
-            v[6] += g[k][0] * w;
-            v[7] += g[k][1] * w;
-            v[8] += g[k][2] * w;
-            const float gc = g[k][0] * p3.x + g[k][1] * p3.z + g[k][2] * p4.x;
-            const float dalpha = gc * Ti - (S[k] + bgg[k]) * iom;
-            S[k] += gc * w;
-            T[k] = Ti;
-            const float da = (clamp && araw[k] > kAlphaMax) ? 0.0f : dalpha;
-            // alpha = o 2^power'; d alpha / d power' = alpha ln 2
-            const float dpp = da * araw[k] * kLn2;
-            const float dx = dxs[k], dy = ev.dy.x;
-            v[5] += da * ee[k];                                  // d opacity_t
-            v[0] -= dpp * (2.0f * p1.x * dx + p1.z * dy);        // d mean2d.x
-            v[1] -= dpp * (p1.z * dx + 2.0f * p2.x * dy);        // d mean2d.y
-            v[2] += dpp * dx * dx;                               // d A'
-            v[3] += dpp * dx * dy;                               // d B'
-            v[4] += dpp * dy * dy;                               // d C'
-          }
-        }
-        if (__any_sync(0xffffffffu, any)) {
-          // transpose reduction: values 0..7 end one per group of 4 lanes
-          {
-            const bool up = lane & 16;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float send = up ? v[k] : v[k + 4];
-              const float keep = up ? v[k + 4] : v[k];
-              v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-            }
-          }
-          {
-            const bool up = lane & 8;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              const float send = up ? v[k] : v[k + 2];
-              const float keep = up ? v[k + 2] : v[k];
-              v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-            }
-          }
-          {
-            const bool up = lane & 4;
-            const float send = up ? v[0] : v[1];
-            const float keep = up ? v[1] : v[0];
-            v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-          }
-          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-          v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v[8] += __shfl_xor_sync(0xffffffffu, v[8], o);
+        float v[9];
+        const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true>(S, sg[j0 + jj], p, PY, v)
+                                               : bwd_entry<false>(S, sg[j0 + jj], p, PY, v);
+        if (took) {
+          warp_reduce9(v, lane);
           float* dst = s_slab + (warp * BS + j0 + jj) * 9;
-          if ((lane & 3) == 0) {
-            const int id = lane >> 2;  // value index 0..7
-            // A', B', C' -> conic a, b, c: A' = -L a / 2, B' = -L b, C' = -L c / 2
-            const float scale = (id == 2 || id == 4) ? -0.5f * kLog2e : (id == 3 ? -kLog2e : 1.0f);
-            dst[id] = v[0] * scale;
-          }
+          if ((lane & 3) == 0) dst[lane >> 2] = v[0];
           if (lane == 1) dst[8] = v[8];
         }
       }
     }
     __syncthreads();
-    // each entry of the batch: sum over the warps (fixed order), one write
+    // each entry of the batch: sum over the warps (fixed order), convert, one write
     if (idx < n) {
       float acc[9];
 #pragma unroll
@@ -470,10 +505,24 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
       }
       const uint32_t e = sE[threadIdx.x];
       if (e < cap) {
+        const StagedG& gs = sg[threadIdx.x];
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        if (__float_as_uint(gs.p5.z) & ((1u << B::NW) - 1u)) {
+          // power' = A' dx^2 + B' dx dy + C' dy^2 with A' = -a/(2 ln 2), B' = -b/ln 2,
+          // C' = -c/(2 ln 2) for the conic (a, b, c); d power/d mean = (a dx + b dy, b dx + c dy)
+          const float Ap = gs.p1.x, Bp = gs.p1.z, Cp = gs.p2.x, o = gs.p2.z;
+          r0.x = -(2.0f * Ap * acc[1] + Bp * acc[2]) * kLn2;  // d mean2d.x
+          r0.y = -(Bp * acc[1] + 2.0f * Cp * acc[2]) * kLn2;  // d mean2d.y
+          r0.z = -0.5f * acc[3];                             // d conic a
+          r0.w = -acc[4];                                    // d conic b
+          r1.x = -0.5f * acc[5];                             // d conic c
+          r1.y = o > 0.0f ? acc[0] / o : 0.0f;               // d opacity_t (alpha = opacity_t 2^power')
+          r2 = make_float4(acc[6], acc[7], acc[8], 0.0f);    // d rgb
+        }
         float4* d = gbuf + 3 * static_cast<size_t>(e);
-        d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        d[1] = make_float4(acc[4], acc[5], 0.0f, 0.0f);
-        d[2] = make_float4(acc[6], acc[7], acc[8], 0.0f);
+        d[0] = r0;
+        d[1] = r1;
+        d[2] = r2;
       }
     }
   }
