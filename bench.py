@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-view batched workload")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian BF16 workload")
+    ap.add_argument("--batch-only", action="store_true", help="batched and large workloads only (profiling)")
     ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
     ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
     return ap.parse_args()
@@ -156,7 +159,9 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     if args.train_only:
-        return {"train": train_bench(args, rend, params, dev, stream)}
+        return {"train": train_bench(args, rend, params, dev, stream, flush)}
+    if args.batch_only:
+        return {"batched": batch_bench(args, dev, stream, flush), "large": large_bench(args, dev, stream, flush)}
 
     def barrier():
         if world > 1:
@@ -269,50 +274,215 @@ def run_ours(args, rank, world, local):
 
     # ---- training step: 4 views forward + L1 + backward --------------------------
     if not args.no_train and not args.frames_only:
-        out["train"] = train_bench(args, rend, params, dev, stream)
+        out["train"] = train_bench(args, rend, params, dev, stream, flush)
+    # ---- batched views (autotuned tile, CUDA graph) and the large BF16 scene ---------
+    if not args.no_batch and not args.frames_only:
+        out["batched"] = batch_bench(args, dev, stream, flush)
+    if not args.no_large and not args.frames_only:
+        out["large"] = large_bench(args, dev, stream, flush)
     # ---- end to end through host buffers ---------------------------------------------
     if not args.no_e2e and not args.frames_only:
         out["e2e"] = e2e_bench(args, rend, g, dev, stream, frames, cap)
     return out
 
 
-def train_bench(args, rend, params, dev, stream):
+def _timed(fn, steps: int, stream, flush=None) -> float:
+    """Mean ms of fn() over `steps` calls, CUDA events on `stream` around each
+    call; the L2 flush (when given) runs between calls, outside the events."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def _packed_target(views, seed, dev):
+    import numpy as np
     import torch
     import synth
+    parts = [synth.smooth_target(seed + k, cam.width, cam.height).reshape(-1) for k, (cam, _) in enumerate(views)]
+    return torch.as_tensor(np.concatenate(parts)).to(dev)
+
+
+def train_bench(args, rend, params, dev, stream, flush):
+    """Training step of 4 views at seeded (t, angle), 1352x1014, L1 loss
+    against a seeded smooth target: (a) through the autograd function of the
+    batched render (one batched call), (b) the plain path, one single-view
+    render + backward per view, (c) the batched step captured in a CUDA graph."""
+    import torch
+    import synth
+    import paper_2402_03307_gb300 as r4g
 
     views = synth.train_views(seed=33, views=TRAIN_VIEWS)
-    target = torch.as_tensor(synth.smooth_target(34, WIDTH, HEIGHT)).to(dev)
+    target = _packed_target([(c, t) for c, t in views], 34, dev)
+    npix = target.numel()
+    leaves = {k: v.clone().requires_grad_(True) for k, v in params.items()}
+
+    def step_autograd():
+        for v in leaves.values():
+            v.grad = None
+        img = r4g.render_batch(leaves, views, renderer=rend)
+        loss = (img - target).abs().mean()
+        loss.backward()
+
     grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
-    caps = []
-    for cam, t in views:
-        r = rend.render(params, cam, t)
-        caps.append(int(rend.status(r)[1] * 1.1) + 1024)
+    res0 = [rend.render(params, cam, t) for cam, t in views]
+    caps = [int(rend.status(r)[1] * 1.1) + 1024 for r in res0]
     frames = [rend.new_frame(N_GAUSS, WIDTH, HEIGHT, c, dev) for c in caps]
     imgs = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev) for _ in views]
+    tviews = [target[k * 3 * WIDTH * HEIGHT:(k + 1) * 3 * WIDTH * HEIGHT].view(3, HEIGHT, WIDTH)
+              for k in range(len(views))]
     gimg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
-    inv = 1.0 / (3 * WIDTH * HEIGHT * len(views))
+    inv = 1.0 / npix
 
-    def step():
+    def step_plain():
         for v in grads.values():
             v.zero_()
-        for (cam, t), fr, im, c in zip(views, frames, imgs, caps):
+        for (cam, t), fr, im, c, tv in zip(views, frames, imgs, caps, tviews):
             res = rend.render(params, cam, t, frame=fr, key_capacity=c, out=im, check=False)
-            torch.sign(im - target, out=gimg)
+            torch.sign(im - tv, out=gimg)
             gimg.mul_(inv)
             rend.backward(params, cam, t, res, gimg, grads)
 
+    graph = r4g.BatchGraph(rend, params, views, grad_fn=lambda img: torch.sign(img - target) * inv)
     for _ in range(3):
-        step()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.train_steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.train_steps
-    return {"value": round(1000.0 / ms, 3), "unit": "it/s", "ms_per_it": round(ms, 3), "views": TRAIN_VIEWS,
-            "steps": args.train_steps, "loss": "L1 vs seeded smooth target (sign gradient in torch)"}
+        step_autograd()
+        step_plain()
+        graph.replay()
+    ms_a = _timed(step_autograd, args.train_steps, stream, flush)
+    ms_p = _timed(step_plain, args.train_steps, stream, flush)
+    ms_g = _timed(graph.replay, args.train_steps, stream, flush)
+    return {"value": round(1000.0 / ms_a, 3), "unit": "it/s", "ms_per_it": round(ms_a, 3), "views": TRAIN_VIEWS,
+            "steps": args.train_steps,
+            "path": "autograd.Function over the batched render (one call for the 4 views), L1 loss in torch",
+            "plain_path": {"value": round(1000.0 / ms_p, 3), "ms_per_it": round(ms_p, 3),
+                           "path": "per view: r4g_render + r4g_render_backward (FP32, 16x16)"},
+            "graph": {"value": round(1000.0 / ms_g, 3), "ms_per_it": round(ms_g, 3),
+                      "path": "batched render + L1 sign gradient + batched backward in one CUDA graph"},
+            "l2": "flushed between steps"}
+
+
+def batch_bench(args, dev, stream, flush):
+    """Batched multi-view render and backward: 100k Gaussians, 16 views of
+    uneven resolution (6 x 800x800, 5 x 640x480, 5 x 1352x1014), one batched
+    call per step, tile shape from the autotuner, captured in a CUDA graph;
+    against the plain path (a single-view 16x16 render per view)."""
+    import torch
+    import synth
+    import paper_2402_03307_gb300 as r4g
+
+    g = synth.gaussians(100_000, 5, mean_lo=-3.0, mean_hi=3.0)
+    params = {k: torch.as_tensor(v).to(dev).contiguous() for k, v in g.items()}
+    views = synth.batched_views(6)
+    rend = r4g.Renderer()
+    tune = rend.autotune(params, views, backward=True, reps=3)
+    target = _packed_target(views, 60, dev)
+    inv = 1.0 / target.numel()
+    gf = r4g.BatchGraph(rend, params, views)
+    gt = r4g.BatchGraph(rend, params, views, grad_fn=lambda img: torch.sign(img - target) * inv)
+    alt = [synth.batched_views(6 + 100 * j) for j in range(1, 4)]  # same sizes, other cameras / times
+    alt = [[(c2, t2) for (c2, t2) in a] for a in alt]
+    sizes = [(c.width, c.height) for c, _ in views]
+    alt = [a for a in alt if [(c.width, c.height) for c, _ in a] == sizes] or [views]
+    it = {"k": 0}
+
+    def fwd():
+        gf.replay(alt[it["k"] % len(alt)])
+        it["k"] += 1
+
+    def train():
+        gt.replay(alt[it["k"] % len(alt)])
+        it["k"] += 1
+
+    plain = r4g.Renderer()
+    pf = []
+    for cam, t in views:
+        r = plain.render(params, cam, t)
+        c = int(plain.status(r)[1] * 1.1) + 1024
+        pf.append((cam, t, c, plain.new_frame(100_000, cam.width, cam.height, c, dev),
+                   torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=dev)))
+    pgrads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+    tv, off = [], 0
+    for cam, t, *_ in pf:
+        n = 3 * cam.width * cam.height
+        tv.append(target[off:off + n].view(3, cam.height, cam.width))
+        off += n
+
+    def plain_fwd():
+        for cam, t, c, fr, im in pf:
+            plain.render(params, cam, t, frame=fr, key_capacity=c, out=im, check=False)
+
+    def plain_train():
+        for v in pgrads.values():
+            v.zero_()
+        for (cam, t, c, fr, im), tt in zip(pf, tv):
+            res = plain.render(params, cam, t, frame=fr, key_capacity=c, out=im, check=False)
+            plain.backward(params, cam, t, res, torch.sign(im - tt) * inv, pgrads)
+
+    for f in (fwd, train, plain_fwd, plain_train):
+        for _ in range(3):
+            f()
+    steps = max(5, args.train_steps)
+    ms_f = _timed(fwd, steps, stream, flush)
+    ms_t = _timed(train, steps, stream, flush)
+    ms_pf = _timed(plain_fwd, steps, stream, flush)
+    ms_pt = _timed(plain_train, steps, stream, flush)
+    if gt.status()[0] != 0 or gf.status()[0] != 0:
+        raise RuntimeError("batched render overflowed its key buffer")
+    nv = len(views)
+    return {"workload": "100k 4D Gaussians, 16 views (6x 800x800, 5x 640x480, 5x 1352x1014), FP32",
+            "tile": f"{tune['tile'][0]}x{tune['tile'][1]}", "autotune_ms": tune["ms"],
+            "render": {"ms_per_batch": round(ms_f, 3), "views_per_s": round(nv * 1000.0 / ms_f, 1)},
+            "train": {"ms_per_batch": round(ms_t, 3), "it_per_s": round(1000.0 / ms_t, 2)},
+            "plain_path": {"render_ms_per_batch": round(ms_pf, 3), "train_ms_per_batch": round(ms_pt, 3)},
+            "speedup_vs_plain": {"render": round(ms_pf / ms_f, 3), "train": round(ms_pt / ms_t, 3)},
+            "launch": "one persistent blend launch per batch; whole step replayed as a CUDA graph",
+            "l2": "flushed between steps"}
+
+
+def large_bench(args, dev, stream, flush):
+    """Large scene: 2M Gaussians, 8 views at 1920x1080, training step (batched
+    render + L1 + batched backward, CUDA graph), with the scales and SH
+    coefficients stored in BF16 against the FP32 path; the BF16 images' error
+    against the FP32 images."""
+    import torch
+    import synth
+    import paper_2402_03307_gb300 as r4g
+
+    g = synth.gaussians(2_000_000, 7, mean_lo=-3.0, mean_hi=3.0)
+    p32 = {k: torch.as_tensor(v).to(dev).contiguous() for k, v in g.items()}
+    p16 = dict(p32)
+    p16["logscale"] = p32["logscale"].to(torch.bfloat16).contiguous()
+    p16["sh"] = p32["sh"].to(torch.bfloat16).contiguous()
+    views = synth.large_views(8, 8)
+    target = _packed_target(views, 70, dev)
+    inv = 1.0 / target.numel()
+    out = {"workload": "2M 4D Gaussians, 8 views 1920x1080, training step (graph)", "tile": "16x16"}
+    imgs = {}
+    for name, p in (("fp32", p32), ("bf16", p16)):
+        rend = r4g.Renderer()
+        gt = r4g.BatchGraph(rend, p, views, grad_fn=lambda img: torch.sign(img - target) * inv)
+        for _ in range(2):
+            gt.replay()
+        ms = _timed(gt.replay, 5, stream, flush)
+        if gt.status()[0] != 0:
+            raise RuntimeError("large batch overflowed its key buffer")
+        imgs[name] = gt.packed.clone()
+        out[name] = {"ms_per_step": round(ms, 2), "it_per_s": round(1000.0 / ms, 3),
+                     "param_bytes": int(sum(v.numel() * v.element_size() for v in p.values())),
+                     "keys": int(gt.status()[1])}
+        del gt
+    d = (imgs["bf16"] - imgs["fp32"]).abs()
+    mse = float((d.double() ** 2).mean())
+    out["bf16_vs_fp32"] = {"max_abs": float(d.max()), "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-30)), 2),
+                           "speedup": round(out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"], 3)}
+    return out
 
 
 def e2e_bench(args, rend, g, dev, stream, frames, cap):
@@ -394,7 +564,8 @@ def main():
         print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local)
-    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.frames_only or args.train_only):
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.frames_only or args.train_only
+                                          or args.batch_only):
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(out))

@@ -138,20 +138,22 @@ r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t
                            int64_t key_capacity, size_t* bytes /* host out */);
 
 /* Wait for `stream`, then report the frame's device-side status: R4G_OK,
- * R4G_EOVERFLOW, or R4G_ETIMEOUT when a radix-sort look-back wait reached its
- * iteration limit (the image of that render is then invalid). *keys_needed (host, may be NULL) receives the number of
- * (tile, Gaussian) pairs of the last render into this frame. */
+ * R4G_EOVERFLOW, R4G_ETIMEOUT when a radix-sort look-back wait reached its
+ * iteration limit, or R4G_EDEVICE when device views (r4g_render_batch) had
+ * other image sizes than the host views (the image of that render is then
+ * invalid). *keys_needed (host, may be NULL) receives the number of (tile,
+ * Gaussian) pairs of the last render into this frame. */
 r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
                             int64_t* keys_needed, void* stream);
 
 /* Statistics of the last render into a frame (waits for `stream`). */
 typedef struct r4g_frame_info {
-  int64_t n_visible;         /* Gaussians with at least one tile */
+  int64_t n_visible;         /* (view, Gaussian) items with at least one tile */
   int64_t key_count;         /* (tile, Gaussian) pairs in the sorted list */
   int64_t key_needed;        /* pairs the render needed (> key_count after an overflow) */
   int64_t composited_pairs;  /* (pixel, Gaussian) pairs composited; -1 unless the context
                                 has R4G_FLAG_COUNT_PAIRS */
-  int32_t status;            /* R4G_OK, R4G_EOVERFLOW or R4G_ETIMEOUT */
+  int32_t status;            /* R4G_OK, R4G_EOVERFLOW, R4G_ETIMEOUT or R4G_EDEVICE */
   int32_t reserved;
 } r4g_frame_info;
 r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, r4g_frame_info* out,
@@ -194,6 +196,64 @@ r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_c
                                float t, const float* grad_rgb, r4g_grads* grads,
                                void* frame, size_t frame_bytes, int64_t key_capacity,
                                void* stream);
+
+/* ---- batched views ------------------------------------------------------------
+ * The training of the paper (Sec. 4.2 implementation details; the batch
+ * training ablation of Sec. 4.5) renders several (camera, t) views of the
+ * same Gaussians per step.
+ * A batched call renders V = nviews views (1..64, of any sizes) in one launch
+ * sequence: the view-independent work of a Gaussian (rotor, R, Sigma4) is
+ * done once, every per-item stage runs over all V x N (view, Gaussian) items,
+ * the tile ids of all views form one list sorted once, and the blend is one
+ * persistent launch over the tiles of every view. Each view's image is
+ * bit-identical to r4g_render of that view.
+ *
+ * Packed images: out_rgb (and grad_rgb) hold the views one after another,
+ * view v as [3, height_v, width_v] planar FP32 starting at float offset
+ * 3 * sum_{u<v} width_u height_u; out_T (NULL or [sum width_v height_v])
+ * likewise. `views` is a HOST array (sizes and, when views_dev is NULL, the
+ * cameras and times). `views_dev`, when not NULL, is a DEVICE array of nviews
+ * r4g_view read by the kernels for the cameras and times, so a captured CUDA
+ * graph can be replayed with new cameras written there; its image sizes must
+ * equal the host views' (else the frame reports R4G_EDEVICE). No call
+ * allocates, synchronises or copies from host memory: a render and its
+ * backward can be captured in a CUDA graph (with stage timing off). */
+r4g_status r4g_batch_frame_bytes(const r4g_ctx* ctx, int64_t n, const r4g_view* views, int32_t nviews,
+                                 int64_t key_capacity, int32_t tile_w, int32_t tile_h,
+                                 size_t* bytes /* host out */);
+/* tile_w = tile_h = 0 in r4g_batch_frame_bytes means the context's tile shape. */
+r4g_status r4g_render_batch(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                            const r4g_view* views_dev, float* out_rgb, float* out_T, void* frame,
+                            size_t frame_bytes, int64_t key_capacity, void* stream);
+/* Backward of r4g_render_batch (same g, views and frame): adds into `grads`
+ * the gradient of L given dL/d out_rgb (packed like out_rgb), summed over the
+ * views. The cameras are those the render used (kept in the frame). */
+r4g_status r4g_render_batch_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views,
+                                     int32_t nviews, const float* grad_rgb, r4g_grads* grads, void* frame,
+                                     size_t frame_bytes, int64_t key_capacity, void* stream);
+
+/* Tile-shape autotuner. Times r4g_render_batch (and, when grad_rgb is not
+ * NULL, r4g_render_batch_backward into `grads`, which it changes) for the
+ * tile shapes 8x8, 16x16 and 16x32: one warm-up call and `reps` timed calls
+ * each, CUDA events on `stream`. A shape whose frame does not fit
+ * frame_bytes, whose views exceed the tile limit, or whose render overflows
+ * key_capacity is skipped (ms < 0). The fastest shape is set on the context
+ * and returned. The images do not depend on the tile shape (the per-pixel 3
+ * sigma test, Sec. 3.1). Synchronises the stream; not for graph capture. */
+typedef struct r4g_tune_result {
+  int32_t tile_w, tile_h;  /* the chosen shape */
+  float ms[3];             /* mean ms per call for 8x8, 16x16, 16x32 (< 0: skipped) */
+  int64_t keys_needed[3];  /* (tile, Gaussian) pairs of each shape (-1: not run) */
+} r4g_tune_result;
+r4g_status r4g_autotune_batch(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                              float* out_rgb, const float* grad_rgb, r4g_grads* grads, void* frame,
+                              size_t frame_bytes, int64_t key_capacity, int32_t reps, void* stream,
+                              r4g_tune_result* out /* host */);
+/* Change the context's tile shape (8x8, 16x16 or 16x32); frames sized for
+ * another shape must be re-queried. */
+r4g_status r4g_set_tile(r4g_ctx* ctx, int32_t tile_w, int32_t tile_h);
+/* The context's current configuration (host out). */
+r4g_status r4g_get_config(const r4g_ctx* ctx, r4g_config* out);
 
 /* ---- measurement ------------------------------------------------------------
  * Stage timing: when enabled on a context, r4g_render / r4g_render_backward

@@ -7,8 +7,8 @@ Importing it loads the library and fails if it has not been built
 """
 from . import abi  # noqa: F401
 from .render import (  # noqa: F401
-    PARAM_NAMES, Render4DFunction, Renderer, RenderResult, camera_struct, gaussians_struct, render,
-    sort_pairs,
+    PARAM_NAMES, BatchGraph, BatchResult, Render4DBatchFunction, Render4DFunction, Renderer, RenderResult,
+    camera_struct, gaussians_struct, render, render_batch, sort_pairs, view_struct, views_tensor,
 )
 
 abi.lib()  # fail loudly here if libr4g.so is missing

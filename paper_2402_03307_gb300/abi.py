@@ -48,6 +48,14 @@ class r4g_view(C.Structure):
     _fields_ = [("cam", r4g_camera), ("t", C.c_float)]
 
 
+class r4g_tune_result(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("ms", C.c_float * 3),
+                ("keys_needed", C.c_int64 * 3)]
+
+
+TUNE_SHAPES = ((8, 8), (16, 16), (16, 32))
+
+
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = [
     ("r4g_version", C.c_int32, []),
@@ -66,6 +74,19 @@ SIGNATURES = [
     ("r4g_render_backward", C.c_int, [C.c_void_p, C.POINTER(r4g_gaussians), C.POINTER(r4g_camera),
                                       C.c_float, C.c_void_p, C.POINTER(r4g_grads), C.c_void_p,
                                       C.c_size_t, C.c_int64, C.c_void_p]),
+    ("r4g_batch_frame_bytes", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(r4g_view), C.c_int32, C.c_int64,
+                                        C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("r4g_render_batch", C.c_int, [C.c_void_p, C.POINTER(r4g_gaussians), C.POINTER(r4g_view), C.c_int32,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64,
+                                   C.c_void_p]),
+    ("r4g_render_batch_backward", C.c_int, [C.c_void_p, C.POINTER(r4g_gaussians), C.POINTER(r4g_view),
+                                            C.c_int32, C.c_void_p, C.POINTER(r4g_grads), C.c_void_p,
+                                            C.c_size_t, C.c_int64, C.c_void_p]),
+    ("r4g_autotune_batch", C.c_int, [C.c_void_p, C.POINTER(r4g_gaussians), C.POINTER(r4g_view), C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.POINTER(r4g_grads), C.c_void_p, C.c_size_t,
+                                     C.c_int64, C.c_int32, C.c_void_p, C.POINTER(r4g_tune_result)]),
+    ("r4g_set_tile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("r4g_get_config", C.c_int, [C.c_void_p, C.POINTER(r4g_config)]),
     ("r4g_set_timing", C.c_int, [C.c_void_p, C.c_int32]),
     ("r4g_stage_times", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     ("r4g_sort_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
@@ -164,6 +185,57 @@ def r4g_render_backward(ctx, g: r4g_gaussians, cam: r4g_camera, t: float, grad_r
                         frame, frame_bytes, key_capacity, stream) -> None:
     check(lib().r4g_render_backward(ctx, C.byref(g), C.byref(cam), t, grad_rgb, C.byref(grads), frame,
                                     frame_bytes, key_capacity, stream), ctx)
+
+
+def view_array(views) -> C.Array:
+    """Host r4g_view[] from a sequence of r4g_view."""
+    arr = (r4g_view * len(views))()
+    for k, v in enumerate(views):
+        arr[k] = v
+    return arr
+
+
+def r4g_batch_frame_bytes(ctx, n: int, views, key_capacity: int, tile=(0, 0)) -> int:
+    out = C.c_size_t()
+    arr = view_array(views)
+    check(lib().r4g_batch_frame_bytes(ctx, n, arr, len(views), key_capacity, tile[0], tile[1], C.byref(out)), ctx)
+    return out.value
+
+
+def r4g_render_batch(ctx, g: r4g_gaussians, views, views_dev, out_rgb, out_T, frame, frame_bytes,
+                     key_capacity, stream) -> None:
+    arr = view_array(views)
+    check(lib().r4g_render_batch(ctx, C.byref(g), arr, len(views), views_dev, out_rgb, out_T, frame, frame_bytes,
+                                 key_capacity, stream), ctx)
+
+
+def r4g_render_batch_backward(ctx, g: r4g_gaussians, views, grad_rgb, grads: r4g_grads, frame, frame_bytes,
+                              key_capacity, stream) -> None:
+    arr = view_array(views)
+    check(lib().r4g_render_batch_backward(ctx, C.byref(g), arr, len(views), grad_rgb, C.byref(grads), frame,
+                                          frame_bytes, key_capacity, stream), ctx)
+
+
+def r4g_autotune_batch(ctx, g: r4g_gaussians, views, out_rgb, grad_rgb, grads, frame, frame_bytes,
+                       key_capacity, reps, stream) -> dict:
+    arr = view_array(views)
+    res = r4g_tune_result()
+    check(lib().r4g_autotune_batch(ctx, C.byref(g), arr, len(views), out_rgb, grad_rgb,
+                                   C.byref(grads) if grads is not None else None, frame, frame_bytes,
+                                   key_capacity, reps, stream, C.byref(res)), ctx)
+    return {"tile": (res.tile_w, res.tile_h),
+            "ms": {f"{w}x{h}": (res.ms[k] if res.ms[k] >= 0 else None) for k, (w, h) in enumerate(TUNE_SHAPES)},
+            "keys_needed": {f"{w}x{h}": res.keys_needed[k] for k, (w, h) in enumerate(TUNE_SHAPES)}}
+
+
+def r4g_set_tile(ctx, tile_w: int, tile_h: int) -> None:
+    check(lib().r4g_set_tile(ctx, tile_w, tile_h), ctx)
+
+
+def r4g_get_config(ctx) -> r4g_config:
+    cfg = r4g_config()
+    check(lib().r4g_get_config(ctx, C.byref(cfg)), ctx)
+    return cfg
 
 
 STAGES = ("preprocess", "binning", "sort", "ranges", "blend", "blend_bwd", "preprocess_bwd")

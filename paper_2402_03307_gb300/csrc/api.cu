@@ -48,25 +48,6 @@ bool tile_ok(int tw, int th) {
   return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 16 && th == 32);
 }
 
-r4g::CamDev make_cam(const r4g_camera& c) {
-  r4g::CamDev d;
-  for (int k = 0; k < 3; ++k) {
-    for (int j = 0; j < 3; ++j) d.R[3 * k + j] = c.world_to_cam[4 * k + j];
-    d.t[k] = c.world_to_cam[4 * k + 3];
-  }
-  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
-    double acc = 0;
-    for (int k = 0; k < 3; ++k) acc -= static_cast<double>(d.R[3 * k + j]) * d.t[k];
-    d.pos[j] = static_cast<float>(acc);
-  }
-  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
-  d.limx = static_cast<float>(r4g::kClampFov * (c.width / (2.0 * c.fx)));
-  d.limy = static_cast<float>(r4g::kClampFov * (c.height / (2.0 * c.fy)));
-  d.width = c.width;
-  d.height = c.height;
-  return d;
-}
-
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 r4g_status check_gaussians(r4g_ctx* ctx, const r4g_gaussians* g) {
@@ -137,20 +118,43 @@ namespace r4g {
 
 void set_last_error(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
 
-FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h) {
+FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nviews, int64_t cap, int tile_w,
+                        int tile_h) {
   FrameLayout L{};
   L.n = n;
   L.cap = cap;
-  L.width = width;
-  L.height = height;
+  L.nviews = nviews;
+  L.m = n * nviews;
   L.tile_w = tile_w;
   L.tile_h = tile_h;
-  L.tiles_x = (width + tile_w - 1) / tile_w;
-  L.tiles_y = (height + tile_h - 1) / tile_h;
-  L.ntiles = L.tiles_x * L.tiles_y;
-  L.nblocks = static_cast<int>((n + kPreBlock - 1) / kPreBlock);
+  int64_t tiles = 0, pix = 0, td = 0;
+  int maxvt = 0;
+  for (int v = 0; v < nviews; ++v) {
+    ViewGeom& G = L.geom[v];
+    G.width = widths[v];
+    G.height = heights[v];
+    G.tiles_x = (G.width + tile_w - 1) / tile_w;
+    G.tiles_y = (G.height + tile_h - 1) / tile_h;
+    G.tile_off = static_cast<uint32_t>(tiles);
+    G.pix_off = static_cast<uint32_t>(pix);
+    G.tdiff_off = static_cast<uint32_t>(td);
+    tiles += static_cast<int64_t>(G.tiles_x) * G.tiles_y;
+    pix += static_cast<int64_t>(G.width) * G.height;
+    td += static_cast<int64_t>(G.tiles_x + 1) * (G.tiles_y + 1);
+    if (G.tiles_x * G.tiles_y > maxvt) maxvt = G.tiles_x * G.tiles_y;
+  }
+  L.ntiles = static_cast<int>(tiles);
+  L.npix = pix;
+  L.tdiff_words = static_cast<int>(td);
+  L.max_view_tiles = maxvt;
+  L.width = L.geom[0].width;
+  L.height = L.geom[0].height;
+  L.tiles_x = L.geom[0].tiles_x;
+  L.tiles_y = L.geom[0].tiles_y;
+  const int64_t m = L.m;
+  L.nblocks = static_cast<int>((m + kPreBlock - 1) / kPreBlock);
   L.sort_ctas = sort_ctas_for(cap);
-  L.depth_ctas = sort_ctas_for(n);
+  L.depth_ctas = sort_ctas_for(m);
   int tb = 0;
   while ((int64_t(1) << tb) < L.ntiles) ++tb;
   L.tile_bits = tb;
@@ -159,21 +163,24 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
   L.order_in_1 = dpasses % 2 == 1;
   L.keys_in_1 = tpasses % 2 == 1;
   const int cnt_ctas = L.sort_ctas > L.depth_ctas ? L.sort_ctas : L.depth_ctas;
-  const size_t npix = static_cast<size_t>(width) * height;
+  const size_t npix = static_cast<size_t>(pix);
   size_t o = 0;
   L.header = o;   o = align_up(o + sizeof(FrameHeader));
-  L.rec = o;      o = align_up(o + 3 * sizeof(float4) * n);
-  L.rect = o;     o = align_up(o + sizeof(uint2) * n);
-  L.touched = o;  o = align_up(o + sizeof(uint32_t) * n);
-  L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * (L.tiles_x + 1) * (L.tiles_y + 1));
-  L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * n);
-  L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * n);
-  L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * n);
-  L.ord1 = o;     o = align_up(o + sizeof(uint32_t) * n);
-  L.offs = o;     o = align_up(o + sizeof(uint32_t) * (n + 1));
-  L.srect = o;    o = align_up(o + sizeof(uint2) * n);
+  L.views = o;    o = align_up(o + sizeof(ViewDev) * nviews);
+  L.rec = o;      o = align_up(o + 3 * sizeof(float4) * m);
+  L.rect = o;     o = align_up(o + sizeof(uint2) * m);
+  L.touched = o;  o = align_up(o + sizeof(uint32_t) * m);
+  L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * td);
+  L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * m);
+  L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * m);
+  L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * m);
+  L.ord1 = o;     o = align_up(o + sizeof(uint32_t) * m);
+  L.offs = o;     o = align_up(o + sizeof(uint32_t) * (m + 1));
+  L.ioffs = o;    o = align_up(o + sizeof(uint32_t) * m);
+  L.srect = o;    o = align_up(o + sizeof(uint4) * m);
   L.chunks = o;   o = align_up(o + sizeof(uint32_t) * ((cap + 2047) / 2048 + 1));
   L.blocksum = o; o = align_up(o + sizeof(uint32_t) * (L.nblocks + 1));
+  L.glist = o;    o = align_up(o + sizeof(uint32_t) * n);
   L.keys0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.vals0 = o;    o = align_up(o + sizeof(uint32_t) * cap);
   L.keys1 = o;    o = align_up(o + sizeof(uint32_t) * cap);
@@ -185,11 +192,15 @@ FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_
   L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
   L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);
   {
-    const size_t a = onesweep_scratch_bytes(n, 32), b = onesweep_scratch_bytes(cap, tb);
+    const size_t a = onesweep_scratch_bytes(m, 32), b = onesweep_scratch_bytes(cap, tb);
     L.onesweep = o; o = align_up(o + (a > b ? a : b));
   }
   L.total = o;
   return L;
+}
+
+FrameLayout make_layout1(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h) {
+  return make_layout(n, &width, &height, 1, cap, tile_w, tile_h);
 }
 
 // Sorted tile keys / values of a frame (which buffer depends on the number
@@ -204,6 +215,138 @@ static const uint32_t* sorted_vals(const FrameLayout& L, void* f) {
 }  // namespace r4g
 
 using namespace r4g;
+
+namespace {
+
+// Host-side layout of a call; checks the views.
+r4g_status batch_layout(r4g_ctx* ctx, int64_t n, const r4g_view* views, int32_t nviews, int64_t cap, int tile_w,
+                        int tile_h, FrameLayout* L) {
+  if (!views) return fail(ctx, R4G_EINVAL, "views is NULL");
+  if (nviews < 1 || nviews > kMaxViews) return fail(ctx, R4G_EINVAL, "nviews must be 1..64");
+  if (n * nviews > (int64_t(1) << 31) - 1) return fail(ctx, R4G_EINVAL, "n * nviews out of range (< 2^31)");
+  int w[kMaxViews], h[kMaxViews];
+  int64_t pix = 0, tiles = 0;
+  for (int v = 0; v < nviews; ++v) {
+    r4g_status st = check_camera(ctx, &views[v].cam);
+    if (st != R4G_OK) return st;
+    if (!std::isfinite(views[v].t)) return fail(ctx, R4G_EINVAL, "t is not finite");
+    w[v] = views[v].cam.width;
+    h[v] = views[v].cam.height;
+    const int64_t vt = static_cast<int64_t>((w[v] + tile_w - 1) / tile_w) * ((h[v] + tile_h - 1) / tile_h);
+    if (vt > kMaxTiles) return fail(ctx, R4G_EINVAL, "too many tiles (> 51200) in a view for this tile shape");
+    pix += static_cast<int64_t>(w[v]) * h[v];
+    tiles += vt;
+  }
+  if (pix > (int64_t(1) << 31) - 1) return fail(ctx, R4G_EINVAL, "too many pixels in the call (>= 2^31)");
+  if (tiles > (int64_t(1) << 24)) return fail(ctx, R4G_EINVAL, "too many tiles in the call (> 2^24)");
+  *L = make_layout(n, w, h, nviews, cap, tile_w, tile_h);
+  return R4G_OK;
+}
+
+r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                       const r4g_view* views_dev, float* out_rgb, float* out_T, uint32_t* out_last, void* frame,
+                       size_t frame_bytes, int64_t key_capacity, void* stream) {
+  r4g_status st = check_gaussians(ctx, g);
+  if (st != R4G_OK) return st;
+  if (!out_rgb || !frame) return fail(ctx, R4G_EINVAL, "out_rgb / frame is NULL");
+  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(ctx, R4G_EINVAL, "key_capacity out of range (< 2^30)");
+  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
+  if (views_dev && !aligned(views_dev, 4)) return fail(ctx, R4G_EINVAL, "views_dev must be 4-byte aligned");
+  FrameLayout L;
+  if ((st = batch_layout(ctx, g->n, views, nviews, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h, &L)) != R4G_OK)
+    return st;
+  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, sizeof(uint32_t) * L.tdiff_words, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
+  const bool has = L.n > 0;
+  const int dpasses = 32 / kSortRadixBits;
+  const int tpasses = (L.tile_bits + kSortRadixBits - 1) / kSortRadixBits;
+  {
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, has ? 2 : 1);
+    if ((e = launch_setup_views(L, frame, views, views_dev, s)) != cudaSuccess) return cuda_fail(ctx, e, "views");
+    if ((e = launch_preprocess_fwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "preprocess");
+  }
+  uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
+  int which = 0;
+  if (has) {
+    // depth order of the items: stable sort of the depth bits, values = item index
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);
+    e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
+                        at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
+                        nullptr, static_cast<uint32_t>(L.m), L.m, 32, at<void>(frame, L.onesweep), err, s, &which);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
+  }
+  const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
+  {
+    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 4 : 0);
+    if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
+  }
+  const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
+  {
+    // per-tile counts -> tile ranges and the tile sort's digit histograms
+    StageScope sc(ctx, R4G_STAGE_RANGES, s, 1);
+    uint32_t* hist = at<uint32_t>(frame, L.onesweep);
+    e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortRadix * 4, s);
+    if (e == cudaSuccess) e = launch_tile_counts(L, frame, hist, tpasses, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile counts");
+  }
+  if (has && tpasses > 0) {
+    // stable sort of the depth-ordered pairs by tile id
+    StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
+    // values: the emission index of each pair, generated by the first pass
+    e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
+                        at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which, true);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
+  }
+  const uint32_t* vals = sorted_vals(L, frame);
+  {
+    StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
+    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last,
+                              (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) != 0, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "blend");
+  }
+  return R4G_OK;
+}
+
+r4g_status backward_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                         const float* grad_rgb, r4g_grads* grads, void* frame, size_t frame_bytes,
+                         int64_t key_capacity, void* stream) {
+  r4g_status st = check_gaussians(ctx, g);
+  if (st != R4G_OK) return st;
+  if (!grad_rgb || !grads || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
+  if (g->n > 0 && (!grads->mean || !grads->rotor || !grads->logscale || !grads->logit || !grads->sh))
+    return fail(ctx, R4G_EINVAL, "a gradient pointer is NULL");
+  if (g->n > 0 && (!aligned(grads->mean, 16) || !aligned(grads->rotor, 16) || !aligned(grads->logscale, 16) ||
+                   !aligned(grads->sh, 16) || !aligned(grads->logit, 4)))
+    return fail(ctx, R4G_EINVAL, "gradient buffers must be 16-byte aligned");
+  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
+  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
+  FrameLayout L;
+  if ((st = batch_layout(ctx, g->n, views, nviews, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h, &L)) != R4G_OK)
+    return st;
+  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
+  if (L.n == 0) return R4G_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  const uint32_t* vals = sorted_vals(L, frame);
+  {
+    StageScope sc(ctx, R4G_STAGE_BLEND_BWD, s, 1);
+    if ((e = launch_blend_bwd(L, frame, vals, ctx->cfg.bg, grad_rgb, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "blend backward");
+  }
+  {
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, 1);
+    if ((e = launch_preprocess_bwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, *grads, s)) != cudaSuccess)
+      return cuda_fail(ctx, e, "preprocess backward");
+  }
+  return R4G_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -281,7 +424,7 @@ r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t
   if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, R4G_EINVAL, "n out of range");
   if (width <= 0 || height <= 0 || width > 32768 || height > 32768) return fail(c, R4G_EINVAL, "bad image size");
   if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(c, R4G_EINVAL, "key_capacity out of range");
-  *bytes = make_layout(n, width, height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h).total;
+  *bytes = make_layout1(n, width, height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h).total;
   return R4G_OK;
 }
 
@@ -297,6 +440,7 @@ r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   if (keys_needed) *keys_needed = h.key_needed;
   if (h.status & 1u) return fail(ctx, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
   if (h.status & 2u) return fail(ctx, R4G_ETIMEOUT, "a radix-sort look-back wait hit its iteration limit");
+  if (h.status & 4u) return fail(ctx, R4G_EDEVICE, "device views differ in image size from the host views");
   return R4G_OK;
 }
 
@@ -313,7 +457,10 @@ r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, 
   out->key_count = h.key_count;
   out->key_needed = h.key_needed;
   out->composited_pairs = (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) ? static_cast<int64_t>(h.composited) : -1;
-  out->status = (h.status & 1u) ? R4G_EOVERFLOW : ((h.status & 2u) ? R4G_ETIMEOUT : R4G_OK);
+  out->status = (h.status & 1u)   ? R4G_EOVERFLOW
+                : (h.status & 2u) ? R4G_ETIMEOUT
+                : (h.status & 4u) ? R4G_EDEVICE
+                                  : R4G_OK;
   out->reserved = 0;
   return R4G_OK;
 }
@@ -332,10 +479,10 @@ r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   int64_t lo = 0, hi = int64_t(0xffffffffu);
   while (lo < hi) {
     const int64_t mid = lo + (hi - lo + 1) / 2;
-    if (make_layout(n, width, height, mid, ctx->cfg.tile_w, ctx->cfg.tile_h).total <= frame_bytes) lo = mid;
+    if (make_layout1(n, width, height, mid, ctx->cfg.tile_w, ctx->cfg.tile_h).total <= frame_bytes) lo = mid;
     else hi = mid - 1;
   }
-  const FrameLayout L = make_layout(n, width, height, lo, ctx->cfg.tile_w, ctx->cfg.tile_h);
+  const FrameLayout L = make_layout1(n, width, height, lo, ctx->cfg.tile_w, ctx->cfg.tile_h);
   if (L.total > frame_bytes || h.key_count > L.cap) return fail(ctx, R4G_EWORKSPACE, "frame size does not match");
   void* f = const_cast<void*>(frame);
   const uint32_t K = h.key_count;
@@ -357,103 +504,141 @@ r4g_status r4g_render(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* ca
                       float* out_rgb, float* out_T, uint32_t* out_last, void* frame,
                       size_t frame_bytes, int64_t key_capacity, void* stream) {
   if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
-  r4g_status st = check_gaussians(ctx, g);
+  r4g_status st = check_camera(ctx, cam);
   if (st != R4G_OK) return st;
-  if ((st = check_camera(ctx, cam)) != R4G_OK) return st;
-  if (!out_rgb || !frame) return fail(ctx, R4G_EINVAL, "out_rgb / frame is NULL");
   if (!std::isfinite(t)) return fail(ctx, R4G_EINVAL, "t is not finite");
-  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(ctx, R4G_EINVAL, "key_capacity out of range (< 2^30)");
-  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
-  const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
-  if (L.ntiles > kMaxTiles) return fail(ctx, R4G_EINVAL, "too many tiles (> 51200) for this image and tile shape");
-  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const CamDev cd = make_cam(*cam);
-  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, sizeof(uint32_t) * (L.tiles_x + 1) * (L.tiles_y + 1), s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
-  const bool has = L.n > 0;
-  const int dpasses = 32 / kSortRadixBits;
-  const int tpasses = (L.tile_bits + kSortRadixBits - 1) / kSortRadixBits;
-  {
-    StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, has ? 1 : 0);
-    if ((e = launch_preprocess_fwd(*g, cd, t, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, s)) != cudaSuccess)
-      return cuda_fail(ctx, e, "preprocess");
-  }
-  uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
-  int which = 0;
-  if (has) {
-    // depth order of the Gaussians: stable sort of the depth bits, values = index
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);
-    e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
-                        at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
-                        nullptr, static_cast<uint32_t>(L.n), L.n, 32, at<void>(frame, L.onesweep), err, s, &which);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
-  }
-  const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
-  {
-    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 4 : 0);
-    if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
-  }
-  const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
-  {
-    // per-tile counts -> tile ranges and the tile sort's digit histograms
-    StageScope sc(ctx, R4G_STAGE_RANGES, s, 1);
-    if ((e = launch_tile_counts(L, frame, at<uint32_t>(frame, L.onesweep), tpasses, s)) != cudaSuccess)
-      return cuda_fail(ctx, e, "tile counts");
-  }
-  if (has && tpasses > 0) {
-    // stable sort of the depth-ordered pairs by tile id
-    StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
-    // values: the emission index of each pair, generated by the first pass
-    e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
-                        at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which, true);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
-  }
-  const uint32_t* vals = sorted_vals(L, frame);
-  {
-    StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
-    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last,
-                              (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) != 0, s)) != cudaSuccess)
-      return cuda_fail(ctx, e, "blend");
-  }
-  return R4G_OK;
+  r4g_view v;
+  v.cam = *cam;
+  v.t = t;
+  return render_impl(ctx, g, &v, 1, nullptr, out_rgb, out_T, out_last, frame, frame_bytes, key_capacity, stream);
 }
 
 r4g_status r4g_render_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_camera* cam, float t,
                                const float* grad_rgb, r4g_grads* grads, void* frame,
                                size_t frame_bytes, int64_t key_capacity, void* stream) {
   if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
-  r4g_status st = check_gaussians(ctx, g);
+  r4g_status st = check_camera(ctx, cam);
   if (st != R4G_OK) return st;
-  if ((st = check_camera(ctx, cam)) != R4G_OK) return st;
-  if (!grad_rgb || !grads || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
-  if (g->n > 0 && (!grads->mean || !grads->rotor || !grads->logscale || !grads->logit || !grads->sh))
-    return fail(ctx, R4G_EINVAL, "a gradient pointer is NULL");
-  if (g->n > 0 && (!aligned(grads->mean, 16) || !aligned(grads->rotor, 16) || !aligned(grads->logscale, 16) ||
-                   !aligned(grads->sh, 16) || !aligned(grads->logit, 4)))
-    return fail(ctx, R4G_EINVAL, "gradient buffers must be 16-byte aligned");
-  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(ctx, R4G_EINVAL, "key_capacity out of range");
-  if (!aligned(frame, 256)) return fail(ctx, R4G_EINVAL, "frame must be 256-byte aligned");
-  const FrameLayout L = make_layout(g->n, cam->width, cam->height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h);
-  if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
-  if (L.n == 0) return R4G_OK;
+  r4g_view v;
+  v.cam = *cam;
+  v.t = t;
+  return backward_impl(ctx, g, &v, 1, grad_rgb, grads, frame, frame_bytes, key_capacity, stream);
+}
+
+r4g_status r4g_batch_frame_bytes(const r4g_ctx* ctx, int64_t n, const r4g_view* views, int32_t nviews,
+                                 int64_t key_capacity, int32_t tile_w, int32_t tile_h, size_t* bytes) {
+  r4g_ctx* c = const_cast<r4g_ctx*>(ctx);
+  if (!ctx || !bytes) return fail(c, R4G_EINVAL, "NULL argument");
+  if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, R4G_EINVAL, "n out of range");
+  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(c, R4G_EINVAL, "key_capacity out of range");
+  if (tile_w == 0 && tile_h == 0) {
+    tile_w = ctx->cfg.tile_w;
+    tile_h = ctx->cfg.tile_h;
+  }
+  if (!tile_ok(tile_w, tile_h)) return fail(c, R4G_EINVAL, "tile shape must be 8x8, 16x16 or 16x32");
+  FrameLayout L;
+  r4g_status st = batch_layout(c, n, views, nviews, key_capacity, tile_w, tile_h, &L);
+  if (st != R4G_OK) return st;
+  *bytes = L.total;
+  return R4G_OK;
+}
+
+r4g_status r4g_render_batch(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                            const r4g_view* views_dev, float* out_rgb, float* out_T, void* frame,
+                            size_t frame_bytes, int64_t key_capacity, void* stream) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  return render_impl(ctx, g, views, nviews, views_dev, out_rgb, out_T, nullptr, frame, frame_bytes, key_capacity,
+                     stream);
+}
+
+r4g_status r4g_render_batch_backward(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views,
+                                     int32_t nviews, const float* grad_rgb, r4g_grads* grads, void* frame,
+                                     size_t frame_bytes, int64_t key_capacity, void* stream) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  return backward_impl(ctx, g, views, nviews, grad_rgb, grads, frame, frame_bytes, key_capacity, stream);
+}
+
+r4g_status r4g_autotune_batch(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* views, int32_t nviews,
+                              float* out_rgb, const float* grad_rgb, r4g_grads* grads, void* frame,
+                              size_t frame_bytes, int64_t key_capacity, int32_t reps, void* stream,
+                              r4g_tune_result* out) {
+  if (!ctx || !out) return fail(ctx, R4G_EINVAL, "NULL argument");
+  if (reps < 1 || reps > 1000) return fail(ctx, R4G_EINVAL, "reps must be 1..1000");
+  if (ctx->timing) return fail(ctx, R4G_EINVAL, "disable stage timing while tuning");
+  static const int kShapes[3][2] = {{8, 8}, {16, 16}, {16, 32}};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const CamDev cd = make_cam(*cam);
-  cudaError_t e = cudaSuccess;
-  const uint32_t* vals = sorted_vals(L, frame);
-  {
-    StageScope sc(ctx, R4G_STAGE_BLEND_BWD, s, 1);
-    if ((e = launch_blend_bwd(L, frame, vals, ctx->cfg.bg, grad_rgb, s)) != cudaSuccess)
-      return cuda_fail(ctx, e, "blend backward");
+  const int32_t tw0 = ctx->cfg.tile_w, th0 = ctx->cfg.tile_h;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(ctx, R4G_ECUDA, "cudaEventCreate");
   }
-  {
-    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, 1);
-    if ((e = launch_preprocess_bwd(*g, cd, t, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, *grads, s)) != cudaSuccess)
-      return cuda_fail(ctx, e, "preprocess backward");
+  int best = -1;
+  r4g_status result = R4G_OK;
+  for (int k = 0; k < 3; ++k) {
+    out->ms[k] = -1.0f;
+    out->keys_needed[k] = -1;
+    ctx->cfg.tile_w = kShapes[k][0];
+    ctx->cfg.tile_h = kShapes[k][1];
+    FrameLayout L;
+    if (batch_layout(ctx, g ? g->n : 0, views, nviews, key_capacity, kShapes[k][0], kShapes[k][1], &L) != R4G_OK ||
+        L.total > frame_bytes)
+      continue;  // this shape does not fit the frame or the tile limit
+    float ms = 0.0f;
+    cudaError_t e = cudaSuccess;
+    r4g_status st = R4G_OK;
+    for (int r = -1; r < reps && st == R4G_OK && e == cudaSuccess; ++r) {  // r = -1: warm-up
+      if (r == 0) e = cudaEventRecord(e0, s);
+      st = render_impl(ctx, g, views, nviews, nullptr, out_rgb, nullptr, nullptr, frame, frame_bytes, key_capacity,
+                       stream);
+      if (st == R4G_OK && grad_rgb)
+        st = backward_impl(ctx, g, views, nviews, grad_rgb, grads, frame, frame_bytes, key_capacity, stream);
+    }
+    if (st != R4G_OK) {
+      result = st;
+      break;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    FrameHeader h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, frame, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      result = cuda_fail(ctx, e, "r4g_autotune_batch");
+      break;
+    }
+    out->keys_needed[k] = h.key_needed;
+    if (h.status & 3u) continue;  // overflow or a sort wait gave up: not a valid timing
+    out->ms[k] = ms / reps;
+    if (best < 0 || out->ms[k] < out->ms[best]) best = k;
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != R4G_OK || best < 0) {
+    ctx->cfg.tile_w = tw0;
+    ctx->cfg.tile_h = th0;
+    if (result != R4G_OK) return result;
+    return fail(ctx, R4G_EOVERFLOW, "no tile shape rendered within the frame and key capacity");
+  }
+  ctx->cfg.tile_w = kShapes[best][0];
+  ctx->cfg.tile_h = kShapes[best][1];
+  out->tile_w = ctx->cfg.tile_w;
+  out->tile_h = ctx->cfg.tile_h;
+  return R4G_OK;
+}
+
+r4g_status r4g_set_tile(r4g_ctx* ctx, int32_t tile_w, int32_t tile_h) {
+  if (!ctx) return fail(nullptr, R4G_EINVAL, "ctx is NULL");
+  if (!tile_ok(tile_w, tile_h)) return fail(ctx, R4G_EINVAL, "tile shape must be 8x8, 16x16 or 16x32");
+  ctx->cfg.tile_w = tile_w;
+  ctx->cfg.tile_h = tile_h;
+  return R4G_OK;
+}
+
+r4g_status r4g_get_config(const r4g_ctx* ctx, r4g_config* out) {
+  if (!ctx || !out) return fail(const_cast<r4g_ctx*>(ctx), R4G_EINVAL, "NULL argument");
+  *out = ctx->cfg;
   return R4G_OK;
 }
 

@@ -1,13 +1,16 @@
-// Tile binning of the rasteriser (Sec. 3.1). The Gaussians are first put in
-// depth order (a stable radix sort of their depth bits, ties by index), then
-// one (tile, Gaussian) pair is emitted per tile a Gaussian's box covers, in
-// that order and row-major within a Gaussian. A stable sort of the pairs by
-// tile id then gives, bit for bit, the order of a stable sort of 64-bit keys
-// tile_id << 32 | float_bits(depth) emitted in Gaussian-index order.
+// Tile binning of the rasteriser (Sec. 3.1). The (view, Gaussian) items of
+// all the views of a call are first put in depth order (a stable radix sort
+// of their depth bits, ties by item index), then one (tile, item) pair is
+// emitted per tile an item's box covers, in that order and row-major within
+// an item. Tile ids are global over the views, so a tile's pairs all come
+// from one view, and a stable sort of the pairs by tile id gives, bit for
+// bit, the order of a stable sort of 64-bit keys tile_id << 32 |
+// float_bits(depth) emitted in Gaussian-index order, view by view.
 // This file holds: the per-block totals of tile counts in depth order, their
-// exclusive scan, per-Gaussian offsets, the emission balanced over the output
-// pairs, the per-tile [begin, end)
-// ranges of the sorted list, and the export of the equivalent 64-bit keys.
+// exclusive scan, per-item offsets (in depth order and by item), the
+// emission balanced over the output pairs, the per-view tile counts -> the
+// [begin, end) ranges of the sorted list, and the export of the equivalent
+// 64-bit keys.
 #include <cuda_runtime.h>
 
 #include "r4g_internal.cuh"
@@ -87,14 +90,15 @@ constexpr int kEmitChunk = 2048;
 
 __global__ void __launch_bounds__(kPreBlock)
     depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
-                         const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect, int n,
-                         uint32_t* __restrict__ offs, uint2* __restrict__ srect,
-                         uint32_t* __restrict__ chunk_start, uint32_t nchunks) {
+                         const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect,
+                         const ViewDev* __restrict__ views, uint32_t ng, int m, uint32_t* __restrict__ offs,
+                         uint32_t* __restrict__ ioffs, uint4* __restrict__ srect, uint32_t* __restrict__ chunk_start,
+                         uint32_t nchunks) {
   __shared__ uint32_t s_warp[kPreBlock / 32];
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t g = j < n ? order[j] : 0u;
-  const uint32_t cnt = j < n ? touched[g] : 0u;
+  const uint32_t item = j < m ? order[j] : 0u;
+  const uint32_t cnt = j < m ? touched[item] : 0u;
   uint32_t x = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -105,11 +109,18 @@ __global__ void __launch_bounds__(kPreBlock)
   __syncthreads();
   uint32_t base = blockoff[blockIdx.x];
   for (int w = 0; w < warp; ++w) base += s_warp[w];
-  if (j < n) {
+  if (j < m) {
     const uint32_t o = base + x - cnt;
     offs[j] = o;
-    srect[j] = cnt ? rect[g] : make_uint2(0u, 0u);
-    // this Gaussian owns the first pair of every emission chunk starting in [o, o + cnt)
+    if (cnt) {
+      ioffs[item] = o;
+      const ViewDev& V = views[item / ng];
+      const uint2 r = rect[item];
+      srect[j] = make_uint4(r.x, r.y, V.tile_off, static_cast<uint32_t>(V.tiles_x));
+    } else {
+      srect[j] = make_uint4(0u, 0u, 0u, 1u);
+    }
+    // this item owns the first pair of every emission chunk starting in [o, o + cnt)
     for (uint32_t c = (o + kEmitChunk - 1) / kEmitChunk; cnt && c * kEmitChunk < o + cnt && c < nchunks; ++c)
       chunk_start[c] = static_cast<uint32_t>(j);
   }
@@ -124,9 +135,9 @@ __global__ void __launch_bounds__(kPreBlock)
 // (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j]. The
 // Gaussian holding the chunk's first pair comes from depth_offsets_kernel.
 __global__ void __launch_bounds__(kPreBlock)
-    emit_kernel(const uint32_t* __restrict__ offs, const uint2* __restrict__ srect,
+    emit_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect,
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
-                int tiles_x, const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
+                const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
                 uint32_t* __restrict__ ident) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   const uint32_t K = hdr->key_count;
@@ -146,11 +157,11 @@ __global__ void __launch_bounds__(kPreBlock)
     }
     const int j = jlo + lo;
     const uint32_t local = q - s_off[lo];
-    const uint2 r = srect[j];
+    const uint4 r = srect[j];  // rect, the view's first tile id and tiles_x
     const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
     const uint32_t w = x1 - x0;
     const uint32_t ty = y0 + local / w, tx = x0 + local % w;
-    tkeys[q] = ty * static_cast<uint32_t>(tiles_x) + tx;
+    tkeys[q] = r.z + ty * r.w + tx;
     egid[q] = order[j];
     if (ident) ident[q] = q;  // a single-tile image has no tile sort to generate the values
   }
@@ -171,25 +182,35 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 }
 
 __global__ void __launch_bounds__(1024)
-    tile_counts_kernel(const uint32_t* __restrict__ tdiff, int tiles_x, int tiles_y, uint32_t cap,
+    tile_counts_kernel(const uint32_t* __restrict__ tdiff, const ViewDev* __restrict__ views, uint32_t cap,
                        const FrameHeader* hdr, uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
                        int passes) {
-  extern __shared__ uint32_t s_c[];  // tiles_y x tiles_x counts
+  extern __shared__ uint32_t s_c[];  // tiles_y x tiles_x counts of this CTA's view
   __shared__ uint32_t s_h[4][kSortRadix];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
+  const int v = blockIdx.x;
+  const ViewDev& V = views[v];
+  const int tiles_x = V.tiles_x, tiles_y = V.tiles_y;
+  const uint32_t toff = V.tile_off;
+  const uint32_t* td = tdiff + V.tdiff_off;
   const int st = tiles_x + 1;
   const int ntiles = tiles_x * tiles_y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int k = threadIdx.x; k < 4 * kSortRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_c[t] = tdiff[(t / tiles_x) * st + (t % tiles_x)];
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_c[t] = td[(t / tiles_x) * st + (t % tiles_x)];
+  if (threadIdx.x == 0) {  // the view's first pair: pairs of the views before it
+    uint32_t base = 0;
+    for (int u = 0; u < v; ++u) base += hdr->view_pairs[u];
+    s_carry = base;
+  }
   __syncthreads();
   for (int y = warp; y < tiles_y; y += nwarp) {  // each warp: running sums along its rows
     uint32_t carry = 0;
     for (int x0 = 0; x0 < tiles_x; x0 += 32) {
       const int x = x0 + lane;
-      const uint32_t v = x < tiles_x ? s_c[y * tiles_x + x] : 0u;
-      const uint32_t inc = warp_incl_scan(v, lane) + carry;
+      const uint32_t val = x < tiles_x ? s_c[y * tiles_x + x] : 0u;
+      const uint32_t inc = warp_incl_scan(val, lane) + carry;
       if (x < tiles_x) s_c[y * tiles_x + x] = inc;
       carry = __shfl_sync(0xffffffffu, inc, 31);
     }
@@ -199,13 +220,12 @@ __global__ void __launch_bounds__(1024)
     uint32_t carry = 0;
     for (int y0 = 0; y0 < tiles_y; y0 += 32) {
       const int y = y0 + lane;
-      const uint32_t v = y < tiles_y ? s_c[y * tiles_x + x] : 0u;
-      const uint32_t inc = warp_incl_scan(v, lane) + carry;
+      const uint32_t val = y < tiles_y ? s_c[y * tiles_x + x] : 0u;
+      const uint32_t inc = warp_incl_scan(val, lane) + carry;
       if (y < tiles_y) s_c[y * tiles_x + x] = inc;
       carry = __shfl_sync(0xffffffffu, inc, 31);
     }
   }
-  if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   // after a key-capacity overflow the list is incomplete: every tile gets an
   // empty range so nothing downstream reads it (the frame reports the overflow)
@@ -223,9 +243,10 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
     const uint32_t start = s_carry + (warp ? s_warp[warp - 1] : 0u) + x - c;
     if (t < ntiles) {
-      ranges[t] = overflow ? make_uint2(0u, 0u) : make_uint2(start, start + c);
+      ranges[toff + t] = overflow ? make_uint2(0u, 0u) : make_uint2(start, start + c);
       if (c) {
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(t >> (8 * p)) & 0xff], c);
+        const uint32_t gt = toff + static_cast<uint32_t>(t);
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(gt >> (8 * p)) & 0xff], c);
       }
     }
     __syncthreads();
@@ -233,30 +254,8 @@ __global__ void __launch_bounds__(1024)
     __syncthreads();
   }
   for (int p = 0; p < passes; ++p)
-    for (int d = threadIdx.x; d < kSortRadix; d += blockDim.x) hist[p * kSortRadix + d] = s_h[p][d];
-}
-
-// ranges[tile] = [first, last+1) of the tile's entries in the sorted list;
-// four consecutive entries per thread.
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const FrameHeader* hdr,
-                              uint2* __restrict__ ranges) {
-  const uint32_t n = hdr->key_count;
-  const uint32_t stride = gridDim.x * blockDim.x * 4;
-  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) * 4; b < n; b += stride) {
-    uint32_t k[6];
-    k[0] = b > 0 ? keys[b - 1] : 0xffffffffu;
-#pragma unroll
-    for (int u = 0; u < 5; ++u) k[u + 1] = (b + u < n) ? keys[b + u] : 0xffffffffu;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint32_t i = b + u;
-      if (i < n) {
-        const uint32_t tile = k[u + 1];
-        if (k[u] != tile) ranges[tile].x = i;
-        if (k[u + 2] != tile) ranges[tile].y = i + 1;
-      }
-    }
-  }
+    for (int d = threadIdx.x; d < kSortRadix; d += blockDim.x)
+      if (s_h[p][d]) atomicAdd(&hist[p * kSortRadix + d], s_h[p][d]);
 }
 
 // The sort carries each pair's emission index e; egid[e] is its Gaussian.
@@ -286,17 +285,19 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   uint32_t* bs = at<uint32_t>(frame, L.blocksum);
   const uint32_t* touched = at<uint32_t>(frame, L.touched);
-  const int n = static_cast<int>(L.n);
+  const int m = static_cast<int>(L.m);
   uint32_t* offs = at<uint32_t>(frame, L.offs);
-  uint2* srect = at<uint2>(frame, L.srect);
+  uint4* srect = at<uint4>(frame, L.srect);
   uint32_t* cstart = at<uint32_t>(frame, L.chunks);
   const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
-  depth_blocksum_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, n, bs);
+  depth_blocksum_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, m, bs);
   scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
-  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect), n, offs,
-                                                        srect, cstart, static_cast<uint32_t>(chunks));
+  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect),
+                                                        at<ViewDev>(frame, L.views), static_cast<uint32_t>(L.n), m,
+                                                        offs, at<uint32_t>(frame, L.ioffs), srect, cstart,
+                                                        static_cast<uint32_t>(chunks));
   if (chunks > 0)
-    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, cstart, n, L.tiles_x, hdr,
+    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, cstart, m, hdr,
                                                                      at<uint32_t>(frame, L.keys0),
                                                                      at<uint32_t>(frame, L.egid),
                                                                      L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0)
@@ -305,30 +306,22 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
 }
 
 cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s) {
-  const size_t smem = sizeof(uint32_t) * static_cast<size_t>(L.ntiles);
+  const size_t smem = sizeof(uint32_t) * static_cast<size_t>(L.max_view_tiles);
   if (smem > kTileCountsMaxSmem) return cudaErrorInvalidValue;
   // opt in to large dynamic shared memory (a per-device function attribute)
   cudaFuncSetAttribute(tile_counts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileCountsMaxSmem);
-  tile_counts_kernel<<<1, 1024, smem, s>>>(at<uint32_t>(frame, L.tdiff), L.tiles_x, L.tiles_y,
-                                        static_cast<uint32_t>(L.cap), at<FrameHeader>(frame, L.header),
-                                        at<uint2>(frame, L.ranges), hist, passes);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* tile_keys, cudaStream_t s) {
-  uint2* ranges = at<uint2>(frame, L.ranges);
-  cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.ntiles, s);
-  if (L.n == 0) return cudaGetLastError();
-  ranges_kernel<<<2 * 152, 256, 0, s>>>(tile_keys, at<FrameHeader>(frame, L.header), ranges);
+  tile_counts_kernel<<<L.nviews, 1024, smem, s>>>(at<uint32_t>(frame, L.tdiff), at<ViewDev>(frame, L.views),
+                                                  static_cast<uint32_t>(L.cap), at<FrameHeader>(frame, L.header),
+                                                  at<uint2>(frame, L.ranges), hist, passes);
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                                const uint32_t* vals, uint64_t* out, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
-  const float4* recB = at<float4>(frame, L.rec) + L.n;
+  const float4* recB = at<float4>(frame, L.rec) + L.m;
   export_keys_kernel<<<4 * 152, 256, 0, s>>>(tile_keys, vals, at<uint32_t>(frame, L.egid), recB,
-                                             at<FrameHeader>(frame, L.header), static_cast<uint32_t>(L.n),
+                                             at<FrameHeader>(frame, L.header), static_cast<uint32_t>(L.m),
                                              static_cast<uint32_t>(L.cap), out);
   return cudaGetLastError();
 }

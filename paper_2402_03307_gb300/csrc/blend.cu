@@ -218,19 +218,45 @@ __device__ __forceinline__ bool fwd_group(FwdState& S, const StagedG* grp, uint3
 template <int TW, int TH>
 constexpr int fwd_min_blocks() { return Blend<TW, TH>::NT <= 128 ? 8 : 4; }
 
+// Where a global tile id lies: its view (binary search over the views'
+// first tile ids), the tile's position in the view and the view's image.
+struct TileLoc {
+  int tx, ty, width, height;
+  uint32_t pix_off;
+};
+
+__device__ __forceinline__ TileLoc locate_tile(const ViewDev* __restrict__ views, int nviews, int tile) {
+  int lo = 0, hi = nviews - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (static_cast<int>(views[mid].tile_off) <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  const ViewDev& V = views[lo];
+  const int local = tile - static_cast<int>(V.tile_off);
+  TileLoc t;
+  t.tx = local % V.tiles_x;
+  t.ty = local / V.tiles_x;
+  t.width = V.cam.width;
+  t.height = V.cam.height;
+  t.pix_off = V.pix_off;
+  return t;
+}
+
+// The tile's pixels, front to back over its list.
 template <int TW, int TH, bool kLast>
-__global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
-    blend_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                     const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
-                     uint32_t cap, int width, int height, int tiles_x, float bg0, float bg1, float bg2,
-                     float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_stop,
-                     uint32_t* __restrict__ out_last, unsigned long long* __restrict__ pair_count) {
+__device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint2* __restrict__ ranges,
+                                               const uint32_t* __restrict__ vals, const float4* __restrict__ recA,
+                                               const float4* __restrict__ recB, const float4* __restrict__ recC,
+                                               const uint32_t* __restrict__ egid, uint32_t ng, uint32_t cap,
+                                               const ViewDev* __restrict__ views, int nviews, float bg0, float bg1,
+                                               float bg2, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                                               uint32_t* __restrict__ out_stop, uint32_t* __restrict__ out_last,
+                                               unsigned long long* __restrict__ pair_count) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT;
-  __shared__ StagedG sg[BS];
-  const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const TileLoc loc = locate_tile(views, nviews, tile);
+  const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int px = tx * TW + 2 * (lane % B::PCOLS);
   const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
@@ -271,31 +297,56 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
     }
   }
   const size_t plane = static_cast<size_t>(width) * height;
+  float* img = out_rgb + 3 * static_cast<size_t>(loc.pix_off);
   if (in0) {
     const size_t pix = static_cast<size_t>(py) * width + px;
-    out_rgb[pix] = S.cr.x + S.T.x * bg0;
-    out_rgb[plane + pix] = S.cg.x + S.T.x * bg1;
-    out_rgb[2 * plane + pix] = S.cb.x + S.T.x * bg2;
-    out_T[pix] = S.T.x;
-    out_stop[pix] = S.stop0;
+    img[pix] = S.cr.x + S.T.x * bg0;
+    img[plane + pix] = S.cg.x + S.T.x * bg1;
+    img[2 * plane + pix] = S.cb.x + S.T.x * bg2;
+    out_T[loc.pix_off + pix] = S.T.x;
+    out_stop[loc.pix_off + pix] = S.stop0;
     if constexpr (kLast) {
-      if (out_last) out_last[pix] = S.last0;
+      if (out_last) out_last[loc.pix_off + pix] = S.last0;
     }
   }
   if (in1) {
     const size_t pix = static_cast<size_t>(py) * width + px + 1;
-    out_rgb[pix] = S.cr.y + S.T.y * bg0;
-    out_rgb[plane + pix] = S.cg.y + S.T.y * bg1;
-    out_rgb[2 * plane + pix] = S.cb.y + S.T.y * bg2;
-    out_T[pix] = S.T.y;
-    out_stop[pix] = S.stop1;
+    img[pix] = S.cr.y + S.T.y * bg0;
+    img[plane + pix] = S.cg.y + S.T.y * bg1;
+    img[2 * plane + pix] = S.cb.y + S.T.y * bg2;
+    out_T[loc.pix_off + pix] = S.T.y;
+    out_stop[loc.pix_off + pix] = S.stop1;
     if constexpr (kLast) {
-      if (out_last) out_last[pix] = S.last1;
+      if (out_last) out_last[loc.pix_off + pix] = S.last1;
     }
   }
   if constexpr (kLast) {
     const uint32_t wsum = __reduce_add_sync(0xffffffffu, S.pairs);
     if (lane == 0 && wsum) atomicAdd(pair_count, static_cast<unsigned long long>(wsum));
+  }
+}
+
+// Persistent blend: each CTA takes tiles (of every view of the call) from a
+// work counter in the frame header until none is left.
+template <int TW, int TH, bool kLast>
+__global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
+    blend_fwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                     const float4* __restrict__ recA, const float4* __restrict__ recB,
+                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
+                     uint32_t cap, const ViewDev* __restrict__ views, int nviews, int ntiles, FrameHeader* hdr,
+                     float bg0, float bg1, float bg2, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                     uint32_t* __restrict__ out_stop, uint32_t* __restrict__ out_last,
+                     unsigned long long* __restrict__ pair_count) {
+  __shared__ StagedG sg[Blend<TW, TH>::NT];
+  __shared__ int s_tile;
+  for (;;) {
+    __syncthreads();  // the previous tile is done with s_tile and sg
+    if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->next_tile, 1u));
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    blend_fwd_tile<TW, TH, kLast>(tile, sg, ranges, vals, recA, recB, recC, egid, ng, cap, views, nviews, bg0, bg1,
+                                  bg2, out_rgb, out_T, out_stop, out_last, pair_count);
   }
 }
 
@@ -406,21 +457,18 @@ __device__ __forceinline__ void warp_reduce9(float v[9], int lane) {
 // backward sums per Gaussian. No float atomics: the gradient is
 // deterministic.
 template <int TW, int TH>
-__global__ void __launch_bounds__(Blend<TW, TH>::NT)
-    blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
-                     const float4* __restrict__ recA, const float4* __restrict__ recB,
-                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
-                     uint32_t cap, int width, int height, int tiles_x, float bg0, float bg1, float bg2,
-                     const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
-                     const float* __restrict__ grad_rgb, float4* __restrict__ gbuf) {
+__device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* sE, uint32_t& s_max, float* s_slab,
+                                               const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                                               const float4* __restrict__ recA, const float4* __restrict__ recB,
+                                               const float4* __restrict__ recC, const uint32_t* __restrict__ egid,
+                                               uint32_t ng, uint32_t cap, const ViewDev* __restrict__ views,
+                                               int nviews, float bg0, float bg1, float bg2,
+                                               const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
+                                               const float* __restrict__ grad_rgb, float4* __restrict__ gbuf) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT;
-  __shared__ StagedG sg[BS];
-  __shared__ uint32_t sE[BS];
-  __shared__ uint32_t s_max;
-  extern __shared__ float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
-  const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const TileLoc loc = locate_tile(views, nviews, tile);
+  const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int px = tx * TW + 2 * (lane % B::PCOLS);
   const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
@@ -430,6 +478,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
   const size_t plane = static_cast<size_t>(width) * height;
+  const float* gimg = grad_rgb + 3 * static_cast<size_t>(loc.pix_off);
   BwdState S;
   S.PX = make_float2(px + 0.5f, px + 1.5f);
   float T[2] = {1.f, 1.f}, U[2] = {0.f, 0.f}, g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -438,11 +487,11 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   for (int k = 0; k < 2; ++k) {
     if (k == 0 ? in0 : in1) {
       const size_t pix = static_cast<size_t>(py) * width + px + k;
-      T[k] = Tfinal[pix];
-      L[k] = stoppos[pix];
-      g[k][0] = grad_rgb[pix];
-      g[k][1] = grad_rgb[plane + pix];
-      g[k][2] = grad_rgb[2 * plane + pix];
+      T[k] = Tfinal[loc.pix_off + pix];
+      L[k] = stoppos[loc.pix_off + pix];
+      g[k][0] = gimg[pix];
+      g[k][1] = gimg[plane + pix];
+      g[k][2] = gimg[2 * plane + pix];
       U[k] = T[k] * (bg0 * g[k][0] + bg1 * g[k][1] + bg2 * g[k][2]);  // T_N (g . bg)
     }
   }
@@ -537,25 +586,66 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   }
 }
 
+// Persistent blend backward over the tiles of every view of the call.
+template <int TW, int TH>
+__global__ void __launch_bounds__(Blend<TW, TH>::NT)
+    blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
+                     const float4* __restrict__ recA, const float4* __restrict__ recB,
+                     const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
+                     uint32_t cap, const ViewDev* __restrict__ views, int nviews, int ntiles, FrameHeader* hdr,
+                     float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
+                     const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
+                     float4* __restrict__ gbuf) {
+  __shared__ StagedG sg[Blend<TW, TH>::NT];
+  __shared__ uint32_t sE[Blend<TW, TH>::NT];
+  __shared__ uint32_t s_max;
+  __shared__ int s_tile;
+  extern __shared__ float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
+  for (;;) {
+    __syncthreads();  // the previous tile is done with the shared buffers
+    if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->next_tile_bwd, 1u));
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    blend_bwd_tile<TW, TH>(tile, sg, sE, s_max, s_slab, ranges, vals, recA, recB, recC, egid, ng, cap, views,
+                           nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf);
+  }
+}
+
+// CTAs of a persistent launch: as many as fit on the device at once, at
+// most one per tile.
+template <typename K>
+static int persistent_ctas(K kernel, int threads, size_t smem, int ntiles) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  const long long c = static_cast<long long>(per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  return static_cast<int>(c < ntiles ? c : ntiles);
+}
+
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, float* out_rgb, float* out_T, uint32_t* out_last, bool count,
                              cudaStream_t s) {
   const float4* recA = at<float4>(frame, L.rec);
-  const float4* recB = recA + L.n;
-  const float4* recC = recB + L.n;
+  const float4* recB = recA + L.m;
+  const float4* recC = recB + L.m;
   const uint2* ranges = at<uint2>(frame, L.ranges);
   // the frame always keeps T and the stop positions for the backward
   float* T = at<float>(frame, L.tfinal);
   uint32_t* stop = at<uint32_t>(frame, L.last);
-  const size_t npix = static_cast<size_t>(L.width) * L.height;
-#define R4G_BLEND(TW_, TH_, LAST_)                                                                \
-  blend_fwd_kernel<TW_, TH_, LAST_><<<L.ntiles, Blend<TW_, TH_>::NT, 0, s>>>(                     \
-      ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.n), static_cast<uint32_t>(L.cap),     \
-      L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], out_rgb, T, stop, out_last, pairs)
+  const ViewDev* views = at<ViewDev>(frame, L.views);
+  FrameHeader* hdr = at<FrameHeader>(frame, L.header);
+#define R4G_BLEND(TW_, TH_, LAST_)                                                                          \
+  blend_fwd_kernel<TW_, TH_, LAST_>                                                                         \
+      <<<persistent_ctas(blend_fwd_kernel<TW_, TH_, LAST_>, Blend<TW_, TH_>::NT, 0, L.ntiles),                \
+         Blend<TW_, TH_>::NT, 0, s>>>(ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),      \
+                                     static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], bg[1], \
+                                     bg[2], out_rgb, T, stop, out_last, pairs)
   const uint32_t* egid = at<uint32_t>(frame, L.egid);
   // the instrumented variant serves both the last-contributor output and the pair count
   const bool lst = out_last != nullptr || count;
-  unsigned long long* pairs = &at<FrameHeader>(frame, L.header)->composited;
+  unsigned long long* pairs = &hdr->composited;
   if (L.tile_w == 16 && L.tile_h == 16) {
     if (lst) R4G_BLEND(16, 16, true); else R4G_BLEND(16, 16, false);
   } else if (L.tile_w == 8 && L.tile_h == 8) {
@@ -566,28 +656,34 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
     return cudaErrorInvalidValue;
   }
 #undef R4G_BLEND
-  if (out_T) cudaMemcpyAsync(out_T, T, npix * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (out_T) cudaMemcpyAsync(out_T, T, static_cast<size_t>(L.npix) * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, const float* grad_rgb, cudaStream_t s) {
   const float4* recA = at<float4>(frame, L.rec);
-  const float4* recB = recA + L.n;
-  const float4* recC = recB + L.n;
+  const float4* recB = recA + L.m;
+  const float4* recC = recB + L.m;
   const uint2* ranges = at<uint2>(frame, L.ranges);
   const float* T = at<float>(frame, L.tfinal);
   const uint32_t* stop = at<uint32_t>(frame, L.last);
   const uint32_t* egid = at<uint32_t>(frame, L.egid);
+  const ViewDev* views = at<ViewDev>(frame, L.views);
+  FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   float4* gbuf = at<float4>(frame, L.gbuf);
-#define R4G_BLEND_BWD(TW_, TH_)                                                                    \
-  {                                                                                                \
-    const size_t slab = sizeof(float) * 9 * Blend<TW_, TH_>::NW * Blend<TW_, TH_>::NT;            \
-    cudaFuncSetAttribute(blend_bwd_kernel<TW_, TH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                         static_cast<int>(slab));                                                  \
-    blend_bwd_kernel<TW_, TH_><<<L.ntiles, Blend<TW_, TH_>::NT, slab, s>>>(                        \
-        ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.n), static_cast<uint32_t>(L.cap), \
-        L.width, L.height, L.tiles_x, bg[0], bg[1], bg[2], T, stop, grad_rgb, gbuf);              \
+  // the backward's work counter (the render zeroed the forward's)
+  cudaMemsetAsync(&hdr->next_tile_bwd, 0, sizeof(uint32_t), s);
+#define R4G_BLEND_BWD(TW_, TH_)                                                                           \
+  {                                                                                                       \
+    const size_t slab = sizeof(float) * 9 * Blend<TW_, TH_>::NW * Blend<TW_, TH_>::NT;                   \
+    cudaFuncSetAttribute(blend_bwd_kernel<TW_, TH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                         static_cast<int>(slab));                                                         \
+    blend_bwd_kernel<TW_, TH_>                                                                            \
+        <<<persistent_ctas(blend_bwd_kernel<TW_, TH_>, Blend<TW_, TH_>::NT, slab, L.ntiles),              \
+           Blend<TW_, TH_>::NT, slab, s>>>(ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),  \
+                                           static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], \
+                                           bg[1], bg[2], T, stop, grad_rgb, gbuf);                        \
   }
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16)
   else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8)

@@ -2,7 +2,9 @@
 // normalisation and rotation (appendix A.1/A.2), Sigma4 (Sec. 3.2.1), the
 // temporal slice and visibility cull (Sec. 3.2.2, appendix A.3), EWA
 // projection (Sec. 3.1), SH colour, and the tile rectangle each Gaussian's
-// contributing pixels can lie in. One thread per Gaussian; coalesced 16-byte
+// contributing pixels can lie in. One thread per Gaussian for all the views
+// of a call: the view-independent part (parameters, rotor, R, Sigma4) is
+// computed once, the slice and projection once per view. Coalesced 16-byte
 // loads of the SoA parameters; the SH row is read only for survivors.
 #include <cuda_runtime.h>
 
@@ -11,17 +13,17 @@
 
 namespace r4g {
 
+// Per-item outputs (item = view * N + Gaussian).
 struct PreOut {
-  float4* recA;  // (mean2d.x, mean2d.y, conic a, conic b)
-  float4* recB;  // (conic c, opacity_t, depth, 0)
-  float4* recC;  // (r, g, b, 0)
+  float4* recA;  // [3][M] records: (mean2d.x, mean2d.y, conic a, conic b),
+                 // (conic c, opacity_t, depth, 0), (r, g, b, 0)
   uint2* rect;   // tile rect: (x0 | y0 << 16, x1 | y1 << 16), [x0, x1) x [y0, y1)
   uint32_t* touched;
-  uint32_t* dkey;  // float bits of the depth for Gaussians with tiles, else 0xffffffff
-  uint32_t* tdiff; // 2D difference array of the tile counts, (tiles_y + 1) x (tiles_x + 1)
-  uint32_t* blocksum;
+  uint32_t* dkey;  // float bits of the depth for items with tiles, else 0xffffffff
+  uint32_t* tdiff; // per view, 2D difference array of the tile counts, (tiles_y + 1) x (tiles_x + 1)
+  uint32_t* glist; // Gaussians visible in some view
   FrameHeader* header;
-  int tile_w, tile_h, tiles_x, tiles_y;
+  int tile_w, tile_h;
 };
 
 // Everything the forward computes for one Gaussian, kept so the backward can
@@ -41,65 +43,75 @@ struct Fwd {
   bool clampx, clampy;
 };
 
-// Intermediates of the rotor / Sigma4 / slice steps in the slice precision S,
-// kept for the backward.
+// View-independent intermediates of one Gaussian (rotor, R, Sigma4) in the
+// slice precision S, kept for the backward.
 template <typename S>
 struct Geo {
   Params p;
   RotorNorm<S> rn;
   S R[16];
   S sc2[4];
-  S C[10];
-  S invW, dt;
+  S C[10];  // Sigma4 upper triangle: xx xy xz xt yy yz yt zz zt tt
+  float opacity;
 };
 
 template <typename S, bool kScaleBF16>
-__device__ __forceinline__ void forward_geometry(const r4g_gaussians& g, int i, const CamDev& cam,
-                                                 float t, bool temporal_cull, Fwd& f,
-                                                 Geo<S>* keep = nullptr) {
-  Params p;
-  load_params<kScaleBF16>(g, i, p);
-  S sc2[4];
+__device__ __forceinline__ void gauss_setup(const r4g_gaussians& g, int i, Geo<S>& G) {
+  load_params<kScaleBF16>(g, i, G.p);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float s = expf(p.ls[k]);
-    sc2[k] = static_cast<S>(s) * static_cast<S>(s);
+    const float s = expf(G.p.ls[k]);
+    G.sc2[k] = static_cast<S>(s) * static_cast<S>(s);
   }
-  f.opacity = 1.0f / (1.0f + expf(-p.logit));
-  RotorNorm<S> rn;
-  rotor_normalize<S>(p.rot, rn);
-  S R[16];
-  rotor_matrix<S>(rn.r, R);
+  G.opacity = 1.0f / (1.0f + expf(-G.p.logit));
+  rotor_normalize<S>(G.p.rot, G.rn);
+  rotor_matrix<S>(G.rn.r, G.R);
+  cov4<S>(G.R, G.sc2, G.C);
+}
+
+// What the per-view steps need of a Gaussian: Sigma4, the 4D mean, opacity.
+template <typename S>
+struct Sig4 {
   S C[10];
-  cov4<S>(R, sc2, C);
+  float mean[4];
+  float opacity;
+};
+
+template <typename S, bool kScaleBF16>
+__device__ __forceinline__ void gauss_sigma(const r4g_gaussians& g, int i, Sig4<S>& Q) {
+  Geo<S> G;
+  gauss_setup<S, kScaleBF16>(g, i, G);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) Q.C[k] = G.C[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Q.mean[k] = G.p.mean[k];
+  Q.opacity = G.opacity;
+}
+
+// Slice at t, cull, and EWA projection for one view; invW = 1 / Sigma_tt and
+// dt = t - mu_t are returned for the backward.
+template <typename S>
+__device__ __forceinline__ void view_geometry(const Sig4<S>& Q, const CamDev& cam, float t, bool temporal_cull,
+                                              Fwd& f, S& invW, S& dt) {
+  const S* C = Q.C;
+  const float* pm = Q.mean;
+  f.opacity = Q.opacity;
   // Sigma4 = [[U, V], [V^T, W]]: U = C[0,1,2; 1,4,5; 2,5,7], V = (C3, C6, C8), W = C9
   const S W = C[9];
-  const S invW = S(1) / W;
-  const S dt = static_cast<S>(t) - static_cast<S>(p.mean[3]);
+  invW = S(1) / W;
+  dt = static_cast<S>(t) - static_cast<S>(pm[3]);
   const S lam_dt2 = dt * dt * invW;
   const S V0 = C[3], V1 = C[6], V2 = C[8];
   const S mv = dt * invW;
-  f.mu3[0] = static_cast<float>(static_cast<S>(p.mean[0]) + mv * V0);
-  f.mu3[1] = static_cast<float>(static_cast<S>(p.mean[1]) + mv * V1);
-  f.mu3[2] = static_cast<float>(static_cast<S>(p.mean[2]) + mv * V2);
+  f.mu3[0] = static_cast<float>(static_cast<S>(pm[0]) + mv * V0);
+  f.mu3[1] = static_cast<float>(static_cast<S>(pm[1]) + mv * V1);
+  f.mu3[2] = static_cast<float>(static_cast<S>(pm[2]) + mv * V2);
   f.sig3[0] = static_cast<float>(C[0] - V0 * V0 * invW);
   f.sig3[1] = static_cast<float>(C[1] - V0 * V1 * invW);
   f.sig3[2] = static_cast<float>(C[2] - V0 * V2 * invW);
   f.sig3[3] = static_cast<float>(C[4] - V1 * V1 * invW);
   f.sig3[4] = static_cast<float>(C[5] - V1 * V2 * invW);
   f.sig3[5] = static_cast<float>(C[7] - V2 * V2 * invW);
-  if (keep) {
-    keep->p = p;
-    keep->rn = rn;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) keep->R[k] = R[k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) keep->sc2[k] = sc2[k];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) keep->C[k] = C[k];
-    keep->invW = invW;
-    keep->dt = dt;
-  }
   const float lam = static_cast<float>(lam_dt2);
   f.temporal = expf(-0.5f * lam);
   f.o_t = f.opacity * f.temporal;
@@ -204,99 +216,194 @@ __device__ __forceinline__ bool pixel_box(const Fwd& f, const CamDev& cam, int& 
   return i0 <= i1 && j0 <= j1;
 }
 
+// ---- view table ---------------------------------------------------------------
+struct HostViews {
+  r4g_view v[kMaxViews];
+};
+struct GeomTable {
+  ViewGeom g[kMaxViews];
+};
+
+// One thread per view: the camera as the kernels use it (rotation, centre
+// -R^T t, focal lengths and the 1.3 tan(fov/2) clamp of J) from the host
+// views (a kernel parameter) or from device views, and the view's place in
+// the batch. A device view whose image size differs from the host layout
+// sets status bit 2 and is rendered with the layout's size.
+__global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* __restrict__ vdev, int nviews,
+                                   ViewDev* __restrict__ out, FrameHeader* hdr) {
+  const int v = threadIdx.x;
+  if (v >= nviews) return;
+  const r4g_view V = vdev ? vdev[v] : hv.v[v];
+  const ViewGeom& G = gt.g[v];
+  ViewDev d;
+  CamDev& c = d.cam;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c.R[3 * k + j] = V.cam.world_to_cam[4 * k + j];
+    c.t[k] = V.cam.world_to_cam[4 * k + 3];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc = __dadd_rn(acc, -__dmul_rn(static_cast<double>(c.R[3 * k + j]), c.t[k]));
+    c.pos[j] = static_cast<float>(acc);
+  }
+  c.fx = V.cam.fx;
+  c.fy = V.cam.fy;
+  c.cx = V.cam.cx;
+  c.cy = V.cam.cy;
+  c.limx = static_cast<float>(static_cast<double>(kClampFov) * (G.width / (2.0 * static_cast<double>(c.fx))));
+  c.limy = static_cast<float>(static_cast<double>(kClampFov) * (G.height / (2.0 * static_cast<double>(c.fy))));
+  c.width = G.width;
+  c.height = G.height;
+  d.t = V.t;
+  d.tiles_x = G.tiles_x;
+  d.tiles_y = G.tiles_y;
+  d.tile_off = G.tile_off;
+  d.pix_off = G.pix_off;
+  d.tdiff_off = G.tdiff_off;
+  d.pad[0] = d.pad[1] = d.pad[2] = 0u;
+  if (V.cam.width != G.width || V.cam.height != G.height) atomicOr(&hdr->status, 4u);
+  out[v] = d;
+}
+
+cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
+                               const r4g_view* views_dev, cudaStream_t s) {
+  HostViews hv;
+  GeomTable gt;
+  for (int v = 0; v < L.nviews; ++v) {
+    hv.v[v] = views_host ? views_host[v] : r4g_view{};
+    gt.g[v] = L.geom[v];
+  }
+  setup_views_kernel<<<1, kMaxViews, 0, s>>>(hv, gt, views_dev, L.nviews, at<ViewDev>(frame, L.views),
+                                             at<FrameHeader>(frame, L.header));
+  return cudaGetLastError();
+}
+
+// ---- forward ------------------------------------------------------------------
 template <typename S, bool kScaleBF16, bool kShBF16>
 __global__ void __launch_bounds__(kPreBlock)
-    preprocess_fwd_kernel(r4g_gaussians g, CamDev cam, float t, PreOut out, int sh_degree,
-                          bool temporal_cull) {
+    preprocess_fwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews, PreOut out,
+                          int sh_degree, bool temporal_cull) {
+  __shared__ uint32_t s_pairs[kMaxViews];
+  __shared__ uint32_t s_wcnt[kPreBlock / 32];
+  __shared__ uint32_t s_vis, s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = threadIdx.x; v < kMaxViews; v += kPreBlock) s_pairs[v] = 0;
+  if (threadIdx.x == 0) s_vis = 0;
+  __syncthreads();
   const int i = blockIdx.x * kPreBlock + threadIdx.x;
-  uint32_t ntiles = 0;
-  if (i < g.n) {
-    Fwd f;
-    forward_geometry<S, kScaleBF16>(g, i, cam, t, temporal_cull, f);
-    int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
-    bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
-    if (vis) {
-      forward_color<kShBF16>(g, i, cam, sh_degree, f);
-      const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
-      const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
-      ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
-      out.recA[i] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
-      out.recB[i] = make_float4(f.conic[2], f.o_t, f.pc[2], 0.0f);
-      out.recC[i] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
-      out.rect[i] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
-                               static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
-      // +1 on every tile of the rectangle, as four corner updates
-      const int st = out.tiles_x + 1;
-      atomicAdd(out.tdiff + y0 * st + x0, 1u);
-      atomicAdd(out.tdiff + y0 * st + x1, 0xffffffffu);
-      atomicAdd(out.tdiff + y1 * st + x0, 0xffffffffu);
-      atomicAdd(out.tdiff + y1 * st + x1, 1u);
-    } else {
-      out.recA[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      out.recB[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      out.recC[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      out.rect[i] = make_uint2(0u, 0u);
+  const bool live = i < g.n;
+  Sig4<S> G;
+  if (live) gauss_sigma<S, kScaleBF16>(g, i, G);
+  uint32_t nvis = 0;
+  const size_t M = static_cast<size_t>(g.n) * nviews;
+  for (int v = 0; v < nviews; ++v) {
+    uint32_t ntiles = 0;
+    if (live) {
+      const ViewDev& V = views[v];
+      const CamDev& cam = V.cam;
+      const size_t item = static_cast<size_t>(v) * g.n + i;
+      Fwd f;
+      S invW, dt;
+      view_geometry<S>(G, cam, V.t, temporal_cull, f, invW, dt);
+      int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
+      const bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
+      if (vis) {
+        forward_color<kShBF16>(g, i, cam, sh_degree, f);
+        const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
+        const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
+        ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
+        out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
+        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], 0.0f);
+        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
+        out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
+                                    static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
+        // +1 on every tile of the rectangle, as four corner updates
+        uint32_t* td = out.tdiff + V.tdiff_off;
+        const int st = V.tiles_x + 1;
+        atomicAdd(td + y0 * st + x0, 1u);
+        atomicAdd(td + y0 * st + x1, 0xffffffffu);
+        atomicAdd(td + y1 * st + x0, 0xffffffffu);
+        atomicAdd(td + y1 * st + x1, 1u);
+      } else {
+        out.recA[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.recA[M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.recA[2 * M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.rect[item] = make_uint2(0u, 0u);
+      }
+      out.touched[item] = ntiles;
+      out.dkey[item] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
     }
-    out.touched[i] = ntiles;
-    out.dkey[i] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, ntiles);
+    if (lane == 0 && ws) atomicAdd(&s_pairs[v], ws);
+    nvis += ntiles > 0 ? 1u : 0u;
   }
-  // per-block totals of the tile counts and of the visible Gaussians
-  __shared__ uint32_t s_sum[kPreBlock / 32], s_vis[kPreBlock / 32];
-  const uint32_t ws = __reduce_add_sync(0xffffffffu, ntiles);
-  const uint32_t wv = __reduce_add_sync(0xffffffffu, ntiles > 0 ? 1u : 0u);
-  if ((threadIdx.x & 31) == 0) {
-    s_sum[threadIdx.x >> 5] = ws;
-    s_vis[threadIdx.x >> 5] = wv;
+  // visible items, pairs per view, and the list of Gaussians visible in some
+  // view (appended per block, in index order within the block)
+  const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
+  const uint32_t lm = __ballot_sync(0xffffffffu, nvis > 0);
+  if (lane == 0) {
+    s_wcnt[warp] = __popc(lm);
+    if (wv) atomicAdd(&s_vis, wv);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t a = 0, b = 0;
+    uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < kPreBlock / 32; ++w) {
-      a += s_sum[w];
-      b += s_vis[w];
+      const uint32_t c = s_wcnt[w];
+      s_wcnt[w] = tot;
+      tot += c;
     }
-    out.blocksum[blockIdx.x] = a;
-    if (b) atomicAdd(&out.header->n_visible, b);
+    s_base = tot ? atomicAdd(&out.header->n_glist, tot) : 0u;
+    if (s_vis) atomicAdd(&out.header->n_visible, s_vis);
   }
+  for (int v = threadIdx.x; v < nviews; v += kPreBlock)
+    if (s_pairs[v]) atomicAdd(&out.header->view_pairs[v], s_pairs[v]);
+  __syncthreads();
+  if (nvis > 0) out.glist[s_base + s_wcnt[warp] + __popc(lm & ((1u << lane) - 1u))] = static_cast<uint32_t>(i);
 }
 
 template <typename S, bool A, bool B>
-static void launch_pre_t(const r4g_gaussians& g, const CamDev& cam, float t, const PreOut& o,
-                         int nblocks, int sh_degree, bool tc, cudaStream_t s) {
-  preprocess_fwd_kernel<S, A, B><<<nblocks, kPreBlock, 0, s>>>(g, cam, t, o, sh_degree, tc);
+static void launch_pre_t(const r4g_gaussians& g, const ViewDev* views, int nviews, const PreOut& o, int nblocks,
+                         int sh_degree, bool tc, cudaStream_t s) {
+  preprocess_fwd_kernel<S, A, B><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
 }
 
-cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, float t,
-                                  const FrameLayout& L, void* frame, int sh_degree,
+cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
   PreOut o;
   o.recA = at<float4>(frame, L.rec);
-  o.recB = o.recA + L.n;
-  o.recC = o.recB + L.n;
   o.rect = at<uint2>(frame, L.rect);
   o.touched = at<uint32_t>(frame, L.touched);
   o.dkey = at<uint32_t>(frame, L.dkey0);
   o.tdiff = at<uint32_t>(frame, L.tdiff);
-  o.blocksum = at<uint32_t>(frame, L.blocksum);
+  o.glist = at<uint32_t>(frame, L.glist);
   o.header = at<FrameHeader>(frame, L.header);
-  o.tile_w = L.tile_w; o.tile_h = L.tile_h; o.tiles_x = L.tiles_x; o.tiles_y = L.tiles_y;
+  o.tile_w = L.tile_w;
+  o.tile_h = L.tile_h;
+  const ViewDev* views = at<ViewDev>(frame, L.views);
   const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
   const bool f64 = flags & R4G_FLAG_FP64_SLICE;
   const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
-  const int nb = L.nblocks;
+  const int nb = static_cast<int>((L.n + kPreBlock - 1) / kPreBlock);
+#define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, o, nb, sh_degree, tc, s)
   if (f64) {
-    if (sb && hb) launch_pre_t<double, true, true>(g, cam, t, o, nb, sh_degree, tc, s);
-    else if (sb) launch_pre_t<double, true, false>(g, cam, t, o, nb, sh_degree, tc, s);
-    else if (hb) launch_pre_t<double, false, true>(g, cam, t, o, nb, sh_degree, tc, s);
-    else launch_pre_t<double, false, false>(g, cam, t, o, nb, sh_degree, tc, s);
+    if (sb && hb) R4G_PF(double, true, true);
+    else if (sb) R4G_PF(double, true, false);
+    else if (hb) R4G_PF(double, false, true);
+    else R4G_PF(double, false, false);
   } else {
-    if (sb && hb) launch_pre_t<float, true, true>(g, cam, t, o, nb, sh_degree, tc, s);
-    else if (sb) launch_pre_t<float, true, false>(g, cam, t, o, nb, sh_degree, tc, s);
-    else if (hb) launch_pre_t<float, false, true>(g, cam, t, o, nb, sh_degree, tc, s);
-    else launch_pre_t<float, false, false>(g, cam, t, o, nb, sh_degree, tc, s);
+    if (sb && hb) R4G_PF(float, true, true);
+    else if (sb) R4G_PF(float, true, false);
+    else if (hb) R4G_PF(float, false, true);
+    else R4G_PF(float, false, false);
   }
+#undef R4G_PF
   return cudaGetLastError();
 }
 
@@ -400,61 +507,26 @@ __device__ __forceinline__ void rotor_normalize_bwd(const float rin[8], const Ro
 
 constexpr int kBwdBlock = 128;
 
-// The backward runs over the depth order, whose first n_visible entries are
-// the Gaussians with tiles, so every warp is full. Each warp first sums, for
-// each of its 32 Gaussians in turn, the per-pair gradients the blend
-// backward wrote (a Gaussian's pairs are contiguous, [offs[j], offs[j] + cnt)),
-// reading them coalesced; then every thread runs its Gaussian's chain rule.
-template <typename S, bool kScaleBF16, bool kShBF16>
-__global__ void __launch_bounds__(kBwdBlock, 4)
-    preprocess_bwd_kernel(r4g_gaussians g, CamDev cam, float t, const uint32_t* __restrict__ order,
-                          const uint32_t* __restrict__ offs, const uint32_t* __restrict__ touched,
-                          const float4* __restrict__ gbuf, const FrameHeader* hdr, int sh_degree,
-                          bool temporal_cull, r4g_grads out) {
-  const int j = blockIdx.x * kBwdBlock + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const int nvis = static_cast<int>(hdr->n_visible);
-  if ((hdr->status & 1u) || (j - lane) >= nvis) return;  // warp-uniform (overflowed frame: no gradient)
-  const bool mine = j < nvis;
-  const uint32_t gi = mine ? order[j] : 0u;
-  const uint32_t o = mine ? offs[j] : 0u;
-  const uint32_t cnt = mine ? touched[gi] : 0u;
-  // warp-cooperative gather of the pair gradients: lane l adds pairs l, l+32, ...
-  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
-  for (int q = 0; q < 32; ++q) {
-    const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
-    if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
-    const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
-    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (uint32_t k = lane; k < qc; k += 32) {
-      const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
-      const float4 x = pr[0], y = pr[1], z = pr[2];
-      v[0] += x.x; v[1] += x.y; v[2] += x.z; v[3] += x.w;
-      v[4] += y.x; v[5] += y.y;
-      v[6] += z.x; v[7] += z.y; v[8] += z.z;
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-#pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], sh);
-    }
-    if (lane == q) {
-      ga = make_float4(v[0], v[1], v[2], v[3]);
-      gb = make_float4(v[4], v[5], 0.f, 0.f);
-      gc = make_float4(v[6], v[7], v[8], 0.f);
-    }
-  }
-  if (cnt == 1) {
-    const float4* pr = gbuf + 3 * static_cast<size_t>(o);
-    ga = pr[0];
-    gb = pr[1];
-    gc = pr[2];
-  }
-  if (!mine) return;
-  const int i = static_cast<int>(gi);
+// Gradient sums over the views of one Gaussian, in the slice precision S.
+template <typename S>
+struct BwdAcc {
+  S G4[10];   // symmetric d Sigma4, upper triangle (xx xy xz xt yy yz yt zz zt tt)
+  S gmean[4];
+  S gop;      // d opacity
+};
+
+// One view's part of the backward of one Gaussian: from the summed per-pair
+// gradients (ga = d mean2d.x, d mean2d.y, d conic a, d conic b; gb.x = d conic
+// c, gb.y = d opacity_t; gc = d rgb) through the colour, the conic, the EWA
+// projection and the temporal slice, down to d Sigma4, d mean and d opacity
+// (accumulated in acc) and d SH (added to the SH gradient row).
+template <typename S, bool kShBF16>
+__device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, const Sig4<S>& G, const CamDev& cam,
+                                              float t, int sh_degree, bool temporal_cull, float4 ga, float4 gb,
+                                              float4 gc, float* __restrict__ gsh, BwdAcc<S>& acc) {
   Fwd f;
-  Geo<S> G;
-  forward_geometry<S, kScaleBF16>(g, i, cam, t, temporal_cull, f, &G);
+  S invW, dt;
+  view_geometry<S>(G, cam, t, temporal_cull, f, invW, dt);
   float shc[16][3], Y[16];
   forward_color<kShBF16>(g, i, cam, sh_degree, f, shc, Y);
 
@@ -466,7 +538,7 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   for (int k = 0; k < 16; ++k) wk[k] = shc[k][0] * grgb[0] + shc[k][1] * grgb[1] + shc[k][2] * grgb[2];
   {
     // d c_k = Y_k d rgb, accumulated as 16-byte vectors over the 48-float row
-    float4* gsh4 = reinterpret_cast<float4*>(out.sh + static_cast<size_t>(i) * 48);
+    float4* gsh4 = reinterpret_cast<float4*>(gsh + static_cast<size_t>(i) * 48);
     const int nvec = (nb * 3 + 3) / 4;
 #pragma unroll
     for (int v = 0; v < 12; ++v) {
@@ -574,7 +646,6 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   // ---- temporal slice (slice precision S)
   const S* C = G.C;
   const S V[3] = {C[3], C[6], C[8]};
-  const S invW = G.invW, dt = G.dt;
   const S got = static_cast<S>(gb.y);
   const S g_o = got * static_cast<S>(f.temporal);
   const S g_lam = S(-0.5) * got * static_cast<S>(f.o_t);
@@ -600,15 +671,99 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   gdt += S(2) * dt * invW * g_lam;
   ginvW += dt * dt * g_lam;
   const S gW = -invW * invW * ginvW;
+  acc.G4[0] += static_cast<S>(GS[0][0]);
+  acc.G4[1] += static_cast<S>(GS[0][1]);
+  acc.G4[2] += static_cast<S>(GS[0][2]);
+  acc.G4[3] += S(0.5) * gV[0];
+  acc.G4[4] += static_cast<S>(GS[1][1]);
+  acc.G4[5] += static_cast<S>(GS[1][2]);
+  acc.G4[6] += S(0.5) * gV[1];
+  acc.G4[7] += static_cast<S>(GS[2][2]);
+  acc.G4[8] += S(0.5) * gV[2];
+  acc.G4[9] += gW;
+  acc.gmean[0] += gmxyz[0];
+  acc.gmean[1] += gmxyz[1];
+  acc.gmean[2] += gmxyz[2];
+  acc.gmean[3] -= gdt;
+  acc.gop += g_o;
+}
+
+// Backward of the preprocess over the Gaussians visible in some view (the
+// list the forward built). For each view, each warp first sums, for each of
+// its 32 Gaussians in turn, the per-pair gradients the blend backward wrote
+// (an item's pairs are contiguous, [ioffs[item], ioffs[item] + touched[item])),
+// reading them coalesced; then every thread runs its Gaussian's view
+// backward. After the views, the Sigma4 -> R -> rotor and scale backward runs
+// once per Gaussian and the gradients are added to the caller's buffers.
+// Every Gaussian is one thread's: the gradient is deterministic.
+template <typename S, bool kScaleBF16, bool kShBF16>
+__global__ void __launch_bounds__(kBwdBlock, 3)
+    preprocess_bwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews,
+                          const uint32_t* __restrict__ glist, const uint32_t* __restrict__ ioffs,
+                          const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
+                          const FrameHeader* hdr, int sh_degree, bool temporal_cull, r4g_grads out) {
+  const int j = blockIdx.x * kBwdBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int nlist = static_cast<int>(hdr->n_glist);
+  if ((hdr->status & 1u) || (j - lane) >= nlist) return;  // warp-uniform (overflowed frame: no gradient)
+  const bool mine = j < nlist;
+  const int i = mine ? static_cast<int>(glist[j]) : 0;
+  Sig4<S> Q;
+  if (mine) gauss_sigma<S, kScaleBF16>(g, i, Q);
+  BwdAcc<S> acc;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc.G4[k] = S(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc.gmean[k] = S(0);
+  acc.gop = S(0);
+  for (int v = 0; v < nviews; ++v) {
+    const size_t item = static_cast<size_t>(v) * g.n + i;
+    const uint32_t cnt = mine ? touched[item] : 0u;
+    if (__ballot_sync(0xffffffffu, cnt != 0u) == 0u) continue;
+    const uint32_t o = cnt ? ioffs[item] : 0u;
+    // warp-cooperative gather of the pair gradients: lane l adds pairs l, l+32, ...
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+    for (int q = 0; q < 32; ++q) {
+      const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
+      if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
+      const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
+      float v9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (uint32_t k = lane; k < qc; k += 32) {
+        const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
+        const float4 x = pr[0], y = pr[1], z = pr[2];
+        v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
+        v9[4] += y.x; v9[5] += y.y;
+        v9[6] += z.x; v9[7] += z.y; v9[8] += z.z;
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], sh);
+      }
+      if (lane == q) {
+        ga = make_float4(v9[0], v9[1], v9[2], v9[3]);
+        gb = make_float4(v9[4], v9[5], 0.f, 0.f);
+        gc = make_float4(v9[6], v9[7], v9[8], 0.f);
+      }
+    }
+    if (cnt == 1) {
+      const float4* pr = gbuf + 3 * static_cast<size_t>(o);
+      ga = pr[0];
+      gb = pr[1];
+      gc = pr[2];
+    }
+    if (cnt) view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc,
+                                       out.sh, acc);
+  }
+  if (!mine) return;
+  Geo<S> G;  // the rotor and scale intermediates, recomputed rather than kept through the views
+  gauss_setup<S, kScaleBF16>(g, i, G);
   // symmetric gradient of Sigma4
   S G4[4][4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int b = 0; b < 3; ++b) G4[a][b] = static_cast<S>(GS[a][b]);
-    G4[a][3] = G4[3][a] = S(0.5) * gV[a];
-  }
-  G4[3][3] = gW;
+  G4[0][0] = acc.G4[0]; G4[0][1] = G4[1][0] = acc.G4[1]; G4[0][2] = G4[2][0] = acc.G4[2];
+  G4[0][3] = G4[3][0] = acc.G4[3]; G4[1][1] = acc.G4[4]; G4[1][2] = G4[2][1] = acc.G4[5];
+  G4[1][3] = G4[3][1] = acc.G4[6]; G4[2][2] = acc.G4[7]; G4[2][3] = G4[3][2] = acc.G4[8];
+  G4[3][3] = acc.G4[9];
   // ---- Sigma4 = R diag(sc2) R^T
   const S* R = G.R;
   S gR[16], gsc2[4];
@@ -634,10 +789,10 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   // accumulate (+=) with 16-byte vector accesses
   float4* gm = reinterpret_cast<float4*>(out.mean) + i;
   float4 vm = *gm;
-  vm.x += static_cast<float>(gmxyz[0]);
-  vm.y += static_cast<float>(gmxyz[1]);
-  vm.z += static_cast<float>(gmxyz[2]);
-  vm.w += static_cast<float>(-gdt);
+  vm.x += static_cast<float>(acc.gmean[0]);
+  vm.y += static_cast<float>(acc.gmean[1]);
+  vm.z += static_cast<float>(acc.gmean[2]);
+  vm.w += static_cast<float>(acc.gmean[3]);
   *gm = vm;
   float4* gr = reinterpret_cast<float4*>(out.rotor) + 2 * static_cast<size_t>(i);
   float4 r0 = gr[0], r1 = gr[1];
@@ -654,37 +809,26 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   vl.z += static_cast<float>(gsc2[2] * S(2) * G.sc2[2]);
   vl.w += static_cast<float>(gsc2[3] * S(2) * G.sc2[3]);
   *gl = vl;
-  out.logit[i] += static_cast<float>(g_o) * f.opacity * (1.0f - f.opacity);
+  out.logit[i] += static_cast<float>(acc.gop) * G.opacity * (1.0f - G.opacity);
 }
-
-struct BwdIn {
-  const uint32_t *order, *offs, *touched;
-  const float4* gbuf;
-  const FrameHeader* hdr;
-};
 
 template <typename S, bool A, bool B>
-static void launch_pre_bwd_t(const r4g_gaussians& g, const CamDev& cam, float t, const BwdIn& in, int nblocks,
-                             int sh_degree, bool tc, const r4g_grads& out, cudaStream_t s) {
-  preprocess_bwd_kernel<S, A, B><<<nblocks, kBwdBlock, 0, s>>>(g, cam, t, in.order, in.offs, in.touched, in.gbuf,
-                                                               in.hdr, sh_degree, tc, out);
+static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree, bool tc,
+                             const r4g_grads& out, cudaStream_t s) {
+  const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
+  preprocess_bwd_kernel<S, A, B><<<nb, kBwdBlock, 0, s>>>(
+      g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist), at<uint32_t>(frame, L.ioffs),
+      at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf), at<FrameHeader>(frame, L.header), sh_degree, tc,
+      out);
 }
 
-cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const CamDev& cam, float t,
-                                  const FrameLayout& L, void* frame, int sh_degree,
+cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, r4g_grads grads, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
-  BwdIn in;
-  in.order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
-  in.offs = at<uint32_t>(frame, L.offs);
-  in.touched = at<uint32_t>(frame, L.touched);
-  in.gbuf = at<float4>(frame, L.gbuf);
-  in.hdr = at<FrameHeader>(frame, L.header);
   const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
   const bool f64 = flags & R4G_FLAG_FP64_SLICE;
   const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
-  const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
-#define R4G_PB(S_, A_, B_) launch_pre_bwd_t<S_, A_, B_>(g, cam, t, in, nb, sh_degree, tc, grads, s)
+#define R4G_PB(S_, A_, B_) launch_pre_bwd_t<S_, A_, B_>(g, L, frame, sh_degree, tc, grads, s)
   if (f64) {
     if (sb && hb) R4G_PB(double, true, true);
     else if (sb) R4G_PB(double, true, false);

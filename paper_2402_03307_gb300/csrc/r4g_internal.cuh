@@ -19,7 +19,7 @@ constexpr float kNear = 0.2f;
 constexpr float kDilation = 0.3f;      // low-pass term added to the 2D covariance
 constexpr float kClampFov = 1.3f;      // J is taken with x/z, y/z within 1.3 tan(fov/2)
 
-// Camera as the kernels see it (passed by value).
+// Camera as the kernels see it.
 struct CamDev {
   float R[9];
   float t[3];
@@ -29,33 +29,66 @@ struct CamDev {
   int width, height;
 };
 
+// Views of one call. A call renders V (camera, t) views of the same
+// Gaussians; every per-Gaussian array of the frame holds V * N items, item
+// v * N + i being Gaussian i seen by view v. Tile ids are global: view v owns
+// [tile_off, tile_off + tiles_x * tiles_y). Images, T and stop positions are
+// packed view after view (view v's pixels start at pix_off).
+constexpr int kMaxViews = 64;
+
+struct ViewDev {  // kernel-side view table entry (in the frame), 128 bytes
+  CamDev cam;
+  float t;
+  int tiles_x, tiles_y;
+  uint32_t tile_off, pix_off, tdiff_off;
+  uint32_t pad[3];
+};
+static_assert(sizeof(ViewDev) == 128, "view table entry size");
+
+struct ViewGeom {  // host-side view geometry (what the launch sizes depend on)
+  int width, height, tiles_x, tiles_y;
+  uint32_t tile_off, pix_off, tdiff_off;
+};
+
 // Frame header at the start of every frame buffer (device memory).
 struct FrameHeader {
   uint32_t status;        // bit 0: key overflow, bit 1: a sort look-back gave up waiting
   uint32_t key_count;     // pairs actually written (min(needed, capacity))
   uint32_t key_needed;    // pairs the render needed
-  uint32_t n_visible;
+  uint32_t n_visible;     // visible (view, Gaussian) items
   unsigned long long composited;  // composited (pixel, Gaussian) pairs, counted on request
-  uint32_t pad[58];
+  uint32_t n_glist;       // Gaussians visible in at least one view (the backward's work list)
+  uint32_t next_tile;     // work counter of the persistent blend
+  uint32_t next_tile_bwd; // work counter of the persistent blend backward
+  uint32_t pad[55];
+  uint32_t view_pairs[kMaxViews];  // (tile, Gaussian) pairs per view
 };
+static_assert(sizeof(FrameHeader) == 512, "frame header size");
 
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
-  size_t header, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, srect, chunks, blocksum, keys0, vals0,
-      keys1, vals1, egid, gbuf,
-      ranges, tfinal, last, sortcnt, onesweep, total;
+  size_t header, views, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, ioffs, srect, chunks,
+      blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, ranges, tfinal, last, sortcnt, onesweep, total;
   int64_t n, cap;
-  int width, height, tile_w, tile_h, tiles_x, tiles_y, ntiles;
-  int nblocks;       // preprocess blocks (kPreBlock Gaussians each)
+  int64_t m;         // items: n * nviews
+  int nviews;
+  ViewGeom geom[kMaxViews];
+  int tile_w, tile_h;
+  int ntiles;        // tiles of all views
+  int64_t npix;      // pixels of all views
+  int tdiff_words;   // difference-array entries of all views
+  int max_view_tiles;
+  int width, height, tiles_x, tiles_y;  // of view 0
+  int nblocks;       // preprocess-order blocks over the items (kPreBlock each)
   int sort_ctas;     // CTAs of each radix pass over the keys
-  int depth_ctas;    // CTAs of each radix pass over the N depth keys
+  int depth_ctas;    // CTAs of each radix pass over the depth keys of the items
   int tile_bits;     // ceil(log2(ntiles)): bits of the tile sort
   bool order_in_1;   // the depth order ends in ord1 (else ord0)
   bool keys_in_1;    // the tile-sorted values end in vals1 (else vals0)
 };
 
-constexpr int kPreBlock = 256;
-constexpr int kMaxTiles = 51200;   // tiles per image (the tile-count kernel keeps them in shared memory)     // Gaussians per preprocess / key-build block
+constexpr int kPreBlock = 256;     // items per preprocess-order / key-build block
+constexpr int kMaxTiles = 51200;   // tiles per view (the tile-count kernel keeps them in shared memory)
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;        // items per thread per tile
 constexpr int kSortTile = kSortThreads * kSortIPT;
@@ -66,7 +99,9 @@ constexpr int kSortMaxCtas = 2 * 152;  // two CTAs per SM of a GB300; a multiple
 int sort_ctas_for(int64_t cap);
 // Sets the message r4g_last_error(NULL) returns on this host thread.
 void set_last_error(const char* msg);
-FrameLayout make_layout(int64_t n, int width, int height, int64_t cap, int tile_w, int tile_h);
+// Layout of a frame for n Gaussians and nviews views of the given sizes.
+FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nviews, int64_t cap, int tile_w,
+                        int tile_h);
 
 // Exponent of a Gaussian at a pixel, power = -1/2 (a dx^2 + 2 b dx dy + c dy^2),
 // with A = (mean2d.x, mean2d.y, a, b). Every rounding step is explicit so the
@@ -87,8 +122,10 @@ inline T* at(void* base, size_t off) {
 }
 
 // ---- launchers (return cudaGetLastError() after enqueueing) -----------------
-cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const CamDev& cam, float t,
-                                  const FrameLayout& L, void* frame, int sh_degree,
+// View table of the frame from host views (views_dev NULL) or device views.
+cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
+                               const r4g_view* views_dev, cudaStream_t s);
+cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, cudaStream_t s);
 // scan of the tile counts in depth order and key emission (tile key, index)
 cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s);
@@ -97,10 +134,6 @@ cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf
                         const uint32_t* count_dev, uint32_t count_host, int64_t cap,
                         int begin_bit, int end_bit, uint32_t* counts, int ctas,
                         cudaStream_t s, int* result_in_buf);
-cudaError_t launch_sort_u32(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
-                            uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
-                            int begin_bit, int end_bit, uint32_t* counts, int ctas, cudaStream_t s,
-                            int* result_in_buf);
 // One-kernel-per-pass radix sort of (uint32 key, uint32 value) on key bits
 // [0, bits) (see onesweep.cu); scratch holds onesweep_scratch_bytes(cap, bits).
 size_t onesweep_scratch_bytes(int64_t cap, int bits);
@@ -108,14 +141,13 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
                             int* result_in_buf, bool hist_ready = false);
-// per-tile counts -> ranges and the tile sort's digit histograms (hist[p][256])
+// per-tile counts -> ranges and the tile sort's digit histograms (hist[p][256],
+// zeroed by the caller)
 cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s);
-cudaError_t launch_ranges(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
-                          cudaStream_t s);
 // 64-bit (tile << 32 | depth bits) keys of the sorted list, for export
 cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                                const uint32_t* vals, uint64_t* out, cudaStream_t s);
-// Gaussian index of each sorted pair (the sort carries emission indices)
+// item index of each sorted pair (the sort carries emission indices)
 cudaError_t launch_export_values(const FrameLayout& L, void* frame, const uint32_t* vals, uint32_t* out,
                                  cudaStream_t s);
 cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* vals,
@@ -123,8 +155,7 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
                              uint32_t* out_last, bool count, cudaStream_t s);
 cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* vals,
                              const float* bg, const float* grad_rgb, cudaStream_t s);
-cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const CamDev& cam, float t,
-                                  const FrameLayout& L, void* frame, int sh_degree,
+cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
                                   uint32_t flags, r4g_grads grads, cudaStream_t s);
 
 }  // namespace r4g

@@ -275,12 +275,4 @@ cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf
                                counts, ctas, s, result_in_buf);
 }
 
-cudaError_t launch_sort_u32(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
-                            uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
-                            int begin_bit, int end_bit, uint32_t* counts, int ctas, cudaStream_t s,
-                            int* result_in_buf) {
-  return sort_passes<uint32_t>(kin, vin, kbuf1, vbuf1, kbuf2, vbuf2, count_dev, count_host, begin_bit, end_bit,
-                               counts, ctas, s, result_in_buf);
-}
-
 }  // namespace r4g

@@ -5,6 +5,8 @@ kernels.
     r = Renderer()                       # 16x16 tiles, black background, SH degree 3
     img = r.render(params, cam, t).image # [3, H, W] float32 on the GPU
     img = render(params, cam, t)         # autograd-aware (Render4DFunction)
+    res = r.render_batch(params, [(cam0, t0), (cam1, t1)])   # many views, one launch sequence
+    g = BatchGraph(r, params, views)     # the same, captured in a CUDA graph
 """
 from __future__ import annotations
 
@@ -30,6 +32,13 @@ def camera_struct(cam) -> abi.r4g_camera:
     c.fx, c.fy, c.cx, c.cy = float(get("fx")), float(get("fy")), float(get("cx")), float(get("cy"))
     c.width, c.height = int(get("width")), int(get("height"))
     return c
+
+
+def view_struct(cam, t: float) -> abi.r4g_view:
+    v = abi.r4g_view()
+    v.cam = camera_struct(cam)
+    v.t = float(t)
+    return v
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -69,6 +78,25 @@ class RenderResult:
     width: int
     height: int
     n: int
+
+
+@dataclass
+class BatchResult:
+    images: list               # per view [3, H_v, W_v] views into `packed`
+    packed: torch.Tensor       # all views' images, view after view
+    frame: torch.Tensor
+    key_capacity: int
+    views: list                # r4g_view structs of the call
+    n: int
+
+
+def _packed_views(packed: torch.Tensor, structs) -> list:
+    out, off = [], 0
+    for v in structs:
+        h, w = v.cam.height, v.cam.width
+        out.append(packed[off:off + 3 * h * w].view(3, h, w))
+        off += 3 * h * w
+    return out
 
 
 class Renderer:
@@ -147,6 +175,8 @@ class Renderer:
         s = (stream or torch.cuda.current_stream()).cuda_stream
         return abi.r4g_frame_status(self.ctx, res.frame.data_ptr(), res.frame.numel(), s)
 
+    status_of = status
+
     def backward(self, params: dict, cam, t: float, res: RenderResult, grad_image: torch.Tensor,
                  grads: dict, stream=None) -> None:
         """Accumulate dL/dparams into ``grads`` (float32 tensors shaped like the
@@ -165,6 +195,93 @@ class Renderer:
         s = (stream or torch.cuda.current_stream(gi.device)).cuda_stream
         abi.r4g_render_backward(self.ctx, g, c, float(t), gi.data_ptr(), out, res.frame.data_ptr(),
                                 res.frame.numel(), res.key_capacity, s)
+
+    # ---- batched views ---------------------------------------------------------
+    @staticmethod
+    def view_structs(views) -> list:
+        """r4g_view structs from (camera, t) pairs (or r4g_view structs)."""
+        return [v if isinstance(v, abi.r4g_view) else view_struct(v[0], v[1]) for v in views]
+
+    def batch_frame_bytes(self, n: int, views, key_capacity: int, tile=None) -> int:
+        return abi.r4g_batch_frame_bytes(self.ctx, n, self.view_structs(views), key_capacity, tile or (0, 0))
+
+    def render_batch(self, params: dict, views, *, frame: torch.Tensor | None = None,
+                     key_capacity: int | None = None, out: torch.Tensor | None = None,
+                     views_dev: torch.Tensor | None = None, check: bool = True, stream=None) -> BatchResult:
+        """Render every (camera, t) view of ``views`` in one batched call. The
+        images come back packed view after view (``packed``) and as per-view
+        [3, H, W] views (``images``). ``views_dev``: optional device copy of the
+        view structs (see :func:`views_tensor`) read by the kernels."""
+        g = gaussians_struct(params)
+        vs = self.view_structs(views)
+        dev = params["mean"].device
+        npix = sum(v.cam.width * v.cam.height for v in vs)
+        key = (g.n, tuple((v.cam.width, v.cam.height) for v in vs), self.tile)
+        cap = int(key_capacity or self._cap_hint.get(key) or max(1 << 16, self.keys_per_gaussian * max(g.n, 1) * len(vs)))
+        s = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        while True:
+            need_bytes = self.batch_frame_bytes(g.n, vs, cap)
+            if frame is None or frame.numel() < need_bytes:
+                frame = torch.empty(need_bytes, dtype=torch.uint8, device=dev)
+            packed = out if out is not None else torch.empty(3 * npix, dtype=torch.float32, device=dev)
+            abi.r4g_render_batch(self.ctx, g, vs, views_dev.data_ptr() if views_dev is not None else None,
+                                 packed.data_ptr(), None, frame.data_ptr(), frame.numel(), cap, s)
+            res = BatchResult(_packed_views(packed, vs), packed, frame, cap, vs, g.n)
+            if not check:
+                return res
+            st, need = abi.r4g_frame_status(self.ctx, frame.data_ptr(), frame.numel(), s)
+            if st == abi.R4G_OK:
+                return res
+            cap = int(need * 1.25) + 1024
+            self._cap_hint[key] = cap
+            frame = None
+
+    def backward_batch(self, params: dict, res: BatchResult, grad_packed: torch.Tensor, grads: dict,
+                       stream=None) -> None:
+        """Accumulate dL/dparams (summed over the views) into ``grads`` given
+        dL/d(packed images) of a batched render ``res``."""
+        g = gaussians_struct(params)
+        gp = grad_packed.contiguous()
+        if gp.dtype != torch.float32 or gp.numel() != res.packed.numel():
+            raise ValueError("grad_packed must be float32 with as many elements as the packed images")
+        out = abi.r4g_grads()
+        for k in PARAM_NAMES:
+            t_ = grads[k]
+            if t_.dtype != torch.float32 or not t_.is_contiguous() or t_.numel() != params[k].numel():
+                raise ValueError(f"grads[{k}] must be a contiguous float32 tensor like the parameter")
+            setattr(out, k, t_.data_ptr())
+        s = (stream or torch.cuda.current_stream(gp.device)).cuda_stream
+        abi.r4g_render_batch_backward(self.ctx, g, res.views, gp.data_ptr(), out, res.frame.data_ptr(),
+                                      res.frame.numel(), res.key_capacity, s)
+
+    def autotune(self, params: dict, views, *, backward: bool = True, reps: int = 3,
+                 key_capacity: int | None = None) -> dict:
+        """Time the batched render (and backward) for 8x8, 16x16 and 16x32 tiles
+        and keep the fastest on this renderer (r4g_autotune_batch)."""
+        g = gaussians_struct(params)
+        vs = self.view_structs(views)
+        dev = params["mean"].device
+        npix = sum(v.cam.width * v.cam.height for v in vs)
+        cap = int(key_capacity or max(1 << 16, self.keys_per_gaussian * max(g.n, 1) * len(vs)))
+        nbytes = max(self.batch_frame_bytes(g.n, vs, cap, tile) for tile in abi.TUNE_SHAPES)
+        frame = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        packed = torch.empty(3 * npix, dtype=torch.float32, device=dev)
+        gimg = grads = gstruct = None
+        if backward:
+            gimg = torch.full((3 * npix,), 1.0 / (3 * npix), dtype=torch.float32, device=dev)
+            grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+            gstruct = abi.r4g_grads()
+            for k in PARAM_NAMES:
+                setattr(gstruct, k, grads[k].data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream
+        out = abi.r4g_autotune_batch(self.ctx, g, vs, packed.data_ptr(), gimg.data_ptr() if backward else None,
+                                     gstruct, frame.data_ptr(), frame.numel(), cap, reps, s)
+        self.tile = tuple(out["tile"])
+        return out
+
+    def set_tile(self, tile) -> None:
+        abi.r4g_set_tile(self.ctx, int(tile[0]), int(tile[1]))
+        self.tile = (int(tile[0]), int(tile[1]))
 
     def export(self, res: RenderResult, stream=None) -> dict:
         """Sorted keys / values, tile ranges and screen records of a frame (tests, tools)."""
@@ -209,6 +326,97 @@ class Render4DFunction(torch.autograd.Function):
         return (*out, None, None, None)
 
 
+class Render4DBatchFunction(torch.autograd.Function):
+    """packed images of V views = render_batch(mean, ..., sh; views) with the
+    batched CUDA backward (r4g_render_batch_backward)."""
+
+    @staticmethod
+    def forward(ctx, mean, rotor, logscale, logit, sh, renderer: Renderer, views):
+        params = {"mean": mean.detach(), "rotor": rotor.detach(), "logscale": logscale.detach(),
+                  "logit": logit.detach(), "sh": sh.detach()}
+        res = renderer.render_batch(params, views)
+        ctx.renderer, ctx.res = renderer, res
+        ctx.save_for_backward(mean, rotor, logscale, logit, sh)
+        return res.packed
+
+    @staticmethod
+    def backward(ctx, grad_packed):
+        mean, rotor, logscale, logit, sh = ctx.saved_tensors
+        params = {"mean": mean, "rotor": rotor, "logscale": logscale, "logit": logit, "sh": sh}
+        grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=v.device) for k, v in params.items()}
+        ctx.renderer.backward_batch(params, ctx.res, grad_packed.float(), grads)
+        out = [grads[k].to(params[k].dtype) for k in PARAM_NAMES]
+        return (*out, None, None)
+
+
+def views_tensor(structs, device) -> torch.Tensor:
+    """Device copy (uint8 bytes) of r4g_view structs, for ``views_dev``."""
+    arr = abi.view_array(structs)
+    host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    return host.to(device)
+
+
+class BatchGraph:
+    """One batched render, and optionally its backward, captured in a CUDA
+    graph. The cameras and times live in a device table the kernels read, so
+    :meth:`replay` can take new views of the same image sizes. ``grad_fn``
+    (optional) maps the packed image to dL/d(packed image) with torch ops; it
+    is captured too. Gradients accumulate into ``self.grads`` (zeroed inside
+    the graph before the backward)."""
+
+    def __init__(self, renderer: Renderer, params: dict, views, key_capacity: int | None = None,
+                 grad_fn=None):
+        self.r = renderer
+        self.params = params
+        self.structs = renderer.view_structs(views)
+        dev = params["mean"].device
+        first = renderer.render_batch(params, self.structs, key_capacity=key_capacity)  # sizes the key buffer
+        self.cap = first.key_capacity if key_capacity else int(renderer.status_of(first)[1] * 1.2) + 4096
+        self.views_dev = views_tensor(self.structs, dev)
+        self.pinned = torch.empty(self.views_dev.numel(), dtype=torch.uint8).pin_memory()
+        self.frame = torch.empty(renderer.batch_frame_bytes(first.n, self.structs, self.cap), dtype=torch.uint8,
+                                 device=dev)
+        self.packed = torch.empty_like(first.packed)
+        self.grad_fn = grad_fn
+        self.grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()} \
+            if grad_fn is not None else None
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(2):  # warm up outside the capture
+                self._body(side)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body(torch.cuda.current_stream(dev))
+        self.images = _packed_views(self.packed, self.structs)
+
+    def _body(self, stream) -> None:
+        res = self.r.render_batch(self.params, self.structs, frame=self.frame, key_capacity=self.cap,
+                                  out=self.packed, views_dev=self.views_dev, check=False, stream=stream)
+        if self.grad_fn is not None:
+            for v in self.grads.values():
+                v.zero_()
+            gp = self.grad_fn(self.packed)
+            self.r.backward_batch(self.params, res, gp, self.grads, stream=stream)
+
+    def replay(self, views=None) -> None:
+        """Run the graph, with new (camera, t) views of the same sizes if given."""
+        if views is not None:
+            structs = self.r.view_structs(views)
+            if [(v.cam.width, v.cam.height) for v in structs] != [(v.cam.width, v.cam.height) for v in self.structs]:
+                raise ValueError("replayed views must keep the captured image sizes")
+            self.pinned.copy_(torch.frombuffer(bytearray(bytes(abi.view_array(structs))), dtype=torch.uint8))
+            self.views_dev.copy_(self.pinned, non_blocking=True)
+        self.graph.replay()
+
+    def status(self) -> tuple[int, int]:
+        """(status, keys needed) of the last replay (waits for the stream)."""
+        s = torch.cuda.current_stream(self.frame.device).cuda_stream
+        return abi.r4g_frame_status(self.r.ctx, self.frame.data_ptr(), self.frame.numel(), s)
+
+
 _default: Renderer | None = None
 
 
@@ -217,6 +425,13 @@ def default_renderer() -> Renderer:
     if _default is None:
         _default = Renderer()
     return _default
+
+
+def render_batch(params: dict, views, renderer: Renderer | None = None) -> torch.Tensor:
+    """Differentiable batched render -> packed images of all views."""
+    r = renderer or default_renderer()
+    return Render4DBatchFunction.apply(params["mean"], params["rotor"], params["logscale"], params["logit"],
+                                       params["sh"], r, list(views))
 
 
 def render(params: dict, cam, t: float, renderer: Renderer | None = None) -> torch.Tensor:
