@@ -58,6 +58,25 @@ def dist_env():
     return rank, world, local
 
 
+def frames_for_rank(rank: int, steps: int) -> list[int]:
+    """The sweep frames a replica renders: rank r takes steps r*K .. r*K+K-1 of
+    the sequence k -> 7k mod 300 (7 is prime to 300, so ranks do not repeat
+    each other's frames until the sweep is exhausted)."""
+    return [(rank * steps + i) * 7 % FRAMES for i in range(steps)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank float over the process group (the slowest replica
+    sets the job's time); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---- clocks ------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -178,7 +197,7 @@ def run_ours(args, rank, world, local):
         cap = max(cap, int(need * 1.1))
     frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
     img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
-    frames = [(rank * args.steps + i) * 7 % FRAMES for i in range(args.steps)]
+    frames = frames_for_rank(rank, args.steps)
 
     def render_frame(k):
         cam, t = frame_camera(k)
@@ -210,12 +229,7 @@ def run_ours(args, rank, world, local):
     if st != abi.R4G_OK:
         raise RuntimeError("key buffer overflow during the timed region")
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     fps = world * len(frames) / (total_ms / 1e3)
 
     # per-frame work of the timed frames, counted in an untimed instrumented pass

@@ -17,7 +17,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libr4g.so")
-SOURCES = ["preprocess.cu", "binning.cu", "sort.cu", "sort_noalloc.cu", "onesweep.cu", "blend.cu", "api.cu"]
+SOURCES = ["preprocess_fwd.cu", "preprocess.cu", "binning.cu", "sort.cu", "sort_noalloc.cu", "onesweep.cu",
+           "blend.cu", "api.cu"]
+# per-file flags: the forward preprocess rounds every multiply and add as
+# written (no contraction), so its one-view and multi-view kernels agree bit
+# for bit
+FILE_FLAGS = {"preprocess_fwd.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -51,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
   __shared__ uint32_t s_max;
   __shared__ int s_tile;
-  extern __shared__ float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
+  extern __shared__ __align__(16) float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
   for (;;) {
     __syncthreads();  // the previous tile is done with the shared buffers
     if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->next_tile_bwd, 1u));

@@ -1,412 +1,12 @@
-// Per-Gaussian preprocess of the render (forward): activations, rotor
-// normalisation and rotation (appendix A.1/A.2), Sigma4 (Sec. 3.2.1), the
-// temporal slice and visibility cull (Sec. 3.2.2, appendix A.3), EWA
-// projection (Sec. 3.1), SH colour, and the tile rectangle each Gaussian's
-// contributing pixels can lie in. One thread per Gaussian for all the views
-// of a call: the view-independent part (parameters, rotor, R, Sigma4) is
-// computed once, the slice and projection once per view. Coalesced 16-byte
-// loads of the SoA parameters; the SH row is read only for survivors.
+// Backward of the per-Gaussian preprocess (Sec. 4.2 "CUDA Acceleration":
+// the rotor -> rotation and slicing steps differentiated by hand): colour,
+// conic, EWA projection, temporal slice per view, then Sigma4 -> R -> F_norm
+// and the activations once per Gaussian.
 #include <cuda_runtime.h>
 
-#include "r4g_internal.cuh"
-#include "r4g_math.cuh"
+#include "preprocess_common.cuh"
 
 namespace r4g {
-
-// Per-item outputs (item = view * N + Gaussian).
-struct PreOut {
-  float4* recA;  // [3][M] records: (mean2d.x, mean2d.y, conic a, conic b),
-                 // (conic c, opacity_t, depth, 0), (r, g, b, 0)
-  uint2* rect;   // tile rect: (x0 | y0 << 16, x1 | y1 << 16), [x0, x1) x [y0, y1)
-  uint32_t* touched;
-  uint32_t* dkey;  // float bits of the depth for items with tiles, else 0xffffffff
-  uint32_t* tdiff; // per view, 2D difference array of the tile counts, (tiles_y + 1) x (tiles_x + 1)
-  uint32_t* glist; // Gaussians visible in some view
-  FrameHeader* header;
-  int tile_w, tile_h;
-};
-
-// Everything the forward computes for one Gaussian, kept so the backward can
-// reuse the same code path.
-struct Fwd {
-  bool visible;
-  float opacity, o_t, temporal;
-  float mu3[3], sig3[6];  // xx, xy, xz, yy, yz, zz
-  float pc[3];
-  float mean2d[2];
-  float cov[3];  // dilated 2D covariance a, b, c
-  float conic[3];
-  float rgb[3];
-  bool rgb_pos[3];  // colour channel not clamped at 0
-  float dir[3];     // unit view direction
-  float dist;       // |mu3 - campos|
-  bool clampx, clampy;
-};
-
-// View-independent intermediates of one Gaussian (rotor, R, Sigma4) in the
-// slice precision S, kept for the backward.
-template <typename S>
-struct Geo {
-  Params p;
-  RotorNorm<S> rn;
-  S R[16];
-  S sc2[4];
-  S C[10];  // Sigma4 upper triangle: xx xy xz xt yy yz yt zz zt tt
-  float opacity;
-};
-
-template <typename S, bool kScaleBF16>
-__device__ __forceinline__ void gauss_setup(const r4g_gaussians& g, int i, Geo<S>& G) {
-  load_params<kScaleBF16>(g, i, G.p);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float s = expf(G.p.ls[k]);
-    G.sc2[k] = static_cast<S>(s) * static_cast<S>(s);
-  }
-  G.opacity = 1.0f / (1.0f + expf(-G.p.logit));
-  rotor_normalize<S>(G.p.rot, G.rn);
-  rotor_matrix<S>(G.rn.r, G.R);
-  cov4<S>(G.R, G.sc2, G.C);
-}
-
-// What the per-view steps need of a Gaussian: Sigma4, the 4D mean, opacity.
-template <typename S>
-struct Sig4 {
-  S C[10];
-  float mean[4];
-  float opacity;
-};
-
-template <typename S, bool kScaleBF16>
-__device__ __forceinline__ void gauss_sigma(const r4g_gaussians& g, int i, Sig4<S>& Q) {
-  Geo<S> G;
-  gauss_setup<S, kScaleBF16>(g, i, G);
-#pragma unroll
-  for (int k = 0; k < 10; ++k) Q.C[k] = G.C[k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Q.mean[k] = G.p.mean[k];
-  Q.opacity = G.opacity;
-}
-
-// Slice at t, cull, and EWA projection for one view; invW = 1 / Sigma_tt and
-// dt = t - mu_t are returned for the backward.
-template <typename S>
-__device__ __forceinline__ void view_geometry(const Sig4<S>& Q, const CamDev& cam, float t, bool temporal_cull,
-                                              Fwd& f, S& invW, S& dt) {
-  const S* C = Q.C;
-  const float* pm = Q.mean;
-  f.opacity = Q.opacity;
-  // Sigma4 = [[U, V], [V^T, W]]: U = C[0,1,2; 1,4,5; 2,5,7], V = (C3, C6, C8), W = C9
-  const S W = C[9];
-  invW = S(1) / W;
-  dt = static_cast<S>(t) - static_cast<S>(pm[3]);
-  const S lam_dt2 = dt * dt * invW;
-  const S V0 = C[3], V1 = C[6], V2 = C[8];
-  const S mv = dt * invW;
-  f.mu3[0] = static_cast<float>(static_cast<S>(pm[0]) + mv * V0);
-  f.mu3[1] = static_cast<float>(static_cast<S>(pm[1]) + mv * V1);
-  f.mu3[2] = static_cast<float>(static_cast<S>(pm[2]) + mv * V2);
-  f.sig3[0] = static_cast<float>(C[0] - V0 * V0 * invW);
-  f.sig3[1] = static_cast<float>(C[1] - V0 * V1 * invW);
-  f.sig3[2] = static_cast<float>(C[2] - V0 * V2 * invW);
-  f.sig3[3] = static_cast<float>(C[4] - V1 * V1 * invW);
-  f.sig3[4] = static_cast<float>(C[5] - V1 * V2 * invW);
-  f.sig3[5] = static_cast<float>(C[7] - V2 * V2 * invW);
-  const float lam = static_cast<float>(lam_dt2);
-  f.temporal = expf(-0.5f * lam);
-  f.o_t = f.opacity * f.temporal;
-  bool vis = !(temporal_cull && lam > kTemporalCut);
-
-  // world -> camera
-  const float* Rc = cam.R;
-  const float x = Rc[0] * f.mu3[0] + Rc[1] * f.mu3[1] + Rc[2] * f.mu3[2] + cam.t[0];
-  const float y = Rc[3] * f.mu3[0] + Rc[4] * f.mu3[1] + Rc[5] * f.mu3[2] + cam.t[1];
-  const float z = Rc[6] * f.mu3[0] + Rc[7] * f.mu3[1] + Rc[8] * f.mu3[2] + cam.t[2];
-  f.pc[0] = x; f.pc[1] = y; f.pc[2] = z;
-  vis = vis && (z > kNear);
-  const float iz = 1.0f / z;
-  // Jacobian of (fx x/z + cx, fy y/z + cy) at the clamped position
-  const float rx = x * iz, ry = y * iz;
-  const float crx = fminf(fmaxf(rx, -cam.limx), cam.limx);
-  const float cry = fminf(fmaxf(ry, -cam.limy), cam.limy);
-  f.clampx = crx != rx;
-  f.clampy = cry != ry;
-  const float j00 = cam.fx * iz, j02 = -cam.fx * crx * iz;
-  const float j11 = cam.fy * iz, j12 = -cam.fy * cry * iz;
-  // T = J Rc (2x3)
-  const float T0[3] = {j00 * Rc[0] + j02 * Rc[6], j00 * Rc[1] + j02 * Rc[7], j00 * Rc[2] + j02 * Rc[8]};
-  const float T1[3] = {j11 * Rc[3] + j12 * Rc[6], j11 * Rc[4] + j12 * Rc[7], j11 * Rc[5] + j12 * Rc[8]};
-  const float* s3 = f.sig3;
-  // M = T Sigma3
-  const float M0[3] = {T0[0] * s3[0] + T0[1] * s3[1] + T0[2] * s3[2],
-                       T0[0] * s3[1] + T0[1] * s3[3] + T0[2] * s3[4],
-                       T0[0] * s3[2] + T0[1] * s3[4] + T0[2] * s3[5]};
-  const float M1[3] = {T1[0] * s3[0] + T1[1] * s3[1] + T1[2] * s3[2],
-                       T1[0] * s3[1] + T1[1] * s3[3] + T1[2] * s3[4],
-                       T1[0] * s3[2] + T1[1] * s3[4] + T1[2] * s3[5]};
-  f.cov[0] = M0[0] * T0[0] + M0[1] * T0[1] + M0[2] * T0[2] + kDilation;
-  f.cov[1] = M0[0] * T1[0] + M0[1] * T1[1] + M0[2] * T1[2];
-  f.cov[2] = M1[0] * T1[0] + M1[1] * T1[1] + M1[2] * T1[2] + kDilation;
-  const float det = f.cov[0] * f.cov[2] - f.cov[1] * f.cov[1];
-  vis = vis && (det > 0.0f);
-  const float idet = 1.0f / det;
-  f.conic[0] = f.cov[2] * idet;
-  f.conic[1] = -f.cov[1] * idet;
-  f.conic[2] = f.cov[0] * idet;
-  f.mean2d[0] = cam.fx * rx + cam.cx;
-  f.mean2d[1] = cam.fy * ry + cam.cy;
-  // alpha <= opacity_t, so below 1/255 nothing is ever composited
-  vis = vis && (f.o_t >= kAlphaMin);
-  f.visible = vis;
-}
-
-template <bool kShBF16>
-__device__ __forceinline__ void forward_color(const r4g_gaussians& g, int i, const CamDev& cam,
-                                              int sh_degree, Fwd& f, float (*keep_c)[3] = nullptr,
-                                              float* keep_Y = nullptr) {
-  float d0 = f.mu3[0] - cam.pos[0], d1 = f.mu3[1] - cam.pos[1], d2 = f.mu3[2] - cam.pos[2];
-  const float dist = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-  const float idist = 1.0f / dist;
-  f.dist = dist;
-  f.dir[0] = d0 * idist; f.dir[1] = d1 * idist; f.dir[2] = d2 * idist;
-  float Y[16];
-  sh_basis(f.dir[0], f.dir[1], f.dir[2], Y);
-  const int nb = (sh_degree + 1) * (sh_degree + 1);
-  float c[16][3];
-  load_sh<kShBF16>(g.sh, i, nb, c);
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float acc = 0.5f;
-#pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (k < nb) acc += Y[k] * c[k][ch];
-    f.rgb_pos[ch] = acc > 0.0f;
-    f.rgb[ch] = fmaxf(acc, 0.0f);
-  }
-  if (keep_c) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      keep_Y[k] = k < nb ? Y[k] : 0.0f;
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) keep_c[k][ch] = k < nb ? c[k][ch] : 0.0f;
-    }
-  }
-}
-
-// Pixel-column range whose centres can lie inside the region where
-// alpha >= 1/255 and power >= -4.5, i.e. d^T conic d <= min(9, 2 ln(255 o_t)).
-// The axis-aligned box of that ellipse has half-widths sqrt(k2 Sigma'_xx) and
-// sqrt(k2 Sigma'_yy); a relative and an absolute slack keep the box a
-// superset under FP32 rounding. The box only selects tiles: each pixel still
-// applies the exact tests, so the image does not depend on the tile shape.
-__device__ __forceinline__ bool pixel_box(const Fwd& f, const CamDev& cam, int& i0, int& i1,
-                                          int& j0, int& j1) {
-  const float k2 = 1.01f * fminf(9.0f, 2.0f * logf(255.0f * f.o_t));
-  const float hx = sqrtf(k2 * f.cov[0]) + 0.5f;
-  const float hy = sqrtf(k2 * f.cov[2]) + 0.5f;
-  const float lim = 1e7f;
-  const float xa = fminf(fmaxf(f.mean2d[0] - hx - 0.5f, -lim), lim);
-  const float xb = fminf(fmaxf(f.mean2d[0] + hx - 0.5f, -lim), lim);
-  const float ya = fminf(fmaxf(f.mean2d[1] - hy - 0.5f, -lim), lim);
-  const float yb = fminf(fmaxf(f.mean2d[1] + hy - 0.5f, -lim), lim);
-  i0 = max(static_cast<int>(ceilf(xa)), 0);
-  i1 = min(static_cast<int>(floorf(xb)), cam.width - 1);
-  j0 = max(static_cast<int>(ceilf(ya)), 0);
-  j1 = min(static_cast<int>(floorf(yb)), cam.height - 1);
-  return i0 <= i1 && j0 <= j1;
-}
-
-// ---- view table ---------------------------------------------------------------
-struct HostViews {
-  r4g_view v[kMaxViews];
-};
-struct GeomTable {
-  ViewGeom g[kMaxViews];
-};
-
-// One thread per view: the camera as the kernels use it (rotation, centre
-// -R^T t, focal lengths and the 1.3 tan(fov/2) clamp of J) from the host
-// views (a kernel parameter) or from device views, and the view's place in
-// the batch. A device view whose image size differs from the host layout
-// sets status bit 2 and is rendered with the layout's size.
-__global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* __restrict__ vdev, int nviews,
-                                   ViewDev* __restrict__ out, FrameHeader* hdr) {
-  const int v = threadIdx.x;
-  if (v >= nviews) return;
-  const r4g_view V = vdev ? vdev[v] : hv.v[v];
-  const ViewGeom& G = gt.g[v];
-  ViewDev d;
-  CamDev& c = d.cam;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) c.R[3 * k + j] = V.cam.world_to_cam[4 * k + j];
-    c.t[k] = V.cam.world_to_cam[4 * k + 3];
-  }
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) acc = __dadd_rn(acc, -__dmul_rn(static_cast<double>(c.R[3 * k + j]), c.t[k]));
-    c.pos[j] = static_cast<float>(acc);
-  }
-  c.fx = V.cam.fx;
-  c.fy = V.cam.fy;
-  c.cx = V.cam.cx;
-  c.cy = V.cam.cy;
-  c.limx = static_cast<float>(static_cast<double>(kClampFov) * (G.width / (2.0 * static_cast<double>(c.fx))));
-  c.limy = static_cast<float>(static_cast<double>(kClampFov) * (G.height / (2.0 * static_cast<double>(c.fy))));
-  c.width = G.width;
-  c.height = G.height;
-  d.t = V.t;
-  d.tiles_x = G.tiles_x;
-  d.tiles_y = G.tiles_y;
-  d.tile_off = G.tile_off;
-  d.pix_off = G.pix_off;
-  d.tdiff_off = G.tdiff_off;
-  d.pad[0] = d.pad[1] = d.pad[2] = 0u;
-  if (V.cam.width != G.width || V.cam.height != G.height) atomicOr(&hdr->status, 4u);
-  out[v] = d;
-}
-
-cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
-                               const r4g_view* views_dev, cudaStream_t s) {
-  HostViews hv;
-  GeomTable gt;
-  for (int v = 0; v < L.nviews; ++v) {
-    hv.v[v] = views_host ? views_host[v] : r4g_view{};
-    gt.g[v] = L.geom[v];
-  }
-  setup_views_kernel<<<1, kMaxViews, 0, s>>>(hv, gt, views_dev, L.nviews, at<ViewDev>(frame, L.views),
-                                             at<FrameHeader>(frame, L.header));
-  return cudaGetLastError();
-}
-
-// ---- forward ------------------------------------------------------------------
-template <typename S, bool kScaleBF16, bool kShBF16>
-__global__ void __launch_bounds__(kPreBlock)
-    preprocess_fwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews, PreOut out,
-                          int sh_degree, bool temporal_cull) {
-  __shared__ uint32_t s_pairs[kMaxViews];
-  __shared__ uint32_t s_wcnt[kPreBlock / 32];
-  __shared__ uint32_t s_vis, s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = threadIdx.x; v < kMaxViews; v += kPreBlock) s_pairs[v] = 0;
-  if (threadIdx.x == 0) s_vis = 0;
-  __syncthreads();
-  const int i = blockIdx.x * kPreBlock + threadIdx.x;
-  const bool live = i < g.n;
-  Sig4<S> G;
-  if (live) gauss_sigma<S, kScaleBF16>(g, i, G);
-  uint32_t nvis = 0;
-  const size_t M = static_cast<size_t>(g.n) * nviews;
-  for (int v = 0; v < nviews; ++v) {
-    uint32_t ntiles = 0;
-    if (live) {
-      const ViewDev& V = views[v];
-      const CamDev& cam = V.cam;
-      const size_t item = static_cast<size_t>(v) * g.n + i;
-      Fwd f;
-      S invW, dt;
-      view_geometry<S>(G, cam, V.t, temporal_cull, f, invW, dt);
-      int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
-      const bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
-      if (vis) {
-        forward_color<kShBF16>(g, i, cam, sh_degree, f);
-        const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
-        const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
-        ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
-        out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
-        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], 0.0f);
-        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
-        out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
-                                    static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
-        // +1 on every tile of the rectangle, as four corner updates
-        uint32_t* td = out.tdiff + V.tdiff_off;
-        const int st = V.tiles_x + 1;
-        atomicAdd(td + y0 * st + x0, 1u);
-        atomicAdd(td + y0 * st + x1, 0xffffffffu);
-        atomicAdd(td + y1 * st + x0, 0xffffffffu);
-        atomicAdd(td + y1 * st + x1, 1u);
-      } else {
-        out.recA[item] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.recA[M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.recA[2 * M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
-        out.rect[item] = make_uint2(0u, 0u);
-      }
-      out.touched[item] = ntiles;
-      out.dkey[item] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
-    }
-    const uint32_t ws = __reduce_add_sync(0xffffffffu, ntiles);
-    if (lane == 0 && ws) atomicAdd(&s_pairs[v], ws);
-    nvis += ntiles > 0 ? 1u : 0u;
-  }
-  // visible items, pairs per view, and the list of Gaussians visible in some
-  // view (appended per block, in index order within the block)
-  const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
-  const uint32_t lm = __ballot_sync(0xffffffffu, nvis > 0);
-  if (lane == 0) {
-    s_wcnt[warp] = __popc(lm);
-    if (wv) atomicAdd(&s_vis, wv);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-#pragma unroll
-    for (int w = 0; w < kPreBlock / 32; ++w) {
-      const uint32_t c = s_wcnt[w];
-      s_wcnt[w] = tot;
-      tot += c;
-    }
-    s_base = tot ? atomicAdd(&out.header->n_glist, tot) : 0u;
-    if (s_vis) atomicAdd(&out.header->n_visible, s_vis);
-  }
-  for (int v = threadIdx.x; v < nviews; v += kPreBlock)
-    if (s_pairs[v]) atomicAdd(&out.header->view_pairs[v], s_pairs[v]);
-  __syncthreads();
-  if (nvis > 0) out.glist[s_base + s_wcnt[warp] + __popc(lm & ((1u << lane) - 1u))] = static_cast<uint32_t>(i);
-}
-
-template <typename S, bool A, bool B>
-static void launch_pre_t(const r4g_gaussians& g, const ViewDev* views, int nviews, const PreOut& o, int nblocks,
-                         int sh_degree, bool tc, cudaStream_t s) {
-  preprocess_fwd_kernel<S, A, B><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
-}
-
-cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
-                                  uint32_t flags, cudaStream_t s) {
-  if (L.n == 0) return cudaSuccess;
-  PreOut o;
-  o.recA = at<float4>(frame, L.rec);
-  o.rect = at<uint2>(frame, L.rect);
-  o.touched = at<uint32_t>(frame, L.touched);
-  o.dkey = at<uint32_t>(frame, L.dkey0);
-  o.tdiff = at<uint32_t>(frame, L.tdiff);
-  o.glist = at<uint32_t>(frame, L.glist);
-  o.header = at<FrameHeader>(frame, L.header);
-  o.tile_w = L.tile_w;
-  o.tile_h = L.tile_h;
-  const ViewDev* views = at<ViewDev>(frame, L.views);
-  const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
-  const bool f64 = flags & R4G_FLAG_FP64_SLICE;
-  const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
-  const int nb = static_cast<int>((L.n + kPreBlock - 1) / kPreBlock);
-#define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, o, nb, sh_degree, tc, s)
-  if (f64) {
-    if (sb && hb) R4G_PF(double, true, true);
-    else if (sb) R4G_PF(double, true, false);
-    else if (hb) R4G_PF(double, false, true);
-    else R4G_PF(double, false, false);
-  } else {
-    if (sb && hb) R4G_PF(float, true, true);
-    else if (sb) R4G_PF(float, true, false);
-    else if (hb) R4G_PF(float, false, true);
-    else R4G_PF(float, false, false);
-  }
-#undef R4G_PF
-  return cudaGetLastError();
-}
-
 
 // ---- backward ---------------------------------------------------------------
 // Gradient of the rotor -> matrix map (appendix A.2): every entry of R is a
@@ -696,8 +296,8 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 // backward. After the views, the Sigma4 -> R -> rotor and scale backward runs
 // once per Gaussian and the gradients are added to the caller's buffers.
 // Every Gaussian is one thread's: the gradient is deterministic.
-template <typename S, bool kScaleBF16, bool kShBF16>
-__global__ void __launch_bounds__(kBwdBlock, 3)
+template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
+__global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     preprocess_bwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews,
                           const uint32_t* __restrict__ glist, const uint32_t* __restrict__ ioffs,
                           const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
@@ -716,7 +316,7 @@ __global__ void __launch_bounds__(kBwdBlock, 3)
 #pragma unroll
   for (int k = 0; k < 4; ++k) acc.gmean[k] = S(0);
   acc.gop = S(0);
-  for (int v = 0; v < nviews; ++v) {
+  for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
     const size_t item = static_cast<size_t>(v) * g.n + i;
     const uint32_t cnt = mine ? touched[item] : 0u;
     if (__ballot_sync(0xffffffffu, cnt != 0u) == 0u) continue;
@@ -816,10 +416,10 @@ template <typename S, bool A, bool B>
 static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree, bool tc,
                              const r4g_grads& out, cudaStream_t s) {
   const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
-  preprocess_bwd_kernel<S, A, B><<<nb, kBwdBlock, 0, s>>>(
-      g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist), at<uint32_t>(frame, L.ioffs),
-      at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf), at<FrameHeader>(frame, L.header), sh_degree, tc,
-      out);
+  auto k = L.nviews > 1 ? preprocess_bwd_kernel<S, A, B, true> : preprocess_bwd_kernel<S, A, B, false>;
+  k<<<nb, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist),
+                             at<uint32_t>(frame, L.ioffs), at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf),
+                             at<FrameHeader>(frame, L.header), sh_degree, tc, out);
 }
 
 cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,

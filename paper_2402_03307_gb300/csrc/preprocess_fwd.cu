@@ -1,0 +1,216 @@
+// Per-Gaussian preprocess of the render (forward). One thread per Gaussian
+// for all the views of a call: the view-independent part (parameters,
+// rotor, R, Sigma4) is computed once, the slice and projection once per
+// view. Coalesced 16-byte loads of the SoA parameters; the SH row is read
+// only for survivors.
+//
+// This file is compiled without floating-point contraction (-fmad=false):
+// every multiply and add rounds as written, so the one-view and the
+// multi-view kernels (which the compiler schedules differently) produce the
+// same bits, and a view of a batch equals its single-view render.
+#include <cuda_runtime.h>
+
+#include "preprocess_common.cuh"
+
+namespace r4g {
+
+// ---- view table ---------------------------------------------------------------
+struct HostViews {
+  r4g_view v[kMaxViews];
+};
+struct GeomTable {
+  ViewGeom g[kMaxViews];
+};
+
+// One thread per view: the camera as the kernels use it (rotation, centre
+// -R^T t, focal lengths and the 1.3 tan(fov/2) clamp of J) from the host
+// views (a kernel parameter) or from device views, and the view's place in
+// the batch. A device view whose image size differs from the host layout
+// sets status bit 2 and is rendered with the layout's size.
+__global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* __restrict__ vdev, int nviews,
+                                   ViewDev* __restrict__ out, FrameHeader* hdr) {
+  const int v = threadIdx.x;
+  if (v >= nviews) return;
+  const r4g_view V = vdev ? vdev[v] : hv.v[v];
+  const ViewGeom& G = gt.g[v];
+  ViewDev d;
+  CamDev& c = d.cam;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c.R[3 * k + j] = V.cam.world_to_cam[4 * k + j];
+    c.t[k] = V.cam.world_to_cam[4 * k + 3];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc = __dadd_rn(acc, -__dmul_rn(static_cast<double>(c.R[3 * k + j]), c.t[k]));
+    c.pos[j] = static_cast<float>(acc);
+  }
+  c.fx = V.cam.fx;
+  c.fy = V.cam.fy;
+  c.cx = V.cam.cx;
+  c.cy = V.cam.cy;
+  c.limx = static_cast<float>(static_cast<double>(kClampFov) * (G.width / (2.0 * static_cast<double>(c.fx))));
+  c.limy = static_cast<float>(static_cast<double>(kClampFov) * (G.height / (2.0 * static_cast<double>(c.fy))));
+  c.width = G.width;
+  c.height = G.height;
+  d.t = V.t;
+  d.tiles_x = G.tiles_x;
+  d.tiles_y = G.tiles_y;
+  d.tile_off = G.tile_off;
+  d.pix_off = G.pix_off;
+  d.tdiff_off = G.tdiff_off;
+  d.pad[0] = d.pad[1] = d.pad[2] = 0u;
+  if (V.cam.width != G.width || V.cam.height != G.height) atomicOr(&hdr->status, 4u);
+  out[v] = d;
+}
+
+cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
+                               const r4g_view* views_dev, cudaStream_t s) {
+  HostViews hv;
+  GeomTable gt;
+  for (int v = 0; v < L.nviews; ++v) {
+    hv.v[v] = views_host ? views_host[v] : r4g_view{};
+    gt.g[v] = L.geom[v];
+  }
+  setup_views_kernel<<<1, kMaxViews, 0, s>>>(hv, gt, views_dev, L.nviews, at<ViewDev>(frame, L.views),
+                                             at<FrameHeader>(frame, L.header));
+  return cudaGetLastError();
+}
+
+// ---- forward ------------------------------------------------------------------
+// kMulti: several views (a loop keeping the view-independent values live);
+// otherwise exactly one, with a smaller register footprint.
+template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
+__global__ void __launch_bounds__(kPreBlock)
+    preprocess_fwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews, PreOut out,
+                          int sh_degree, bool temporal_cull) {
+  if constexpr (!kMulti) nviews = 1;
+  __shared__ uint32_t s_pairs[kMaxViews];
+  __shared__ uint32_t s_wcnt[kPreBlock / 32];
+  __shared__ uint32_t s_vis, s_base;
+  __shared__ __align__(16) ViewDev s_views[kMaxViews];  // the view table (copied as 16-byte words)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = threadIdx.x; v < kMaxViews; v += kPreBlock) s_pairs[v] = 0;
+  for (int k = threadIdx.x; k < nviews * 8; k += kPreBlock)
+    reinterpret_cast<uint4*>(s_views)[k] = reinterpret_cast<const uint4*>(views)[k];
+  if (threadIdx.x == 0) s_vis = 0;
+  __syncthreads();
+  const int i = blockIdx.x * kPreBlock + threadIdx.x;
+  const bool live = i < g.n;
+  Sig4<S> G;
+  if (live) gauss_sigma<S, kScaleBF16>(g, i, G);
+  uint32_t nvis = 0;
+  const size_t M = static_cast<size_t>(g.n) * nviews;
+  for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
+    uint32_t ntiles = 0;
+    if (live) {
+      const ViewDev& V = s_views[v];
+      const CamDev& cam = V.cam;
+      const size_t item = static_cast<size_t>(v) * g.n + i;
+      Fwd f;
+      S invW, dt;
+      view_geometry<S>(G, cam, V.t, temporal_cull, f, invW, dt);
+      int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
+      const bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
+      if (vis) {
+        forward_color<kShBF16>(g, i, cam, sh_degree, f);
+        const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
+        const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
+        ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
+        out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
+        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], 0.0f);
+        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
+        out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
+                                    static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
+        // +1 on every tile of the rectangle, as four corner updates
+        uint32_t* td = out.tdiff + V.tdiff_off;
+        const int st = V.tiles_x + 1;
+        atomicAdd(td + y0 * st + x0, 1u);
+        atomicAdd(td + y0 * st + x1, 0xffffffffu);
+        atomicAdd(td + y1 * st + x0, 0xffffffffu);
+        atomicAdd(td + y1 * st + x1, 1u);
+      } else {
+        out.recA[item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.recA[M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.recA[2 * M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
+        out.rect[item] = make_uint2(0u, 0u);
+      }
+      out.touched[item] = ntiles;
+      out.dkey[item] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
+    }
+    const uint32_t ws = __reduce_add_sync(0xffffffffu, ntiles);
+    if (lane == 0 && ws) atomicAdd(&s_pairs[v], ws);
+    nvis += ntiles > 0 ? 1u : 0u;
+  }
+  // visible items, pairs per view, and the list of Gaussians visible in some
+  // view (appended per block, in index order within the block)
+  const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
+  const uint32_t lm = __ballot_sync(0xffffffffu, nvis > 0);
+  if (lane == 0) {
+    s_wcnt[warp] = __popc(lm);
+    if (wv) atomicAdd(&s_vis, wv);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kPreBlock / 32; ++w) {
+      const uint32_t c = s_wcnt[w];
+      s_wcnt[w] = tot;
+      tot += c;
+    }
+    s_base = tot ? atomicAdd(&out.header->n_glist, tot) : 0u;
+    if (s_vis) atomicAdd(&out.header->n_visible, s_vis);
+  }
+  for (int v = threadIdx.x; v < nviews; v += kPreBlock)
+    if (s_pairs[v]) atomicAdd(&out.header->view_pairs[v], s_pairs[v]);
+  __syncthreads();
+  if (nvis > 0) out.glist[s_base + s_wcnt[warp] + __popc(lm & ((1u << lane) - 1u))] = static_cast<uint32_t>(i);
+}
+
+template <typename S, bool A, bool B>
+static void launch_pre_t(const r4g_gaussians& g, const ViewDev* views, int nviews, const PreOut& o, int nblocks,
+                         int sh_degree, bool tc, cudaStream_t s) {
+  if (nviews > 1) preprocess_fwd_kernel<S, A, B, true><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
+  else preprocess_fwd_kernel<S, A, B, false><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
+}
+
+cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
+                                  uint32_t flags, cudaStream_t s) {
+  if (L.n == 0) return cudaSuccess;
+  PreOut o;
+  o.recA = at<float4>(frame, L.rec);
+  o.rect = at<uint2>(frame, L.rect);
+  o.touched = at<uint32_t>(frame, L.touched);
+  o.dkey = at<uint32_t>(frame, L.dkey0);
+  o.tdiff = at<uint32_t>(frame, L.tdiff);
+  o.glist = at<uint32_t>(frame, L.glist);
+  o.header = at<FrameHeader>(frame, L.header);
+  o.tile_w = L.tile_w;
+  o.tile_h = L.tile_h;
+  const ViewDev* views = at<ViewDev>(frame, L.views);
+  const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
+  const bool f64 = flags & R4G_FLAG_FP64_SLICE;
+  const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
+  const int nb = static_cast<int>((L.n + kPreBlock - 1) / kPreBlock);
+#define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, o, nb, sh_degree, tc, s)
+  if (f64) {
+    if (sb && hb) R4G_PF(double, true, true);
+    else if (sb) R4G_PF(double, true, false);
+    else if (hb) R4G_PF(double, false, true);
+    else R4G_PF(double, false, false);
+  } else {
+    if (sb && hb) R4G_PF(float, true, true);
+    else if (sb) R4G_PF(float, true, false);
+    else if (hb) R4G_PF(float, false, true);
+    else R4G_PF(float, false, false);
+  }
+#undef R4G_PF
+  return cudaGetLastError();
+}
+
+
+}  // namespace r4g

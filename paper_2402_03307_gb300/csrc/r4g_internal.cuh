@@ -36,14 +36,14 @@ struct CamDev {
 // packed view after view (view v's pixels start at pix_off).
 constexpr int kMaxViews = 64;
 
-struct ViewDev {  // kernel-side view table entry (in the frame), 128 bytes
+struct __align__(16) ViewDev {  // kernel-side view table entry (in the frame), 128 bytes
   CamDev cam;
   float t;
   int tiles_x, tiles_y;
   uint32_t tile_off, pix_off, tdiff_off;
   uint32_t pad[3];
 };
-static_assert(sizeof(ViewDev) == 128, "view table entry size");
+static_assert(sizeof(ViewDev) == 128 && alignof(ViewDev) == 16, "view table entry size and alignment");
 
 struct ViewGeom {  // host-side view geometry (what the launch sizes depend on)
   int width, height, tiles_x, tiles_y;

@@ -42,6 +42,26 @@ __device__ __forceinline__ void load_params(const r4g_gaussians& g, int i, Param
   p.logit = __ldg(g.logit + i);
 }
 
+// Read-only 16-byte loads the compiler must issue where they are written: a
+// Gaussian's SH row is loop-invariant over the views of a call, and hoisting
+// it out of the view loop (and out of the visibility test) would keep 48
+// registers live throughout and read the rows of invisible Gaussians.
+__device__ __forceinline__ float4 ld_nc_f4(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ uint4 ld_nc_u4(const uint4* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
 // SH coefficients of one Gaussian: c[k][ch] for the first nb = (deg+1)^2 bands.
 template <bool kShBF16>
 __device__ __forceinline__ void load_sh(const void* sh, int i, int nb, float c[16][3]) {
@@ -51,7 +71,7 @@ __device__ __forceinline__ void load_sh(const void* sh, int i, int nb, float c[1
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
       if (v < nvec) {
-        const uint4 w = __ldg(p + v);
+        const uint4 w = ld_nc_u4(p + v);
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int h = 0; h < 8; ++h) {
@@ -67,7 +87,7 @@ __device__ __forceinline__ void load_sh(const void* sh, int i, int nb, float c[1
 #pragma unroll
     for (int v = 0; v < 12; ++v) {
       if (v < nvec) {
-        const float4 w = __ldg(p + v);
+        const float4 w = ld_nc_f4(p + v);
         const float ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int h = 0; h < 4; ++h) {

@@ -37,8 +37,8 @@ def _crop_rec(rec: dict, x0: int, y0: int) -> dict:
     """The oracle's records restricted to Gaussians whose 3-sigma box meets the crop."""
     m = rec["mean2d"].detach()
     cov = rec["cov2d"].detach()
-    hx = 3.0 * torch.sqrt(torch.clamp(cov[:, 0], min=0)) + 1.0
-    hy = 3.0 * torch.sqrt(torch.clamp(cov[:, 2], min=0)) + 1.0
+    hx = 3.0 * torch.sqrt(torch.clamp(cov[:, 0, 0], min=0)) + 1.0
+    hy = 3.0 * torch.sqrt(torch.clamp(cov[:, 1, 1], min=0)) + 1.0
     keep = (rec["visible"] & (m[:, 0] + hx >= x0) & (m[:, 0] - hx <= x0 + CROP)
             & (m[:, 1] + hy >= y0) & (m[:, 1] - hy <= y0 + CROP))
     idx = torch.nonzero(keep).flatten()
