@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-view batched workload")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian BF16 workload")
+    ap.add_argument("--no-extras", action="store_true", help="skip the flow / KNN / regulariser timings")
     ap.add_argument("--batch-only", action="store_true", help="batched and large workloads only (profiling)")
     ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
     ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
@@ -187,14 +188,14 @@ def run_ours(args, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    # size the key buffer once over the whole sweep (not timed)
-    cap = 0
-    for k in range(0, FRAMES, 15):
+    # size the key buffer once over the whole sweep (not timed): 10 % above the
+    # largest (tile, Gaussian) pair count of any frame
+    need_max = 0
+    for k in range(FRAMES):
         cam, t = frame_camera(k)
         res = rend.render(params, cam, t)
-        cap = max(cap, res.key_capacity)
-        _, need = rend.status(res)
-        cap = max(cap, int(need * 1.1))
+        need_max = max(need_max, rend.status(res)[1])
+    cap = int(need_max * 1.1) + 1024
     frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
     img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
     frames = frames_for_rank(rank, args.steps)
@@ -225,9 +226,9 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     abi.r4g_set_timing(rend.ctx, False)
     stage_ms, stage_launch = abi.r4g_stage_times(rend.ctx, reset=True)
-    st, need = rend.status(res)
-    if st != abi.R4G_OK:
-        raise RuntimeError("key buffer overflow during the timed region")
+    for k in frames[-3:]:
+        if rend.status(render_frame(k))[0] != abi.R4G_OK:
+            raise RuntimeError("key buffer overflow during the timed region")
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = max_over_ranks(sum(step_ms), dev)
     fps = world * len(frames) / (total_ms / 1e3)
@@ -294,6 +295,8 @@ def run_ours(args, rank, world, local):
         out["batched"] = batch_bench(args, dev, stream, flush)
     if not args.no_large and not args.frames_only:
         out["large"] = large_bench(args, dev, stream, flush)
+    if not args.no_extras and not args.frames_only:
+        out["extras"] = extras_bench(args, params, dev, stream, flush, frames, cap)
     # ---- end to end through host buffers ---------------------------------------------
     if not args.no_e2e and not args.frames_only:
         out["e2e"] = e2e_bench(args, rend, g, dev, stream, frames, cap)
@@ -497,6 +500,61 @@ def large_bench(args, dev, stream, flush):
     out["bf16_vs_fp32"] = {"max_abs": float(d.max()), "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-30)), 2),
                            "speedup": round(out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"], 3)}
     return out
+
+
+def extras_bench(args, params, dev, stream, flush, frames, cap):
+    """The optical-flow render on the sweep (frames/s) and, at 300k Gaussians,
+    the 4D KNN (K = 8) and the entropy + 4D-consistency losses with their
+    gradients (ms)."""
+    import torch
+    import paper_2402_03307_gb300 as r4g
+    from paper_2402_03307_gb300 import abi
+
+    fr = r4g.Renderer(flags=abi.R4G_FLAG_FLOW)
+    frame = fr.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    it = {"k": 0}
+
+    def flow_frame():
+        cam, t = frame_camera(frames[it["k"] % len(frames)])
+        it["k"] += 1
+        fr.render(params, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
+
+    for _ in range(3):
+        flow_frame()
+    ms_flow = _timed(flow_frame, min(100, len(frames)), stream, flush)
+    knn = {}
+
+    def run_knn():
+        knn["idx"] = r4g.knn4d(params["mean"], 6.0, 1.0, 8)
+
+    for _ in range(2):
+        run_knn()
+    ms_knn = _timed(run_knn, 5, stream, flush)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+
+    def run_reg():
+        r4g.regularizers(params, knn["idx"], 0.01, 0.05, grads)
+
+    for _ in range(2):
+        run_reg()
+    ms_reg = _timed(run_reg, 10, stream, flush)
+    target = torch.rand((3, HEIGHT, WIDTH), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+
+    def run_loss():
+        r4g.image_loss(img, target, 0.2)
+
+    for _ in range(2):
+        run_loss()
+    ms_loss = _timed(run_loss, 20, stream, flush)
+    return {"image_loss": {"ms": round(ms_loss, 3), "what": "0.8 L1 + 0.2 (1 - SSIM) and its gradient, 3x1014x1352",
+                           "note": "includes scratch allocation by the Python wrapper"},
+            "flow": {"value": round(1000.0 / ms_flow, 1), "unit": "frames/s",
+                     "workload": "optical-flow render of the 300k sweep (d mean2d / dt composited)"},
+            "knn4d": {"ms": round(ms_knn, 3), "k": 8, "n": N_GAUSS,
+                      "note": "includes scratch allocation by the Python wrapper"},
+            "regularizers": {"ms": round(ms_reg, 3), "n": N_GAUSS,
+                             "what": "entropy + 4D consistency losses and their gradients"}}
 
 
 def e2e_bench(args, rend, g, dev, stream, frames, cap):

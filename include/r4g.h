@@ -59,6 +59,10 @@ typedef enum r4g_dtype { R4G_F32 = 0, R4G_BF16 = 1 } r4g_dtype;
 #define R4G_FLAG_NO_TEMPORAL_CULL 0x2u  /* keep Gaussians with lambda (t-mu_t)^2 > 16 */
 #define R4G_FLAG_COUNT_PAIRS 0x4u  /* measurement: count composited (pixel, Gaussian) pairs
                                      (a slower, instrumented blend; see r4g_frame_stats) */
+#define R4G_FLAG_FLOW 0x8u         /* optical-flow render (Sec. 3.2.2 speed V/W): out_rgb
+                                     channels 0, 1 receive d(mean2d)/dt in pixels per unit of
+                                     t, composited with the colour render's weights over a
+                                     zero background; channel 2 is 0. No backward. */
 
 /* Render configuration. tile_w x tile_h in {8x8, 16x16, 16x32}. */
 typedef struct r4g_config {
@@ -276,6 +280,55 @@ r4g_status r4g_set_timing(r4g_ctx* ctx, int32_t enable);
  * receive the accumulated stage times and kernel launch counts since the
  * last reset; reset != 0 clears them afterwards. */
 r4g_status r4g_stage_times(r4g_ctx* ctx, double* ms, int64_t* launches, int32_t reset);
+
+/* ---- regularisers (Sec. 3.3) -----------------------------------------------------
+ * 4D K-nearest neighbours of the Gaussian means (Sec. 3.3 "4D Consistency
+ * Loss"): Euclidean distance after dividing x, y, z by scale_xyz and t by
+ * scale_t (the spatial and temporal scene scales). means: device [n, 4]
+ * (16-byte aligned). out_idx: device int32 [n, k], the neighbours of each
+ * point in increasing distance, ties to the smaller index, the point itself
+ * excluded; out_dist2 (device float [n, k] or NULL): their squared scaled
+ * distances. k in {4, 8, 16}, k < n <= 2^28. Exact (a grid search that stops
+ * only when no unsearched cell can hold a closer point). scratch: device,
+ * 256-byte aligned, r4g_knn_scratch_bytes(n) bytes. Deterministic. */
+r4g_status r4g_knn_scratch_bytes(int64_t n, size_t* bytes /* host out */);
+r4g_status r4g_knn4d(const float* means, int64_t n, float scale_xyz, float scale_t, int32_t k,
+                     int32_t* out_idx, float* out_dist2, void* scratch, size_t scratch_bytes,
+                     void* stream);
+/* Waits for `stream`; R4G_ETIMEOUT if the last r4g_knn4d in `scratch` had a
+ * radix-sort look-back wait reach its iteration limit (its result is then
+ * invalid), else R4G_OK. */
+r4g_status r4g_knn_status(const void* scratch, int64_t n, void* stream);
+
+/* The entropy loss L_e = 1/N sum -o log o (o = sigmoid(logit)) and the 4D
+ * consistency loss L_c = 1/N sum_i || s_i - 1/k sum_{j in knn_idx[i]} s_j ||_1
+ * on the speeds s = V / W of Sigma4 (Sec. 3.2.2), for k-nearest-neighbour
+ * lists knn_idx (device int32 [n, k], as r4g_knn4d writes them; an index
+ * outside [0, n) counts as the point itself). out_loss (device float [2])
+ * receives (L_e, L_c), unweighted. When `grads` is not NULL, ADDS
+ * lambda_entropy dL_e/dlogit into grads->logit and lambda_consistency dL_c/d
+ * (rotor, log-scale) into grads->rotor and grads->logscale (the neighbour
+ * lists are constants). mean and sh are not used. scratch: device, 256-byte
+ * aligned, r4g_regularizers_scratch_bytes(n) bytes. Deterministic. */
+r4g_status r4g_regularizers_scratch_bytes(int64_t n, size_t* bytes /* host out */);
+r4g_status r4g_regularizers(const r4g_gaussians* g, const int32_t* knn_idx, int32_t k,
+                            float lambda_entropy, float lambda_consistency, float* out_loss,
+                            r4g_grads* grads, void* scratch, size_t scratch_bytes, void* stream);
+
+/* The image loss of the optimisation (Sec. 3.3 total loss, as in 3D Gaussian
+ * Splatting): L = (1 - lambda_ssim) L1 + lambda_ssim (1 - SSIM) between a
+ * rendered image and a target (device float [channels, height, width],
+ * planar), L1 = mean |x - y|, SSIM the mean structural similarity over an
+ * 11 x 11 Gaussian window (sigma 1.5, zero padding, C1 = 0.01^2,
+ * C2 = 0.03^2). out_loss (device float [3]) receives (L, L1, SSIM);
+ * grad_image (device, like the image, or NULL) receives dL/d image
+ * (written, not added). scratch: device, 256-byte aligned,
+ * r4g_image_loss_scratch_bytes bytes. Deterministic. */
+r4g_status r4g_image_loss_scratch_bytes(int32_t channels, int32_t height, int32_t width,
+                                        size_t* bytes /* host out */);
+r4g_status r4g_image_loss(const float* image, const float* target, int32_t channels, int32_t height,
+                          int32_t width, float lambda_ssim, float* out_loss, float* grad_image,
+                          void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---- sort -------------------------------------------------------------------
  * Stable LSD radix sort of (uint64 key, uint32 value) pairs on key bits

@@ -14,6 +14,7 @@ R4G_F32, R4G_BF16 = 0, 1
 R4G_FLAG_FP64_SLICE = 0x1
 R4G_FLAG_NO_TEMPORAL_CULL = 0x2
 R4G_FLAG_COUNT_PAIRS = 0x4
+R4G_FLAG_FLOW = 0x8
 STATUS_NAMES = {0: "R4G_OK", 1: "R4G_EINVAL", 2: "R4G_ENOMEM", 3: "R4G_EWORKSPACE", 4: "R4G_ECUDA",
                 5: "R4G_ETIMEOUT", 6: "R4G_EDEVICE", 7: "R4G_EOVERFLOW"}
 
@@ -87,6 +88,16 @@ SIGNATURES = [
                                      C.c_int64, C.c_int32, C.c_void_p, C.POINTER(r4g_tune_result)]),
     ("r4g_set_tile", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     ("r4g_get_config", C.c_int, [C.c_void_p, C.POINTER(r4g_config)]),
+    ("r4g_knn_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    ("r4g_knn4d", C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("r4g_knn_status", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    ("r4g_regularizers_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    ("r4g_regularizers", C.c_int, [C.POINTER(r4g_gaussians), C.c_void_p, C.c_int32, C.c_float, C.c_float,
+                                   C.c_void_p, C.POINTER(r4g_grads), C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("r4g_image_loss_scratch_bytes", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("r4g_image_loss", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("r4g_set_timing", C.c_int, [C.c_void_p, C.c_int32]),
     ("r4g_stage_times", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     ("r4g_sort_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
@@ -226,6 +237,45 @@ def r4g_autotune_batch(ctx, g: r4g_gaussians, views, out_rgb, grad_rgb, grads, f
     return {"tile": (res.tile_w, res.tile_h),
             "ms": {f"{w}x{h}": (res.ms[k] if res.ms[k] >= 0 else None) for k, (w, h) in enumerate(TUNE_SHAPES)},
             "keys_needed": {f"{w}x{h}": res.keys_needed[k] for k, (w, h) in enumerate(TUNE_SHAPES)}}
+
+
+def r4g_knn_scratch_bytes(n: int) -> int:
+    out = C.c_size_t()
+    check(lib().r4g_knn_scratch_bytes(n, C.byref(out)))
+    return out.value
+
+
+def r4g_knn4d(means, n, scale_xyz, scale_t, k, out_idx, out_dist2, scratch, scratch_bytes, stream) -> None:
+    check(lib().r4g_knn4d(means, n, scale_xyz, scale_t, k, out_idx, out_dist2, scratch, scratch_bytes, stream))
+
+
+def r4g_knn_status(scratch, n, stream) -> int:
+    st = lib().r4g_knn_status(scratch, n, stream)
+    if st not in (R4G_OK, R4G_ETIMEOUT):
+        check(st)
+    return st
+
+
+def r4g_regularizers_scratch_bytes(n: int) -> int:
+    out = C.c_size_t()
+    check(lib().r4g_regularizers_scratch_bytes(n, C.byref(out)))
+    return out.value
+
+
+def r4g_regularizers(g: r4g_gaussians, knn_idx, k, lambda_entropy, lambda_consistency, out_loss,
+                     grads: r4g_grads | None, scratch, scratch_bytes, stream) -> None:
+    check(lib().r4g_regularizers(C.byref(g), knn_idx, k, lambda_entropy, lambda_consistency, out_loss,
+                                 C.byref(grads) if grads is not None else None, scratch, scratch_bytes, stream))
+
+
+def r4g_image_loss_scratch_bytes(c: int, h: int, w: int) -> int:
+    out = C.c_size_t()
+    check(lib().r4g_image_loss_scratch_bytes(c, h, w, C.byref(out)))
+    return out.value
+
+
+def r4g_image_loss(image, target, c, h, w, lam, out_loss, grad, scratch, scratch_bytes, stream) -> None:
+    check(lib().r4g_image_loss(image, target, c, h, w, lam, out_loss, grad, scratch, scratch_bytes, stream))
 
 
 def r4g_set_tile(ctx, tile_w: int, tile_h: int) -> None:

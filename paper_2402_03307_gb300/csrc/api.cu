@@ -264,9 +264,9 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   const int dpasses = 32 / kSortRadixBits;
   const int tpasses = (L.tile_bits + kSortRadixBits - 1) / kSortRadixBits;
   {
-    StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, has ? 2 : 1);
-    if ((e = launch_setup_views(L, frame, views, views_dev, s)) != cudaSuccess) return cuda_fail(ctx, e, "views");
-    if ((e = launch_preprocess_fwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, s)) != cudaSuccess)
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS, s, (L.nviews > 1 || !has) ? (has ? 2 : 1) : 1);
+    if ((e = launch_preprocess_fwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, views, views_dev, s)) !=
+        cudaSuccess)
       return cuda_fail(ctx, e, "preprocess");
   }
   uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
@@ -305,7 +305,9 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   const uint32_t* vals = sorted_vals(L, frame);
   {
     StageScope sc(ctx, R4G_STAGE_BLEND, s, 1);
-    if ((e = launch_blend_fwd(L, frame, vals, ctx->cfg.bg, out_rgb, out_T, out_last,
+    static const float kZero[3] = {0.0f, 0.0f, 0.0f};  // the flow has no background
+    const float* bg = (ctx->cfg.flags & R4G_FLAG_FLOW) ? kZero : ctx->cfg.bg;
+    if ((e = launch_blend_fwd(L, frame, vals, bg, out_rgb, out_T, out_last,
                               (ctx->cfg.flags & R4G_FLAG_COUNT_PAIRS) != 0, s)) != cudaSuccess)
       return cuda_fail(ctx, e, "blend");
   }
@@ -317,6 +319,7 @@ r4g_status backward_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* v
                          int64_t key_capacity, void* stream) {
   r4g_status st = check_gaussians(ctx, g);
   if (st != R4G_OK) return st;
+  if (ctx->cfg.flags & R4G_FLAG_FLOW) return fail(ctx, R4G_EINVAL, "the flow render has no backward");
   if (!grad_rgb || !grads || !frame) return fail(ctx, R4G_EINVAL, "NULL argument");
   if (g->n > 0 && (!grads->mean || !grads->rotor || !grads->logscale || !grads->logit || !grads->sh))
     return fail(ctx, R4G_EINVAL, "a gradient pointer is NULL");
@@ -366,7 +369,7 @@ r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg) {
   }
   if (!tile_ok(c.tile_w, c.tile_h)) return fail(nullptr, R4G_EINVAL, "tile shape must be 8x8, 16x16 or 16x32");
   if (c.sh_degree < 0 || c.sh_degree > 3) return fail(nullptr, R4G_EINVAL, "sh_degree must be 0..3");
-  if (c.flags & ~(R4G_FLAG_FP64_SLICE | R4G_FLAG_NO_TEMPORAL_CULL | R4G_FLAG_COUNT_PAIRS))
+  if (c.flags & ~(R4G_FLAG_FP64_SLICE | R4G_FLAG_NO_TEMPORAL_CULL | R4G_FLAG_COUNT_PAIRS | R4G_FLAG_FLOW))
     return fail(nullptr, R4G_EINVAL, "unknown flag");
   r4g_ctx* ctx = new (std::nothrow) r4g_ctx;
   if (!ctx) return fail(nullptr, R4G_ENOMEM, "out of host memory");

@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kPreBlock)
   }
 }
 
-// Pair emission balanced over the output: CTA c writes pairs
-// [c E, (c + 1) E) of the depth-ordered list. Gaussians with pairs are at the
+// Pair emission balanced over the output: chunk c holds pairs
+// [c E, (c + 1) E) of the depth-ordered list (CTAs stride over the chunks). Gaussians with pairs are at the
 // front of the depth order (a Gaussian without tiles has the largest key), so
 // their offsets increase strictly and a chunk of E pairs involves at most
 // E + 1 of them: their offsets are loaded into shared memory and each pair
@@ -141,29 +141,35 @@ __global__ void __launch_bounds__(kPreBlock)
                 uint32_t* __restrict__ ident) {
   __shared__ uint32_t s_off[kEmitChunk + 1];
   const uint32_t K = hdr->key_count;
-  const uint32_t q0 = blockIdx.x * kEmitChunk;
-  if (q0 >= K) return;  // CTA-uniform: the grid is sized for the capacity
-  const int jlo = static_cast<int>(chunk_start[blockIdx.x]);
-  const int m = min(kEmitChunk + 1, n - jlo);  // window of Gaussians
-  for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
-  __syncthreads();
-  const uint32_t qend = min(K, q0 + kEmitChunk);
-  for (uint32_t q = q0 + threadIdx.x; q < qend; q += kPreBlock) {
-    int lo = 0, hi = m - 1;  // last i with s_off[i] <= q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= q) lo = mid;
-      else hi = mid - 1;
+  // grid-stride over the output chunks: the grid is sized for the device,
+  // the chunk count is only known here
+  for (uint32_t c = blockIdx.x; static_cast<uint64_t>(c) * kEmitChunk < K; c += gridDim.x) {
+    const uint32_t q0 = c * kEmitChunk;
+    const int jlo = static_cast<int>(chunk_start[c]);
+    // window of items: up to the item holding the next chunk's first pair
+    const int jhi = (q0 + kEmitChunk < K) ? static_cast<int>(chunk_start[c + 1]) : n - 1;
+    const int m = min(kEmitChunk + 1, min(jhi, n - 1) - jlo + 1);
+    __syncthreads();  // the previous chunk is done with s_off
+    for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
+    __syncthreads();
+    const uint32_t qend = min(K, q0 + kEmitChunk);
+    for (uint32_t q = q0 + threadIdx.x; q < qend; q += kPreBlock) {
+      int lo = 0, hi = m - 1;  // last i with s_off[i] <= q
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= q) lo = mid;
+        else hi = mid - 1;
+      }
+      const int j = jlo + lo;
+      const uint32_t local = q - s_off[lo];
+      const uint4 r = srect[j];  // rect, the view's first tile id and tiles_x
+      const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
+      const uint32_t w = x1 - x0;
+      const uint32_t ty = y0 + local / w, tx = x0 + local % w;
+      tkeys[q] = r.z + ty * r.w + tx;
+      egid[q] = order[j];
+      if (ident) ident[q] = q;  // a single-tile image has no tile sort to generate the values
     }
-    const int j = jlo + lo;
-    const uint32_t local = q - s_off[lo];
-    const uint4 r = srect[j];  // rect, the view's first tile id and tiles_x
-    const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-    const uint32_t w = x1 - x0;
-    const uint32_t ty = y0 + local / w, tx = x0 + local % w;
-    tkeys[q] = r.z + ty * r.w + tx;
-    egid[q] = order[j];
-    if (ident) ident[q] = q;  // a single-tile image has no tile sort to generate the values
   }
 }
 
@@ -296,8 +302,12 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
                                                         at<ViewDev>(frame, L.views), static_cast<uint32_t>(L.n), m,
                                                         offs, at<uint32_t>(frame, L.ioffs), srect, cstart,
                                                         static_cast<uint32_t>(chunks));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t egrid = chunks < 8LL * sms ? chunks : 8LL * sms;  // eight 256-thread CTAs per SM
   if (chunks > 0)
-    emit_kernel<<<static_cast<unsigned>(chunks), kPreBlock, 0, s>>>(offs, srect, order, cstart, m, hdr,
+    emit_kernel<<<static_cast<unsigned>(egrid), kPreBlock, 0, s>>>(offs, srect, order, cstart, m, hdr,
                                                                      at<uint32_t>(frame, L.keys0),
                                                                      at<uint32_t>(frame, L.egid),
                                                                      L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0)

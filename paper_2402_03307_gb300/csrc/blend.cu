@@ -1,11 +1,10 @@
 // Tiled front-to-back alpha compositing (Sec. 3.1, Eq. 3) and its backward.
 //
-// One CTA per tile; each thread owns two horizontally adjacent pixels and
-// evaluates them together with Blackwell's packed FP32x2 instructions. Each
-// warp owns a 64-pixel block of the tile (16x4 for 16-wide tiles, 8x8 for
-// 8x8 tiles). Batches of screen records are staged in shared memory with
-// every operand already duplicated into the (x, x) pairs the packed
-// instructions take. While staging, each Gaussian gets one bit per warp
+// Persistent CTAs take tiles; each thread owns two horizontally adjacent
+// pixels and evaluates them together with Blackwell's packed FP32x2
+// instructions. Each warp owns an 8x8 block of the tile. Batches of screen
+// records are staged in shared memory with every operand already duplicated
+// into the (x, x) pairs the packed instructions take. While staging, each Gaussian gets one bit per warp
 // telling whether its contributing ellipse can reach a pixel centre of that
 // warp's block; a warp then walks only the set bits of a 32-entry ballot, so
 // Gaussians that cannot touch it cost nothing. Every pixel applies the exact
@@ -40,13 +39,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Each warp owns an 8x8 pixel block of the tile (4 threads x 2 pixels
+// across, 8 rows): of the block shapes of 64 pixels the square one meets the
+// fewest ellipses that only graze it.
 template <int TW, int TH>
 struct Blend {
   static constexpr int NT = TW * TH / 2;     // threads per CTA
   static constexpr int NW = NT / 32;         // warps per CTA
-  static constexpr int PCOLS = TW / 2;       // thread columns
-  static constexpr int WROWS = 32 / PCOLS;   // pixel rows per warp block
-  static_assert(NT % 32 == 0 && 32 % PCOLS == 0 && NW <= 16, "tile shape");
+  static constexpr int WX = TW / 8;          // warp blocks across the tile
+  static constexpr int PCOLS = 4;            // thread columns of a warp block
+  static constexpr int WROWS = 8;            // pixel rows of a warp block
+  static_assert(TW % 8 == 0 && TH % 8 == 0 && NW <= 16, "tile shape");
+  __device__ static int px0(int tx, int warp) { return tx * TW + (warp % WX) * 8; }
+  __device__ static int py0(int ty, int warp) { return ty * TH + (warp / WX) * 8; }
 };
 
 // A staged Gaussian (128-byte slot), operands duplicated for the packed pairs:
@@ -103,11 +108,10 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   const float mid = 0.5f * pmin, half = fmaxf(-0.5f * pmin, 1e-6f);
   const float ih = 1.0f / half, nm = -mid * ih;
   uint32_t m = o > kAlphaMax ? kClampBit : 0u;
-  const float x0 = tx * TW + 0.5f, x1 = tx * TW + TW - 0.5f;
 #pragma unroll
-  for (int w = 0; w < B::NW; ++w) {
-    const float y0 = ty * TH + w * B::WROWS + 0.5f;
-    const float y1 = y0 + B::WROWS - 1.0f;
+  for (int w = 0; w < B::NW; ++w) {  // pixel centres of warp w's 8x8 block
+    const float x0 = B::px0(tx, w) + 0.5f, x1 = x0 + 7.0f;
+    const float y0 = B::py0(ty, w) + 0.5f, y1 = y0 + 7.0f;
     if (ellipse_meets_rect(A, Bv.x, o, x0, x1, y0, y1)) m |= 1u << w;
   }
   sg->p0 = make_float4(-A.x, -A.x, -A.y, -A.y);
@@ -258,8 +262,8 @@ __device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint
   const TileLoc loc = locate_tile(views, nviews, tile);
   const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int px = tx * TW + 2 * (lane % B::PCOLS);
-  const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
+  const int px = B::px0(tx, warp) + 2 * (lane % B::PCOLS);
+  const int py = B::py0(ty, warp) + lane / B::PCOLS;
   const bool in0 = px < width && py < height;
   const bool in1 = px + 1 < width && py < height;
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);
@@ -470,8 +474,8 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
   const TileLoc loc = locate_tile(views, nviews, tile);
   const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int px = tx * TW + 2 * (lane % B::PCOLS);
-  const int py = ty * TH + warp * B::WROWS + lane / B::PCOLS;
+  const int px = B::px0(tx, warp) + 2 * (lane % B::PCOLS);
+  const int py = B::py0(ty, warp) + lane / B::PCOLS;
   const bool in0 = px < width && py < height;
   const bool in1 = px + 1 < width && py < height;
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);

@@ -8,103 +8,6 @@
 
 namespace r4g {
 
-// ---- backward ---------------------------------------------------------------
-// Gradient of the rotor -> matrix map (appendix A.2): every entry of R is a
-// quadratic form of the normalised rotor, so dR_e / dr is linear in r.
-// Off-diagonal entries are 2 * sum of signed products r_a r_b.
-template <typename S>
-__device__ __forceinline__ void prod_term(S w, const S r[8], S g[8], int a, int b) {
-  g[a] += w * r[b];
-  g[b] += w * r[a];
-}
-
-template <typename S>
-__device__ __forceinline__ void rotor_matrix_bwd(const S r[8], const S gR[16], S g[8]) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) g[k] = S(0);
-  // diagonal entries: sums of +-r_k^2; signs over (s, b01, b02, b12, b03, b13, b23, p)
-  const int dsg[4][8] = {{1, -1, -1, 1, -1, 1, 1, -1},
-                         {1, -1, 1, -1, 1, -1, 1, -1},
-                         {1, 1, -1, -1, 1, 1, -1, -1},
-                         {1, 1, 1, 1, -1, -1, -1, -1}};
-#pragma unroll
-  for (int d = 0; d < 4; ++d) {
-    const S w = S(2) * gR[5 * d];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) g[k] += dsg[d][k] > 0 ? w * r[k] : -w * r[k];
-  }
-  // indices: s 0, b01 1, b02 2, b12 3, b03 4, b13 5, b23 6, p 7
-  S w;
-  w = S(2) * gR[1];   // R01 = 2(b01 s - b02 b12 - b03 b13 + b23 p)
-  prod_term(w, r, g, 1, 0); prod_term(-w, r, g, 2, 3); prod_term(-w, r, g, 4, 5); prod_term(w, r, g, 6, 7);
-  w = S(2) * gR[2];   // R02 = 2(b01 b12 + b02 s - b03 b23 - b13 p)
-  prod_term(w, r, g, 1, 3); prod_term(w, r, g, 2, 0); prod_term(-w, r, g, 4, 6); prod_term(-w, r, g, 5, 7);
-  w = S(2) * gR[3];   // R03 = 2(b01 b13 + b02 b23 + b03 s + b12 p)
-  prod_term(w, r, g, 1, 5); prod_term(w, r, g, 2, 6); prod_term(w, r, g, 4, 0); prod_term(w, r, g, 3, 7);
-  w = S(2) * gR[4];   // R10 = 2(-b01 s - b02 b12 - b03 b13 - b23 p)
-  prod_term(-w, r, g, 1, 0); prod_term(-w, r, g, 2, 3); prod_term(-w, r, g, 4, 5); prod_term(-w, r, g, 6, 7);
-  w = S(2) * gR[6];   // R12 = 2(-b01 b02 + b03 p + b12 s - b13 b23)
-  prod_term(-w, r, g, 1, 2); prod_term(w, r, g, 4, 7); prod_term(w, r, g, 3, 0); prod_term(-w, r, g, 5, 6);
-  w = S(2) * gR[7];   // R13 = 2(-b01 b03 - b02 p + b12 b23 + b13 s)
-  prod_term(-w, r, g, 1, 4); prod_term(-w, r, g, 2, 7); prod_term(w, r, g, 3, 6); prod_term(w, r, g, 5, 0);
-  w = S(2) * gR[8];   // R20 = 2(b01 b12 - b02 s - b03 b23 + b13 p)
-  prod_term(w, r, g, 1, 3); prod_term(-w, r, g, 2, 0); prod_term(-w, r, g, 4, 6); prod_term(w, r, g, 5, 7);
-  w = S(2) * gR[9];   // R21 = 2(-b01 b02 - b03 p - b12 s - b13 b23)
-  prod_term(-w, r, g, 1, 2); prod_term(-w, r, g, 4, 7); prod_term(-w, r, g, 3, 0); prod_term(-w, r, g, 5, 6);
-  w = S(2) * gR[11];  // R23 = 2(b01 p - b02 b03 - b12 b13 + b23 s)
-  prod_term(w, r, g, 1, 7); prod_term(-w, r, g, 2, 4); prod_term(-w, r, g, 3, 5); prod_term(w, r, g, 6, 0);
-  w = S(2) * gR[12];  // R30 = 2(b01 b13 + b02 b23 - b03 s - b12 p)
-  prod_term(w, r, g, 1, 5); prod_term(w, r, g, 2, 6); prod_term(-w, r, g, 4, 0); prod_term(-w, r, g, 3, 7);
-  w = S(2) * gR[13];  // R31 = 2(-b01 b03 + b02 p + b12 b23 - b13 s)
-  prod_term(-w, r, g, 1, 4); prod_term(w, r, g, 2, 7); prod_term(w, r, g, 3, 6); prod_term(-w, r, g, 5, 0);
-  w = S(2) * gR[14];  // R32 = 2(-b01 p - b02 b03 - b12 b13 - b23 s)
-  prod_term(-w, r, g, 1, 7); prod_term(-w, r, g, 2, 4); prod_term(-w, r, g, 3, 5); prod_term(-w, r, g, 6, 0);
-}
-
-// Gradient of F_norm (appendix A.1): r1 = r + delta(r) P r with P r = grad eps
-// (P symmetric, P^2 = I), r_hat = r1 / |r1|; delta depends on eps and l^2.
-template <typename S>
-__device__ __forceinline__ void rotor_normalize_bwd(const float rin[8], const RotorNorm<S>& rn,
-                                                    const S gh[8], S gr[8]) {
-  if (rn.ident) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) gr[k] = S(0);
-    return;
-  }
-  const S invn = S(1) / sqrt(rn.n2);
-  S dot = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) dot += rn.r[k] * gh[k];
-  S g1[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) g1[k] = (gh[k] - rn.r[k] * dot) * invn;
-  S r[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) r[k] = static_cast<S>(rin[k]);
-  S Pr[8], Pg[8];
-  eps_grad(r, Pr);
-  eps_grad(g1, Pg);
-  S gdot = 0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) gdot += g1[k] * Pr[k];
-  S dd_de = 0, dd_dl2 = 0;
-  if (rn.l2 > S(0)) {
-    S disc = rn.l2 * rn.l2 - S(4) * rn.eps * rn.eps;
-    disc = disc > S(0) ? disc : S(0);
-    const S sq = sqrt(disc);
-    const S D = rn.l2 + sq;
-    dd_de = S(-2) / D;
-    dd_dl2 = S(2) * rn.eps / (D * D);
-    if (sq > S(0)) {
-      dd_de -= S(8) * rn.eps * rn.eps / (D * D * sq);
-      dd_dl2 *= S(1) + rn.l2 / sq;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    gr[k] = g1[k] + rn.delta * Pg[k] + gdot * (dd_de * Pr[k] + dd_dl2 * S(2) * r[k]);
-}
-
 constexpr int kBwdBlock = 128;
 
 // Gradient sums over the views of one Gaussian, in the slice precision S.
@@ -364,26 +267,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
   G4[0][3] = G4[3][0] = acc.G4[3]; G4[1][1] = acc.G4[4]; G4[1][2] = G4[2][1] = acc.G4[5];
   G4[1][3] = G4[3][1] = acc.G4[6]; G4[2][2] = acc.G4[7]; G4[2][3] = G4[3][2] = acc.G4[8];
   G4[3][3] = acc.G4[9];
-  // ---- Sigma4 = R diag(sc2) R^T
-  const S* R = G.R;
-  S gR[16], gsc2[4];
-  S G4R[4][4];  // G4 R
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      G4R[a][k] = G4[a][0] * R[k] + G4[a][1] * R[4 + k] + G4[a][2] * R[8 + k] + G4[a][3] * R[12 + k];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) gR[4 * a + k] = S(2) * G4R[a][k] * G.sc2[k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    gsc2[k] = R[k] * G4R[0][k] + R[4 + k] * G4R[1][k] + R[8 + k] * G4R[2][k] + R[12 + k] * G4R[3][k];
-  // ---- rotor
-  S grh[8], grot[8];
-  rotor_matrix_bwd<S>(G.rn.r, gR, grh);
-  rotor_normalize_bwd<S>(G.p.rot, G.rn, grh, grot);
+  S grot[8], gls[4];
+  sigma4_backward<S>(G, G4, grot, gls);
 
   // ---- write (accumulate)
   // accumulate (+=) with 16-byte vector accesses
@@ -404,10 +289,10 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
   gr[1] = r1;
   float4* gl = reinterpret_cast<float4*>(out.logscale) + i;
   float4 vl = *gl;
-  vl.x += static_cast<float>(gsc2[0] * S(2) * G.sc2[0]);
-  vl.y += static_cast<float>(gsc2[1] * S(2) * G.sc2[1]);
-  vl.z += static_cast<float>(gsc2[2] * S(2) * G.sc2[2]);
-  vl.w += static_cast<float>(gsc2[3] * S(2) * G.sc2[3]);
+  vl.x += static_cast<float>(gls[0]);
+  vl.y += static_cast<float>(gls[1]);
+  vl.z += static_cast<float>(gls[2]);
+  vl.w += static_cast<float>(gls[3]);
   *gl = vl;
   out.logit[i] += static_cast<float>(acc.gop) * G.opacity * (1.0f - G.opacity);
 }

@@ -192,6 +192,28 @@ __device__ __forceinline__ void forward_color(const r4g_gaussians& g, int i, con
   }
 }
 
+// Image-plane velocity of the sliced centre (Sec. 3.2.2: slicing adds
+// (t - mu_t) V / W to the centre, so V / W is its speed): with
+// p_c = (x, y, z) and p_c' = R_cw V / W,
+//   d(mean2d)/dt = (fx (x' z - x z') / z^2, fy (y' z - y z') / z^2),
+// stored in f.rgb as (du/dt, dv/dt, 0) so the blend composites it with the
+// colour's weights.
+template <typename S>
+__device__ __forceinline__ void image_velocity(const Sig4<S>& Q, S invW, const CamDev& cam, Fwd& f) {
+  const float v0 = static_cast<float>(Q.C[3] * invW);
+  const float v1 = static_cast<float>(Q.C[6] * invW);
+  const float v2 = static_cast<float>(Q.C[8] * invW);
+  const float* Rc = cam.R;
+  const float xd = Rc[0] * v0 + Rc[1] * v1 + Rc[2] * v2;
+  const float yd = Rc[3] * v0 + Rc[4] * v1 + Rc[5] * v2;
+  const float zd = Rc[6] * v0 + Rc[7] * v1 + Rc[8] * v2;
+  const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+  const float iz2 = 1.0f / (z * z);
+  f.rgb[0] = cam.fx * (xd * z - x * zd) * iz2;
+  f.rgb[1] = cam.fy * (yd * z - y * zd) * iz2;
+  f.rgb[2] = 0.0f;
+}
+
 // Pixel-column range whose centres can lie inside the region where
 // alpha >= 1/255 and power >= -4.5, i.e. d^T conic d <= min(9, 2 ln(255 o_t)).
 // The axis-aligned box of that ellipse has half-widths sqrt(k2 Sigma'_xx) and
@@ -213,6 +235,130 @@ __device__ __forceinline__ bool pixel_box(const Fwd& f, const CamDev& cam, int& 
   j0 = max(static_cast<int>(ceilf(ya)), 0);
   j1 = min(static_cast<int>(floorf(yb)), cam.height - 1);
   return i0 <= i1 && j0 <= j1;
+}
+
+// ---- backward ---------------------------------------------------------------
+// Gradient of the rotor -> matrix map (appendix A.2): every entry of R is a
+// quadratic form of the normalised rotor, so dR_e / dr is linear in r.
+// Off-diagonal entries are 2 * sum of signed products r_a r_b.
+template <typename S>
+__device__ __forceinline__ void prod_term(S w, const S r[8], S g[8], int a, int b) {
+  g[a] += w * r[b];
+  g[b] += w * r[a];
+}
+
+template <typename S>
+__device__ __forceinline__ void rotor_matrix_bwd(const S r[8], const S gR[16], S g[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) g[k] = S(0);
+  // diagonal entries: sums of +-r_k^2; signs over (s, b01, b02, b12, b03, b13, b23, p)
+  const int dsg[4][8] = {{1, -1, -1, 1, -1, 1, 1, -1},
+                         {1, -1, 1, -1, 1, -1, 1, -1},
+                         {1, 1, -1, -1, 1, 1, -1, -1},
+                         {1, 1, 1, 1, -1, -1, -1, -1}};
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const S w = S(2) * gR[5 * d];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] += dsg[d][k] > 0 ? w * r[k] : -w * r[k];
+  }
+  // indices: s 0, b01 1, b02 2, b12 3, b03 4, b13 5, b23 6, p 7
+  S w;
+  w = S(2) * gR[1];   // R01 = 2(b01 s - b02 b12 - b03 b13 + b23 p)
+  prod_term(w, r, g, 1, 0); prod_term(-w, r, g, 2, 3); prod_term(-w, r, g, 4, 5); prod_term(w, r, g, 6, 7);
+  w = S(2) * gR[2];   // R02 = 2(b01 b12 + b02 s - b03 b23 - b13 p)
+  prod_term(w, r, g, 1, 3); prod_term(w, r, g, 2, 0); prod_term(-w, r, g, 4, 6); prod_term(-w, r, g, 5, 7);
+  w = S(2) * gR[3];   // R03 = 2(b01 b13 + b02 b23 + b03 s + b12 p)
+  prod_term(w, r, g, 1, 5); prod_term(w, r, g, 2, 6); prod_term(w, r, g, 4, 0); prod_term(w, r, g, 3, 7);
+  w = S(2) * gR[4];   // R10 = 2(-b01 s - b02 b12 - b03 b13 - b23 p)
+  prod_term(-w, r, g, 1, 0); prod_term(-w, r, g, 2, 3); prod_term(-w, r, g, 4, 5); prod_term(-w, r, g, 6, 7);
+  w = S(2) * gR[6];   // R12 = 2(-b01 b02 + b03 p + b12 s - b13 b23)
+  prod_term(-w, r, g, 1, 2); prod_term(w, r, g, 4, 7); prod_term(w, r, g, 3, 0); prod_term(-w, r, g, 5, 6);
+  w = S(2) * gR[7];   // R13 = 2(-b01 b03 - b02 p + b12 b23 + b13 s)
+  prod_term(-w, r, g, 1, 4); prod_term(-w, r, g, 2, 7); prod_term(w, r, g, 3, 6); prod_term(w, r, g, 5, 0);
+  w = S(2) * gR[8];   // R20 = 2(b01 b12 - b02 s - b03 b23 + b13 p)
+  prod_term(w, r, g, 1, 3); prod_term(-w, r, g, 2, 0); prod_term(-w, r, g, 4, 6); prod_term(w, r, g, 5, 7);
+  w = S(2) * gR[9];   // R21 = 2(-b01 b02 - b03 p - b12 s - b13 b23)
+  prod_term(-w, r, g, 1, 2); prod_term(-w, r, g, 4, 7); prod_term(-w, r, g, 3, 0); prod_term(-w, r, g, 5, 6);
+  w = S(2) * gR[11];  // R23 = 2(b01 p - b02 b03 - b12 b13 + b23 s)
+  prod_term(w, r, g, 1, 7); prod_term(-w, r, g, 2, 4); prod_term(-w, r, g, 3, 5); prod_term(w, r, g, 6, 0);
+  w = S(2) * gR[12];  // R30 = 2(b01 b13 + b02 b23 - b03 s - b12 p)
+  prod_term(w, r, g, 1, 5); prod_term(w, r, g, 2, 6); prod_term(-w, r, g, 4, 0); prod_term(-w, r, g, 3, 7);
+  w = S(2) * gR[13];  // R31 = 2(-b01 b03 + b02 p + b12 b23 - b13 s)
+  prod_term(-w, r, g, 1, 4); prod_term(w, r, g, 2, 7); prod_term(w, r, g, 3, 6); prod_term(-w, r, g, 5, 0);
+  w = S(2) * gR[14];  // R32 = 2(-b01 p - b02 b03 - b12 b13 - b23 s)
+  prod_term(-w, r, g, 1, 7); prod_term(-w, r, g, 2, 4); prod_term(-w, r, g, 3, 5); prod_term(-w, r, g, 6, 0);
+}
+
+// Gradient of F_norm (appendix A.1): r1 = r + delta(r) P r with P r = grad eps
+// (P symmetric, P^2 = I), r_hat = r1 / |r1|; delta depends on eps and l^2.
+template <typename S>
+__device__ __forceinline__ void rotor_normalize_bwd(const float rin[8], const RotorNorm<S>& rn,
+                                                    const S gh[8], S gr[8]) {
+  if (rn.ident) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) gr[k] = S(0);
+    return;
+  }
+  const S invn = S(1) / sqrt(rn.n2);
+  S dot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dot += rn.r[k] * gh[k];
+  S g1[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) g1[k] = (gh[k] - rn.r[k] * dot) * invn;
+  S r[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) r[k] = static_cast<S>(rin[k]);
+  S Pr[8], Pg[8];
+  eps_grad(r, Pr);
+  eps_grad(g1, Pg);
+  S gdot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gdot += g1[k] * Pr[k];
+  S dd_de = 0, dd_dl2 = 0;
+  if (rn.l2 > S(0)) {
+    S disc = rn.l2 * rn.l2 - S(4) * rn.eps * rn.eps;
+    disc = disc > S(0) ? disc : S(0);
+    const S sq = sqrt(disc);
+    const S D = rn.l2 + sq;
+    dd_de = S(-2) / D;
+    dd_dl2 = S(2) * rn.eps / (D * D);
+    if (sq > S(0)) {
+      dd_de -= S(8) * rn.eps * rn.eps / (D * D * sq);
+      dd_dl2 *= S(1) + rn.l2 / sq;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    gr[k] = g1[k] + rn.delta * Pg[k] + gdot * (dd_de * Pr[k] + dd_dl2 * S(2) * r[k]);
+}
+
+// Backward of Sigma4 = R diag(s^2) R^T, R = F_map(F_norm(rotor)), s =
+// exp(log-scale): from the symmetric gradient G4 of Sigma4 to the gradients
+// of the raw rotor (grot) and of the log-scales (gls).
+template <typename S>
+__device__ __forceinline__ void sigma4_backward(const Geo<S>& G, const S G4[4][4], S grot[8], S gls[4]) {
+  const S* R = G.R;
+  S gR[16], gsc2[4];
+  S G4R[4][4];  // G4 R
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      G4R[a][k] = G4[a][0] * R[k] + G4[a][1] * R[4 + k] + G4[a][2] * R[8 + k] + G4[a][3] * R[12 + k];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gR[4 * a + k] = S(2) * G4R[a][k] * G.sc2[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    gsc2[k] = R[k] * G4R[0][k] + R[4 + k] * G4R[1][k] + R[8 + k] * G4R[2][k] + R[12 + k] * G4R[3][k];
+  S grh[8];
+  rotor_matrix_bwd<S>(G.rn.r, gR, grh);
+  rotor_normalize_bwd<S>(G.p.rot, G.rn, grh, grot);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gls[k] = gsc2[k] * S(2) * G.sc2[k];  // d s^2 / d log s = 2 s^2
 }
 
 }  // namespace r4g

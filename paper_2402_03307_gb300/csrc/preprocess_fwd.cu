@@ -22,17 +22,11 @@ struct GeomTable {
   ViewGeom g[kMaxViews];
 };
 
-// One thread per view: the camera as the kernels use it (rotation, centre
-// -R^T t, focal lengths and the 1.3 tan(fov/2) clamp of J) from the host
-// views (a kernel parameter) or from device views, and the view's place in
-// the batch. A device view whose image size differs from the host layout
-// sets status bit 2 and is rendered with the layout's size.
-__global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* __restrict__ vdev, int nviews,
-                                   ViewDev* __restrict__ out, FrameHeader* hdr) {
-  const int v = threadIdx.x;
-  if (v >= nviews) return;
-  const r4g_view V = vdev ? vdev[v] : hv.v[v];
-  const ViewGeom& G = gt.g[v];
+// The camera as the kernels use it (rotation, centre -R^T t, focal lengths
+// and the 1.3 tan(fov/2) clamp of J) and the view's place in the batch. A
+// device view whose image size differs from the host layout sets status
+// bit 2 and is rendered with the layout's size.
+__device__ __forceinline__ ViewDev make_view(const r4g_view& V, const ViewGeom& G, FrameHeader* hdr) {
   ViewDev d;
   CamDev& c = d.cam;
 #pragma unroll
@@ -42,18 +36,18 @@ __global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* _
     c.t[k] = V.cam.world_to_cam[4 * k + 3];
   }
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {  // centre = -R^T t, in double
-    double acc = 0.0;
+  for (int j = 0; j < 3; ++j) {  // centre = -R^T t
+    float acc = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) acc = __dadd_rn(acc, -__dmul_rn(static_cast<double>(c.R[3 * k + j]), c.t[k]));
-    c.pos[j] = static_cast<float>(acc);
+    for (int k = 0; k < 3; ++k) acc = __fsub_rn(acc, __fmul_rn(c.R[3 * k + j], c.t[k]));
+    c.pos[j] = acc;
   }
   c.fx = V.cam.fx;
   c.fy = V.cam.fy;
   c.cx = V.cam.cx;
   c.cy = V.cam.cy;
-  c.limx = static_cast<float>(static_cast<double>(kClampFov) * (G.width / (2.0 * static_cast<double>(c.fx))));
-  c.limy = static_cast<float>(static_cast<double>(kClampFov) * (G.height / (2.0 * static_cast<double>(c.fy))));
+  c.limx = __fmul_rn(kClampFov, __fdiv_rn(static_cast<float>(G.width), __fmul_rn(2.0f, c.fx)));
+  c.limy = __fmul_rn(kClampFov, __fdiv_rn(static_cast<float>(G.height), __fmul_rn(2.0f, c.fy)));
   c.width = G.width;
   c.height = G.height;
   d.t = V.t;
@@ -63,8 +57,18 @@ __global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* _
   d.pix_off = G.pix_off;
   d.tdiff_off = G.tdiff_off;
   d.pad[0] = d.pad[1] = d.pad[2] = 0u;
-  if (V.cam.width != G.width || V.cam.height != G.height) atomicOr(&hdr->status, 4u);
-  out[v] = d;
+  if (hdr && (V.cam.width != G.width || V.cam.height != G.height)) atomicOr(&hdr->status, 4u);
+  return d;
+}
+
+// Multi-view calls: one thread per view writes the frame's view table, from
+// the host views (a kernel parameter) or from device views.
+__global__ void setup_views_kernel(HostViews hv, GeomTable gt, const r4g_view* __restrict__ vdev, int nviews,
+                                   ViewDev* __restrict__ out, FrameHeader* hdr) {
+  const int v = threadIdx.x;
+  if (v >= nviews) return;
+  const r4g_view V = vdev ? vdev[v] : hv.v[v];
+  out[v] = make_view(V, gt.g[v], hdr);
 }
 
 cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
@@ -83,10 +87,19 @@ cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view
 // ---- forward ------------------------------------------------------------------
 // kMulti: several views (a loop keeping the view-independent values live);
 // otherwise exactly one, with a smaller register footprint.
+// One view (kMulti false) needs no setup launch: every block builds the
+// view's table entry from the host view (or the device view) itself, and
+// block 0 stores it in the frame for the later kernels.
+struct OneView {
+  r4g_view v;
+  ViewGeom g;
+  const r4g_view* vdev;
+};
+
 template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
 __global__ void __launch_bounds__(kPreBlock)
-    preprocess_fwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews, PreOut out,
-                          int sh_degree, bool temporal_cull) {
+    preprocess_fwd_kernel(r4g_gaussians g, ViewDev* __restrict__ views, int nviews, OneView one, PreOut out,
+                          int sh_degree, bool temporal_cull, bool flow) {
   if constexpr (!kMulti) nviews = 1;
   __shared__ uint32_t s_pairs[kMaxViews];
   __shared__ uint32_t s_wcnt[kPreBlock / 32];
@@ -94,8 +107,14 @@ __global__ void __launch_bounds__(kPreBlock)
   __shared__ __align__(16) ViewDev s_views[kMaxViews];  // the view table (copied as 16-byte words)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v = threadIdx.x; v < kMaxViews; v += kPreBlock) s_pairs[v] = 0;
-  for (int k = threadIdx.x; k < nviews * 8; k += kPreBlock)
-    reinterpret_cast<uint4*>(s_views)[k] = reinterpret_cast<const uint4*>(views)[k];
+  if constexpr (kMulti) {
+    for (int k = threadIdx.x; k < nviews * 8; k += kPreBlock)
+      reinterpret_cast<uint4*>(s_views)[k] = reinterpret_cast<const uint4*>(views)[k];
+  } else if (threadIdx.x == 0) {
+    const ViewDev d = make_view(one.vdev ? one.vdev[0] : one.v, one.g, blockIdx.x == 0 ? out.header : nullptr);
+    s_views[0] = d;
+    if (blockIdx.x == 0) views[0] = d;
+  }
   if (threadIdx.x == 0) s_vis = 0;
   __syncthreads();
   const int i = blockIdx.x * kPreBlock + threadIdx.x;
@@ -116,7 +135,11 @@ __global__ void __launch_bounds__(kPreBlock)
       int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
       const bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
       if (vis) {
-        forward_color<kShBF16>(g, i, cam, sh_degree, f);
+        if (flow) {  // the colour slot carries d(mean2d)/dt (channel 2 zero)
+          image_velocity<S>(G, invW, cam, f);
+        } else {
+          forward_color<kShBF16>(g, i, cam, sh_degree, f);
+        }
         const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
         const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
         ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
@@ -172,14 +195,31 @@ __global__ void __launch_bounds__(kPreBlock)
 }
 
 template <typename S, bool A, bool B>
-static void launch_pre_t(const r4g_gaussians& g, const ViewDev* views, int nviews, const PreOut& o, int nblocks,
-                         int sh_degree, bool tc, cudaStream_t s) {
-  if (nviews > 1) preprocess_fwd_kernel<S, A, B, true><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
-  else preprocess_fwd_kernel<S, A, B, false><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, o, sh_degree, tc);
+static void launch_pre_t(const r4g_gaussians& g, ViewDev* views, int nviews, const OneView& one, const PreOut& o,
+                         int nblocks, int sh_degree, bool tc, bool fl, cudaStream_t s) {
+  if (nviews > 1)
+    preprocess_fwd_kernel<S, A, B, true><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc, fl);
+  else
+    preprocess_fwd_kernel<S, A, B, false><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc,
+                                                                         fl);
 }
 
 cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
-                                  uint32_t flags, cudaStream_t s) {
+                                  uint32_t flags, const r4g_view* views_host, const r4g_view* views_dev,
+                                  cudaStream_t s) {
+  OneView one{};
+  if (L.nviews > 1) {
+    cudaError_t e = launch_setup_views(L, frame, views_host, views_dev, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    one.v = views_host[0];
+    one.g = L.geom[0];
+    one.vdev = views_dev;
+    if (L.n == 0) {  // no preprocess blocks: the table still has to be written
+      cudaError_t e = launch_setup_views(L, frame, views_host, views_dev, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
   if (L.n == 0) return cudaSuccess;
   PreOut o;
   o.recA = at<float4>(frame, L.rec);
@@ -191,12 +231,13 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
   o.header = at<FrameHeader>(frame, L.header);
   o.tile_w = L.tile_w;
   o.tile_h = L.tile_h;
-  const ViewDev* views = at<ViewDev>(frame, L.views);
+  ViewDev* views = at<ViewDev>(frame, L.views);
   const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
+  const bool fl = (flags & R4G_FLAG_FLOW) != 0;
   const bool f64 = flags & R4G_FLAG_FP64_SLICE;
   const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
   const int nb = static_cast<int>((L.n + kPreBlock - 1) / kPreBlock);
-#define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, o, nb, sh_degree, tc, s)
+#define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, one, o, nb, sh_degree, tc, fl, s)
   if (f64) {
     if (sb && hb) R4G_PF(double, true, true);
     else if (sb) R4G_PF(double, true, false);

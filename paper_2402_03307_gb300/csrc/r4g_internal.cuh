@@ -122,11 +122,14 @@ inline T* at(void* base, size_t off) {
 }
 
 // ---- launchers (return cudaGetLastError() after enqueueing) -----------------
-// View table of the frame from host views (views_dev NULL) or device views.
+// View table of the frame from host views (views_dev NULL) or device views,
+// then the per-item preprocess (a one-view call builds the table inside the
+// preprocess kernel).
 cudaError_t launch_setup_views(const FrameLayout& L, void* frame, const r4g_view* views_host,
                                const r4g_view* views_dev, cudaStream_t s);
 cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
-                                  uint32_t flags, cudaStream_t s);
+                                  uint32_t flags, const r4g_view* views_host, const r4g_view* views_dev,
+                                  cudaStream_t s);
 // scan of the tile counts in depth order and key emission (tile key, index)
 cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s);
 cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf1,

@@ -427,6 +427,20 @@ def default_renderer() -> Renderer:
     return _default
 
 
+_flow: Renderer | None = None
+
+
+def render_flow(params: dict, cam, t: float, renderer: Renderer | None = None) -> torch.Tensor:
+    """Optical-flow render (R4G_FLAG_FLOW): [2, H, W] image-plane velocity of
+    the sliced centres, d(mean2d)/dt, composited with the colour weights."""
+    global _flow
+    if renderer is None:
+        if _flow is None:
+            _flow = Renderer(flags=abi.R4G_FLAG_FLOW)
+        renderer = _flow
+    return renderer.render(params, cam, t).image[:2]
+
+
 def render_batch(params: dict, views, renderer: Renderer | None = None) -> torch.Tensor:
     """Differentiable batched render -> packed images of all views."""
     r = renderer or default_renderer()
@@ -439,6 +453,68 @@ def render(params: dict, cam, t: float, renderer: Renderer | None = None) -> tor
     r = renderer or default_renderer()
     return Render4DFunction.apply(params["mean"], params["rotor"], params["logscale"], params["logit"],
                                   params["sh"], r, cam, t)
+
+
+def knn4d(means: torch.Tensor, scale_xyz: float, scale_t: float, k: int = 8, with_dist: bool = False):
+    """K nearest neighbours of the 4D means ([N, 4] float32 CUDA) after
+    dividing x, y, z by scale_xyz and t by scale_t (r4g_knn4d). Returns int32
+    [N, k] (and the squared scaled distances [N, k] with ``with_dist``)."""
+    m = means.contiguous()
+    if m.dtype != torch.float32 or m.dim() != 2 or m.shape[1] != 4 or not m.is_cuda:
+        raise ValueError("means must be a float32 CUDA tensor [N, 4]")
+    n = int(m.shape[0])
+    idx = torch.empty((n, k), dtype=torch.int32, device=m.device)
+    d2 = torch.empty((n, k), dtype=torch.float32, device=m.device) if with_dist else None
+    nb = abi.r4g_knn_scratch_bytes(n)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=m.device)
+    s = torch.cuda.current_stream(m.device).cuda_stream
+    abi.r4g_knn4d(m.data_ptr(), n, float(scale_xyz), float(scale_t), int(k), idx.data_ptr(),
+                  d2.data_ptr() if d2 is not None else None, scratch.data_ptr(), nb, s)
+    if abi.r4g_knn_status(scratch.data_ptr(), n, s) != abi.R4G_OK:
+        raise abi.R4GError(abi.R4G_ETIMEOUT, "knn sort wait gave up")
+    return (idx, d2) if with_dist else idx
+
+
+def regularizers(params: dict, knn_idx: torch.Tensor, lambda_entropy: float = 1.0,
+                 lambda_consistency: float = 1.0, grads: dict | None = None) -> torch.Tensor:
+    """(L_entropy, L_consistent4D) as a float32 CUDA tensor [2]; with ``grads``
+    (float32 tensors shaped like the parameters) adds lambda-weighted
+    gradients into grads['logit'], grads['rotor'] and grads['logscale']."""
+    g = gaussians_struct(params)
+    k = int(knn_idx.shape[1])
+    idx = knn_idx.contiguous()
+    if idx.dtype != torch.int32 or idx.shape[0] != g.n:
+        raise ValueError("knn_idx must be int32 [N, k]")
+    dev = params["mean"].device
+    loss = torch.empty(2, dtype=torch.float32, device=dev)
+    gs = None
+    if grads is not None:
+        gs = abi.r4g_grads()
+        for name in PARAM_NAMES:
+            setattr(gs, name, grads[name].data_ptr())
+    nb = abi.r4g_regularizers_scratch_bytes(g.n)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    abi.r4g_regularizers(g, idx.data_ptr(), k, float(lambda_entropy), float(lambda_consistency), loss.data_ptr(),
+                         gs, scratch.data_ptr(), nb, s)
+    return loss
+
+
+def image_loss(image: torch.Tensor, target: torch.Tensor, lambda_ssim: float = 0.2, with_grad: bool = True):
+    """(L, L1, SSIM) as a float32 CUDA tensor [3] and, with ``with_grad``,
+    dL/d image (r4g_image_loss: (1 - lambda) L1 + lambda (1 - SSIM))."""
+    x, y = image.contiguous(), target.contiguous()
+    if x.shape != y.shape or x.dim() != 3 or x.dtype != torch.float32 or y.dtype != torch.float32:
+        raise ValueError("image and target must be float32 [C, H, W] of one shape")
+    c, h, w = (int(v) for v in x.shape)
+    out = torch.empty(3, dtype=torch.float32, device=x.device)
+    grad = torch.empty_like(x) if with_grad else None
+    nb = abi.r4g_image_loss_scratch_bytes(c, h, w)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=x.device)
+    s = torch.cuda.current_stream(x.device).cuda_stream
+    abi.r4g_image_loss(x.data_ptr(), y.data_ptr(), c, h, w, float(lambda_ssim), out.data_ptr(),
+                       grad.data_ptr() if grad is not None else None, scratch.data_ptr(), nb, s)
+    return (out, grad) if with_grad else out
 
 
 def sort_pairs(keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end_bit: int = 64):
