@@ -85,10 +85,11 @@ def depth_order(rec: dict) -> torch.Tensor:
     return vis[perm]
 
 
-def _composite(m2, con, o, col, z, px, py, bg):
-    """Composite a chunk of pixels (px, py: [P]) over G depth-ordered Gaussians."""
-    G = m2.shape[0]
-    pos = torch.arange(G)
+def _inclusion(m2, con, o, px, py):
+    """The per-pixel rules for a chunk of pixels (px, py: [P]) over G
+    depth-ordered Gaussians: [P, G] exponent, cutoff test, raw and clamped
+    alpha, the alpha rule, the effective alpha, the transmittance after and
+    before each Gaussian, and which Gaussians are composited."""
     dx = px[:, None] - m2[None, :, 0]
     dy = py[:, None] - m2[None, :, 1]
     power = -0.5 * (con[None, :, 0] * dx * dx + con[None, :, 2] * dy * dy) - con[None, :, 1] * dx * dy
@@ -102,6 +103,15 @@ def _composite(m2, con, o, col, z, px, py, bg):
     ones = torch.ones_like(T_after[:, :1])
     T_before = torch.cat([ones, T_after[:, :-1]], dim=1)
     included = valid & (T_after >= T_MIN)
+    return power, in_cut, alpha_raw, alpha, valid, a_eff, one_minus, T_after, T_before, included
+
+
+def _composite(m2, con, o, col, z, px, py, bg):
+    """Composite a chunk of pixels (px, py: [P]) over G depth-ordered Gaussians."""
+    G = m2.shape[0]
+    pos = torch.arange(G)
+    power, in_cut, alpha_raw, alpha, valid, a_eff, one_minus, T_after, T_before, included = \
+        _inclusion(m2, con, o, px, py)
     w = torch.where(included, a_eff * T_before, torch.zeros_like(a_eff))
     C = w @ col  # [P,3]
     T_final = torch.prod(torch.where(included, one_minus, torch.ones_like(one_minus)), dim=1)
@@ -211,6 +221,32 @@ def render_pixels(scene: dict, cam, t: float, pixels, bg=(0.0, 0.0, 0.0), rec: d
     img, T, last, mt, md, mi, mdi = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
     return {"rgb": img, "T": T, "last": last, "margin": mt, "margin_depth": md, "margin_img": mi,
             "margin_depth_img": mdi}
+
+
+def composited_counts(scene: dict, cam, t: float, rec: dict | None = None, budget: int = 4_000_000) -> torch.Tensor:
+    """Number of pixels of the image each Gaussian is composited into (int64
+    [N]; 0 for Gaussians no pixel takes), by the same per-pixel rules."""
+    cam = _cam(cam)
+    if rec is None:
+        rec = preprocess(scene, cam, t)
+    order = depth_order(rec)
+    n = int(rec["z"].shape[0])
+    counts = torch.zeros(n, dtype=torch.long)
+    G = int(order.numel())
+    if G == 0:
+        return counts
+    with torch.no_grad():
+        m2 = rec["mean2d"].detach()[order]
+        con = rec["conic"].detach()[order]
+        o = rec["opacity_t"].detach()[order]
+        cols, rows = _pixel_grid(cam["width"], cam["height"])
+        step = max(1, budget // G)
+        for s in range(0, cols.numel(), step):
+            px = cols[s:s + step].to(torch.float64) + 0.5
+            py = rows[s:s + step].to(torch.float64) + 0.5
+            included = _inclusion(m2, con, o, px, py)[-1]
+            counts[order] += included.sum(dim=0)
+    return counts
 
 
 REC_GRAD_KEYS = ("mean2d", "conic", "opacity_t", "rgb")

@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "gaussians", "look_at", "orbit_camera", "Camera", "smooth_target",
     "small_scene", "fwd300k_scene", "train_views", "batched_views", "large_views",
-    "random_pixels", "random_keys",
+    "random_pixels", "random_keys", "density_inputs",
 ]
 
 
@@ -207,3 +207,18 @@ def random_keys(seed: int, n: int, high_bits: int) -> tuple[np.ndarray, np.ndarr
     keys = (hi << np.uint64(32)) | lo
     vals = np.arange(n, dtype=np.uint32)
     return keys, vals
+
+
+def density_inputs(seed: int, n: int, threshold: float = 2e-4, max_views: int = 8) -> dict[str, np.ndarray]:
+    """Seeded statistics and split draws for a densify-and-prune step over n
+    Gaussians: vs_count integer in [0, max_views], a mean view-space gradient
+    threshold * exp(N(-0.5, 1)) (about a third at or above the threshold),
+    vs_grad = mean * count, max_radius ~ U[0, 40] pixels, and z ~ N(0, 1)
+    f32[n, 2, 4] for the split children."""
+    rng = np.random.default_rng(seed)
+    count = rng.integers(0, max_views + 1, n).astype(np.float32)
+    mean = threshold * np.exp(rng.normal(-0.5, 1.0, n))
+    vs_grad = (mean * count).astype(np.float32)
+    max_radius = rng.uniform(0.0, 40.0, n).astype(np.float32)
+    z = rng.normal(0.0, 1.0, (n, 2, 4)).astype(np.float32)
+    return {"vs_grad": vs_grad, "vs_count": count, "max_radius": max_radius, "z": z}
