@@ -142,9 +142,15 @@ SMS, FP32_LANES = 152, 128
 # C += c w (3); the exponential itself runs on the MUFU unit.
 FP32_OPS_PER_PAIR = 19
 
+# DRAM bytes (read + write) of one launch of the kernel, from one ncu capture
+# of the sweep (--metrics dram__bytes_read.sum,dram__bytes_write.sum); None
+# for a kernel changed since its counters were taken.
+DRAM_TRAFFIC = {"blend": 24_906_816}
+
 
 def algorithmic_bytes(stage: str, n: int, n_vis: int, keys: int, npix: int) -> float:
-    """Bytes a stage must move per launch (the per-unit figures of the design doc)."""
+    """Bytes a stage must move per launch: per Gaussian, per visible item, per
+    (tile, Gaussian) pair and per pixel."""
     if stage == "preprocess":
         return 68.0 * n + 192.0 * n_vis + 48.0 * n_vis + 12.0 * n
     if stage == "binning":
@@ -248,11 +254,7 @@ def run_ours(args, rank, world, local):
     keys, n_vis = work["keys"], work["n_visible"]
     per_stage = {k: v / len(frames) for k, v in stage_ms.items() if v > 0}
     top = max(per_stage, key=per_stage.get)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
+    peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
@@ -269,7 +271,7 @@ def run_ours(args, rank, world, local):
                 "frac": round(ach / hbm_peak, 4)}
 
     roofline = dict(stage_roof(top))
-    roofline.update({"kernel": top, "traffic": None,
+    roofline.update({"kernel": top, "traffic": DRAM_TRAFFIC.get(top),
                      "peak_source": (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
                                      f"MEASURED_PEAKS.json)") if top == "blend" else f"{src} hbm_gbs",
                      "work_per_frame": {"composited_pairs": round(work["pairs"]), "keys": round(keys),
@@ -301,6 +303,14 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e and not args.frames_only:
         out["e2e"] = e2e_bench(args, rend, g, dev, stream, frames, cap)
     return out
+
+
+def measured_peaks() -> dict:
+    """MEASURED_PEAKS.json (HBM copy GB/s, bf16 TFLOP/s, clocks) when present."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 def _timed(fn, steps: int, stream, flush=None) -> float:
@@ -547,7 +557,9 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
     for _ in range(2):
         run_loss()
     ms_loss = _timed(run_loss, 20, stream, flush)
-    return {"image_loss": {"ms": round(ms_loss, 3), "what": "0.8 L1 + 0.2 (1 - SSIM) and its gradient, 3x1014x1352",
+    dens = densify_bench(params, dev, stream, flush)
+    return {"densify": dens,
+            "image_loss": {"ms": round(ms_loss, 3), "what": "0.8 L1 + 0.2 (1 - SSIM) and its gradient, 3x1014x1352",
                            "note": "includes scratch allocation by the Python wrapper"},
             "flow": {"value": round(1000.0 / ms_flow, 1), "unit": "frames/s",
                      "workload": "optical-flow render of the 300k sweep (d mean2d / dt composited)"},
@@ -555,6 +567,61 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
                       "note": "includes scratch allocation by the Python wrapper"},
             "regularizers": {"ms": round(ms_reg, 3), "n": N_GAUSS,
                              "what": "entropy + 4D consistency losses and their gradients"}}
+
+
+def densify_bench(params, dev, stream, flush):
+    """One densify-and-prune step (r4g_densify_plan + r4g_densify_apply) on the
+    300k scene with seeded statistics, outputs preallocated at 2N rows (no host
+    synchronisation inside the timed region), against the HBM roofline:
+    algorithmic bytes = plan 28 B per Gaussian (log-scales, logit, vs_grad,
+    vs_count) + 5 B of decisions and offsets written and read back + 260 B per
+    source row read + 264 B per output row written (with its source index) +
+    32 B of draws per split Gaussian."""
+    import numpy as np
+    import torch
+    import paper_2402_03307_gb300 as r4g
+    import synth
+    from paper_2402_03307_gb300 import abi
+
+    n = int(params["mean"].shape[0])
+    d = synth.density_inputs(90, n)
+    st = {k: torch.as_tensor(d[k]).to(dev) for k in ("vs_grad", "vs_count")}
+    z = torch.as_tensor(d["z"]).to(dev)
+    cfg = r4g.densify_config()
+    g = r4g.gaussians_struct(params)
+    nb = abi.r4g_densify_scratch_bytes(n)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    cap = 2 * n
+    out = {"mean": torch.empty((cap, 4), device=dev), "rotor": torch.empty((cap, 8), device=dev),
+           "logscale": torch.empty((cap, 4), device=dev), "logit": torch.empty((cap,), device=dev),
+           "sh": torch.empty((cap, 16, 3), device=dev)}
+    src = torch.empty(cap, dtype=torch.int32, device=dev)
+    o = abi.r4g_params_out()
+    for k in r4g.PARAM_NAMES:
+        setattr(o, k, out[k].data_ptr())
+    s = stream.cuda_stream
+
+    def step():
+        abi.r4g_densify_plan(g, st["vs_grad"].data_ptr(), st["vs_count"].data_ptr(), None, cfg,
+                             scratch.data_ptr(), nb, count.data_ptr(), s)
+        abi.r4g_densify_apply(g, z.data_ptr(), cfg, scratch.data_ptr(), nb, o, cap, src.data_ptr(), s)
+
+    for _ in range(3):
+        step()
+    ms = _timed(step, 20, stream, flush)
+    m = int(count.item())
+    sm = src[:m].cpu().numpy()
+    idx = np.where(sm >= 0, sm, -sm - 1)
+    sources = len(np.unique(idx))
+    splits = int(((sm < 0) & (np.bincount(idx, minlength=n)[idx] == 2) & (np.r_[True, idx[1:] != idx[:-1]])).sum())
+    bytes_ = 28 * n + 10 * n + 260 * sources + 264 * m + 32 * splits
+    peak = measured_peaks().get("hbm_gbs")
+    achieved = bytes_ / (ms * 1e-3) / 1e9
+    return {"ms": round(ms, 4), "n": n, "rows_out": m, "split_or_clone_sources": splits,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4) if peak else None, "bytes": bytes_},
+            "what": "plan + apply, 2 launches + 1 scan launch, outputs preallocated"}
 
 
 def e2e_bench(args, rend, g, dev, stream, frames, cap):

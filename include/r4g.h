@@ -102,13 +102,32 @@ typedef struct r4g_camera {
 
 /* Parameter gradients (device pointers, FP32, same shapes as r4g_gaussians,
  * 16-byte aligned rows). The backward ADDS into them, so several views can
- * accumulate one step; the caller zeroes them. */
+ * accumulate one step; the caller zeroes them.
+ *
+ * The last three members are optional (NULL = not kept) per-Gaussian
+ * statistics of adaptive density control (Sec. 4.2: densification by the
+ * view-space positional gradient, as in 3D Gaussian Splatting), each device
+ * float [n], updated by r4g_render_backward and r4g_render_batch_backward
+ * once per view in which the Gaussian was composited into at least one
+ * pixel:
+ *   vs_grad    += | (dL/du * W/2, dL/dv * H/2) |, the norm of the gradient
+ *                 of the loss with respect to the projected centre (u, v) in
+ *                 normalised device coordinates (pixels / (W/2, H/2)) for a
+ *                 W x H view; only the blend's direct dependence on (u, v)
+ *                 counts (not the conic's);
+ *   vs_count   += 1;
+ *   max_radius  = max(max_radius, 3 sqrt(lambda_max(Sigma'))) in pixels,
+ *                 Sigma' the dilated 2D covariance.
+ * r4g_regularizers ignores them. */
 typedef struct r4g_grads {
   float* mean;
   float* rotor;
   float* logscale;
   float* logit;
   float* sh;
+  float* vs_grad;
+  float* vs_count;
+  float* max_radius;
 } r4g_grads;
 
 /* One (camera, t) view of a batched call. */
@@ -329,6 +348,82 @@ r4g_status r4g_image_loss_scratch_bytes(int32_t channels, int32_t height, int32_
 r4g_status r4g_image_loss(const float* image, const float* target, int32_t channels, int32_t height,
                           int32_t width, float lambda_ssim, float* out_loss, float* grad_image,
                           void* scratch, size_t scratch_bytes, void* stream);
+
+/* ---- adaptive density control (Sec. 4.2 "CUDA Acceleration" and training
+ * details: duplication and pruning of the 4D Gaussians on the GPU, with the
+ * densification gradient threshold and the 3D Gaussian Splatting rules) ----
+ * One densify-and-prune step over n Gaussians in two calls, from the
+ * statistics the backward kept (r4g_grads.vs_grad / vs_count / max_radius):
+ *
+ *   densify  Gaussian i when vs_grad[i] >= grad_threshold * vs_count[i] and
+ *            vs_count[i] > 0 (its mean view-space gradient reaches the
+ *            threshold; decided exactly, in double precision);
+ *   clone    a densified Gaussian whose largest spatial scale
+ *            max(exp(logscale[i][0..2])) <= dense_scale: it is kept and an
+ *            identical copy follows it;
+ *   split    a densified Gaussian with a larger spatial scale: it is replaced
+ *            by two children drawn from its own 4D distribution,
+ *            mean_c = mean + R diag(s) z_c (R the rotation of the normalised
+ *            rotor, s = exp(logscale), z_c = z[i][c][0..3] standard normal,
+ *            c = 0, 1), log-scales logscale - ln(split_divisor) on all four
+ *            axes, the same rotor, logit and SH;
+ *   prune    every output row whose opacity sigmoid(logit) < min_opacity; if
+ *            max_scale > 0, every row whose largest spatial scale exceeds
+ *            max_scale; if max_screen_radius > 0 and max_radius is given,
+ *            every row continuing a Gaussian (not a new copy or child) whose
+ *            max_radius exceeds max_screen_radius.
+ *
+ * Output order: for i = 0..n-1, the surviving rows of Gaussian i (kept: i;
+ * clone: i, then its copy; split: child 0, child 1). out_src[j] receives, for
+ * output row j, i when the row continues Gaussian i (its optimiser state
+ * carries over) and -(i + 1) when it is new (a copy or a child). All
+ * parameters are FP32 (scale_dtype = sh_dtype = R4G_F32). */
+typedef struct r4g_densify_config {
+  float grad_threshold;     /* view-space gradient threshold (2e-4 Plenoptic, 5e-5 D-NeRF) */
+  float dense_scale;        /* clone / split boundary on the largest spatial scale
+                               (3D Gaussian Splatting: 0.01 x scene extent) */
+  float split_divisor;      /* children's scale divisor (1.6); > 1 */
+  float min_opacity;        /* prune below this opacity (0.005); in [0, 1) */
+  float max_scale;          /* prune above this spatial scale; 0 = off */
+  float max_screen_radius;  /* prune above this radius in pixels; 0 = off */
+} r4g_densify_config;
+
+/* Output parameter buffers (device, FP32, rows like r4g_gaussians, 16-byte
+ * aligned), capacity rows each. */
+typedef struct r4g_params_out {
+  float* mean;
+  float* rotor;
+  float* logscale;
+  float* logit;
+  float* sh;
+} r4g_params_out;
+
+/* scratch of the two calls: device, 256-byte aligned, r4g_densify_scratch_bytes(n). */
+r4g_status r4g_densify_scratch_bytes(int64_t n, size_t* bytes /* host out */);
+
+/* Plan: decide every Gaussian's outputs from g (logit, logscale), vs_grad,
+ * vs_count and (optional, NULL allowed) max_radius (device float [n]) and
+ * write into scratch the per-Gaussian decisions and output offsets;
+ * *out_count (device int64 [1]) receives the number of output rows.
+ * n <= 2^28. Deterministic. */
+r4g_status r4g_densify_plan(const r4g_gaussians* g, const float* vs_grad, const float* vs_count,
+                            const float* max_radius, const r4g_densify_config* cfg, void* scratch,
+                            size_t scratch_bytes, int64_t* out_count, void* stream);
+
+/* Apply: write the output rows planned into `scratch` by r4g_densify_plan for
+ * the same g and cfg. z: device float [n, 2, 4] standard normal draws (read
+ * only for split Gaussians). Rows j >= capacity are not written: allocate
+ * capacity >= *out_count (2 n always suffices). out and g must not overlap.
+ * out_src: device int32 [capacity] or NULL. */
+r4g_status r4g_densify_apply(const r4g_gaussians* g, const float* z, const r4g_densify_config* cfg,
+                             const void* scratch, size_t scratch_bytes, r4g_params_out* out,
+                             int64_t capacity, int32_t* out_src, void* stream);
+
+/* Opacity reset of the training schedule (every 3,000 steps in Sec. 4.2's
+ * settings, as in 3D Gaussian Splatting): logit[i] = min(logit[i],
+ * logit(max_opacity)), logit(p) = ln(p / (1 - p)) rounded to FP32 once on
+ * the host. max_opacity in (0, 1) (0.01). logit: device float [n]. */
+r4g_status r4g_opacity_reset(float* logit, int64_t n, float max_opacity, void* stream);
 
 /* ---- sort -------------------------------------------------------------------
  * Stable LSD radix sort of (uint64 key, uint32 value) pairs on key bits

@@ -8,8 +8,8 @@ Importing it loads the library and fails if it has not been built
 from . import abi  # noqa: F401
 from .render import (  # noqa: F401
     PARAM_NAMES, BatchGraph, BatchResult, Render4DBatchFunction, Render4DFunction, Renderer, RenderResult,
-    camera_struct, gaussians_struct, image_loss, knn4d, regularizers, render, render_batch, render_flow, sort_pairs,
-    view_struct, views_tensor,
+    camera_struct, densify, densify_config, density_stats, gaussians_struct, image_loss, knn4d, opacity_reset,
+    regularizers, render, render_batch, render_flow, sort_pairs, view_struct, views_tensor,
 )
 
 abi.lib()  # fail loudly here if libr4g.so is missing

@@ -37,6 +37,17 @@ class r4g_camera(C.Structure):
 
 class r4g_grads(C.Structure):
     _fields_ = [("mean", C.c_void_p), ("rotor", C.c_void_p), ("logscale", C.c_void_p),
+                ("logit", C.c_void_p), ("sh", C.c_void_p), ("vs_grad", C.c_void_p),
+                ("vs_count", C.c_void_p), ("max_radius", C.c_void_p)]
+
+
+class r4g_densify_config(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("dense_scale", C.c_float), ("split_divisor", C.c_float),
+                ("min_opacity", C.c_float), ("max_scale", C.c_float), ("max_screen_radius", C.c_float)]
+
+
+class r4g_params_out(C.Structure):
+    _fields_ = [("mean", C.c_void_p), ("rotor", C.c_void_p), ("logscale", C.c_void_p),
                 ("logit", C.c_void_p), ("sh", C.c_void_p)]
 
 
@@ -98,6 +109,13 @@ SIGNATURES = [
     ("r4g_image_loss_scratch_bytes", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     ("r4g_image_loss", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("r4g_densify_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    ("r4g_densify_plan", C.c_int, [C.POINTER(r4g_gaussians), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(r4g_densify_config), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    ("r4g_densify_apply", C.c_int, [C.POINTER(r4g_gaussians), C.c_void_p, C.POINTER(r4g_densify_config),
+                                    C.c_void_p, C.c_size_t, C.POINTER(r4g_params_out), C.c_int64, C.c_void_p,
+                                    C.c_void_p]),
+    ("r4g_opacity_reset", C.c_int, [C.c_void_p, C.c_int64, C.c_float, C.c_void_p]),
     ("r4g_set_timing", C.c_int, [C.c_void_p, C.c_int32]),
     ("r4g_stage_times", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     ("r4g_sort_scratch_bytes", C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
@@ -276,6 +294,28 @@ def r4g_image_loss_scratch_bytes(c: int, h: int, w: int) -> int:
 
 def r4g_image_loss(image, target, c, h, w, lam, out_loss, grad, scratch, scratch_bytes, stream) -> None:
     check(lib().r4g_image_loss(image, target, c, h, w, lam, out_loss, grad, scratch, scratch_bytes, stream))
+
+
+def r4g_densify_scratch_bytes(n: int) -> int:
+    out = C.c_size_t()
+    check(lib().r4g_densify_scratch_bytes(n, C.byref(out)))
+    return out.value
+
+
+def r4g_densify_plan(g: r4g_gaussians, vs_grad, vs_count, max_radius, cfg: r4g_densify_config, scratch,
+                     scratch_bytes, out_count, stream) -> None:
+    check(lib().r4g_densify_plan(C.byref(g), vs_grad, vs_count, max_radius, C.byref(cfg), scratch, scratch_bytes,
+                                 out_count, stream))
+
+
+def r4g_densify_apply(g: r4g_gaussians, z, cfg: r4g_densify_config, scratch, scratch_bytes,
+                      out: r4g_params_out, capacity, out_src, stream) -> None:
+    check(lib().r4g_densify_apply(C.byref(g), z, C.byref(cfg), scratch, scratch_bytes, C.byref(out), capacity,
+                                  out_src, stream))
+
+
+def r4g_opacity_reset(logit, n, max_opacity, stream) -> None:
+    check(lib().r4g_opacity_reset(logit, n, max_opacity, stream))
 
 
 def r4g_set_tile(ctx, tile_w: int, tile_h: int) -> None:

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libr4g.so")
 SOURCES = ["preprocess_fwd.cu", "preprocess.cu", "binning.cu", "sort.cu", "sort_noalloc.cu", "onesweep.cu",
-           "blend.cu", "regular.cu", "imageloss.cu", "api.cu"]
+           "blend.cu", "regular.cu", "imageloss.cu", "density.cu", "api.cu"]
 # per-file flags: the forward preprocess rounds every multiply and add as
 # written (no contraction), so its one-view and multi-view kernels agree bit
 # for bit

@@ -461,7 +461,8 @@ __device__ __forceinline__ void warp_reduce9(float v[9], int lane) {
 // backward sums per Gaussian. No float atomics: the gradient is
 // deterministic.
 template <int TW, int TH>
-__device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* sE, uint32_t& s_max, float* s_slab,
+__device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* sE, uint32_t* sTook, uint32_t& s_max,
+                                               float* s_slab,
                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                const float4* __restrict__ recA, const float4* __restrict__ recB,
                                                const float4* __restrict__ recC, const uint32_t* __restrict__ egid,
@@ -518,6 +519,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
     __syncthreads();
     for (int k = threadIdx.x; k < B::NW * BS * 9 / 4; k += BS)
       reinterpret_cast<float4*>(s_slab)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    sTook[threadIdx.x] = 0u;
     if (idx < n) {
       const uint32_t e = vals[rg.x + idx];
       sE[threadIdx.x] = e;
@@ -538,6 +540,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
         const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true>(S, sg[j0 + jj], p, PY, v)
                                                : bwd_entry<false>(S, sg[j0 + jj], p, PY, v);
         if (took) {
+          if (lane == 0) atomicOr(&sTook[j0 + jj], wbit);
           warp_reduce9(v, lane);
           float* dst = s_slab + (warp * BS + j0 + jj) * 9;
           if ((lane & 3) == 0) dst[lane >> 2] = v[0];
@@ -570,7 +573,8 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
           r0.w = -acc[4];                                    // d conic b
           r1.x = -0.5f * acc[5];                             // d conic c
           r1.y = o > 0.0f ? acc[0] / o : 0.0f;               // d opacity_t (alpha = opacity_t 2^power')
-          r2 = make_float4(acc[6], acc[7], acc[8], 0.0f);    // d rgb
+          // d rgb; w = 1 when a pixel of the tile composited the entry
+          r2 = make_float4(acc[6], acc[7], acc[8], sTook[threadIdx.x] ? 1.0f : 0.0f);
         }
         float4* d = gbuf + 3 * static_cast<size_t>(e);
         d[0] = r0;
@@ -602,6 +606,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
                      float4* __restrict__ gbuf) {
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
+  __shared__ uint32_t sTook[Blend<TW, TH>::NT];  // per batch entry: warps that composited it
   __shared__ uint32_t s_max;
   __shared__ int s_tile;
   extern __shared__ __align__(16) float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
-    blend_bwd_tile<TW, TH>(tile, sg, sE, s_max, s_slab, ranges, vals, recA, recB, recC, egid, ng, cap, views,
+    blend_bwd_tile<TW, TH>(tile, sg, sE, sTook, s_max, s_slab, ranges, vals, recA, recB, recC, egid, ng, cap, views,
                            nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf);
   }
 }

@@ -26,7 +26,8 @@ struct BwdAcc {
 template <typename S, bool kShBF16>
 __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, const Sig4<S>& G, const CamDev& cam,
                                               float t, int sh_degree, bool temporal_cull, float4 ga, float4 gb,
-                                              float4 gc, float* __restrict__ gsh, BwdAcc<S>& acc) {
+                                              float4 gc, float* __restrict__ gsh, BwdAcc<S>& acc,
+                                              float& radius) {
   Fwd f;
   S invW, dt;
   view_geometry<S>(G, cam, t, temporal_cull, f, invW, dt);
@@ -91,6 +92,10 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 
   // ---- conic = inverse of the dilated 2D covariance (A, B; B, C)
   const float A = f.cov[0], B = f.cov[1], Cc = f.cov[2];
+  {  // screen radius 3 sqrt(lambda_max(Sigma')) for the density-control statistics
+    const float hm = 0.5f * (A - Cc);
+    radius = 3.0f * sqrtf(0.5f * (A + Cc) + sqrtf(hm * hm + B * B));
+  }
   const float det = A * Cc - B * B;
   const float idet = 1.0f / det, id2 = idet * idet;
   const float gA = ga.z * (-Cc * Cc * id2) + ga.w * (B * Cc * id2) + gb.x * (idet - A * Cc * id2);
@@ -199,7 +204,7 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 // backward. After the views, the Sigma4 -> R -> rotor and scale backward runs
 // once per Gaussian and the gradients are added to the caller's buffers.
 // Every Gaussian is one thread's: the gradient is deterministic.
-template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
+template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti, bool kStats>
 __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     preprocess_bwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews,
                           const uint32_t* __restrict__ glist, const uint32_t* __restrict__ ioffs,
@@ -219,6 +224,7 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
 #pragma unroll
   for (int k = 0; k < 4; ++k) acc.gmean[k] = S(0);
   acc.gop = S(0);
+  float vs_grad = 0.0f, vs_count = 0.0f, max_radius = 0.0f;  // density-control statistics
   for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
     const size_t item = static_cast<size_t>(v) * g.n + i;
     const uint32_t cnt = mine ? touched[item] : 0u;
@@ -230,23 +236,28 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
       const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
       if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
       const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
-      float v9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      // v9[9]: tiles in which a pixel composited the item (the blend backward's flag)
+      float v9[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (uint32_t k = lane; k < qc; k += 32) {
         const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
         const float4 x = pr[0], y = pr[1], z = pr[2];
         v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
         v9[4] += y.x; v9[5] += y.y;
-        v9[6] += z.x; v9[7] += z.y; v9[8] += z.z;
+        v9[6] += z.x; v9[7] += z.y; v9[8] += z.z; v9[9] += z.w;
       }
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], sh);
       }
+      if constexpr (kStats) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v9[9] += __shfl_xor_sync(0xffffffffu, v9[9], sh);
+      }
       if (lane == q) {
         ga = make_float4(v9[0], v9[1], v9[2], v9[3]);
         gb = make_float4(v9[4], v9[5], 0.f, 0.f);
-        gc = make_float4(v9[6], v9[7], v9[8], 0.f);
+        gc = make_float4(v9[6], v9[7], v9[8], v9[9]);
       }
     }
     if (cnt == 1) {
@@ -255,10 +266,25 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
       gb = pr[1];
       gc = pr[2];
     }
-    if (cnt) view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc,
-                                       out.sh, acc);
+    if (cnt) {
+      float radius;
+      view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc, out.sh,
+                                acc, radius);
+      if (kStats && gc.w > 0.0f) {  // composited into a pixel of this view
+        const float ux = ga.x * (0.5f * static_cast<float>(views[v].cam.width));
+        const float uy = ga.y * (0.5f * static_cast<float>(views[v].cam.height));
+        vs_grad += sqrtf(ux * ux + uy * uy);
+        vs_count += 1.0f;
+        max_radius = fmaxf(max_radius, radius);
+      }
+    }
   }
   if (!mine) return;
+  if (kStats && vs_count > 0.0f) {
+    if (out.vs_grad) out.vs_grad[i] += vs_grad;
+    if (out.vs_count) out.vs_count[i] += vs_count;
+    if (out.max_radius) out.max_radius[i] = fmaxf(out.max_radius[i], max_radius);
+  }
   Geo<S> G;  // the rotor and scale intermediates, recomputed rather than kept through the views
   gauss_setup<S, kScaleBF16>(g, i, G);
   // symmetric gradient of Sigma4
@@ -301,7 +327,9 @@ template <typename S, bool A, bool B>
 static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree, bool tc,
                              const r4g_grads& out, cudaStream_t s) {
   const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
-  auto k = L.nviews > 1 ? preprocess_bwd_kernel<S, A, B, true> : preprocess_bwd_kernel<S, A, B, false>;
+  const bool stats = out.vs_grad || out.vs_count || out.max_radius;
+  auto k = L.nviews > 1 ? (stats ? preprocess_bwd_kernel<S, A, B, true, true> : preprocess_bwd_kernel<S, A, B, true, false>)
+                        : (stats ? preprocess_bwd_kernel<S, A, B, false, true> : preprocess_bwd_kernel<S, A, B, false, false>);
   k<<<nb, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist),
                              at<uint32_t>(frame, L.ioffs), at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf),
                              at<FrameHeader>(frame, L.header), sh_degree, tc, out);

@@ -99,6 +99,29 @@ def _packed_views(packed: torch.Tensor, structs) -> list:
     return out
 
 
+STAT_NAMES = ("vs_grad", "vs_count", "max_radius")
+
+
+def density_stats(n: int, device) -> dict:
+    """Zeroed density-control statistics for n Gaussians (float32 [n] each):
+    the summed view-space gradient norms, the number of views that
+    composited each Gaussian, and its largest screen radius."""
+    return {k: torch.zeros(n, dtype=torch.float32, device=device) for k in STAT_NAMES}
+
+
+def _set_stats(out: abi.r4g_grads, stats: dict | None, params: dict) -> None:
+    if stats is None:
+        return
+    n = int(params["mean"].shape[0])
+    for k in STAT_NAMES:
+        t_ = stats.get(k)
+        if t_ is None:
+            continue
+        if t_.dtype != torch.float32 or not t_.is_contiguous() or t_.numel() != n or not t_.is_cuda:
+            raise ValueError(f"stats[{k}] must be a contiguous float32 CUDA tensor [N]")
+        setattr(out, k, t_.data_ptr())
+
+
 class Renderer:
     """Owns an r4g context (tile shape, background, SH degree, flags)."""
 
@@ -116,6 +139,8 @@ class Renderer:
         self.ctx = abi.r4g_create(cfg)
         self.keys_per_gaussian = float(keys_per_gaussian)
         self._cap_hint: dict = {}
+        # density-control statistics the backward updates when set (see density_stats)
+        self.density: dict | None = None
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)
@@ -178,9 +203,11 @@ class Renderer:
     status_of = status
 
     def backward(self, params: dict, cam, t: float, res: RenderResult, grad_image: torch.Tensor,
-                 grads: dict, stream=None) -> None:
+                 grads: dict, stream=None, stats: dict | None = None) -> None:
         """Accumulate dL/dparams into ``grads`` (float32 tensors shaped like the
-        parameters) given dL/dimage for a render ``res`` of (params, cam, t)."""
+        parameters) given dL/dimage for a render ``res`` of (params, cam, t).
+        ``stats`` (default: ``self.density``), a :func:`density_stats` dict,
+        receives the view's density-control statistics."""
         g = gaussians_struct(params)
         c = camera_struct(cam)
         gi = grad_image.contiguous()
@@ -192,6 +219,7 @@ class Renderer:
             if t_.dtype != torch.float32 or not t_.is_contiguous() or t_.numel() != params[k].numel():
                 raise ValueError(f"grads[{k}] must be a contiguous float32 tensor like the parameter")
             setattr(out, k, t_.data_ptr())
+        _set_stats(out, stats if stats is not None else self.density, params)
         s = (stream or torch.cuda.current_stream(gi.device)).cuda_stream
         abi.r4g_render_backward(self.ctx, g, c, float(t), gi.data_ptr(), out, res.frame.data_ptr(),
                                 res.frame.numel(), res.key_capacity, s)
@@ -237,9 +265,10 @@ class Renderer:
             frame = None
 
     def backward_batch(self, params: dict, res: BatchResult, grad_packed: torch.Tensor, grads: dict,
-                       stream=None) -> None:
+                       stream=None, stats: dict | None = None) -> None:
         """Accumulate dL/dparams (summed over the views) into ``grads`` given
-        dL/d(packed images) of a batched render ``res``."""
+        dL/d(packed images) of a batched render ``res``; ``stats`` as in
+        :meth:`backward` (updated once per view)."""
         g = gaussians_struct(params)
         gp = grad_packed.contiguous()
         if gp.dtype != torch.float32 or gp.numel() != res.packed.numel():
@@ -250,6 +279,7 @@ class Renderer:
             if t_.dtype != torch.float32 or not t_.is_contiguous() or t_.numel() != params[k].numel():
                 raise ValueError(f"grads[{k}] must be a contiguous float32 tensor like the parameter")
             setattr(out, k, t_.data_ptr())
+        _set_stats(out, stats if stats is not None else self.density, params)
         s = (stream or torch.cuda.current_stream(gp.device)).cuda_stream
         abi.r4g_render_batch_backward(self.ctx, g, res.views, gp.data_ptr(), out, res.frame.data_ptr(),
                                       res.frame.numel(), res.key_capacity, s)
@@ -531,3 +561,60 @@ def sort_pairs(keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end
     abi.r4g_sort_pairs(keys.data_ptr(), values.data_ptr(), ko.data_ptr(), vo.data_ptr(), n, begin_bit,
                        end_bit, scratch.data_ptr(), nb, s)
     return ko, vo
+
+
+def densify_config(grad_threshold: float = 2e-4, dense_scale: float = 0.06, split_divisor: float = 1.6,
+                   min_opacity: float = 0.005, max_scale: float = 0.0,
+                   max_screen_radius: float = 0.0) -> abi.r4g_densify_config:
+    """r4g_densify_config; the defaults are the paper's Plenoptic threshold and
+    the 3D Gaussian Splatting rules (dense_scale = 0.01 x a scene extent of 6)."""
+    c = abi.r4g_densify_config()
+    c.grad_threshold, c.dense_scale, c.split_divisor = float(grad_threshold), float(dense_scale), float(split_divisor)
+    c.min_opacity, c.max_scale, c.max_screen_radius = float(min_opacity), float(max_scale), float(max_screen_radius)
+    return c
+
+
+def densify(params: dict, stats: dict, z: torch.Tensor, cfg: abi.r4g_densify_config | None = None):
+    """One densify-and-prune step (r4g_densify_plan + r4g_densify_apply).
+    ``z``: float32 [N, 2, 4] standard normal draws for the split children.
+    Returns (new params dict, int32 [M] source map: i for a row continuing
+    Gaussian i, -(i + 1) for a new row). Reads the row count back to the host
+    to size the outputs."""
+    cfg = cfg or densify_config()
+    g = gaussians_struct(params)
+    dev = params["mean"].device
+    zz = z.contiguous()
+    if zz.dtype != torch.float32 or tuple(zz.shape) != (g.n, 2, 4):
+        raise ValueError("z must be float32 [N, 2, 4]")
+    for k in ("vs_grad", "vs_count"):
+        if k not in stats:
+            raise ValueError(f"stats needs {k}")
+    rad = stats.get("max_radius")
+    nb = abi.r4g_densify_scratch_bytes(g.n)
+    scratch = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    abi.r4g_densify_plan(g, stats["vs_grad"].data_ptr(), stats["vs_count"].data_ptr(),
+                         rad.data_ptr() if rad is not None else None, cfg, scratch.data_ptr(), nb,
+                         count.data_ptr(), s)
+    m = int(count.item())
+    new = {"mean": torch.empty((m, 4), dtype=torch.float32, device=dev),
+           "rotor": torch.empty((m, 8), dtype=torch.float32, device=dev),
+           "logscale": torch.empty((m, 4), dtype=torch.float32, device=dev),
+           "logit": torch.empty((m,), dtype=torch.float32, device=dev),
+           "sh": torch.empty((m, 16, 3), dtype=torch.float32, device=dev)}
+    src = torch.empty(m, dtype=torch.int32, device=dev)
+    out = abi.r4g_params_out()
+    for k in PARAM_NAMES:
+        setattr(out, k, new[k].data_ptr())
+    abi.r4g_densify_apply(g, zz.data_ptr(), cfg, scratch.data_ptr(), nb, out, m, src.data_ptr(), s)
+    return new, src
+
+
+def opacity_reset(params: dict, max_opacity: float = 0.01) -> None:
+    """In place: opacity = min(opacity, max_opacity) (r4g_opacity_reset)."""
+    lg = params["logit"]
+    if lg.dtype != torch.float32 or not lg.is_contiguous() or not lg.is_cuda:
+        raise ValueError("logit must be a contiguous float32 CUDA tensor")
+    abi.r4g_opacity_reset(lg.data_ptr(), int(lg.numel()), float(max_opacity),
+                          torch.cuda.current_stream(lg.device).cuda_stream)

@@ -98,3 +98,38 @@ def test_sort_argument_checks(lib):
     assert lib.r4g_sort_pairs(None, None, None, None, 0, 0, 64, None, 0, None) == abi.R4G_OK
     assert lib.r4g_sort_pairs(256, 512, 1024, 2048, 10, 0, 64, 4096, 1, None) == abi.R4G_EWORKSPACE
     assert lib.r4g_sort_pairs(256, 512, 256, 2048, 10, 0, 64, 4096, 1 << 20, None) == abi.R4G_EINVAL
+
+
+def test_density_argument_checks(lib):
+    from paper_2402_03307_gb300 import abi
+    out = C.c_size_t()
+    assert lib.r4g_densify_scratch_bytes(1000, C.byref(out)) == abi.R4G_OK and out.value >= 5000
+    assert lib.r4g_densify_scratch_bytes(-1, C.byref(out)) == abi.R4G_EINVAL
+    g = abi.r4g_gaussians()
+    g.n = 10
+    g.mean = g.rotor = g.logscale = g.sh = 256
+    g.logit = 256
+    cfg = abi.r4g_densify_config(2e-4, 0.06, 1.6, 0.005, 0.0, 0.0)
+    nb = out.value
+    # each bad configuration field is refused before any launch
+    for field, value in (("grad_threshold", -1.0), ("dense_scale", 0.0), ("split_divisor", 1.0),
+                         ("min_opacity", 1.0), ("max_scale", -1.0), ("max_screen_radius", float("inf"))):
+        bad = abi.r4g_densify_config(2e-4, 0.06, 1.6, 0.005, 0.0, 0.0)
+        setattr(bad, field, value)
+        assert lib.r4g_densify_plan(C.byref(g), 256, 512, None, C.byref(bad), 4096, 1 << 20, 8, None) \
+            == abi.R4G_EINVAL, field
+    # missing statistics, misaligned scratch, undersized scratch, BF16 storage
+    assert lib.r4g_densify_plan(C.byref(g), None, 512, None, C.byref(cfg), 4096, 1 << 20, 8, None) == abi.R4G_EINVAL
+    assert lib.r4g_densify_plan(C.byref(g), 256, 512, None, C.byref(cfg), 4100, 1 << 20, 8, None) == abi.R4G_EINVAL
+    assert lib.r4g_densify_plan(C.byref(g), 256, 512, None, C.byref(cfg), 4096, 16, 8, None) == abi.R4G_EWORKSPACE
+    g.sh_dtype = abi.R4G_BF16
+    assert lib.r4g_densify_plan(C.byref(g), 256, 512, None, C.byref(cfg), 4096, nb, 8, None) == abi.R4G_EINVAL
+    g.sh_dtype = abi.R4G_F32
+    o = abi.r4g_params_out()
+    assert lib.r4g_densify_apply(C.byref(g), 256, C.byref(cfg), 4096, nb, C.byref(o), 5, None, None) \
+        == abi.R4G_EINVAL  # NULL output rows
+    assert lib.r4g_densify_apply(C.byref(g), 256, C.byref(cfg), 4096, nb, C.byref(o), -1, None, None) \
+        == abi.R4G_EINVAL
+    assert lib.r4g_opacity_reset(256, 10, 1.0, None) == abi.R4G_EINVAL
+    assert lib.r4g_opacity_reset(None, 10, 0.01, None) == abi.R4G_EINVAL
+    assert lib.r4g_opacity_reset(None, 0, 0.01, None) == abi.R4G_OK

@@ -1,0 +1,212 @@
+"""Adaptive density control on the GPU (Sec. 4.2: duplication and pruning of
+the 4D Gaussians in CUDA, densification by the view-space positional
+gradient) against the FP64 oracle, through the C ABI.
+
+Statistics: the backward's per-view vs_count (views that composited each
+Gaussian) must equal the oracle's, vs_grad (summed norms of the gradient
+with respect to the projected centre in normalised device coordinates) must
+meet the gradient tolerance (per element 1e-2 (|g| + 1e-3 max|g|) for 99.9%),
+max_radius (3 sqrt(lambda_max(Sigma'))) a relative 1e-4. Upstream gradients
+are zeroed on the oracle's ambiguous pixels, as in the backward tests.
+
+Densify-and-prune: every decision, the row count, the source map and every
+copied value are bit-exact (decisions are exact on both sides); the split
+children's means, FP32 arithmetic against FP64, within 2e-6 (|mean| + the
+length of R diag(s) z)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import ambiguous, to_device
+from oracle import density as od
+
+pytestmark = pytest.mark.gpu
+NAMES = ("mean", "rotor", "logscale", "logit", "sh")
+
+
+@pytest.fixture(scope="module")
+def r4g():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2402_03307_gb300 as m
+    return m
+
+
+def _weights(g, cam, t, seed):
+    ref = oracle.render(oracle.to_f64(g), cam, t)
+    amb = ambiguous(ref, image=False)
+    w = np.random.default_rng(seed).normal(0, 1, (3, cam.height, cam.width))
+    w[:, amb] = 0.0
+    return w.astype(np.float32)
+
+
+def _zero_grads(p):
+    return {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in p.items()}
+
+
+def _compare_stats(got, ref, n):
+    cnt = got["vs_count"]
+    mism = cnt != ref["vs_count"]
+    assert mism.sum() <= max(1, n // 500), int(mism.sum())
+    ok = ~mism
+    assert (cnt > 0).sum() > n // 10
+    a, b = got["vs_grad"][ok], ref["vs_grad"][ok]
+    bad = np.abs(a - b) > 1e-2 * (np.abs(b) + 1e-3 * np.abs(b).max())
+    assert bad.mean() <= 1e-3, (bad.mean(), int(bad.sum()))
+    assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b)
+    ra, rb = got["max_radius"][ok], ref["max_radius"][ok]
+    assert np.all(np.abs(ra - rb) <= 1e-4 * rb + 1e-6)
+
+
+def test_view_statistics_match_the_oracle(r4g):
+    g, cam, t = synth.small_scene(seed=1, n=1000, width=128, height=96)
+    w = _weights(g, cam, t, 3)
+    p = to_device(g)
+    rend = r4g.Renderer()
+    res = rend.render(p, cam, t)
+    grads = _zero_grads(p)
+    stats = r4g.density_stats(1000, "cuda")
+    rend.backward(p, cam, t, res, torch.as_tensor(w).cuda(), grads, stats=stats)
+    got = {k: v.double().cpu().numpy() for k, v in stats.items()}
+    ref = od.view_stats(oracle.to_f64(g), cam, t, w)
+    _compare_stats(got, ref, 1000)
+    # keeping the statistics does not change the gradient (a separately compiled
+    # kernel variant: equal up to the contraction of multiply-adds)
+    grads2 = _zero_grads(p)
+    rend.backward(p, cam, t, res, torch.as_tensor(w).cuda(), grads2)
+    for k in NAMES:
+        a, b = grads[k].double(), grads2[k].double()
+        assert float((a - b).norm()) <= 1e-5 * float(b.norm()), k
+
+
+def test_batched_statistics_sum_the_views(r4g):
+    g = synth.gaussians(800, 5, mean_lo=-1.0, mean_hi=1.0)
+    views = [(synth.look_at((0.0, 0.0, -4.0), (0, 0, 0), 96, 80), np.float32(0.3)),
+             (synth.look_at((3.0, 0.5, -2.5), (0, 0, 0), 64, 72), np.float32(0.6))]
+    ws = [_weights(g, c, t, 10 + k) for k, (c, t) in enumerate(views)]
+    p = to_device(g)
+    rend = r4g.Renderer()
+    res = rend.render_batch(p, views)
+    grads = _zero_grads(p)
+    stats = r4g.density_stats(800, "cuda")
+    gp = torch.cat([torch.as_tensor(w).reshape(-1) for w in ws]).cuda()
+    rend.backward_batch(p, res, gp, grads, stats=stats)
+    got = {k: v.double().cpu().numpy() for k, v in stats.items()}
+    ref = None
+    for (c, t), w in zip(views, ws):
+        ref = od.view_stats(oracle.to_f64(g), c, t, w, ref)
+    assert ref["vs_count"].max() == 2
+    _compare_stats(got, ref, 800)
+
+
+def _gpu_densify(r4g, g, d, cfg):
+    p = to_device(g)
+    z = torch.as_tensor(d["z"]).cuda()
+    stats = {k: torch.as_tensor(d[k]).cuda() for k in ("vs_grad", "vs_count", "max_radius")}
+    out, src = r4g.densify(p, stats, z, r4g.densify_config(**cfg))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}, src.cpu().numpy()
+
+
+def _compare_densify(g, d, out, src, cfg):
+    ref, src_ref = od.densify(g, d["vs_grad"], d["vs_count"], d["max_radius"], d["z"], cfg)
+    assert np.array_equal(src, src_ref)
+    for k in ("rotor", "logscale", "logit", "sh"):
+        assert np.array_equal(out[k], ref[k]), k
+    idx = np.where(src >= 0, src, -src - 1)
+    child = (src < 0) & ~np.all(out["logscale"] == np.asarray(g["logscale"])[idx], axis=1)
+    assert np.array_equal(out["mean"][~child], ref["mean"][~child])
+    if child.any():
+        s = np.exp(np.asarray(g["logscale"], np.float64)[idx[child]])
+        zz = d["z"].reshape(-1, 4)  # a child's draw is z[i, c]
+        mu = np.asarray(g["mean"], np.float64)[idx[child]]
+        bound = 2e-6 * (np.abs(mu).max(axis=1) + np.linalg.norm(s, axis=1) * np.abs(zz).max() + 1.0)
+        err = np.abs(out["mean"][child].astype(np.float64) - ref["mean"][child].astype(np.float64)).max(axis=1)
+        assert np.all(err <= bound), float((err / bound).max())
+    return child.sum(), (src >= 0).sum(), len(src)
+
+
+@pytest.mark.parametrize("n,cfg", [
+    (5003, {}),
+    (4099, {"min_opacity": 0.2, "max_scale": 0.09, "max_screen_radius": 30.0}),
+    (777, {"grad_threshold": 1e-4, "dense_scale": 0.045, "split_divisor": 2.0, "min_opacity": 0.4}),
+])
+def test_densify_matches_the_oracle(r4g, n, cfg):
+    g = synth.gaussians(n, 70 + n % 7)
+    d = synth.density_inputs(80 + n % 5, n)
+    out, src = _gpu_densify(r4g, g, d, cfg)
+    n_child, n_kept, m = _compare_densify(g, d, out, src, cfg)
+    assert n_child > 0 and n_kept > 0 and 0 < m < 2 * n
+
+
+def test_densify_full_size(r4g):
+    """300k Gaussians (the throughput scene's size), every row checked."""
+    n = 300_000
+    g = synth.fwd300k_scene(seed=2, n=n)
+    d = synth.density_inputs(90, n)
+    cfg = {"min_opacity": 0.005, "max_screen_radius": 35.0}
+    out, src = _gpu_densify(r4g, g, d, cfg)
+    n_child, n_kept, m = _compare_densify(g, d, out, src, cfg)
+    assert n_child > 10_000 and m > n
+
+
+def test_densify_edge_cases(r4g):
+    from paper_2402_03307_gb300 import abi
+    # nothing survives: every opacity below the threshold
+    g = synth.gaussians(300, 3)
+    g["logit"][:] = -8.0
+    d = synth.density_inputs(4, 300)
+    out, src = _gpu_densify(r4g, g, d, {"min_opacity": 0.01})
+    assert len(src) == 0 and out["mean"].shape == (0, 4)
+    # no Gaussians at all
+    g0 = {k: v[:0] for k, v in g.items()}
+    d0 = {k: v[:0] for k, v in d.items()}
+    out, src = _gpu_densify(r4g, g0, d0, {})
+    assert len(src) == 0
+    # a capacity below the planned count: rows past it are not written
+    g = synth.gaussians(1000, 6)
+    d = synth.density_inputs(7, 1000)
+    p = to_device(g)
+    cfg = r4g.densify_config()
+    gs = r4g.gaussians_struct(p)
+    nb = abi.r4g_densify_scratch_bytes(1000)
+    scratch = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = {k: torch.as_tensor(d[k]).cuda() for k in ("vs_grad", "vs_count", "max_radius")}
+    s = torch.cuda.current_stream().cuda_stream
+    abi.r4g_densify_plan(gs, st["vs_grad"].data_ptr(), st["vs_count"].data_ptr(), st["max_radius"].data_ptr(),
+                         cfg, scratch.data_ptr(), nb, count.data_ptr(), s)
+    m = int(count.item())
+    cap = m // 2
+    bufs = {"mean": torch.full((m, 4), -7.0, device="cuda"), "rotor": torch.full((m, 8), -7.0, device="cuda"),
+            "logscale": torch.full((m, 4), -7.0, device="cuda"), "logit": torch.full((m,), -7.0, device="cuda"),
+            "sh": torch.full((m, 16, 3), -7.0, device="cuda")}
+    srcb = torch.full((m,), 12345, dtype=torch.int32, device="cuda")
+    o = abi.r4g_params_out()
+    for k in NAMES:
+        setattr(o, k, bufs[k].data_ptr())
+    z = torch.as_tensor(d["z"]).cuda()
+    abi.r4g_densify_apply(gs, z.data_ptr(), cfg, scratch.data_ptr(), nb, o, cap, srcb.data_ptr(), s)
+    torch.cuda.synchronize()
+    ref, src_ref = od.densify(g, d["vs_grad"], d["vs_count"], d["max_radius"], d["z"], {})
+    assert m == len(src_ref)
+    assert np.array_equal(srcb[:cap].cpu().numpy(), src_ref[:cap])
+    assert bool((srcb[cap:] == 12345).all()) and bool((bufs["sh"][cap:] == -7.0).all())
+    # bad arguments are refused on the host
+    bad = r4g.densify_config(split_divisor=1.0)
+    with pytest.raises(abi.R4GError):
+        abi.r4g_densify_plan(gs, st["vs_grad"].data_ptr(), st["vs_count"].data_ptr(), None, bad,
+                             scratch.data_ptr(), nb, count.data_ptr(), s)
+    with pytest.raises(abi.R4GError):
+        abi.r4g_densify_plan(gs, st["vs_grad"].data_ptr(), st["vs_count"].data_ptr(), None, cfg,
+                             scratch.data_ptr(), nb - 256, count.data_ptr(), s)
+
+
+def test_opacity_reset(r4g):
+    g = synth.gaussians(10_001, 8)
+    p = to_device(g)
+    r4g.opacity_reset(p, 0.01)
+    torch.cuda.synchronize()
+    assert np.array_equal(p["logit"].cpu().numpy(), od.opacity_reset(g["logit"], 0.01))
