@@ -195,6 +195,10 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
     const size_t a = onesweep_scratch_bytes(m, 32), b = onesweep_scratch_bytes(cap, tb);
     L.onesweep = o; o = align_up(o + (a > b ? a : b));
   }
+  // multi-view backward: the visible items and their partial gradients (96 B each)
+  const int64_t mi = nviews > 1 ? m : 0;
+  L.ilist = o;    o = align_up(o + sizeof(uint32_t) * mi);
+  L.ipart = o;    o = align_up(o + 96 * static_cast<size_t>(mi));
   L.total = o;
   return L;
 }
@@ -342,7 +346,9 @@ r4g_status backward_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* v
       return cuda_fail(ctx, e, "blend backward");
   }
   {
-    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, 1);
+    // a multi-view FP32 call lists its items, then runs the item and Gaussian passes
+    const bool two_pass = L.nviews > 1 && !(ctx->cfg.flags & R4G_FLAG_FP64_SLICE);
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, two_pass ? 3 : 1);
     if ((e = launch_preprocess_bwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, *grads, s)) != cudaSuccess)
       return cuda_fail(ctx, e, "preprocess backward");
   }

@@ -23,11 +23,14 @@ struct BwdAcc {
 // c, gb.y = d opacity_t; gc = d rgb) through the colour, the conic, the EWA
 // projection and the temporal slice, down to d Sigma4, d mean and d opacity
 // (accumulated in acc) and d SH (added to the SH gradient row).
-template <typename S, bool kShBF16>
+// With kShOut the SH gradient is added into the caller's row gsh; without
+// it the unit view direction and the clamped colour gradient go to dirg[6]
+// (the SH gradient being Y(dir) (x) d rgb, formed later).
+template <typename S, bool kShBF16, bool kShOut = true>
 __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, const Sig4<S>& G, const CamDev& cam,
                                               float t, int sh_degree, bool temporal_cull, float4 ga, float4 gb,
                                               float4 gc, float* __restrict__ gsh, BwdAcc<S>& acc,
-                                              float& radius) {
+                                              float& radius, float* dirg = nullptr) {
   Fwd f;
   S invW, dt;
   view_geometry<S>(G, cam, t, temporal_cull, f, invW, dt);
@@ -40,7 +43,10 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
   float wk[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) wk[k] = shc[k][0] * grgb[0] + shc[k][1] * grgb[1] + shc[k][2] * grgb[2];
-  {
+  if constexpr (!kShOut) {
+    dirg[0] = f.dir[0]; dirg[1] = f.dir[1]; dirg[2] = f.dir[2];
+    dirg[3] = grgb[0]; dirg[4] = grgb[1]; dirg[5] = grgb[2];
+  } else {
     // d c_k = Y_k d rgb, accumulated as 16-byte vectors over the 48-float row
     float4* gsh4 = reinterpret_cast<float4*>(gsh + static_cast<size_t>(i) * 48);
     const int nvec = (nb * 3 + 3) / 4;
@@ -196,6 +202,52 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
   acc.gop += g_o;
 }
 
+// Sum of an item's per-pair gradients (pairs [o, o + cnt) of the gradient
+// buffer) for each lane's item: the warp walks its lanes' items in turn,
+// lane l adding pairs l, l + 32, ... (coalesced), then a butterfly sum; a
+// single pair is read by its owner. gc.w counts the tiles in which a pixel
+// composited the item (summed only with kStats).
+template <bool kStats>
+__device__ __forceinline__ void gather_pairs(uint32_t cnt, uint32_t o, int lane, const float4* __restrict__ gbuf,
+                                             float4& ga, float4& gb, float4& gc) {
+  ga = make_float4(0.f, 0.f, 0.f, 0.f);
+  gb = ga;
+  gc = ga;
+  for (int q = 0; q < 32; ++q) {
+    const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
+    if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
+    const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
+    float v9[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t k = lane; k < qc; k += 32) {
+      const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
+      const float4 x = pr[0], y = pr[1], z = pr[2];
+      v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
+      v9[4] += y.x; v9[5] += y.y;
+      v9[6] += z.x; v9[7] += z.y; v9[8] += z.z; v9[9] += z.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], sh);
+    }
+    if constexpr (kStats) {
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) v9[9] += __shfl_xor_sync(0xffffffffu, v9[9], sh);
+    }
+    if (lane == q) {
+      ga = make_float4(v9[0], v9[1], v9[2], v9[3]);
+      gb = make_float4(v9[4], v9[5], 0.f, 0.f);
+      gc = make_float4(v9[6], v9[7], v9[8], v9[9]);
+    }
+  }
+  if (cnt == 1) {
+    const float4* pr = gbuf + 3 * static_cast<size_t>(o);
+    ga = pr[0];
+    gb = pr[1];
+    gc = pr[2];
+  }
+}
+
 // Backward of the preprocess over the Gaussians visible in some view (the
 // list the forward built). For each view, each warp first sums, for each of
 // its 32 Gaussians in turn, the per-pair gradients the blend backward wrote
@@ -230,42 +282,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     const uint32_t cnt = mine ? touched[item] : 0u;
     if (__ballot_sync(0xffffffffu, cnt != 0u) == 0u) continue;
     const uint32_t o = cnt ? ioffs[item] : 0u;
-    // warp-cooperative gather of the pair gradients: lane l adds pairs l, l+32, ...
-    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
-    for (int q = 0; q < 32; ++q) {
-      const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
-      if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
-      const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
-      // v9[9]: tiles in which a pixel composited the item (the blend backward's flag)
-      float v9[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (uint32_t k = lane; k < qc; k += 32) {
-        const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
-        const float4 x = pr[0], y = pr[1], z = pr[2];
-        v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
-        v9[4] += y.x; v9[5] += y.y;
-        v9[6] += z.x; v9[7] += z.y; v9[8] += z.z; v9[9] += z.w;
-      }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], sh);
-      }
-      if constexpr (kStats) {
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v9[9] += __shfl_xor_sync(0xffffffffu, v9[9], sh);
-      }
-      if (lane == q) {
-        ga = make_float4(v9[0], v9[1], v9[2], v9[3]);
-        gb = make_float4(v9[4], v9[5], 0.f, 0.f);
-        gc = make_float4(v9[6], v9[7], v9[8], v9[9]);
-      }
-    }
-    if (cnt == 1) {
-      const float4* pr = gbuf + 3 * static_cast<size_t>(o);
-      ga = pr[0];
-      gb = pr[1];
-      gc = pr[2];
-    }
+    float4 ga, gb, gc;
+    gather_pairs<kStats>(cnt, o, lane, gbuf, ga, gb, gc);
     if (cnt) {
       float radius;
       view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc, out.sh,
@@ -323,13 +341,186 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
   out.logit[i] += static_cast<float>(acc.gop) * G.opacity * (1.0f - G.opacity);
 }
 
+// ---- multi-view backward in two passes -------------------------------------
+// With several views, a thread per Gaussian would idle in every view that does
+// not see its Gaussian. Instead: (1) the visible (view, Gaussian) items are
+// listed, (2) one thread per listed item runs that view's backward and keeps a
+// partial gradient (96 B), (3) one thread per Gaussian sums its items'
+// partials in view order (deterministic) and runs the Sigma4 -> rotor and
+// scale backward once.
+constexpr int kPartFloats = 24;  // d Sigma4 (10), d mean (4), d opacity, dir (3), d rgb (3), statistics (3)
+
+__global__ void __launch_bounds__(256)
+    list_items_kernel(const uint32_t* __restrict__ touched, uint32_t m, uint32_t* __restrict__ ilist,
+                      FrameHeader* hdr) {
+  const uint32_t k = blockIdx.x * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool vis = k < m && touched[k] != 0u;
+  const uint32_t b = __ballot_sync(0xffffffffu, vis);
+  if (!b) return;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(&hdr->n_ilist, static_cast<uint32_t>(__popc(b)));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (vis) ilist[base + __popc(b & ((1u << lane) - 1u))] = k;
+}
+
+template <bool kScaleBF16, bool kShBF16, bool kStats>
+__global__ void __launch_bounds__(kBwdBlock, 4)
+    preprocess_bwd_items_kernel(r4g_gaussians g, const ViewDev* __restrict__ views,
+                                const uint32_t* __restrict__ ilist, const uint32_t* __restrict__ ioffs,
+                                const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
+                                const FrameHeader* hdr, int sh_degree, bool temporal_cull,
+                                float4* __restrict__ ipart) {
+  const int j = blockIdx.x * kBwdBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int nlist = static_cast<int>(hdr->n_ilist);
+  if ((hdr->status & 1u) || (j - lane) >= nlist) return;  // warp-uniform
+  const bool mine = j < nlist;
+  const uint32_t item = mine ? ilist[j] : 0u;
+  const uint32_t cnt = mine ? touched[item] : 0u;
+  const uint32_t o = cnt ? ioffs[item] : 0u;
+  float4 ga, gb, gc;
+  gather_pairs<kStats>(cnt, o, lane, gbuf, ga, gb, gc);
+  if (!mine) return;
+  const int v = static_cast<int>(item / static_cast<uint32_t>(g.n));
+  const int i = static_cast<int>(item - static_cast<uint32_t>(v) * static_cast<uint32_t>(g.n));
+  Sig4<float> Q;
+  gauss_sigma<float, kScaleBF16>(g, i, Q);
+  BwdAcc<float> acc;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc.G4[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc.gmean[k] = 0.0f;
+  acc.gop = 0.0f;
+  float radius, dirg[6];
+  view_backward<float, kShBF16, false>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc,
+                                       nullptr, acc, radius, dirg);
+  float st[3] = {0.0f, 0.0f, 0.0f};
+  if (kStats && gc.w > 0.0f) {  // composited into a pixel of this view
+    const float ux = ga.x * (0.5f * static_cast<float>(views[v].cam.width));
+    const float uy = ga.y * (0.5f * static_cast<float>(views[v].cam.height));
+    st[0] = sqrtf(ux * ux + uy * uy);
+    st[1] = 1.0f;
+    st[2] = radius;
+  }
+  float4* d = ipart + 6 * static_cast<size_t>(item);
+  d[0] = make_float4(acc.G4[0], acc.G4[1], acc.G4[2], acc.G4[3]);
+  d[1] = make_float4(acc.G4[4], acc.G4[5], acc.G4[6], acc.G4[7]);
+  d[2] = make_float4(acc.G4[8], acc.G4[9], acc.gmean[0], acc.gmean[1]);
+  d[3] = make_float4(acc.gmean[2], acc.gmean[3], acc.gop, dirg[0]);
+  d[4] = make_float4(dirg[1], dirg[2], dirg[3], dirg[4]);
+  d[5] = make_float4(dirg[5], st[0], st[1], st[2]);
+}
+
+template <bool kScaleBF16, bool kStats>
+__global__ void __launch_bounds__(kBwdBlock)
+    preprocess_bwd_gauss_kernel(r4g_gaussians g, int nviews, const uint32_t* __restrict__ glist,
+                                const uint32_t* __restrict__ touched, const float4* __restrict__ ipart,
+                                const FrameHeader* hdr, int sh_degree, r4g_grads out) {
+  const int j = blockIdx.x * kBwdBlock + threadIdx.x;
+  const int nlist = static_cast<int>(hdr->n_glist);
+  if ((hdr->status & 1u) || j >= nlist) return;
+  const int i = static_cast<int>(glist[j]);
+  float G4s[10], gm[4], gop = 0.0f, vs_grad = 0.0f, vs_count = 0.0f, max_radius = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 10; ++k) G4s[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gm[k] = 0.0f;
+  const int nb = (sh_degree + 1) * (sh_degree + 1);
+  float4* gsh4 = reinterpret_cast<float4*>(out.sh + static_cast<size_t>(i) * 48);
+  for (int v = 0; v < nviews; ++v) {
+    const size_t item = static_cast<size_t>(v) * g.n + i;
+    if (touched[item] == 0u) continue;
+    const float4* p = ipart + 6 * item;
+    const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4], f = p[5];
+    G4s[0] += a.x; G4s[1] += a.y; G4s[2] += a.z; G4s[3] += a.w;
+    G4s[4] += b.x; G4s[5] += b.y; G4s[6] += b.z; G4s[7] += b.w;
+    G4s[8] += c.x; G4s[9] += c.y; gm[0] += c.z; gm[1] += c.w;
+    gm[2] += d.x; gm[3] += d.y; gop += d.z;
+    const float grgb[3] = {e.z, e.w, f.x};
+    float Y[16];
+    sh_basis(d.w, e.x, e.y, Y);
+    // d c_k += Y_k d rgb over the row's 16-byte vectors
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      if (4 * q < nb * 3) {
+        float4 w = gsh4[q];
+        float* wp = reinterpret_cast<float*>(&w);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int el = 4 * q + h;
+          if (el < nb * 3) wp[h] += Y[el / 3] * grgb[el % 3];
+        }
+        gsh4[q] = w;
+      }
+    }
+    if constexpr (kStats) {
+      vs_grad += f.y;
+      vs_count += f.z;
+      max_radius = fmaxf(max_radius, f.w);
+    }
+  }
+  Geo<float> G;
+  gauss_setup<float, kScaleBF16>(g, i, G);
+  float G4[4][4];
+  G4[0][0] = G4s[0]; G4[0][1] = G4[1][0] = G4s[1]; G4[0][2] = G4[2][0] = G4s[2];
+  G4[0][3] = G4[3][0] = G4s[3]; G4[1][1] = G4s[4]; G4[1][2] = G4[2][1] = G4s[5];
+  G4[1][3] = G4[3][1] = G4s[6]; G4[2][2] = G4s[7]; G4[2][3] = G4[3][2] = G4s[8];
+  G4[3][3] = G4s[9];
+  float grot[8], gls[4];
+  sigma4_backward<float>(G, G4, grot, gls);
+  float4* gmo = reinterpret_cast<float4*>(out.mean) + i;
+  float4 vm = *gmo;
+  vm.x += gm[0]; vm.y += gm[1]; vm.z += gm[2]; vm.w += gm[3];
+  *gmo = vm;
+  float4* gr = reinterpret_cast<float4*>(out.rotor) + 2 * static_cast<size_t>(i);
+  float4 r0 = gr[0], r1 = gr[1];
+  r0.x += grot[0]; r0.y += grot[1]; r0.z += grot[2]; r0.w += grot[3];
+  r1.x += grot[4]; r1.y += grot[5]; r1.z += grot[6]; r1.w += grot[7];
+  gr[0] = r0;
+  gr[1] = r1;
+  float4* gl = reinterpret_cast<float4*>(out.logscale) + i;
+  float4 vl = *gl;
+  vl.x += gls[0]; vl.y += gls[1]; vl.z += gls[2]; vl.w += gls[3];
+  *gl = vl;
+  out.logit[i] += gop * G.opacity * (1.0f - G.opacity);
+  if (kStats && vs_count > 0.0f) {
+    if (out.vs_grad) out.vs_grad[i] += vs_grad;
+    if (out.vs_count) out.vs_count[i] += vs_count;
+    if (out.max_radius) out.max_radius[i] = fmaxf(out.max_radius[i], max_radius);
+  }
+}
+
 template <typename S, bool A, bool B>
 static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree, bool tc,
                              const r4g_grads& out, cudaStream_t s) {
   const int nb = static_cast<int>((L.n + kBwdBlock - 1) / kBwdBlock);
+  if constexpr (sizeof(S) == sizeof(float)) {
+    if (L.nviews > 1) {  // the two-pass multi-view backward (FP32 slice)
+      const bool stats = out.vs_grad || out.vs_count || out.max_radius;
+      FrameHeader* hdr = at<FrameHeader>(frame, L.header);
+      const uint32_t* touched = at<uint32_t>(frame, L.touched);
+      uint32_t* ilist = at<uint32_t>(frame, L.ilist);
+      float4* ipart = at<float4>(frame, L.ipart);
+      cudaMemsetAsync(&hdr->n_ilist, 0, sizeof(uint32_t), s);
+      const int nbm = static_cast<int>((L.m + 255) / 256);
+      list_items_kernel<<<nbm, 256, 0, s>>>(touched, static_cast<uint32_t>(L.m), ilist, hdr);
+      const int nbi = static_cast<int>((L.m + kBwdBlock - 1) / kBwdBlock);
+      auto ki = stats ? preprocess_bwd_items_kernel<A, B, true> : preprocess_bwd_items_kernel<A, B, false>;
+      ki<<<nbi, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), ilist, at<uint32_t>(frame, L.ioffs), touched,
+                                   at<float4>(frame, L.gbuf), hdr, sh_degree, tc, ipart);
+      auto kg = stats ? preprocess_bwd_gauss_kernel<A, true> : preprocess_bwd_gauss_kernel<A, false>;
+      kg<<<nb, kBwdBlock, 0, s>>>(g, L.nviews, at<uint32_t>(frame, L.glist), touched, ipart, hdr, sh_degree, out);
+      return;
+    }
+  }
   const bool stats = out.vs_grad || out.vs_count || out.max_radius;
-  auto k = L.nviews > 1 ? (stats ? preprocess_bwd_kernel<S, A, B, true, true> : preprocess_bwd_kernel<S, A, B, true, false>)
-                        : (stats ? preprocess_bwd_kernel<S, A, B, false, true> : preprocess_bwd_kernel<S, A, B, false, false>);
+  // one thread per Gaussian over the views: every one-view call, and
+  // multi-view calls of the FP64 debug slice
+  auto k = stats ? preprocess_bwd_kernel<S, A, B, false, true> : preprocess_bwd_kernel<S, A, B, false, false>;
+  if constexpr (sizeof(S) != sizeof(float)) {
+    if (L.nviews > 1) k = stats ? preprocess_bwd_kernel<S, A, B, true, true> : preprocess_bwd_kernel<S, A, B, true, false>;
+  }
   k<<<nb, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist),
                              at<uint32_t>(frame, L.ioffs), at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf),
                              at<FrameHeader>(frame, L.header), sh_degree, tc, out);

@@ -60,7 +60,8 @@ struct FrameHeader {
   uint32_t n_glist;       // Gaussians visible in at least one view (the backward's work list)
   uint32_t next_tile;     // work counter of the persistent blend
   uint32_t next_tile_bwd; // work counter of the persistent blend backward
-  uint32_t pad[55];
+  uint32_t n_ilist;       // visible (view, Gaussian) items listed for a multi-view backward
+  uint32_t pad[54];
   uint32_t view_pairs[kMaxViews];  // (tile, Gaussian) pairs per view
 };
 static_assert(sizeof(FrameHeader) == 512, "frame header size");
@@ -68,7 +69,8 @@ static_assert(sizeof(FrameHeader) == 512, "frame header size");
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
   size_t header, views, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, ioffs, srect, chunks,
-      blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, ranges, tfinal, last, sortcnt, onesweep, total;
+      blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, ranges, tfinal, last, sortcnt, onesweep, ilist,
+      ipart, total;
   int64_t n, cap;
   int64_t m;         // items: n * nviews
   int nviews;
