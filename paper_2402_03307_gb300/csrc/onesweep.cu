@@ -4,18 +4,23 @@
 // once; each pass is then a single kernel in which a CTA
 //   1. takes the next tile of 2048 items from an atomic ticket (so every tile
 //      before it belongs to a CTA that is already running),
-//   2. ranks its items stably by the pass's digit (warp match + per-warp
+//   2. ranks its items stably by the pass's digit (the lanes holding the
+//      same digit found by one warp ballot per digit bit, per-warp
 //      histograms), publishes its per-digit counts,
 //   3. looks back over the tiles before it, summing their published counts
 //      until it meets a tile that has published its inclusive prefix, and
 //      publishes its own prefix,
 //   4. scatters its items, staged in shared memory in digit order, to
 //      digit start + prefix + local rank.
-// The look-back only waits on tiles that publish their counts before they
-// wait themselves; each wait is bounded by an iteration limit after which the
-// CTA sets an error bit in the frame header, treats the tile as empty and
-// carries on (the image is then wrong and the status reports it, but nothing
-// hangs). Counts and values are limited to 2^30.
+// The look-back reads a window of 4 predecessors per round and backs off
+// (32 ns doubling to 256 ns) after a round without progress: wider windows
+// and tight polling measured slower, the statuses' cache lines being shared
+// by every waiting CTA. It only waits on tiles that publish their counts
+// before they wait themselves; each wait is bounded by an iteration limit
+// after which the CTA sets an error bit in the frame header, treats the tile
+// as empty and carries on (the image is then wrong and the status reports it,
+// but nothing hangs). Counts and values are limited to 2^30. A launch sized
+// for the key capacity has more CTAs than tiles; the surplus leaves at once.
 #include <cuda_runtime.h>
 
 #include "r4g_internal.cuh"
@@ -28,7 +33,7 @@ constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kOsIPT = 8;                           // items per thread
 constexpr int kOsTile = kSortThreads * kOsIPT;      // 2048 items per tile
-constexpr int kOsWin = 8;                           // predecessors read per look-back round
+constexpr int kOsWin = 4;                           // predecessors read per look-back round
 constexpr int kOsHistCtas = 2 * 152;
 
 __device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) {
@@ -99,6 +104,10 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ uint32_t s_v[kOsTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  {
+    const uint32_t nn = count_dev ? *count_dev : count_host;
+    if (static_cast<uint64_t>(blockIdx.x) * kOsTile >= nn) return;  // more CTAs than tiles: leave at once
+  }
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   for (int k = threadIdx.x; k < NW * kSortRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
   __syncthreads();
@@ -129,8 +138,14 @@ __global__ void __launch_bounds__(kSortThreads)
     const bool ok = d[j] != 0xffffffffu;
     const uint32_t act = __ballot_sync(0xffffffffu, ok);
     rk[j] = 0;
+    uint32_t peers = act;
+#pragma unroll
+    for (int b = 0; b < kSortRadixBits; ++b) {
+      const uint32_t bit = (d[j] >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
     if (ok) {
-      const uint32_t peers = __match_any_sync(act, d[j]);
       const uint32_t base = s_whist[warp][d[j]];
       __syncwarp(act);
       if (lane == __ffs(peers) - 1) s_whist[warp][d[j]] = base + __popc(peers);
@@ -163,7 +178,7 @@ __global__ void __launch_bounds__(kSortThreads)
   if (t > 0) {
     constexpr int WIN = kOsWin;
     int64_t kt = static_cast<int64_t>(t) - 1;
-    uint32_t idle = 0;
+    uint32_t idle = 0, nap = 32u;
     bool found = false;
     while (!found && kt >= 0) {
       uint32_t sv[WIN];
@@ -180,9 +195,13 @@ __global__ void __launch_bounds__(kSortThreads)
         if (sv[w] & kFlagPrefix) found = true;
       }
       kt -= used;
-      if (used == 0 && ++idle >= kSpinLimit) {  // gave up: record it and go on
-        atomicOr(err, 2u);
-        break;
+      if (used == 0) {
+        if (++idle >= kSpinLimit) {  // gave up: record it and go on
+          atomicOr(err, 2u);
+          break;
+        }
+        __nanosleep(nap);
+        nap = nap < 256u ? 2u * nap : 256u;
       }
     }
     store_relaxed(st + dd, kFlagPrefix | (excl + cnt));
