@@ -169,6 +169,15 @@ r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t
 r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
                             int64_t* keys_needed, void* stream);
 
+/* The same status without waiting: enqueues on `stream` a copy of the
+ * frame's three status words into host_out (HOST memory, uint32 [3]; pinned
+ * memory makes the copy asynchronous). Once the stream has passed that point
+ * (an event, a synchronisation), r4g_frame_status_decode turns the words into
+ * the r4g_frame_status result and *keys_needed (may be NULL). Lets a training
+ * step check a render's key capacity without stalling the stream. */
+r4g_status r4g_frame_status_async(const void* frame, size_t frame_bytes, uint32_t* host_out, void* stream);
+r4g_status r4g_frame_status_decode(const uint32_t* words /* host [3] */, int64_t* keys_needed);
+
 /* Statistics of the last render into a frame (waits for `stream`). */
 typedef struct r4g_frame_info {
   int64_t n_visible;         /* (view, Gaussian) items with at least one tile */

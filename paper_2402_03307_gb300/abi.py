@@ -77,6 +77,8 @@ SIGNATURES = [
     ("r4g_frame_bytes", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int64,
                                   C.POINTER(C.c_size_t)]),
     ("r4g_frame_status", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int64), C.c_void_p]),
+    ("r4g_frame_status_async", C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    ("r4g_frame_status_decode", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("r4g_frame_stats", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(r4g_frame_info), C.c_void_p]),
     ("r4g_frame_export", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int64, C.c_int32, C.c_int32,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -189,6 +191,18 @@ def r4g_frame_status(ctx, frame: int, frame_bytes: int, stream: int) -> tuple[in
     st = lib().r4g_frame_status(ctx, frame, frame_bytes, C.byref(need), stream)
     if st not in (R4G_OK, R4G_EOVERFLOW):
         check(st, ctx)
+    return st, need.value
+
+
+def r4g_frame_status_async(frame: int, frame_bytes: int, host_out: int, stream: int) -> None:
+    check(lib().r4g_frame_status_async(frame, frame_bytes, host_out, stream))
+
+
+def r4g_frame_status_decode(words: int) -> tuple[int, int]:
+    need = C.c_int64()
+    st = lib().r4g_frame_status_decode(words, C.byref(need))
+    if st not in (R4G_OK, R4G_EOVERFLOW, R4G_ETIMEOUT, R4G_EDEVICE):
+        check(st)
     return st, need.value
 
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -450,6 +451,27 @@ r4g_status r4g_frame_status(r4g_ctx* ctx, const void* frame, size_t frame_bytes,
   if (h.status & 1u) return fail(ctx, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
   if (h.status & 2u) return fail(ctx, R4G_ETIMEOUT, "a radix-sort look-back wait hit its iteration limit");
   if (h.status & 4u) return fail(ctx, R4G_EDEVICE, "device views differ in image size from the host views");
+  return R4G_OK;
+}
+
+r4g_status r4g_frame_status_async(const void* frame, size_t frame_bytes, uint32_t* host_out, void* stream) {
+  if (!frame || !host_out) return fail(nullptr, R4G_EINVAL, "NULL argument");
+  if (frame_bytes < sizeof(FrameHeader)) return fail(nullptr, R4G_EWORKSPACE, "frame too small");
+  static_assert(offsetof(FrameHeader, status) == 0 && offsetof(FrameHeader, key_count) == 4 &&
+                    offsetof(FrameHeader, key_needed) == 8,
+                "the status words lead the frame header");
+  const cudaError_t e = cudaMemcpyAsync(host_out, frame, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "r4g_frame_status_async");
+  return R4G_OK;
+}
+
+r4g_status r4g_frame_status_decode(const uint32_t* words, int64_t* keys_needed) {
+  if (!words) return fail(nullptr, R4G_EINVAL, "NULL argument");
+  if (keys_needed) *keys_needed = words[2];
+  if (words[0] & 1u) return fail(nullptr, R4G_EOVERFLOW, "key capacity exceeded: re-render with a larger frame");
+  if (words[0] & 2u) return fail(nullptr, R4G_ETIMEOUT, "a radix-sort look-back wait hit its iteration limit");
+  if (words[0] & 4u) return fail(nullptr, R4G_EDEVICE, "device views differ in image size from the host views");
   return R4G_OK;
 }
 

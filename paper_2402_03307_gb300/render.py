@@ -90,6 +90,23 @@ class BatchResult:
     n: int
 
 
+class PendingStatus:
+    """A render's status words on their way to pinned host memory
+    (r4g_frame_status_async) and the event after which they are there."""
+
+    def __init__(self, res, stream, key):
+        self.key = key  # the renderer's capacity-hint key of the render
+        self.words = torch.zeros(3, dtype=torch.int32, pin_memory=True)
+        abi.r4g_frame_status_async(res.frame.data_ptr(), res.frame.numel(), self.words.data_ptr(), stream.cuda_stream)
+        self.event = torch.cuda.Event()
+        self.event.record(stream)
+
+    def result(self) -> tuple[int, int]:
+        """(status, keys_needed); waits for the event only."""
+        self.event.synchronize()
+        return abi.r4g_frame_status_decode(self.words.data_ptr())
+
+
 def _packed_views(packed: torch.Tensor, structs) -> list:
     out, off = [], 0
     for v in structs:
@@ -189,6 +206,47 @@ class Renderer:
             cap = int(need * 1.25) + 1024
             self._cap_hint[(g.n, c.width, c.height)] = cap
             frame = None
+
+    # ---- deferred status checks (training steps) --------------------------------
+    # The first render of a given size waits for its status (and grows the key
+    # buffer until it fits, remembering the size); later ones only enqueue the
+    # status copy, and settle() -- called by the backward, when the stream is
+    # long past the render -- raises if the key buffer overflowed after all
+    # (the capacity hint has then grown, so repeating the step succeeds).
+    def render_deferred(self, params: dict, cam, t: float, stream=None):
+        g = gaussians_struct(params)
+        c = camera_struct(cam)
+        st = stream or torch.cuda.current_stream(params["mean"].device)
+        if (g.n, c.width, c.height) not in self._cap_hint:
+            res = self.render(params, cam, t, stream=st)
+            self._cap_hint.setdefault((g.n, c.width, c.height), res.key_capacity)
+            return res, None
+        res = self.render(params, cam, t, check=False, stream=st)
+        return res, PendingStatus(res, st, (g.n, c.width, c.height))
+
+    def render_batch_deferred(self, params: dict, views, stream=None):
+        vs = self.view_structs(views)
+        st = stream or torch.cuda.current_stream(params["mean"].device)
+        key = (int(params["mean"].shape[0]), tuple((v.cam.width, v.cam.height) for v in vs), self.tile)
+        if key not in self._cap_hint:
+            res = self.render_batch(params, vs, stream=st)
+            self._cap_hint.setdefault(key, res.key_capacity)
+            return res, None
+        res = self.render_batch(params, vs, check=False, stream=st)
+        return res, PendingStatus(res, st, key)
+
+    def settle(self, pending: "PendingStatus | None", res) -> None:
+        """Raise if a deferred render's frame reports an error."""
+        if pending is None:
+            return
+        status, need = pending.result()
+        if status == abi.R4G_OK:
+            return
+        if status == abi.R4G_EOVERFLOW:
+            self._cap_hint[pending.key] = int(need * 1.25) + 1024
+            raise abi.R4GError(status, f"the render needed {need} (tile, Gaussian) pairs, more than its key "
+                                       f"capacity {res.key_capacity}; the capacity has grown, repeat the step")
+        raise abi.R4GError(status, "the render's frame reports an error")
 
     def stats(self, res: RenderResult, stream=None) -> dict:
         """n_visible, key_count, key_needed, composited_pairs (-1 unless the
@@ -341,7 +399,7 @@ class Render4DFunction(torch.autograd.Function):
     def forward(ctx, mean, rotor, logscale, logit, sh, renderer: Renderer, cam, t: float):
         params = {"mean": mean.detach(), "rotor": rotor.detach(), "logscale": logscale.detach(),
                   "logit": logit.detach(), "sh": sh.detach()}
-        res = renderer.render(params, cam, t)
+        res, ctx.pending = renderer.render_deferred(params, cam, t)
         ctx.renderer, ctx.cam, ctx.t, ctx.res = renderer, cam, t, res
         ctx.save_for_backward(mean, rotor, logscale, logit, sh)
         return res.image
@@ -349,6 +407,7 @@ class Render4DFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_image):
         mean, rotor, logscale, logit, sh = ctx.saved_tensors
+        ctx.renderer.settle(ctx.pending, ctx.res)
         params = {"mean": mean, "rotor": rotor, "logscale": logscale, "logit": logit, "sh": sh}
         grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=v.device) for k, v in params.items()}
         ctx.renderer.backward(params, ctx.cam, ctx.t, ctx.res, grad_image.float(), grads)
@@ -364,7 +423,7 @@ class Render4DBatchFunction(torch.autograd.Function):
     def forward(ctx, mean, rotor, logscale, logit, sh, renderer: Renderer, views):
         params = {"mean": mean.detach(), "rotor": rotor.detach(), "logscale": logscale.detach(),
                   "logit": logit.detach(), "sh": sh.detach()}
-        res = renderer.render_batch(params, views)
+        res, ctx.pending = renderer.render_batch_deferred(params, views)
         ctx.renderer, ctx.res = renderer, res
         ctx.save_for_backward(mean, rotor, logscale, logit, sh)
         return res.packed
@@ -372,6 +431,7 @@ class Render4DBatchFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_packed):
         mean, rotor, logscale, logit, sh = ctx.saved_tensors
+        ctx.renderer.settle(ctx.pending, ctx.res)
         params = {"mean": mean, "rotor": rotor, "logscale": logscale, "logit": logit, "sh": sh}
         grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=v.device) for k, v in params.items()}
         ctx.renderer.backward_batch(params, ctx.res, grad_packed.float(), grads)

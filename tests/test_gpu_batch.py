@@ -187,6 +187,44 @@ def test_batch_overflow_retry(r4g):
     assert torch.equal(res.packed, rend.render_batch(p, views).packed)
 
 
+def test_autograd_deferred_status(r4g):
+    """The autograd functions check a render's key capacity without stalling:
+    the first render of a size waits (and sizes the key buffer), later ones
+    are checked by the backward, which raises on an overflow and grows the
+    capacity so that the repeated step succeeds."""
+    g, cam, t = synth.small_scene(seed=49)
+    p = to_device(g)
+    views = _uneven_views(12, SIZES[:3])
+    rend = r4g.Renderer()
+    leaves = {k: v.clone().requires_grad_(True) for k, v in p.items()}
+    for _ in range(2):  # checked on the first call, deferred on the second
+        r4g.render_batch(leaves, views, renderer=rend).sum().backward()
+    key = next(k for k in rend._cap_hint if isinstance(k[1], tuple))
+    rend._cap_hint[key] = 64  # too small for this scene
+    for v in leaves.values():
+        v.grad = None
+    with pytest.raises(r4g.abi.R4GError) as e:
+        r4g.render_batch(leaves, views, renderer=rend).sum().backward()
+    assert e.value.status == r4g.abi.R4G_EOVERFLOW and rend._cap_hint[key] > 64
+    for v in leaves.values():
+        v.grad = None
+    packed = r4g.render_batch(leaves, views, renderer=rend)
+    assert torch.equal(packed.detach(), rend.render_batch(p, views).packed)
+    packed.sum().backward()
+    ref = _zeros_like(p)
+    rend.backward_batch(p, rend.render_batch(p, views), torch.ones_like(packed), ref)
+    for k in NAMES:
+        assert torch.equal(leaves[k].grad, ref[k]), k
+    # the single-view function the same way
+    one = r4g.Renderer()
+    img = r4g.render(leaves, cam, t, renderer=one)
+    img.sum().backward()
+    one._cap_hint[(1000, cam.width, cam.height)] = 64
+    with pytest.raises(r4g.abi.R4GError):
+        r4g.render(leaves, cam, t, renderer=one).sum().backward()
+    r4g.render(leaves, cam, t, renderer=one).sum().backward()
+
+
 def test_batch_limits_and_device_view_mismatch(r4g):
     g, _, _ = synth.small_scene(seed=48)
     p = to_device(g)
