@@ -1,8 +1,10 @@
 // Tiled front-to-back alpha compositing (Sec. 3.1, Eq. 3) and its backward.
 //
-// Persistent CTAs take tiles; each thread owns two horizontally adjacent
-// pixels and evaluates them together with Blackwell's packed FP32x2
-// instructions. Each warp owns an 8x8 block of the tile. Batches of screen
+// Persistent CTAs take tiles; each thread owns Q packed pairs of
+// horizontally adjacent pixels (Q = 2 for tiles 16 wide, 1 for 8x8 tiles)
+// and evaluates them with Blackwell's packed FP32x2 instructions; a
+// Gaussian's per-row terms are computed once for all of the thread's pixels.
+// Each warp owns a (8 Q) x 8 block of the tile. Batches of screen
 // records are staged in shared memory with every operand already duplicated
 // into the (x, x) pairs the packed instructions take. While staging, each Gaussian gets one bit per warp
 // telling whether its contributing ellipse can reach a pixel centre of that
@@ -39,18 +41,22 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Each warp owns an 8x8 pixel block of the tile (4 threads x 2 pixels
-// across, 8 rows): of the block shapes of 64 pixels the square one meets the
-// fewest ellipses that only graze it.
+// Each warp owns a block of 8 rows, 4 threads across, each thread Q packed
+// pairs: 8x8 pixels with Q = 1, 16x8 with Q = 2. Two pairs per thread share
+// the Gaussian's per-row terms and its staged operands and halve the warp
+// reductions of the backward per pixel; the wider block costs a few more
+// Gaussians that only graze it.
 template <int TW, int TH>
 struct Blend {
-  static constexpr int NT = TW * TH / 2;     // threads per CTA
-  static constexpr int NW = NT / 32;         // warps per CTA
-  static constexpr int WX = TW / 8;          // warp blocks across the tile
-  static constexpr int PCOLS = 4;            // thread columns of a warp block
-  static constexpr int WROWS = 8;            // pixel rows of a warp block
-  static_assert(TW % 8 == 0 && TH % 8 == 0 && NW <= 16, "tile shape");
-  __device__ static int px0(int tx, int warp) { return tx * TW + (warp % WX) * 8; }
+  static constexpr int Q = TW % 16 == 0 ? 2 : 1;  // packed pixel pairs per thread
+  static constexpr int BW = 8 * Q;                // warp block width
+  static constexpr int NT = TW * TH / (2 * Q);    // threads per CTA
+  static constexpr int NW = NT / 32;              // warps per CTA
+  static constexpr int WX = TW / BW;              // warp blocks across the tile
+  static constexpr int PCOLS = 4;                 // thread columns of a warp block
+  static constexpr int WROWS = 8;                 // pixel rows of a warp block
+  static_assert(TW % BW == 0 && TH % 8 == 0 && NW >= 1 && NW <= 16, "tile shape");
+  __device__ static int px0(int tx, int warp) { return tx * TW + (warp % WX) * BW; }
   __device__ static int py0(int ty, int warp) { return ty * TH + (warp / WX) * 8; }
 };
 
@@ -109,8 +115,8 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   const float ih = 1.0f / half, nm = -mid * ih;
   uint32_t m = o > kAlphaMax ? kClampBit : 0u;
 #pragma unroll
-  for (int w = 0; w < B::NW; ++w) {  // pixel centres of warp w's 8x8 block
-    const float x0 = B::px0(tx, w) + 0.5f, x1 = x0 + 7.0f;
+  for (int w = 0; w < B::NW; ++w) {  // pixel centres of warp w's block
+    const float x0 = B::px0(tx, w) + 0.5f, x1 = x0 + static_cast<float>(B::BW - 1);
     const float y0 = B::py0(ty, w) + 0.5f, y1 = y0 + 7.0f;
     if (ellipse_meets_rect(A, Bv.x, o, x0, x1, y0, y1)) m |= 1u << w;
   }
@@ -122,66 +128,99 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   sg->p5 = make_float4(nm, nm, __uint_as_float(m), 0.0f);
 }
 
-// Evaluation of one staged Gaussian at the pixel pair (px, py), (px + 1, py):
-// power', 2^power', opacity_t 2^power' and whether the window takes it, every
-// rounding explicit.
+// Evaluation of one staged Gaussian at the thread's Q pixel pairs (PX[q],
+// py): power', 2^power', opacity_t 2^power' and whether the window takes it,
+// every rounding explicit. dy and the row terms B' dy and C' dy^2 are shared
+// by the pairs (they are the same numbers a pair alone would compute).
+template <int Q>
 struct PairEval {
-  float2 p, e, araw, dx, dy;
-  bool v0, v1;
+  float2 araw[Q], dx[Q];
+  float dy;
+  bool v[2 * Q];
 };
 
-__device__ __forceinline__ PairEval eval_pair(const StagedG& g, float2 PX, float2 PY) {
-  PairEval r;
+template <int Q>
+__device__ __forceinline__ void eval_pairs(const StagedG& g, const float2 (&PX)[Q], float2 PY, PairEval<Q>& r) {
   const float4 p0 = g.p0, p1 = g.p1, p2 = g.p2, p4 = g.p4, p5 = g.p5;
-  r.dx = __fadd2_rn(PX, make_float2(p0.x, p0.y));
-  r.dy = __fadd2_rn(PY, make_float2(p0.z, p0.w));
-  const float2 bdy = __fmul2_rn(make_float2(p1.z, p1.w), r.dy);
-  const float2 t = __ffma2_rn(make_float2(p1.x, p1.y), r.dx, bdy);
-  const float2 u = __fmul2_rn(__fmul2_rn(make_float2(p2.x, p2.y), r.dy), r.dy);
-  r.p = __ffma2_rn(r.dx, t, u);
-  r.e = make_float2(ex2_approx(r.p.x), ex2_approx(r.p.y));
-  r.araw = __fmul2_rn(make_float2(p2.z, p2.w), r.e);
-  const float2 q = __ffma2_rn(r.p, make_float2(p4.z, p4.w), make_float2(p5.x, p5.y));
-  r.v0 = fabsf(q.x) <= 1.0f;
-  r.v1 = fabsf(q.y) <= 1.0f;
-  return r;
+  const float2 dy = __fadd2_rn(PY, make_float2(p0.z, p0.w));
+  const float2 bdy = __fmul2_rn(make_float2(p1.z, p1.w), dy);
+  const float2 u = __fmul2_rn(__fmul2_rn(make_float2(p2.x, p2.y), dy), dy);
+  r.dy = dy.x;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    r.dx[q] = __fadd2_rn(PX[q], make_float2(p0.x, p0.y));
+    const float2 t = __ffma2_rn(make_float2(p1.x, p1.y), r.dx[q], bdy);
+    const float2 p = __ffma2_rn(r.dx[q], t, u);
+    const float2 e = make_float2(ex2_approx(p.x), ex2_approx(p.y));
+    r.araw[q] = __fmul2_rn(make_float2(p2.z, p2.w), e);
+    const float2 w = __ffma2_rn(p, make_float2(p4.z, p4.w), make_float2(p5.x, p5.y));
+    r.v[2 * q] = fabsf(w.x) <= 1.0f;
+    r.v[2 * q + 1] = fabsf(w.y) <= 1.0f;
+  }
 }
 
-// Per-thread state of the forward walk over a tile list.
+// Per-thread state of the forward walk over a tile list (pixel j = 2 q + h
+// is lane h of pair q).
+template <int Q>
 struct FwdState {
-  float2 PX, T, cr, cg, cb;
-  uint32_t stop0, stop1, last0, last1, pairs;
-  bool done0, done1;
+  float2 PX[Q], T[Q], cr[Q], cg[Q], cb[Q];
+  uint32_t stop[2 * Q], last[2 * Q], pairs;
+  bool done[2 * Q];
 };
 
-// Composite one evaluated Gaussian into the thread's two pixels. kClamp: the
+__device__ __forceinline__ float& lane_of(float2& v, int h) { return h ? v.y : v.x; }
+
+// Composite one evaluated Gaussian into the thread's pixels. kClamp: the
 // Gaussian's opacity_t exceeds 0.99 so alpha is clamped; kLast: track the
 // last composited position. Returns true when every pixel of the warp has
 // stopped.
-template <bool kClamp, bool kLast>
-__device__ __forceinline__ bool fwd_apply(FwdState& S, const PairEval& ev, const StagedG& g, uint32_t pos) {
-  bool v0 = ev.v0, v1 = ev.v1;
-  float2 a = make_float2(v0 ? ev.araw.x : 0.0f, v1 ? ev.araw.y : 0.0f);
-  if constexpr (kClamp) a = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
-  float2 Tn = __ffma2_rn(make_float2(-S.T.x, -S.T.y), a, S.T);  // T (1 - alpha)
-  const bool st0 = Tn.x < kTMin, st1 = Tn.y < kTMin;            // only a taken Gaussian can stop
+template <bool kClamp, bool kLast, int Q>
+__device__ __forceinline__ bool fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const StagedG& g, uint32_t pos) {
+  float2 a[Q], Tn[Q];
+  bool st[2 * Q], any = false;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    a[q] = make_float2(ev.v[2 * q] ? ev.araw[q].x : 0.0f, ev.v[2 * q + 1] ? ev.araw[q].y : 0.0f);
+    if constexpr (kClamp) a[q] = make_float2(fminf(a[q].x, kAlphaMax), fminf(a[q].y, kAlphaMax));
+    Tn[q] = __ffma2_rn(make_float2(-S.T[q].x, -S.T[q].y), a[q], S.T[q]);  // T (1 - alpha)
+    st[2 * q] = Tn[q].x < kTMin;  // only a taken Gaussian can stop
+    st[2 * q + 1] = Tn[q].y < kTMin;
+    any = any || st[2 * q] || st[2 * q + 1];
+  }
   bool wdone = false;
-  if (__any_sync(0xffffffffu, st0 || st1)) {
+  if (__any_sync(0xffffffffu, any)) {
     // stop before this Gaussian: it is not composited; the pixel is done
-    if (st0) { a.x = 0.0f; Tn.x = S.T.x; S.PX.x = kFar; v0 = false; S.done0 = true; S.stop0 = pos; }
-    if (st1) { a.y = 0.0f; Tn.y = S.T.y; S.PX.y = kFar; v1 = false; S.done1 = true; S.stop1 = pos; }
-    wdone = __all_sync(0xffffffffu, S.done0 && S.done1);
+    bool all = true;
+#pragma unroll
+    for (int j = 0; j < 2 * Q; ++j) {
+      const int q = j >> 1, h = j & 1;
+      if (st[j]) {
+        lane_of(a[q], h) = 0.0f;
+        lane_of(Tn[q], h) = lane_of(S.T[q], h);
+        lane_of(S.PX[q], h) = kFar;
+        ev.v[j] = false;
+        S.done[j] = true;
+        S.stop[j] = pos;
+      }
+      all = all && S.done[j];
+    }
+    wdone = __all_sync(0xffffffffu, all);
   }
   const float4 p3 = g.p3, p4 = g.p4;
-  const float2 w = __fmul2_rn(a, S.T);
-  S.cr = __ffma2_rn(make_float2(p3.x, p3.y), w, S.cr);
-  S.cg = __ffma2_rn(make_float2(p3.z, p3.w), w, S.cg);
-  S.cb = __ffma2_rn(make_float2(p4.x, p4.y), w, S.cb);
-  S.T = Tn;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float2 w = __fmul2_rn(a[q], S.T[q]);
+    S.cr[q] = __ffma2_rn(make_float2(p3.x, p3.y), w, S.cr[q]);
+    S.cg[q] = __ffma2_rn(make_float2(p3.z, p3.w), w, S.cg[q]);
+    S.cb[q] = __ffma2_rn(make_float2(p4.x, p4.y), w, S.cb[q]);
+    S.T[q] = Tn[q];
+  }
   if constexpr (kLast) {  // instrumented variant: last composited position and a pair count
-    S.last0 = v0 ? pos + 1 : S.last0;
-    S.last1 = v1 ? pos + 1 : S.last1;
-    S.pairs += (v0 ? 1u : 0u) + (v1 ? 1u : 0u);
+#pragma unroll
+    for (int j = 0; j < 2 * Q; ++j) {
+      S.last[j] = ev.v[j] ? pos + 1 : S.last[j];
+      S.pairs += ev.v[j] ? 1u : 0u;
+    }
   }
   return wdone;
 }
@@ -190,9 +229,11 @@ __device__ __forceinline__ bool fwd_apply(FwdState& S, const PairEval& ev, const
 // two evaluations are independent and overlap; the composites stay in order.
 // A pixel that stops inside an iteration has moved to infinity before the
 // second composite only through its done flag: the second evaluation saw the
-// old position, so its result is discarded for that pixel.
-template <bool kClamp, bool kLast>
-__device__ __forceinline__ bool fwd_group(FwdState& S, const StagedG* grp, uint32_t bits, uint32_t cbits,
+// old position, so its result is discarded for that pixel. (The backward
+// walks one entry at a time: two would cost it more in occupancy than they
+// gain in overlap.)
+template <bool kClamp, bool kLast, int Q>
+__device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StagedG* grp, uint32_t bits, uint32_t cbits,
                                           float2 PY, uint32_t pos0) {
   while (bits) {
     const int j0 = __ffs(bits) - 1;
@@ -200,19 +241,24 @@ __device__ __forceinline__ bool fwd_group(FwdState& S, const StagedG* grp, uint3
     if (bits) {
       const int j1 = __ffs(bits) - 1;
       bits &= bits - 1;
-      const PairEval e0 = eval_pair(grp[j0], S.PX, PY);
-      PairEval e1 = eval_pair(grp[j1], S.PX, PY);
+      PairEval<Q> e0, e1;
+      eval_pairs<Q>(grp[j0], S.PX, PY, e0);
+      eval_pairs<Q>(grp[j1], S.PX, PY, e1);
       const bool c0 = kClamp && ((cbits >> j0) & 1u), c1 = kClamp && ((cbits >> j1) & 1u);
-      if (c0 ? fwd_apply<true, kLast>(S, e0, grp[j0], pos0 + j0) : fwd_apply<false, kLast>(S, e0, grp[j0], pos0 + j0))
+      if (c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
+             : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0))
         return true;
-      e1.v0 = e1.v0 && !S.done0;
-      e1.v1 = e1.v1 && !S.done1;
-      if (c1 ? fwd_apply<true, kLast>(S, e1, grp[j1], pos0 + j1) : fwd_apply<false, kLast>(S, e1, grp[j1], pos0 + j1))
+#pragma unroll
+      for (int j = 0; j < 2 * Q; ++j) e1.v[j] = e1.v[j] && !S.done[j];
+      if (c1 ? fwd_apply<true, kLast, Q>(S, e1, grp[j1], pos0 + j1)
+             : fwd_apply<false, kLast, Q>(S, e1, grp[j1], pos0 + j1))
         return true;
     } else {
-      const PairEval e0 = eval_pair(grp[j0], S.PX, PY);
+      PairEval<Q> e0;
+      eval_pairs<Q>(grp[j0], S.PX, PY, e0);
       const bool c0 = kClamp && ((cbits >> j0) & 1u);
-      if (c0 ? fwd_apply<true, kLast>(S, e0, grp[j0], pos0 + j0) : fwd_apply<false, kLast>(S, e0, grp[j0], pos0 + j0))
+      if (c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
+             : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0))
         return true;
     }
   }
@@ -220,7 +266,9 @@ __device__ __forceinline__ bool fwd_group(FwdState& S, const StagedG* grp, uint3
 }
 
 template <int TW, int TH>
-constexpr int fwd_min_blocks() { return Blend<TW, TH>::NT <= 128 ? 8 : 4; }
+constexpr int fwd_min_blocks() {
+  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 12 : Blend<TW, TH>::NT <= 128 ? 6 : 3;
+}
 
 // Where a global tile id lies: its view (binary search over the views'
 // first tile ids), the tile's position in the view and the view's image.
@@ -258,29 +306,40 @@ __device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint
                                                uint32_t* __restrict__ out_stop, uint32_t* __restrict__ out_last,
                                                unsigned long long* __restrict__ pair_count) {
   using B = Blend<TW, TH>;
-  constexpr int BS = B::NT;
+  constexpr int BS = B::NT, Q = B::Q;
   const TileLoc loc = locate_tile(views, nviews, tile);
   const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int px = B::px0(tx, warp) + 2 * (lane % B::PCOLS);
+  const int px = B::px0(tx, warp) + 2 * Q * (lane % B::PCOLS);  // the thread's pixels: px .. px + 2Q - 1
   const int py = B::py0(ty, warp) + lane / B::PCOLS;
-  const bool in0 = px < width && py < height;
-  const bool in1 = px + 1 < width && py < height;
+  bool in[2 * Q];
+#pragma unroll
+  for (int j = 0; j < 2 * Q; ++j) in[j] = px + j < width && py < height;
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
-  FwdState S;
-  S.PX = make_float2(in0 ? px + 0.5f : kFar, in1 ? px + 1.5f : kFar);
-  S.T = make_float2(1.0f, 1.0f);
-  S.cr = S.cg = S.cb = make_float2(0.f, 0.f);
-  S.stop0 = S.stop1 = static_cast<uint32_t>(n);
-  S.last0 = S.last1 = 0;
+  FwdState<Q> S;
+  bool all_done = true;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    S.PX[q] = make_float2(in[2 * q] ? px + 2 * q + 0.5f : kFar, in[2 * q + 1] ? px + 2 * q + 1.5f : kFar);
+    S.T[q] = make_float2(1.0f, 1.0f);
+    S.cr[q] = S.cg[q] = S.cb[q] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * Q; ++j) {
+    S.stop[j] = static_cast<uint32_t>(n);
+    S.last[j] = 0;
+    S.done[j] = !in[j];
+    all_done = all_done && S.done[j];
+  }
   S.pairs = 0;
-  S.done0 = !in0;
-  S.done1 = !in1;
   const uint32_t wbit = 1u << warp;
   for (int b = 0; b < n; b += BS) {
-    if (__syncthreads_count(S.done0 && S.done1) == BS) break;
+    all_done = true;
+#pragma unroll
+    for (int j = 0; j < 2 * Q; ++j) all_done = all_done && S.done[j];
+    if (__syncthreads_count(all_done) == BS) break;
     const int idx = b + static_cast<int>(threadIdx.x);
     if (idx < n) {
       const uint32_t e = vals[rg.x + idx];  // emission index of the pair
@@ -288,7 +347,7 @@ __device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint
     }
     __syncthreads();
     const int cnt = min(BS, n - b);
-    bool wdone = __all_sync(0xffffffffu, S.done0 && S.done1);
+    bool wdone = __all_sync(0xffffffffu, all_done);
     for (int j0 = 0; j0 < cnt && !wdone; j0 += 32) {
       const uint32_t m = (j0 + lane < cnt) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
       uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
@@ -296,32 +355,25 @@ __device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint
       const StagedG* grp = sg + j0;
       const uint32_t pos0 = static_cast<uint32_t>(b + j0);
       // no Gaussian of this group needs the alpha clamp: the common path
-      wdone = cbits == 0u ? fwd_group<false, kLast>(S, grp, bits, cbits, PY, pos0)
-                          : fwd_group<true, kLast>(S, grp, bits, cbits, PY, pos0);
+      wdone = cbits == 0u ? fwd_group<false, kLast, Q>(S, grp, bits, cbits, PY, pos0)
+                          : fwd_group<true, kLast, Q>(S, grp, bits, cbits, PY, pos0);
     }
   }
   const size_t plane = static_cast<size_t>(width) * height;
   float* img = out_rgb + 3 * static_cast<size_t>(loc.pix_off);
-  if (in0) {
-    const size_t pix = static_cast<size_t>(py) * width + px;
-    img[pix] = S.cr.x + S.T.x * bg0;
-    img[plane + pix] = S.cg.x + S.T.x * bg1;
-    img[2 * plane + pix] = S.cb.x + S.T.x * bg2;
-    out_T[loc.pix_off + pix] = S.T.x;
-    out_stop[loc.pix_off + pix] = S.stop0;
+#pragma unroll
+  for (int j = 0; j < 2 * Q; ++j) {
+    if (!in[j]) continue;
+    const int q = j >> 1, h = j & 1;
+    const float T = lane_of(S.T[q], h);
+    const size_t pix = static_cast<size_t>(py) * width + px + j;
+    img[pix] = lane_of(S.cr[q], h) + T * bg0;
+    img[plane + pix] = lane_of(S.cg[q], h) + T * bg1;
+    img[2 * plane + pix] = lane_of(S.cb[q], h) + T * bg2;
+    out_T[loc.pix_off + pix] = T;
+    out_stop[loc.pix_off + pix] = S.stop[j];
     if constexpr (kLast) {
-      if (out_last) out_last[loc.pix_off + pix] = S.last0;
-    }
-  }
-  if (in1) {
-    const size_t pix = static_cast<size_t>(py) * width + px + 1;
-    img[pix] = S.cr.y + S.T.y * bg0;
-    img[plane + pix] = S.cg.y + S.T.y * bg1;
-    img[2 * plane + pix] = S.cb.y + S.T.y * bg2;
-    out_T[loc.pix_off + pix] = S.T.y;
-    out_stop[loc.pix_off + pix] = S.stop1;
-    if constexpr (kLast) {
-      if (out_last) out_last[loc.pix_off + pix] = S.last1;
+      if (out_last) out_last[loc.pix_off + pix] = S.last[j];
     }
   }
   if constexpr (kLast) {
@@ -360,13 +412,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Per-thread state of the backward walk (two pixels, packed).
+// Per-thread state of the backward walk (Q packed pixel pairs).
+template <int Q>
 struct BwdState {
-  float2 PX, T, U, gr, gg, gb;  // T_{i+1}; U = colour-gradient behind i + T_N (g . bg); d L / d out
-  uint32_t L0, L1;              // stop positions
+  float2 PX[Q], T[Q], U[Q], gr[Q], gg[Q], gb[Q];  // T_{i+1}; U = colour-gradient behind i + T_N (g . bg); dL/d out
+  uint32_t L[2 * Q];                              // stop positions
 };
 
-// Backward of one list entry at position p for the thread's two pixels.
+// Backward of one list entry at position p for the thread's pixels.
 // With alpha_i = opacity_t 2^power' and the per-pixel upstream gradient g:
 //   T_i = T_{i+1} / (1 - alpha_i),
 //   dL/dalpha_i = (g . c_i) T_i - U_{i+1} / (1 - alpha_i),
@@ -376,45 +429,64 @@ struct BwdState {
 // (dalpha/dpower = alpha), so the thread accumulates the raw moments
 //   D = sum dq, M0 = sum dq dx, M1 = sum dq dy, Qxx = sum dq dx^2,
 //   Qxy = sum dq dx dy, Qyy = sum dq dy^2
-// (the two pixels share dy) and the conversion to d mean2d, d conic and
+// (the thread's pixels share dy) and the conversion to d mean2d, d conic and
 // d opacity_t happens once per (tile, entry). Out: v[9] = D, M0, M1, Qxx,
 // Qxy, Qyy, dr, dg, db. Returns false when no pixel of the warp takes it.
-template <bool kClamp>
-__device__ __forceinline__ bool bwd_entry(BwdState& S, const StagedG& gs, uint32_t p, float2 PY, float v[9]) {
-  const PairEval ev = eval_pair(gs, S.PX, PY);
-  const bool a0 = p < S.L0 && ev.v0, a1 = p < S.L1 && ev.v1;
-  if (!__any_sync(0xffffffffu, a0 || a1)) return false;
-  const float2 ar = make_float2(a0 ? ev.araw.x : 0.0f, a1 ? ev.araw.y : 0.0f);
-  float2 al = ar;
-  if constexpr (kClamp) al = make_float2(fminf(ar.x, kAlphaMax), fminf(ar.y, kAlphaMax));
-  const float2 om = __ffma2_rn(al, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - alpha >= 0.01
-  const float2 iom = make_float2(a0 ? rcp_approx(om.x) : 1.0f, a1 ? rcp_approx(om.y) : 1.0f);
-  const float2 Ti = __fmul2_rn(S.T, iom);
-  const float2 w = __fmul2_rn(al, Ti);
-  const float4 p3 = gs.p3, p4 = gs.p4;
-  const float2 gc = __ffma2_rn(S.gb, make_float2(p4.x, p4.y),
-                               __ffma2_rn(S.gg, make_float2(p3.z, p3.w), __fmul2_rn(S.gr, make_float2(p3.x, p3.y))));
-  float2 da = __fmul2_rn(iom, __ffma2_rn(gc, S.T, make_float2(-S.U.x, -S.U.y)));
-  S.U = __ffma2_rn(gc, w, S.U);
-  S.T = Ti;
-  if constexpr (kClamp) {  // a clamped alpha does not depend on power' or opacity_t
-    if (ar.x > kAlphaMax) da.x = 0.0f;
-    if (ar.y > kAlphaMax) da.y = 0.0f;
+template <bool kClamp, int Q>
+__device__ __forceinline__ bool bwd_entry(BwdState<Q>& S, const StagedG& gs, uint32_t p, float2 PY, float v[9]) {
+  PairEval<Q> ev;
+  eval_pairs<Q>(gs, S.PX, PY, ev);
+  bool a[2 * Q], any = false;
+#pragma unroll
+  for (int j = 0; j < 2 * Q; ++j) {
+    a[j] = p < S.L[j] && ev.v[j];
+    any = any || a[j];
   }
-  const float2 dq = __fmul2_rn(da, ar);  // zero for pixels that do not take the entry
-  const float2 t = __fmul2_rn(dq, ev.dx);
-  const float2 q = __fmul2_rn(t, ev.dx);
-  const float dy = ev.dy.x;
-  v[0] = dq.x + dq.y;
-  v[1] = t.x + t.y;
-  v[2] = dy * v[0];
-  v[3] = q.x + q.y;
-  v[4] = dy * v[1];
-  v[5] = dy * v[2];
-  const float2 cr = __fmul2_rn(S.gr, w), cg = __fmul2_rn(S.gg, w), cb = __fmul2_rn(S.gb, w);
-  v[6] = cr.x + cr.y;
-  v[7] = cg.x + cg.y;
-  v[8] = cb.x + cb.y;
+  if (!__any_sync(0xffffffffu, any)) return false;
+  const float4 p3 = gs.p3, p4 = gs.p4;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const bool a0 = a[2 * q], a1 = a[2 * q + 1];
+    const float2 ar = make_float2(a0 ? ev.araw[q].x : 0.0f, a1 ? ev.araw[q].y : 0.0f);
+    float2 al = ar;
+    if constexpr (kClamp) al = make_float2(fminf(ar.x, kAlphaMax), fminf(ar.y, kAlphaMax));
+    const float2 om = __ffma2_rn(al, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - alpha >= 0.01
+    const float2 iom = make_float2(a0 ? rcp_approx(om.x) : 1.0f, a1 ? rcp_approx(om.y) : 1.0f);
+    const float2 Ti = __fmul2_rn(S.T[q], iom);
+    const float2 w = __fmul2_rn(al, Ti);
+    const float2 gc = __ffma2_rn(S.gb[q], make_float2(p4.x, p4.y),
+                                 __ffma2_rn(S.gg[q], make_float2(p3.z, p3.w),
+                                            __fmul2_rn(S.gr[q], make_float2(p3.x, p3.y))));
+    float2 da = __fmul2_rn(iom, __ffma2_rn(gc, S.T[q], make_float2(-S.U[q].x, -S.U[q].y)));
+    S.U[q] = __ffma2_rn(gc, w, S.U[q]);
+    S.T[q] = Ti;
+    if constexpr (kClamp) {  // a clamped alpha does not depend on power' or opacity_t
+      if (ar.x > kAlphaMax) da.x = 0.0f;
+      if (ar.y > kAlphaMax) da.y = 0.0f;
+    }
+    const float2 dq = __fmul2_rn(da, ar);  // zero for pixels that do not take the entry
+    const float2 t = __fmul2_rn(dq, ev.dx[q]);
+    const float2 qq = __fmul2_rn(t, ev.dx[q]);
+    const float2 cr = __fmul2_rn(S.gr[q], w), cg = __fmul2_rn(S.gg[q], w), cb = __fmul2_rn(S.gb[q], w);
+    if (q == 0) {
+      v[0] = dq.x + dq.y;
+      v[1] = t.x + t.y;
+      v[3] = qq.x + qq.y;
+      v[6] = cr.x + cr.y;
+      v[7] = cg.x + cg.y;
+      v[8] = cb.x + cb.y;
+    } else {
+      v[0] += dq.x + dq.y;
+      v[1] += t.x + t.y;
+      v[3] += qq.x + qq.y;
+      v[6] += cr.x + cr.y;
+      v[7] += cg.x + cg.y;
+      v[8] += cb.x + cb.y;
+    }
+  }
+  v[2] = ev.dy * v[0];
+  v[4] = ev.dy * v[1];
+  v[5] = ev.dy * v[2];
   return true;
 }
 
@@ -471,45 +543,49 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
                                                const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
                                                const float* __restrict__ grad_rgb, float4* __restrict__ gbuf) {
   using B = Blend<TW, TH>;
-  constexpr int BS = B::NT;
+  constexpr int BS = B::NT, Q = B::Q;
   const TileLoc loc = locate_tile(views, nviews, tile);
   const int tx = loc.tx, ty = loc.ty, width = loc.width, height = loc.height;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int px = B::px0(tx, warp) + 2 * (lane % B::PCOLS);
+  const int px = B::px0(tx, warp) + 2 * Q * (lane % B::PCOLS);  // the thread's pixels: px .. px + 2Q - 1
   const int py = B::py0(ty, warp) + lane / B::PCOLS;
-  const bool in0 = px < width && py < height;
-  const bool in1 = px + 1 < width && py < height;
   const float2 PY = make_float2(py + 0.5f, py + 0.5f);
   const uint2 rg = ranges[tile];
   const int n = static_cast<int>(rg.y - rg.x);
   const size_t plane = static_cast<size_t>(width) * height;
   const float* gimg = grad_rgb + 3 * static_cast<size_t>(loc.pix_off);
-  BwdState S;
-  S.PX = make_float2(px + 0.5f, px + 1.5f);
-  float T[2] = {1.f, 1.f}, U[2] = {0.f, 0.f}, g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  uint32_t L[2] = {0u, 0u};
+  BwdState<Q> S;
+  uint32_t lmax = 0;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (k == 0 ? in0 : in1) {
-      const size_t pix = static_cast<size_t>(py) * width + px + k;
-      T[k] = Tfinal[loc.pix_off + pix];
-      L[k] = stoppos[loc.pix_off + pix];
-      g[k][0] = gimg[pix];
-      g[k][1] = gimg[plane + pix];
-      g[k][2] = gimg[2 * plane + pix];
-      U[k] = T[k] * (bg0 * g[k][0] + bg1 * g[k][1] + bg2 * g[k][2]);  // T_N (g . bg)
+  for (int q = 0; q < Q; ++q) {
+    float T[2] = {1.f, 1.f}, U[2] = {0.f, 0.f}, g[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    uint32_t L[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int x = px + 2 * q + h;
+      if (x < width && py < height) {
+        const size_t pix = static_cast<size_t>(py) * width + x;
+        T[h] = Tfinal[loc.pix_off + pix];
+        L[h] = stoppos[loc.pix_off + pix];
+        g[h][0] = gimg[pix];
+        g[h][1] = gimg[plane + pix];
+        g[h][2] = gimg[2 * plane + pix];
+        U[h] = T[h] * (bg0 * g[h][0] + bg1 * g[h][1] + bg2 * g[h][2]);  // T_N (g . bg)
+      }
     }
+    S.PX[q] = make_float2(px + 2 * q + 0.5f, px + 2 * q + 1.5f);
+    S.T[q] = make_float2(T[0], T[1]);
+    S.U[q] = make_float2(U[0], U[1]);
+    S.gr[q] = make_float2(g[0][0], g[1][0]);
+    S.gg[q] = make_float2(g[0][1], g[1][1]);
+    S.gb[q] = make_float2(g[0][2], g[1][2]);
+    S.L[2 * q] = L[0];
+    S.L[2 * q + 1] = L[1];
+    lmax = max(lmax, max(L[0], L[1]));
   }
-  S.T = make_float2(T[0], T[1]);
-  S.U = make_float2(U[0], U[1]);
-  S.gr = make_float2(g[0][0], g[1][0]);
-  S.gg = make_float2(g[0][1], g[1][1]);
-  S.gb = make_float2(g[0][2], g[1][2]);
-  S.L0 = L[0];
-  S.L1 = L[1];
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, L[0] > L[1] ? L[0] : L[1]);  // this warp's walk ends here
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, lmax);  // this warp's walk ends here
   if (lane == 0 && wmax) atomicMax(&s_max, wmax);
   __syncthreads();
   const int maxL = static_cast<int>(s_max);
@@ -537,8 +613,8 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
         bits &= ~(1u << jj);
         const uint32_t p = static_cast<uint32_t>(b0 + j0 + jj);
         float v[9];
-        const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true>(S, sg[j0 + jj], p, PY, v)
-                                               : bwd_entry<false>(S, sg[j0 + jj], p, PY, v);
+        const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true, Q>(S, sg[j0 + jj], p, PY, v)
+                                               : bwd_entry<false, Q>(S, sg[j0 + jj], p, PY, v);
         if (took) {
           if (lane == 0) atomicOr(&sTook[j0 + jj], wbit);
           warp_reduce9(v, lane);
