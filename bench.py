@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--batch-only", action="store_true", help="batched and large workloads only (profiling)")
     ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
     ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
+    ap.add_argument("--backward-only", action="store_true",
+                    help="render + backward of sweep frame 37, four times (profiling the backward)")
     return ap.parse_args()
 
 
@@ -186,6 +188,15 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     if args.train_only:
         return {"train": train_bench(args, rend, params, dev, stream, flush)}
+    if args.backward_only:
+        cam, t = frame_camera(37)
+        grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+        gimg = torch.randn((3, HEIGHT, WIDTH), device=dev, generator=torch.Generator(device=dev).manual_seed(3)) * 1e-6
+        for _ in range(4):
+            res = rend.render(params, cam, t)
+            rend.backward(params, cam, t, res, gimg, grads)
+        torch.cuda.synchronize()
+        return {"backward_only": "frame 37, 4 x (render + backward)"}
     if args.batch_only:
         return {"batched": batch_bench(args, dev, stream, flush), "large": large_bench(args, dev, stream, flush)}
 
@@ -704,6 +715,7 @@ def main():
         return
     out = run_ours(args, rank, world, local)
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.frames_only or args.train_only
+                                          or args.backward_only
                                           or args.batch_only):
         out["cpu_baseline"] = cpu_baseline()
     if rank == 0:
