@@ -16,6 +16,11 @@
 struct r4g_ctx {
   r4g_config cfg;
   char err[512];
+  // side stream of a render: the tile counts run there while the depth sort
+  // and the binning run on the caller's stream (made on first use, on the
+  // device current then)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool timing = false;
   struct Pending {
     int stage;
@@ -192,10 +197,10 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.tfinal = o;   o = align_up(o + sizeof(float) * npix);
   L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
   L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);
-  {
-    const size_t a = onesweep_scratch_bytes(m, 32), b = onesweep_scratch_bytes(cap, tb);
-    L.onesweep = o; o = align_up(o + (a > b ? a : b));
-  }
+  // the two sorts' scratch apart: the tile sort's is cleared and filled with
+  // its histograms on a side stream while the depth sort runs
+  L.onesweep = o; o = align_up(o + onesweep_scratch_bytes(m, 32));
+  L.tsort = o;    o = align_up(o + onesweep_scratch_bytes(cap, tb));
   // multi-view backward: the visible items and their partial gradients (96 B each)
   const int64_t mi = nviews > 1 ? m : 0;
   L.ilist = o;    o = align_up(o + sizeof(uint32_t) * mi);
@@ -275,6 +280,25 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
       return cuda_fail(ctx, e, "preprocess");
   }
   uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
+  // fork: the tile counts (ranges and the tile sort's histograms) and the
+  // clearing of the tile sort's scratch need only the preprocess's output
+  if (!ctx->side) {
+    if ((e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(ctx, e, "side stream");
+  }
+  if ((e = cudaEventRecord(ctx->fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
+    return cuda_fail(ctx, e, "fork");
+  {
+    StageScope sc(ctx, R4G_STAGE_RANGES, ctx->side, 1);
+    uint32_t* hist = at<uint32_t>(frame, L.tsort);
+    e = tpasses > 0 ? cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortRadix * tpasses, ctx->side) : cudaSuccess;
+    if (e == cudaSuccess) e = launch_tile_counts(L, frame, hist, tpasses, ctx->side);
+    if (e == cudaSuccess && has && tpasses > 0) e = prepare_onesweep(hist, L.cap, L.tile_bits, true, ctx->side);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->join, ctx->side);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile counts");
+  }
   int which = 0;
   if (has) {
     // depth order of the items: stable sort of the depth bits, values = item index
@@ -290,21 +314,15 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
     if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
   }
   const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
-  {
-    // per-tile counts -> tile ranges and the tile sort's digit histograms
-    StageScope sc(ctx, R4G_STAGE_RANGES, s, 1);
-    uint32_t* hist = at<uint32_t>(frame, L.onesweep);
-    e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortRadix * 4, s);
-    if (e == cudaSuccess) e = launch_tile_counts(L, frame, hist, tpasses, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "tile counts");
-  }
+  // join: the tile sort and the blend need the side stream's work
+  if ((e = cudaStreamWaitEvent(s, ctx->join, 0)) != cudaSuccess) return cuda_fail(ctx, e, "join");
   if (has && tpasses > 0) {
     // stable sort of the depth-ordered pairs by tile id
     StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
     // values: the emission index of each pair, generated by the first pass
     e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
                         at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.onesweep), err, s, &which, true);
+                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.tsort), err, s, &which, true, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
   }
   const uint32_t* vals = sorted_vals(L, frame);
@@ -388,6 +406,9 @@ r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg) {
 
 void r4g_destroy(r4g_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);

@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(kPreBlock)
 // Per-tile pair counts from the 2D difference array the preprocess filled
 // (prefix sums along x, then along y, in shared memory with warp scans), their
 // exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
-// list, and the digit histograms of the tile sort's radix passes. One CTA;
-// the difference array is copied into dynamic shared memory.
+// list, and the digit histograms of the tile sort's radix passes. One CTA per
+// view; the difference array is copied into dynamic shared memory. Needs only
+// what the preprocess wrote.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -205,10 +206,15 @@ __global__ void __launch_bounds__(1024)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int k = threadIdx.x; k < 4 * kSortRadix; k += blockDim.x) (&s_h[0][0])[k] = 0;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_c[t] = td[(t / tiles_x) * st + (t % tiles_x)];
+  __shared__ bool s_overflow;
   if (threadIdx.x == 0) {  // the view's first pair: pairs of the views before it
-    uint32_t base = 0;
-    for (int u = 0; u < v; ++u) base += hdr->view_pairs[u];
+    uint32_t base = 0, total = 0;
+    for (int u = 0; u < kMaxViews; ++u) {
+      if (u < v) base += hdr->view_pairs[u];
+      total += hdr->view_pairs[u];
+    }
     s_carry = base;
+    s_overflow = total > cap;
   }
   __syncthreads();
   for (int y = warp; y < tiles_y; y += nwarp) {  // each warp: running sums along its rows
@@ -234,8 +240,10 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   // after a key-capacity overflow the list is incomplete: every tile gets an
-  // empty range so nothing downstream reads it (the frame reports the overflow)
-  const bool overflow = hdr->key_needed > cap;
+  // empty range so nothing downstream reads it (the frame reports the
+  // overflow). The pair count is the sum of the views' counts the preprocess
+  // kept, so this kernel can run before the binning.
+  const bool overflow = s_overflow;
   for (int base = 0; base < ntiles; base += blockDim.x) {
     const int t = base + threadIdx.x;
     const uint32_t c = t < ntiles ? s_c[t] : 0u;

@@ -264,10 +264,19 @@ size_t onesweep_scratch_bytes(int64_t cap, int bits) {
                              + static_cast<size_t>(passes) * tiles * kSortRadix);  // status
 }
 
+cudaError_t prepare_onesweep(void* scratch, int64_t cap, int bits, bool hist_ready, cudaStream_t s) {
+  const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+  if (passes == 0 || cap == 0) return cudaSuccess;
+  const size_t hbytes = sizeof(uint32_t) * passes * kSortRadix;
+  uint32_t* tickets = static_cast<uint32_t*>(scratch) + passes * kSortRadix;
+  return hist_ready ? cudaMemsetAsync(tickets, 0, onesweep_scratch_bytes(cap, bits) - hbytes, s)
+                    : cudaMemsetAsync(scratch, 0, onesweep_scratch_bytes(cap, bits), s);
+}
+
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf, bool hist_ready) {
+                            int* result_in_buf, bool hist_ready, bool prepared) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   *result_in_buf = 0;
   if (passes == 0 || cap == 0) return cudaSuccess;
@@ -276,11 +285,12 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
   uint32_t* tickets = hist + passes * kSortRadix;
   uint32_t* status = tickets + 32;
   // the histograms either come ready (filled by the caller's kernels) or are
-  // counted here; tickets and statuses always start at zero
-  const size_t hbytes = sizeof(uint32_t) * passes * kSortRadix;
-  cudaError_t e = hist_ready ? cudaMemsetAsync(tickets, 0, onesweep_scratch_bytes(cap, bits) - hbytes, s)
-                             : cudaMemsetAsync(scratch, 0, onesweep_scratch_bytes(cap, bits), s);
-  if (e != cudaSuccess) return e;
+  // counted here; tickets and statuses always start at zero (cleared here
+  // unless the caller did it with prepare_onesweep)
+  if (!prepared) {
+    const cudaError_t e = prepare_onesweep(scratch, cap, bits, hist_ready, s);
+    if (e != cudaSuccess) return e;
+  }
   if (!hist_ready) {
     const int hist_ctas = static_cast<int>(tiles < kOsHistCtas ? tiles : kOsHistCtas);
     onesweep_hist_kernel<<<hist_ctas, kSortThreads, 0, s>>>(kin, count_dev, count_host, passes, bits, hist);

@@ -69,8 +69,8 @@ static_assert(sizeof(FrameHeader) == 512, "frame header size");
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
   size_t header, views, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, ioffs, srect, chunks,
-      blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, ranges, tfinal, last, sortcnt, onesweep, ilist,
-      ipart, total;
+      blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, ranges, tfinal, last, sortcnt, onesweep, tsort,
+      ilist, ipart, total;
   int64_t n, cap;
   int64_t m;         // items: n * nviews
   int nviews;
@@ -145,7 +145,11 @@ size_t onesweep_scratch_bytes(int64_t cap, int bits);
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf, bool hist_ready = false);
+                            int* result_in_buf, bool hist_ready = false, bool prepared = false);
+// What launch_onesweep clears before its passes (tickets, statuses and, unless
+// hist_ready, the histograms), enqueued separately so it can run early on
+// another stream; then call launch_onesweep with prepared = true.
+cudaError_t prepare_onesweep(void* scratch, int64_t cap, int bits, bool hist_ready, cudaStream_t s);
 // per-tile counts -> ranges and the tile sort's digit histograms (hist[p][256],
 // zeroed by the caller)
 cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s);
