@@ -427,11 +427,18 @@ __global__ void __launch_bounds__(kBwdBlock)
 #pragma unroll
   for (int k = 0; k < 4; ++k) gm[k] = 0.0f;
   const int nb = (sh_degree + 1) * (sh_degree + 1);
-  float4* gsh4 = reinterpret_cast<float4*>(out.sh + static_cast<size_t>(i) * 48);
+  // the SH gradient sum_v Y(dir_v) (x) d rgb_v in registers, added to the
+  // caller's row once; the next view's visibility is loaded while this
+  // view's partial is: one memory round trip per view
+  float gsh[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) gsh[k] = 0.0f;
+  uint32_t tnext = touched[i];
   for (int v = 0; v < nviews; ++v) {
-    const size_t item = static_cast<size_t>(v) * g.n + i;
-    if (touched[item] == 0u) continue;
-    const float4* p = ipart + 6 * item;
+    const uint32_t tcur = tnext;
+    if (v + 1 < nviews) tnext = touched[static_cast<size_t>(v + 1) * g.n + i];
+    if (tcur == 0u) continue;
+    const float4* p = ipart + 6 * (static_cast<size_t>(v) * g.n + i);
     const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4], f = p[5];
     G4s[0] += a.x; G4s[1] += a.y; G4s[2] += a.z; G4s[3] += a.w;
     G4s[4] += b.x; G4s[5] += b.y; G4s[6] += b.z; G4s[7] += b.w;
@@ -440,24 +447,26 @@ __global__ void __launch_bounds__(kBwdBlock)
     const float grgb[3] = {e.z, e.w, f.x};
     float Y[16];
     sh_basis(d.w, e.x, e.y, Y);
-    // d c_k += Y_k d rgb over the row's 16-byte vectors
+#pragma unroll
+    for (int el = 0; el < 48; ++el) gsh[el] += Y[el / 3] * grgb[el % 3];
+    if constexpr (kStats) {
+      vs_grad += f.y;
+      vs_count += f.z;
+      max_radius = fmaxf(max_radius, f.w);
+    }
+  }
+  {  // d c_k += sum over the views, 16-byte vectors over the row's first nb bands
+    float4* gsh4 = reinterpret_cast<float4*>(out.sh + static_cast<size_t>(i) * 48);
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
       if (4 * q < nb * 3) {
         float4 w = gsh4[q];
         float* wp = reinterpret_cast<float*>(&w);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int el = 4 * q + h;
-          if (el < nb * 3) wp[h] += Y[el / 3] * grgb[el % 3];
-        }
+        for (int h = 0; h < 4; ++h)
+          if (4 * q + h < nb * 3) wp[h] += gsh[4 * q + h];
         gsh4[q] = w;
       }
-    }
-    if constexpr (kStats) {
-      vs_grad += f.y;
-      vs_count += f.z;
-      max_radius = fmaxf(max_radius, f.w);
     }
   }
   Geo<float> G;
