@@ -541,7 +541,8 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
                                                uint32_t ng, uint32_t cap, const ViewDev* __restrict__ views,
                                                int nviews, float bg0, float bg1, float bg2,
                                                const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
-                                               const float* __restrict__ grad_rgb, float4* __restrict__ gbuf) {
+                                               const float* __restrict__ grad_rgb, float4* __restrict__ gbuf,
+                                               uint8_t* __restrict__ reach) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT, Q = B::Q;
   const TileLoc loc = locate_tile(views, nviews, tile);
@@ -637,36 +638,38 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
       }
       const uint32_t e = sE[threadIdx.x];
       if (e < cap) {
-        const StagedG& gs = sg[threadIdx.x];
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
-        if (__float_as_uint(gs.p5.z) & ((1u << B::NW) - 1u)) {
+        // only entries a pixel of the tile composited have a gradient; the
+        // others are flagged, not written (in a scene whose pixels saturate
+        // early most of a tile's list is never reached)
+        const bool took = sTook[threadIdx.x] != 0u;
+        reach[e] = took ? 1u : 0u;
+        if (took) {
+          const StagedG& gs = sg[threadIdx.x];
           // power' = A' dx^2 + B' dx dy + C' dy^2 with A' = -a/(2 ln 2), B' = -b/ln 2,
           // C' = -c/(2 ln 2) for the conic (a, b, c); d power/d mean = (a dx + b dy, b dx + c dy)
           const float Ap = gs.p1.x, Bp = gs.p1.z, Cp = gs.p2.x, o = gs.p2.z;
+          float4 r0, r1, r2;
           r0.x = -(2.0f * Ap * acc[1] + Bp * acc[2]) * kLn2;  // d mean2d.x
           r0.y = -(Bp * acc[1] + 2.0f * Cp * acc[2]) * kLn2;  // d mean2d.y
           r0.z = -0.5f * acc[3];                             // d conic a
           r0.w = -acc[4];                                    // d conic b
           r1.x = -0.5f * acc[5];                             // d conic c
           r1.y = o > 0.0f ? acc[0] / o : 0.0f;               // d opacity_t (alpha = opacity_t 2^power')
-          // d rgb; w = 1 when a pixel of the tile composited the entry
-          r2 = make_float4(acc[6], acc[7], acc[8], sTook[threadIdx.x] ? 1.0f : 0.0f);
+          r1.z = r1.w = 0.0f;
+          r2 = make_float4(acc[6], acc[7], acc[8], 1.0f);    // d rgb; w = 1: a pixel of the tile composited it
+          float4* d = gbuf + 3 * static_cast<size_t>(e);
+          d[0] = r0;
+          d[1] = r1;
+          d[2] = r2;
         }
-        float4* d = gbuf + 3 * static_cast<size_t>(e);
-        d[0] = r0;
-        d[1] = r1;
-        d[2] = r2;
       }
     }
   }
-  // list entries no pixel of the tile reached: zero gradient
+  // list entries no pixel of the tile reached: no gradient
   const int start = maxL > 0 ? ((maxL - 1) / BS) * BS + BS : 0;
   for (int i = start + static_cast<int>(threadIdx.x); i < n; i += BS) {
     const uint32_t e = vals[rg.x + i];
-    if (e < cap) {
-      float4* d = gbuf + 3 * static_cast<size_t>(e);
-      d[0] = d[1] = d[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    if (e < cap) reach[e] = 0u;
   }
 }
 
@@ -679,7 +682,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
                      uint32_t cap, const ViewDev* __restrict__ views, int nviews, int ntiles, FrameHeader* hdr,
                      float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
                      const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
-                     float4* __restrict__ gbuf) {
+                     float4* __restrict__ gbuf, uint8_t* __restrict__ reach) {
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
   __shared__ uint32_t sTook[Blend<TW, TH>::NT];  // per batch entry: warps that composited it
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
     const int tile = s_tile;
     if (tile >= ntiles) break;
     blend_bwd_tile<TW, TH>(tile, sg, sE, sTook, s_max, s_slab, ranges, vals, recA, recB, recC, egid, ng, cap, views,
-                           nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf);
+                           nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf, reach);
   }
 }
 
@@ -757,6 +760,7 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   const ViewDev* views = at<ViewDev>(frame, L.views);
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   float4* gbuf = at<float4>(frame, L.gbuf);
+  uint8_t* reach = at<uint8_t>(frame, L.reach);
   // the backward's work counter (the render zeroed the forward's)
   cudaMemsetAsync(&hdr->next_tile_bwd, 0, sizeof(uint32_t), s);
 #define R4G_BLEND_BWD(TW_, TH_)                                                                           \
@@ -768,7 +772,7 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
         <<<persistent_ctas(blend_bwd_kernel<TW_, TH_>, Blend<TW_, TH_>::NT, slab, L.ntiles),              \
            Blend<TW_, TH_>::NT, slab, s>>>(ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),  \
                                            static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], \
-                                           bg[1], bg[2], T, stop, grad_rgb, gbuf);                        \
+                                           bg[1], bg[2], T, stop, grad_rgb, gbuf, reach);                 \
   }
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16)
   else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8)

@@ -205,26 +205,36 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 // Sum of an item's per-pair gradients (pairs [o, o + cnt) of the gradient
 // buffer) for each lane's item: the warp walks its lanes' items in turn,
 // lane l adding pairs l, l + 32, ... (coalesced), then a butterfly sum; a
-// single pair is read by its owner. gc.w counts the tiles in which a pixel
-// composited the item (summed only with kStats).
+// single pair is read by its owner. Only pairs whose reach flag is set hold
+// a gradient (a pixel of their tile composited them); the others count as
+// zero and are not read. gc.w counts the tiles in which a pixel composited
+// the item (summed only with kStats). Returns whether any pair of the lane's
+// item holds a gradient (if none, the item's gradient is zero).
 template <bool kStats>
-__device__ __forceinline__ void gather_pairs(uint32_t cnt, uint32_t o, int lane, const float4* __restrict__ gbuf,
-                                             float4& ga, float4& gb, float4& gc) {
+__device__ __forceinline__ bool gather_pairs(uint32_t cnt, uint32_t o, int lane, const float4* __restrict__ gbuf,
+                                             const uint8_t* __restrict__ reach, float4& ga, float4& gb,
+                                             float4& gc) {
   ga = make_float4(0.f, 0.f, 0.f, 0.f);
   gb = ga;
   gc = ga;
+  bool got = false;
   for (int q = 0; q < 32; ++q) {
     const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
     if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
     const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
     float v9[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool found = false;
     for (uint32_t k = lane; k < qc; k += 32) {
+      if (!reach[qo + k]) continue;
+      found = true;
       const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
       const float4 x = pr[0], y = pr[1], z = pr[2];
       v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
       v9[4] += y.x; v9[5] += y.y;
       v9[6] += z.x; v9[7] += z.y; v9[8] += z.z; v9[9] += z.w;
     }
+    if (!__any_sync(0xffffffffu, found)) continue;  // no pair of item q holds a gradient
+    if (lane == q) got = true;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
 #pragma unroll
@@ -240,12 +250,14 @@ __device__ __forceinline__ void gather_pairs(uint32_t cnt, uint32_t o, int lane,
       gc = make_float4(v9[6], v9[7], v9[8], v9[9]);
     }
   }
-  if (cnt == 1) {
+  if (cnt == 1 && reach[o]) {
     const float4* pr = gbuf + 3 * static_cast<size_t>(o);
     ga = pr[0];
     gb = pr[1];
     gc = pr[2];
+    got = true;
   }
+  return got;
 }
 
 // Backward of the preprocess over the Gaussians visible in some view (the
@@ -261,7 +273,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     preprocess_bwd_kernel(r4g_gaussians g, const ViewDev* __restrict__ views, int nviews,
                           const uint32_t* __restrict__ glist, const uint32_t* __restrict__ ioffs,
                           const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
-                          const FrameHeader* hdr, int sh_degree, bool temporal_cull, r4g_grads out) {
+                          const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
+                          bool temporal_cull, r4g_grads out) {
   const int j = blockIdx.x * kBwdBlock + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int nlist = static_cast<int>(hdr->n_glist);
@@ -283,8 +296,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     if (__ballot_sync(0xffffffffu, cnt != 0u) == 0u) continue;
     const uint32_t o = cnt ? ioffs[item] : 0u;
     float4 ga, gb, gc;
-    gather_pairs<kStats>(cnt, o, lane, gbuf, ga, gb, gc);
-    if (cnt) {
+    const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc);
+    if (got) {  // an item no pixel composited has a zero gradient
       float radius;
       view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc, out.sh,
                                 acc, radius);
@@ -350,18 +363,31 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
 // scale backward once.
 constexpr int kPartFloats = 24;  // d Sigma4 (10), d mean (4), d opacity, dir (3), d rgb (3), statistics (3)
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     list_items_kernel(const uint32_t* __restrict__ touched, uint32_t m, uint32_t* __restrict__ ilist,
                       FrameHeader* hdr) {
-  const uint32_t k = blockIdx.x * 256 + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  // one counter update per CTA (per warp, 16M items made the counter the bottleneck)
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_base;
+  const uint32_t k = blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool vis = k < m && touched[k] != 0u;
   const uint32_t b = __ballot_sync(0xffffffffu, vis);
-  if (!b) return;
-  uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(&hdr->n_ilist, static_cast<uint32_t>(__popc(b)));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (vis) ilist[base + __popc(b & ((1u << lane) - 1u))] = k;
+  if (lane == 0) s_warp[warp] = __popc(b);
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t c = s_warp[lane];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_warp[lane] = x - c;  // exclusive over the warps
+    if (lane == 31) s_base = x ? atomicAdd(&hdr->n_ilist, x) : 0u;
+  }
+  __syncthreads();
+  if (vis) ilist[s_base + s_warp[warp] + __popc(b & ((1u << lane) - 1u))] = k;
 }
 
 template <bool kScaleBF16, bool kShBF16, bool kStats>
@@ -369,8 +395,8 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
     preprocess_bwd_items_kernel(r4g_gaussians g, const ViewDev* __restrict__ views,
                                 const uint32_t* __restrict__ ilist, const uint32_t* __restrict__ ioffs,
                                 const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
-                                const FrameHeader* hdr, int sh_degree, bool temporal_cull,
-                                float4* __restrict__ ipart) {
+                                const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
+                                bool temporal_cull, float4* __restrict__ ipart) {
   const int j = blockIdx.x * kBwdBlock + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int nlist = static_cast<int>(hdr->n_ilist);
@@ -380,8 +406,14 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   const uint32_t cnt = mine ? touched[item] : 0u;
   const uint32_t o = cnt ? ioffs[item] : 0u;
   float4 ga, gb, gc;
-  gather_pairs<kStats>(cnt, o, lane, gbuf, ga, gb, gc);
+  const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc);
   if (!mine) return;
+  float4* d = ipart + 6 * static_cast<size_t>(item);
+  if (!got) {  // no pixel composited the item: a zero partial
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    d[0] = d[1] = d[2] = d[3] = d[4] = d[5] = z;
+    return;
+  }
   const int v = static_cast<int>(item / static_cast<uint32_t>(g.n));
   const int i = static_cast<int>(item - static_cast<uint32_t>(v) * static_cast<uint32_t>(g.n));
   Sig4<float> Q;
@@ -403,7 +435,6 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
     st[1] = 1.0f;
     st[2] = radius;
   }
-  float4* d = ipart + 6 * static_cast<size_t>(item);
   d[0] = make_float4(acc.G4[0], acc.G4[1], acc.G4[2], acc.G4[3]);
   d[1] = make_float4(acc.G4[4], acc.G4[5], acc.G4[6], acc.G4[7]);
   d[2] = make_float4(acc.G4[8], acc.G4[9], acc.gmean[0], acc.gmean[1]);
@@ -512,12 +543,13 @@ static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void*
       uint32_t* ilist = at<uint32_t>(frame, L.ilist);
       float4* ipart = at<float4>(frame, L.ipart);
       cudaMemsetAsync(&hdr->n_ilist, 0, sizeof(uint32_t), s);
-      const int nbm = static_cast<int>((L.m + 255) / 256);
-      list_items_kernel<<<nbm, 256, 0, s>>>(touched, static_cast<uint32_t>(L.m), ilist, hdr);
+      const int nbm = static_cast<int>((L.m + 1023) / 1024);
+      list_items_kernel<<<nbm, 1024, 0, s>>>(touched, static_cast<uint32_t>(L.m), ilist, hdr);
       const int nbi = static_cast<int>((L.m + kBwdBlock - 1) / kBwdBlock);
       auto ki = stats ? preprocess_bwd_items_kernel<A, B, true> : preprocess_bwd_items_kernel<A, B, false>;
       ki<<<nbi, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), ilist, at<uint32_t>(frame, L.ioffs), touched,
-                                   at<float4>(frame, L.gbuf), hdr, sh_degree, tc, ipart);
+                                   at<float4>(frame, L.gbuf), at<uint8_t>(frame, L.reach), hdr, sh_degree, tc,
+                                   ipart);
       auto kg = stats ? preprocess_bwd_gauss_kernel<A, true> : preprocess_bwd_gauss_kernel<A, false>;
       kg<<<nb, kBwdBlock, 0, s>>>(g, L.nviews, at<uint32_t>(frame, L.glist), touched, ipart, hdr, sh_degree, out);
       return;
@@ -532,6 +564,7 @@ static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void*
   }
   k<<<nb, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist),
                              at<uint32_t>(frame, L.ioffs), at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf),
+                             at<uint8_t>(frame, L.reach),
                              at<FrameHeader>(frame, L.header), sh_degree, tc, out);
 }
 
