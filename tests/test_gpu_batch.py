@@ -86,11 +86,14 @@ def test_batch_tile_shapes_and_autotune(r4g):
     assert torch.equal(rend.render_batch(p, views).packed, ref)
 
 
-def test_batch_backward_equals_sum_of_views(r4g):
+@pytest.mark.parametrize("fp64", [False, True])
+def test_batch_backward_equals_sum_of_views(r4g, fp64):
+    """Both multi-view backward paths: the two-pass FP32 one (items, then
+    Gaussians) and the one-pass FP64 debug one."""
     g, _, _ = synth.small_scene(seed=43)
     p = to_device(g)
     views = _uneven_views(3, SIZES[:5])
-    rend = r4g.Renderer(bg=(0.2, 0.4, 0.6))
+    rend = r4g.Renderer(bg=(0.2, 0.4, 0.6), flags=r4g.abi.R4G_FLAG_FP64_SLICE if fp64 else 0)
     res = rend.render_batch(p, views)
     w = torch.as_tensor(np.random.default_rng(0).normal(0, 1, res.packed.numel()).astype(np.float32)).cuda()
     gb = _zeros_like(p)
