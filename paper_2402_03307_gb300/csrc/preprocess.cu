@@ -397,23 +397,51 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
                                 const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
                                 const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
                                 bool temporal_cull, float4* __restrict__ ipart) {
+  // Items without a gradient (no pixel composited them) only get a zero
+  // partial; the others are packed to the front of the CTA (their summed
+  // pair gradients through shared memory) so the chain rule runs on full
+  // warps: in a scene whose pixels saturate early most items have none.
+  __shared__ float4 s_g[3][kBwdBlock];
+  __shared__ uint32_t s_item[kBwdBlock];
+  __shared__ uint32_t s_wcnt[kBwdBlock / 32];
   const int j = blockIdx.x * kBwdBlock + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nlist = static_cast<int>(hdr->n_ilist);
-  if ((hdr->status & 1u) || (j - lane) >= nlist) return;  // warp-uniform
+  if ((hdr->status & 1u) || static_cast<int>(blockIdx.x) * kBwdBlock >= nlist) return;  // CTA-uniform
   const bool mine = j < nlist;
-  const uint32_t item = mine ? ilist[j] : 0u;
+  uint32_t item = mine ? ilist[j] : 0u;
   const uint32_t cnt = mine ? touched[item] : 0u;
   const uint32_t o = cnt ? ioffs[item] : 0u;
   float4 ga, gb, gc;
-  const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc);
-  if (!mine) return;
-  float4* d = ipart + 6 * static_cast<size_t>(item);
-  if (!got) {  // no pixel composited the item: a zero partial
+  const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc) && mine;
+  if (mine && !got) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    d[0] = d[1] = d[2] = d[3] = d[4] = d[5] = z;
-    return;
+    float4* dz = ipart + 6 * static_cast<size_t>(item);
+    dz[0] = dz[1] = dz[2] = dz[3] = dz[4] = dz[5] = z;
   }
+  const uint32_t b = __ballot_sync(0xffffffffu, got);
+  if (lane == 0) s_wcnt[warp] = __popc(b);
+  __syncthreads();
+  uint32_t base = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kBwdBlock / 32; ++w) {
+    base += w < warp ? s_wcnt[w] : 0u;
+    total += s_wcnt[w];
+  }
+  if (got) {
+    const uint32_t r = base + __popc(b & ((1u << lane) - 1u));
+    s_item[r] = item;
+    s_g[0][r] = ga;
+    s_g[1][r] = gb;
+    s_g[2][r] = gc;
+  }
+  __syncthreads();
+  if (threadIdx.x >= total) return;
+  item = s_item[threadIdx.x];
+  ga = s_g[0][threadIdx.x];
+  gb = s_g[1][threadIdx.x];
+  gc = s_g[2][threadIdx.x];
+  float4* d = ipart + 6 * static_cast<size_t>(item);
   const int v = static_cast<int>(item / static_cast<uint32_t>(g.n));
   const int i = static_cast<int>(item - static_cast<uint32_t>(v) * static_cast<uint32_t>(g.n));
   Sig4<float> Q;
