@@ -141,7 +141,11 @@ typedef struct r4g_ctx r4g_ctx;
 
 /* Create a context holding a copy of `cfg` (NULL = defaults: 16x16 tiles,
  * black background, degree 3, no flags). The context is not thread-safe;
- * use one per host thread. Returns R4G_EINVAL for an unsupported tile shape. */
+ * use one per host thread. Returns R4G_EINVAL for an unsupported tile shape.
+ * Its first render creates a side stream and two events on the device then
+ * current (the tile counts run there beside the depth sort); later renders
+ * on another device return R4G_EINVAL: use one context per device.
+ * r4g_destroy releases them. */
 r4g_status r4g_create(r4g_ctx** out, const r4g_config* cfg);
 void r4g_destroy(r4g_ctx* ctx);
 /* Message of the last error on this context (static storage, never NULL). */

@@ -21,6 +21,7 @@ struct r4g_ctx {
   // device current then)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  int device = -1;  // the device the side stream belongs to
   bool timing = false;
   struct Pending {
     int stage;
@@ -283,11 +284,18 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   uint32_t* err = &at<FrameHeader>(frame, L.header)->status;
   // fork: the tile counts (ranges and the tile sort's histograms) and the
   // clearing of the tile sort's scratch need only the preprocess's output
-  if (!ctx->side) {
-    if ((e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming)) != cudaSuccess)
-      return cuda_fail(ctx, e, "side stream");
+  {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(ctx, e, "cudaGetDevice");
+    if (!ctx->side) {
+      if ((e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(ctx, e, "side stream");
+      ctx->device = dev;
+    } else if (dev != ctx->device) {
+      return fail(ctx, R4G_EINVAL, "a context renders on the device current at its first render; use one per device");
+    }
   }
   if ((e = cudaEventRecord(ctx->fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0)) != cudaSuccess)
     return cuda_fail(ctx, e, "fork");
