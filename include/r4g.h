@@ -17,8 +17,8 @@
  * Conventions shared by every entry point:
  *  - All buffer pointers are DEVICE pointers unless a parameter says "host".
  *    The caller owns every buffer; the library never frees caller memory and
- *    allocates no device memory (it creates CUDA events only when stage
- *    timing is enabled).
+ *    allocates no device memory (a context creates one side stream and two
+ *    events at its first render, and CUDA events when stage timing is on).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call only enqueues work on that stream; none synchronises, except
  *    r4g_frame_status, which waits for the stream to read the frame's status.
