@@ -311,7 +311,7 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   int which = 0;
   if (has) {
     // depth order of the items: stable sort of the depth bits, values = item index
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 2 + dpasses);  // clear, histogram, passes
     e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
                         at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
                         nullptr, static_cast<uint32_t>(L.m), L.m, 32, at<void>(frame, L.onesweep), err, s, &which);

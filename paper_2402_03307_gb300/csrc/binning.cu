@@ -24,6 +24,8 @@ constexpr int kTileCountsMaxSmem = kMaxTiles * 4;
 __global__ void __launch_bounds__(kPreBlock)
     depth_blocksum_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, int n,
                           uint32_t* __restrict__ blocksum) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ uint32_t s_sum[kPreBlock / 32];
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const uint32_t c = j < n ? touched[order[j]] : 0u;
@@ -42,6 +44,8 @@ __global__ void __launch_bounds__(kPreBlock)
 // count and the overflow flag into the frame header.
 __global__ void __launch_bounds__(kScanThreads)
     scan_blocksums_kernel(uint32_t* blocksum, int nblocks, FrameHeader* hdr, uint32_t cap) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -94,6 +98,8 @@ __global__ void __launch_bounds__(kPreBlock)
                          const ViewDev* __restrict__ views, uint32_t ng, int m, uint32_t* __restrict__ offs,
                          uint32_t* __restrict__ ioffs, uint4* __restrict__ srect, uint32_t* __restrict__ chunk_start,
                          uint32_t nchunks) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ uint32_t s_warp[kPreBlock / 32];
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -139,6 +145,8 @@ __global__ void __launch_bounds__(kPreBlock)
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
                 const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
                 uint32_t* __restrict__ ident) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ uint32_t s_off[kEmitChunk + 1];
   const uint32_t K = hdr->key_count;
   // grid-stride over the output chunks: the grid is sized for the device,
@@ -304,23 +312,25 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   uint4* srect = at<uint4>(frame, L.srect);
   uint32_t* cstart = at<uint32_t>(frame, L.chunks);
   const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
-  depth_blocksum_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, m, bs);
-  scan_blocksums_kernel<<<1, kScanThreads, 0, s>>>(bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
-  depth_offsets_kernel<<<L.nblocks, kPreBlock, 0, s>>>(touched, order, bs, at<uint2>(frame, L.rect),
-                                                        at<ViewDev>(frame, L.views), static_cast<uint32_t>(L.n), m,
-                                                        offs, at<uint32_t>(frame, L.ioffs), srect, cstart,
-                                                        static_cast<uint32_t>(chunks));
+  cudaError_t e = launch_pdl(depth_blocksum_kernel, L.nblocks, kPreBlock, 0, s, touched, order, m, bs);
+  if (e == cudaSuccess)
+    e = launch_pdl(scan_blocksums_kernel, 1, kScanThreads, 0, s, bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
+  if (e == cudaSuccess)
+    e = launch_pdl(depth_offsets_kernel, L.nblocks, kPreBlock, 0, s, touched, order,
+                   static_cast<const uint32_t*>(bs), static_cast<const uint2*>(at<uint2>(frame, L.rect)),
+                   static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)), static_cast<uint32_t>(L.n), m, offs,
+                   at<uint32_t>(frame, L.ioffs), srect, cstart, static_cast<uint32_t>(chunks));
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t egrid = chunks < 8LL * sms ? chunks : 8LL * sms;  // eight 256-thread CTAs per SM
   if (chunks > 0)
-    emit_kernel<<<static_cast<unsigned>(egrid), kPreBlock, 0, s>>>(offs, srect, order, cstart, m, hdr,
-                                                                     at<uint32_t>(frame, L.keys0),
-                                                                     at<uint32_t>(frame, L.egid),
-                                                                     L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0)
-                                                                                      : nullptr);
-  return cudaGetLastError();
+    e = launch_pdl(emit_kernel, static_cast<unsigned>(egrid), kPreBlock, 0, s, static_cast<const uint32_t*>(offs),
+                   static_cast<const uint4*>(srect), order, static_cast<const uint32_t*>(cstart), m,
+                   static_cast<const FrameHeader*>(hdr), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.egid),
+                   L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0) : nullptr);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s) {

@@ -393,6 +393,8 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
                      float bg0, float bg1, float bg2, float* __restrict__ out_rgb, float* __restrict__ out_T,
                      uint32_t* __restrict__ out_stop, uint32_t* __restrict__ out_last,
                      unsigned long long* __restrict__ pair_count) {
+  griddep_wait();
+  griddep_launch_dependents();
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ int s_tile;
   for (;;) {
@@ -725,15 +727,16 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   const ViewDev* views = at<ViewDev>(frame, L.views);
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                          \
-  blend_fwd_kernel<TW_, TH_, LAST_>                                                                         \
-      <<<persistent_ctas(blend_fwd_kernel<TW_, TH_, LAST_>, Blend<TW_, TH_>::NT, 0, L.ntiles),                \
-         Blend<TW_, TH_>::NT, 0, s>>>(ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),      \
-                                     static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], bg[1], \
-                                     bg[2], out_rgb, T, stop, out_last, pairs)
+  e = launch_pdl(blend_fwd_kernel<TW_, TH_, LAST_>,                                                         \
+                 persistent_ctas(blend_fwd_kernel<TW_, TH_, LAST_>, Blend<TW_, TH_>::NT, 0, L.ntiles),        \
+                 Blend<TW_, TH_>::NT, 0, s, ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),    \
+                 static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], bg[1], bg[2], out_rgb, T,   \
+                 stop, out_last, pairs)
   const uint32_t* egid = at<uint32_t>(frame, L.egid);
   // the instrumented variant serves both the last-contributor output and the pair count
   const bool lst = out_last != nullptr || count;
   unsigned long long* pairs = &hdr->composited;
+  cudaError_t e = cudaSuccess;
   if (L.tile_w == 16 && L.tile_h == 16) {
     if (lst) R4G_BLEND(16, 16, true); else R4G_BLEND(16, 16, false);
   } else if (L.tile_w == 8 && L.tile_h == 8) {
@@ -744,6 +747,7 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
     return cudaErrorInvalidValue;
   }
 #undef R4G_BLEND
+  if (e != cudaSuccess) return e;
   if (out_T) cudaMemcpyAsync(out_T, T, static_cast<size_t>(L.npix) * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return cudaGetLastError();
 }

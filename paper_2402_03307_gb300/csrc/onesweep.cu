@@ -53,6 +53,8 @@ __device__ __forceinline__ void store_relaxed(uint32_t* p, uint32_t v) {
 __global__ void __launch_bounds__(kSortThreads)
     onesweep_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
                          int passes, int bits, uint32_t* __restrict__ hist) {
+  griddep_wait();
+  griddep_launch_dependents();
   constexpr int NS = kSortThreads / 64;  // sub-histograms
   __shared__ uint32_t s_h[NS][4][kSortRadix];
   for (int k = threadIdx.x; k < NS * 4 * kSortRadix; k += kSortThreads) (&s_h[0][0][0])[k] = 0;
@@ -102,6 +104,8 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ uint32_t s_scan[NW];
   __shared__ uint32_t s_k[kOsTile];
   __shared__ uint32_t s_v[kOsTile];
+  griddep_wait();
+  griddep_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   {
@@ -256,6 +260,25 @@ __global__ void __launch_bounds__(kSortThreads)
   }
 }
 
+// Clears what the passes expect at zero (instead of a memset, so that the
+// sort's kernels follow one another with programmatic launches): the
+// histograms unless the caller filled them, the tickets, and each pass's
+// look-back statuses for the tiles the item count needs.
+__global__ void onesweep_zero_kernel(uint32_t* __restrict__ hist, int hist_words, uint32_t* __restrict__ tickets,
+                                     uint32_t* __restrict__ status, size_t pass_words, int passes,
+                                     const uint32_t* count_dev, uint32_t count_host) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const uint32_t n = count_dev ? *count_dev : count_host;
+  const size_t words = static_cast<size_t>((n + kOsTile - 1) / kOsTile) * kSortRadix;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  const size_t i0 = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int p = 0; p < passes; ++p)
+    for (size_t i = i0; i < words; i += stride) status[p * pass_words + i] = 0u;
+  if (i0 < 32) tickets[i0] = 0u;
+  for (size_t i = i0; i < static_cast<size_t>(hist_words); i += stride) hist[i] = 0u;
+}
+
 size_t onesweep_scratch_bytes(int64_t cap, int bits) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   const int64_t tiles = (cap + kOsTile - 1) / kOsTile;
@@ -287,13 +310,18 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
   // the histograms either come ready (filled by the caller's kernels) or are
   // counted here; tickets and statuses always start at zero (cleared here
   // unless the caller did it with prepare_onesweep)
+  const size_t pass_words = static_cast<size_t>(tiles) * kSortRadix;
   if (!prepared) {
-    const cudaError_t e = prepare_onesweep(scratch, cap, bits, hist_ready, s);
+    const cudaError_t e =
+        launch_pdl(onesweep_zero_kernel, kOsHistCtas, kSortThreads, 0, s, hist, hist_ready ? 0 : passes * kSortRadix,
+                   tickets, status, pass_words, passes, count_dev, count_host);
     if (e != cudaSuccess) return e;
   }
   if (!hist_ready) {
     const int hist_ctas = static_cast<int>(tiles < kOsHistCtas ? tiles : kOsHistCtas);
-    onesweep_hist_kernel<<<hist_ctas, kSortThreads, 0, s>>>(kin, count_dev, count_host, passes, bits, hist);
+    const cudaError_t e = launch_pdl(onesweep_hist_kernel, hist_ctas, kSortThreads, 0, s, kin, count_dev, count_host,
+                                     passes, bits, hist);
+    if (e != cudaSuccess) return e;
   }
   const uint32_t* ki = kin;
   const uint32_t* vi = vin;
@@ -303,9 +331,11 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
     const int nb = min(kSortRadixBits, bits - shift);
     uint32_t* ko = (which == 1) ? kbuf2 : kbuf1;
     uint32_t* vo = (which == 1) ? vbuf2 : vbuf1;
-    onesweep_pass_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-        ki, vi, ko, vo, count_dev, count_host, shift, (1u << nb) - 1u, hist + p * kSortRadix,
-        status + static_cast<size_t>(p) * tiles * kSortRadix, tickets + p, err);
+    const cudaError_t e =
+        launch_pdl(onesweep_pass_kernel, static_cast<unsigned>(tiles), kSortThreads, 0, s, ki, vi, ko, vo, count_dev,
+                   count_host, shift, (1u << nb) - 1u, static_cast<const uint32_t*>(hist + p * kSortRadix),
+                   status + static_cast<size_t>(p) * pass_words, tickets + p, err);
+    if (e != cudaSuccess) return e;
     ki = ko;
     vi = vo;
     which = (which == 1) ? 2 : 1;

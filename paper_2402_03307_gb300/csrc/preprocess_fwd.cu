@@ -100,6 +100,8 @@ template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
 __global__ void __launch_bounds__(kPreBlock)
     preprocess_fwd_kernel(r4g_gaussians g, ViewDev* __restrict__ views, int nviews, OneView one, PreOut out,
                           int sh_degree, bool temporal_cull, bool flow) {
+  // the next kernel of the render (the depth sort's) may launch now and wait
+  griddep_launch_dependents();
   if constexpr (!kMulti) nviews = 1;
   __shared__ uint32_t s_pairs[kMaxViews];
   __shared__ uint32_t s_wcnt[kPreBlock / 32];

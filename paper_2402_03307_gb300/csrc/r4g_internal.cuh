@@ -2,6 +2,8 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "r4g.h"
@@ -116,6 +118,34 @@ __device__ __forceinline__ float gauss_power(const float4& A, float c, float fx,
   q = __fmaf_rn(__fmul_rn(c, dy), dy, q);
   const float cross = __fmul_rn(__fmul_rn(A.w, dx), dy);
   return __fmaf_rn(-0.5f, q, -cross);
+}
+
+// ---- programmatic dependent launch ---------------------------------------------
+// The render's kernels follow one another on one stream. Launched with
+// launch_pdl, a kernel is scheduled while its predecessor finishes (the
+// predecessor lets its dependents launch as soon as all its CTAs have
+// started: griddep_launch_dependents); it then waits in griddep_wait, before
+// touching any memory, until the predecessor has completed and its writes
+// are visible. Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <typename T>
