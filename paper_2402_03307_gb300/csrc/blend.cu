@@ -685,6 +685,10 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT)
                      float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
                      const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
                      float4* __restrict__ gbuf, uint8_t* __restrict__ reach) {
+  griddep_wait();
+  griddep_launch_dependents();
+  // the multi-view preprocess backward that follows lists its items anew
+  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->n_ilist = 0u;
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
   __shared__ uint32_t sTook[Blend<TW, TH>::NT];  // per batch entry: warps that composited it
@@ -772,18 +776,19 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
     const size_t slab = sizeof(float) * 9 * Blend<TW_, TH_>::NW * Blend<TW_, TH_>::NT;                   \
     cudaFuncSetAttribute(blend_bwd_kernel<TW_, TH_>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
                          static_cast<int>(slab));                                                         \
-    blend_bwd_kernel<TW_, TH_>                                                                            \
-        <<<persistent_ctas(blend_bwd_kernel<TW_, TH_>, Blend<TW_, TH_>::NT, slab, L.ntiles),              \
-           Blend<TW_, TH_>::NT, slab, s>>>(ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),  \
-                                           static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], \
-                                           bg[1], bg[2], T, stop, grad_rgb, gbuf, reach);                 \
+    e = launch_pdl(blend_bwd_kernel<TW_, TH_>,                                                            \
+                   persistent_ctas(blend_bwd_kernel<TW_, TH_>, Blend<TW_, TH_>::NT, slab, L.ntiles),      \
+                   Blend<TW_, TH_>::NT, slab, s, ranges, vals, recA, recB, recC, egid,                    \
+                   static_cast<uint32_t>(L.m), static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, \
+                   bg[0], bg[1], bg[2], T, stop, grad_rgb, gbuf, reach);                                  \
   }
+  cudaError_t e = cudaSuccess;
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16)
   else if (L.tile_w == 8 && L.tile_h == 8) R4G_BLEND_BWD(8, 8)
   else if (L.tile_w == 16 && L.tile_h == 32) R4G_BLEND_BWD(16, 32)
   else return cudaErrorInvalidValue;
 #undef R4G_BLEND_BWD
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace r4g

@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
                           const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
                           const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
                           bool temporal_cull, r4g_grads out) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int j = blockIdx.x * kBwdBlock + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int nlist = static_cast<int>(hdr->n_glist);
@@ -366,6 +368,8 @@ constexpr int kPartFloats = 24;  // d Sigma4 (10), d mean (4), d opacity, dir (3
 __global__ void __launch_bounds__(1024)
     list_items_kernel(const uint32_t* __restrict__ touched, uint32_t m, uint32_t* __restrict__ ilist,
                       FrameHeader* hdr) {
+  griddep_wait();
+  griddep_launch_dependents();
   // one counter update per CTA (per warp, 16M items made the counter the bottleneck)
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_base;
@@ -397,6 +401,8 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
                                 const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
                                 const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
                                 bool temporal_cull, float4* __restrict__ ipart) {
+  griddep_wait();
+  griddep_launch_dependents();
   // Items without a gradient (no pixel composited them) only get a zero
   // partial; the others are packed to the front of the CTA (their summed
   // pair gradients through shared memory) so the chain rule runs on full
@@ -476,6 +482,8 @@ __global__ void __launch_bounds__(kBwdBlock)
     preprocess_bwd_gauss_kernel(r4g_gaussians g, int nviews, const uint32_t* __restrict__ glist,
                                 const uint32_t* __restrict__ touched, const float4* __restrict__ ipart,
                                 const FrameHeader* hdr, int sh_degree, r4g_grads out) {
+  griddep_wait();
+  griddep_launch_dependents();
   const int j = blockIdx.x * kBwdBlock + threadIdx.x;
   const int nlist = static_cast<int>(hdr->n_glist);
   if ((hdr->status & 1u) || j >= nlist) return;
@@ -570,16 +578,19 @@ static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void*
       const uint32_t* touched = at<uint32_t>(frame, L.touched);
       uint32_t* ilist = at<uint32_t>(frame, L.ilist);
       float4* ipart = at<float4>(frame, L.ipart);
-      cudaMemsetAsync(&hdr->n_ilist, 0, sizeof(uint32_t), s);
+      // (the blend backward zeroed the item counter)
       const int nbm = static_cast<int>((L.m + 1023) / 1024);
-      list_items_kernel<<<nbm, 1024, 0, s>>>(touched, static_cast<uint32_t>(L.m), ilist, hdr);
+      launch_pdl(list_items_kernel, nbm, 1024, 0, s, touched, static_cast<uint32_t>(L.m), ilist, hdr);
       const int nbi = static_cast<int>((L.m + kBwdBlock - 1) / kBwdBlock);
       auto ki = stats ? preprocess_bwd_items_kernel<A, B, true> : preprocess_bwd_items_kernel<A, B, false>;
-      ki<<<nbi, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), ilist, at<uint32_t>(frame, L.ioffs), touched,
-                                   at<float4>(frame, L.gbuf), at<uint8_t>(frame, L.reach), hdr, sh_degree, tc,
-                                   ipart);
+      launch_pdl(ki, nbi, kBwdBlock, 0, s, g, static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)),
+                 static_cast<const uint32_t*>(ilist), static_cast<const uint32_t*>(at<uint32_t>(frame, L.ioffs)),
+                 touched, static_cast<const float4*>(at<float4>(frame, L.gbuf)),
+                 static_cast<const uint8_t*>(at<uint8_t>(frame, L.reach)), static_cast<const FrameHeader*>(hdr),
+                 sh_degree, tc, ipart);
       auto kg = stats ? preprocess_bwd_gauss_kernel<A, true> : preprocess_bwd_gauss_kernel<A, false>;
-      kg<<<nb, kBwdBlock, 0, s>>>(g, L.nviews, at<uint32_t>(frame, L.glist), touched, ipart, hdr, sh_degree, out);
+      launch_pdl(kg, nb, kBwdBlock, 0, s, g, L.nviews, static_cast<const uint32_t*>(at<uint32_t>(frame, L.glist)),
+                 touched, static_cast<const float4*>(ipart), static_cast<const FrameHeader*>(hdr), sh_degree, out);
       return;
     }
   }
@@ -590,10 +601,13 @@ static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void*
   if constexpr (sizeof(S) != sizeof(float)) {
     if (L.nviews > 1) k = stats ? preprocess_bwd_kernel<S, A, B, true, true> : preprocess_bwd_kernel<S, A, B, true, false>;
   }
-  k<<<nb, kBwdBlock, 0, s>>>(g, at<ViewDev>(frame, L.views), L.nviews, at<uint32_t>(frame, L.glist),
-                             at<uint32_t>(frame, L.ioffs), at<uint32_t>(frame, L.touched), at<float4>(frame, L.gbuf),
-                             at<uint8_t>(frame, L.reach),
-                             at<FrameHeader>(frame, L.header), sh_degree, tc, out);
+  launch_pdl(k, nb, kBwdBlock, 0, s, g, static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)), L.nviews,
+             static_cast<const uint32_t*>(at<uint32_t>(frame, L.glist)),
+             static_cast<const uint32_t*>(at<uint32_t>(frame, L.ioffs)),
+             static_cast<const uint32_t*>(at<uint32_t>(frame, L.touched)),
+             static_cast<const float4*>(at<float4>(frame, L.gbuf)),
+             static_cast<const uint8_t*>(at<uint8_t>(frame, L.reach)),
+             static_cast<const FrameHeader*>(at<FrameHeader>(frame, L.header)), sh_degree, tc, out);
 }
 
 cudaError_t launch_preprocess_bwd(const r4g_gaussians& g, const FrameLayout& L, void* frame, int sh_degree,
