@@ -169,17 +169,17 @@ __global__ void __launch_bounds__(kSortThreads)
   }
   s_tcount[dd] = cnt;
   // ---- publish the tile's count, then look back for its exclusive prefix
+  // (a digit no item of the pass has -- the histogram says so -- needs no
+  // status and no look-back: its count is zero in every tile)
+  const uint32_t h = hist[dd];
+  const bool live = h != 0u;
   uint32_t* st = status + static_cast<size_t>(t) * kSortRadix;
-  if (t == 0) {
-    store_relaxed(st + dd, kFlagPrefix | cnt);
-  } else {
-    store_relaxed(st + dd, kFlagAgg | cnt);
-  }
+  if (live) store_relaxed(st + dd, (t == 0 ? kFlagPrefix : kFlagAgg) | cnt);
   // Look-back, kOsWin predecessors per round (their statuses are read in
   // parallel): add published counts newest first until a published prefix;
   // a round that makes no progress counts against the spin limit.
   uint32_t excl = 0;
-  if (t > 0) {
+  if (t > 0 && live) {
     constexpr int WIN = kOsWin;
     int64_t kt = static_cast<int64_t>(t) - 1;
     uint32_t idle = 0, nap = 32u;
@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(kSortThreads)
   }
   // global digit start: exclusive scan of this pass's histogram (+ tile prefix)
   {
-    const uint32_t h = hist[dd];
     uint32_t x = h;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
