@@ -133,3 +133,22 @@ def test_density_argument_checks(lib):
     assert lib.r4g_opacity_reset(256, 10, 1.0, None) == abi.R4G_EINVAL
     assert lib.r4g_opacity_reset(None, 10, 0.01, None) == abi.R4G_EINVAL
     assert lib.r4g_opacity_reset(None, 0, 0.01, None) == abi.R4G_OK
+
+
+def test_frame_status_decode(lib):
+    """r4g_frame_status_decode is host logic: the three status words of a frame
+    (status bits, key count, keys needed) to the r4g_frame_status result."""
+    from paper_2402_03307_gb300 import abi
+    words = (C.c_uint32 * 3)(0, 1000, 1000)
+    need = C.c_int64()
+    assert lib.r4g_frame_status_decode(words, C.byref(need)) == abi.R4G_OK and need.value == 1000
+    words[0], words[2] = 1, 5000
+    assert lib.r4g_frame_status_decode(words, C.byref(need)) == abi.R4G_EOVERFLOW and need.value == 5000
+    assert b"capacity" in lib.r4g_last_error(None)
+    words[0] = 2
+    assert lib.r4g_frame_status_decode(words, None) == abi.R4G_ETIMEOUT
+    words[0] = 4
+    assert lib.r4g_frame_status_decode(words, None) == abi.R4G_EDEVICE
+    assert lib.r4g_frame_status_decode(None, None) == abi.R4G_EINVAL
+    assert lib.r4g_frame_status_async(None, 1 << 20, 256, None) == abi.R4G_EINVAL
+    assert lib.r4g_frame_status_async(256, 16, 256, None) == abi.R4G_EWORKSPACE
