@@ -210,3 +210,24 @@ def test_opacity_reset(r4g):
     r4g.opacity_reset(p, 0.01)
     torch.cuda.synchronize()
     assert np.array_equal(p["logit"].cpu().numpy(), od.opacity_reset(g["logit"], 0.01))
+
+
+def test_statistics_through_autograd(r4g):
+    """A renderer with density statistics attached keeps them through the
+    autograd functions (one-view and batched), as a training loop would."""
+    g, cam, t = synth.small_scene(seed=2, n=500, width=64, height=64)
+    p = to_device(g)
+    leaves = {k: v.clone().requires_grad_(True) for k, v in p.items()}
+    w = torch.as_tensor(_weights(g, cam, t, 5)).cuda()
+    rend = r4g.Renderer()
+    rend.density = r4g.density_stats(500, "cuda")
+    (r4g.render(leaves, cam, t, renderer=rend) * w).sum().backward()
+    ref = od.view_stats(oracle.to_f64(g), cam, t, w.cpu().numpy())
+    got = {k: v.double().cpu().numpy() for k, v in rend.density.items()}
+    _compare_stats(got, ref, 500)
+    # batched: two views add two counts where both composite a Gaussian
+    rend.density = r4g.density_stats(500, "cuda")
+    views = [(cam, t), (synth.look_at((1.0, 0.0, -4.0), (0, 0, 0), 64, 64), t)]
+    packed = r4g.render_batch(leaves, views, renderer=rend)
+    packed.sum().backward()
+    assert float(rend.density["vs_count"].max()) == 2.0
