@@ -97,20 +97,26 @@ struct OneView {
 };
 
 template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
-__global__ void __launch_bounds__(kPreBlock)
+__global__ void __launch_bounds__(kPreFwdBlock)
     preprocess_fwd_kernel(r4g_gaussians g, ViewDev* __restrict__ views, int nviews, OneView one, PreOut out,
                           int sh_degree, bool temporal_cull, bool flow) {
   // the next kernel of the render (the depth sort's) may launch now and wait
   griddep_launch_dependents();
   if constexpr (!kMulti) nviews = 1;
   __shared__ uint32_t s_pairs[kMaxViews];
-  __shared__ uint32_t s_wcnt[kPreBlock / 32];
+  __shared__ uint32_t s_wcnt[kPreFwdBlock / 32];
   __shared__ uint32_t s_vis, s_base;
   __shared__ __align__(16) ViewDev s_views[kMaxViews];  // the view table (copied as 16-byte words)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = threadIdx.x; v < kMaxViews; v += kPreBlock) s_pairs[v] = 0;
+  for (int v = threadIdx.x; v < kMaxViews; v += kPreFwdBlock) s_pairs[v] = 0;
+  // the view-independent part first: its loads and Sigma4 overlap the
+  // building of the view table
+  const int i = blockIdx.x * kPreFwdBlock + threadIdx.x;
+  const bool live = i < g.n;
+  Sig4<S> G;
+  if (live) gauss_sigma<S, kScaleBF16>(g, i, G);
   if constexpr (kMulti) {
-    for (int k = threadIdx.x; k < nviews * 8; k += kPreBlock)
+    for (int k = threadIdx.x; k < nviews * 8; k += kPreFwdBlock)
       reinterpret_cast<uint4*>(s_views)[k] = reinterpret_cast<const uint4*>(views)[k];
   } else if (threadIdx.x == 0) {
     const ViewDev d = make_view(one.vdev ? one.vdev[0] : one.v, one.g, blockIdx.x == 0 ? out.header : nullptr);
@@ -119,10 +125,6 @@ __global__ void __launch_bounds__(kPreBlock)
   }
   if (threadIdx.x == 0) s_vis = 0;
   __syncthreads();
-  const int i = blockIdx.x * kPreBlock + threadIdx.x;
-  const bool live = i < g.n;
-  Sig4<S> G;
-  if (live) gauss_sigma<S, kScaleBF16>(g, i, G);
   uint32_t nvis = 0;
   const size_t M = static_cast<size_t>(g.n) * nviews;
   for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kPreBlock)
   if (threadIdx.x == 0) {
     uint32_t tot = 0;
 #pragma unroll
-    for (int w = 0; w < kPreBlock / 32; ++w) {
+    for (int w = 0; w < kPreFwdBlock / 32; ++w) {
       const uint32_t c = s_wcnt[w];
       s_wcnt[w] = tot;
       tot += c;
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kPreBlock)
     s_base = tot ? atomicAdd(&out.header->n_glist, tot) : 0u;
     if (s_vis) atomicAdd(&out.header->n_visible, s_vis);
   }
-  for (int v = threadIdx.x; v < nviews; v += kPreBlock)
+  for (int v = threadIdx.x; v < nviews; v += kPreFwdBlock)
     if (s_pairs[v]) atomicAdd(&out.header->view_pairs[v], s_pairs[v]);
   __syncthreads();
   if (nvis > 0) out.glist[s_base + s_wcnt[warp] + __popc(lm & ((1u << lane) - 1u))] = static_cast<uint32_t>(i);
@@ -200,9 +202,9 @@ template <typename S, bool A, bool B>
 static void launch_pre_t(const r4g_gaussians& g, ViewDev* views, int nviews, const OneView& one, const PreOut& o,
                          int nblocks, int sh_degree, bool tc, bool fl, cudaStream_t s) {
   if (nviews > 1)
-    preprocess_fwd_kernel<S, A, B, true><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc, fl);
+    preprocess_fwd_kernel<S, A, B, true><<<nblocks, kPreFwdBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc, fl);
   else
-    preprocess_fwd_kernel<S, A, B, false><<<nblocks, kPreBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc,
+    preprocess_fwd_kernel<S, A, B, false><<<nblocks, kPreFwdBlock, 0, s>>>(g, views, nviews, one, o, sh_degree, tc,
                                                                          fl);
 }
 
@@ -238,7 +240,7 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
   const bool fl = (flags & R4G_FLAG_FLOW) != 0;
   const bool f64 = flags & R4G_FLAG_FP64_SLICE;
   const bool sb = g.scale_dtype == R4G_BF16, hb = g.sh_dtype == R4G_BF16;
-  const int nb = static_cast<int>((L.n + kPreBlock - 1) / kPreBlock);
+  const int nb = static_cast<int>((L.n + kPreFwdBlock - 1) / kPreFwdBlock);
 #define R4G_PF(S_, A_, B_) launch_pre_t<S_, A_, B_>(g, views, L.nviews, one, o, nb, sh_degree, tc, fl, s)
   if (f64) {
     if (sb && hb) R4G_PF(double, true, true);
