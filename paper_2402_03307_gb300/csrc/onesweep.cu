@@ -99,7 +99,6 @@ __global__ void __launch_bounds__(kSortThreads)
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_dstart[kSortRadix];   // global start of each digit + tile prefix
   __shared__ uint32_t s_tstart[kSortRadix];   // tile-local start of each digit
-  __shared__ uint32_t s_tcount[kSortRadix];
   __shared__ uint32_t s_whist[NW][kSortRadix];
   __shared__ uint32_t s_scan[NW];
   __shared__ uint32_t s_k[kOsTile];
@@ -167,7 +166,6 @@ __global__ void __launch_bounds__(kSortThreads)
     s_whist[w][dd] = cnt;
     cnt += c;
   }
-  s_tcount[dd] = cnt;
   // ---- publish the tile's count, then look back for its exclusive prefix
   // (a digit no item of the pass has -- the histogram says so -- needs no
   // status and no look-back: its count is zero in every tile)
