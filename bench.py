@@ -569,7 +569,8 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
         run_loss()
     ms_loss = _timed(run_loss, 20, stream, flush)
     dens = densify_bench(params, dev, stream, flush)
-    return {"densify": dens,
+    inside = inside_sweep_bench(params, dev, stream, flush)
+    return {"densify": dens, "inside_sweep": inside,
             "image_loss": {"ms": round(ms_loss, 3), "what": "0.8 L1 + 0.2 (1 - SSIM) and its gradient, 3x1014x1352",
                            "note": "includes scratch allocation by the Python wrapper"},
             "flow": {"value": round(1000.0 / ms_flow, 1), "unit": "frames/s",
@@ -578,6 +579,50 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
                       "note": "includes scratch allocation by the Python wrapper"},
             "regularizers": {"ms": round(ms_reg, 3), "n": N_GAUSS,
                              "what": "entropy + 4D consistency losses and their gradients"}}
+
+
+def inside_sweep_bench(params, dev, stream, flush, radius: float = 4.0, stride: int = 3):
+    """The same sweep at orbit radius 4 (the camera inside the cloud, a heavier
+    tile load): every third frame, key buffer sized over those frames, L2
+    flushed between frames, per-stage live times."""
+    import torch
+    import paper_2402_03307_gb300 as r4g
+    from paper_2402_03307_gb300 import abi
+    import synth
+
+    ks = list(range(0, FRAMES, stride))
+    cams = [synth.orbit_camera(k, FRAMES, radius, WIDTH, HEIGHT) for k in ks]
+    rend = r4g.Renderer()
+    need = 0
+    for cam, t in cams:
+        need = max(need, rend.status(rend.render(params, cam, t))[1])
+    cap = int(need * 1.1) + 1024
+    frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    it = {"k": 0}
+
+    def one():
+        cam, t = cams[it["k"] % len(cams)]
+        it["k"] += 1
+        rend.render(params, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    it["k"] = 0
+    abi.r4g_stage_times(rend.ctx, reset=True)
+    abi.r4g_set_timing(rend.ctx, True)
+    ms = _timed(one, len(cams), stream, flush)
+    abi.r4g_set_timing(rend.ctx, False)
+    stage_ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
+    keys = 0
+    for cam, t in cams:
+        keys += rend.status(rend.render(params, cam, t, frame=frame, key_capacity=cap, out=img))[1]
+    return {"value": round(1000.0 / ms, 1), "unit": "frames/s", "frames": len(cams),
+            "keys_per_frame": round(keys / len(cams)),
+            "stage_ms": {k: round(v / len(cams), 4) for k, v in stage_ms.items() if v > 0},
+            "workload": f"300k sweep at orbit radius {radius:g} (camera inside the cloud), every "
+                        f"{stride}rd frame, FP32, 1 view/launch"}
 
 
 def densify_bench(params, dev, stream, flush):

@@ -14,10 +14,11 @@
 //   power = -1/2 d^T conic d, skip if power > 0 or power < -4.5,
 //   alpha = min(0.99, opacity_t exp(power)), skip if alpha < 1/255,
 //   stop before a Gaussian that would take T below 1e-4.
-// The exponent is evaluated in base 2 (power' = log2(e) power, alpha =
-// opacity_t 2^power'). The cutoff and the 1/255 rule form one window
-// pmin <= power' <= 0, pmin = max(-4.5 log2 e, -log2(255 opacity_t)),
-// tested as |(power' - mid) / half| <= 1. A pixel that stops moves to
+// The exponent is evaluated in base 2 with the opacity folded in
+// (power' = log2(e) power, alpha = 2^(power' + log2 opacity_t)). The cutoff
+// and the 1/255 rule form one window pmin <= power' <= 0,
+// pmin = max(-4.5 log2 e, -log2(255 opacity_t)), tested on the shifted
+// exponent as |(power' + log2 opacity_t - mid - log2 opacity_t) / half| <= 1. A pixel that stops moves to
 // infinity, so no later Gaussian reaches it; a warp whose pixels have all
 // stopped leaves the batch, a CTA whose pixels have all stopped leaves the
 // tile. The forward and the backward call the same evaluator, so they take
@@ -62,9 +63,11 @@ struct Blend {
 
 // A staged Gaussian (128-byte slot), operands duplicated for the packed pairs:
 //   p0 = (-mx, -mx, -my, -my)     p1 = (A', A', B', B')
-//   p2 = (C', C', o, o)           p3 = (r, r, g, g)
-//   p4 = (b, b, ih, ih)           p5 = (nm, nm, mask bits, 0)
-// with power' = A' dx^2 + B' dx dy + C' dy^2, ih = 1 / half, nm = -mid / half.
+//   p2 = (C', C', lo, lo)         p3 = (r, r, g, g)
+//   p4 = (b, b, ih, ih)           p5 = (nm, nm, mask bits, o)
+// with power' = A' dx^2 + B' dx dy + C' dy^2, lo = log2 o (the opacity enters
+// the exponent: alpha = 2^(power' + lo)), ih = 1 / half, nm = -(mid + lo) / half
+// (the window on power' shifted by lo).
 struct __align__(128) StagedG {
   float4 p0, p1, p2, p3, p4, p5;
   float4 pad0, pad1;  // 128-byte stride: the entry address is a shift
@@ -112,7 +115,8 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   const float Ap = -0.5f * kLog2e * A.z, Bp = -kLog2e * A.w, Cp = -0.5f * kLog2e * Bv.x, o = Bv.y;
   const float pmin = fmaxf(kCut2, -log2f(255.0f * o));
   const float mid = 0.5f * pmin, half = fmaxf(-0.5f * pmin, 1e-6f);
-  const float ih = 1.0f / half, nm = -mid * ih;
+  const float lo = fmaxf(log2f(o), -126.0f);
+  const float ih = 1.0f / half, nm = -(mid + lo) * ih;
   uint32_t m = o > kAlphaMax ? kClampBit : 0u;
 #pragma unroll
   for (int w = 0; w < B::NW; ++w) {  // pixel centres of warp w's block
@@ -122,16 +126,17 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   }
   sg->p0 = make_float4(-A.x, -A.x, -A.y, -A.y);
   sg->p1 = make_float4(Ap, Ap, Bp, Bp);
-  sg->p2 = make_float4(Cp, Cp, o, o);
+  sg->p2 = make_float4(Cp, Cp, lo, lo);
   sg->p3 = make_float4(C.x, C.x, C.y, C.y);
   sg->p4 = make_float4(C.z, C.z, ih, ih);
-  sg->p5 = make_float4(nm, nm, __uint_as_float(m), 0.0f);
+  sg->p5 = make_float4(nm, nm, __uint_as_float(m), o);
 }
 
 // Evaluation of one staged Gaussian at the thread's Q pixel pairs (PX[q],
-// py): power', 2^power', opacity_t 2^power' and whether the window takes it,
-// every rounding explicit. dy and the row terms B' dy and C' dy^2 are shared
-// by the pairs (they are the same numbers a pair alone would compute).
+// py): power' + log2 opacity_t, alpha = 2^(power' + log2 opacity_t) before the
+// clamp, and whether the window takes it, every rounding explicit. dy and the
+// row terms B' dy and C' dy^2 + log2 opacity_t are shared by the pairs (they
+// are the same numbers a pair alone would compute).
 template <int Q>
 struct PairEval {
   float2 araw[Q], dx[Q];
@@ -144,15 +149,14 @@ __device__ __forceinline__ void eval_pairs(const StagedG& g, const float2 (&PX)[
   const float4 p0 = g.p0, p1 = g.p1, p2 = g.p2, p4 = g.p4, p5 = g.p5;
   const float2 dy = __fadd2_rn(PY, make_float2(p0.z, p0.w));
   const float2 bdy = __fmul2_rn(make_float2(p1.z, p1.w), dy);
-  const float2 u = __fmul2_rn(__fmul2_rn(make_float2(p2.x, p2.y), dy), dy);
+  const float2 u = __ffma2_rn(__fmul2_rn(make_float2(p2.x, p2.y), dy), dy, make_float2(p2.z, p2.w));
   r.dy = dy.x;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     r.dx[q] = __fadd2_rn(PX[q], make_float2(p0.x, p0.y));
     const float2 t = __ffma2_rn(make_float2(p1.x, p1.y), r.dx[q], bdy);
     const float2 p = __ffma2_rn(r.dx[q], t, u);
-    const float2 e = make_float2(ex2_approx(p.x), ex2_approx(p.y));
-    r.araw[q] = __fmul2_rn(make_float2(p2.z, p2.w), e);
+    r.araw[q] = make_float2(ex2_approx(p.x), ex2_approx(p.y));
     const float2 w = __ffma2_rn(p, make_float2(p4.z, p4.w), make_float2(p5.x, p5.y));
     r.v[2 * q] = fabsf(w.x) <= 1.0f;
     r.v[2 * q + 1] = fabsf(w.y) <= 1.0f;
@@ -649,7 +653,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
           const StagedG& gs = sg[threadIdx.x];
           // power' = A' dx^2 + B' dx dy + C' dy^2 with A' = -a/(2 ln 2), B' = -b/ln 2,
           // C' = -c/(2 ln 2) for the conic (a, b, c); d power/d mean = (a dx + b dy, b dx + c dy)
-          const float Ap = gs.p1.x, Bp = gs.p1.z, Cp = gs.p2.x, o = gs.p2.z;
+          const float Ap = gs.p1.x, Bp = gs.p1.z, Cp = gs.p2.x, o = gs.p5.w;
           float4 r0, r1, r2;
           r0.x = -(2.0f * Ap * acc[1] + Bp * acc[2]) * kLn2;  // d mean2d.x
           r0.y = -(Bp * acc[1] + 2.0f * Cp * acc[2]) * kLn2;  // d mean2d.y
@@ -675,9 +679,14 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
   }
 }
 
+template <int TW, int TH>
+constexpr int bwd_min_blocks() {
+  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 11 : Blend<TW, TH>::NT <= 128 ? 5 : 2;
+}
+
 // Persistent blend backward over the tiles of every view of the call.
 template <int TW, int TH>
-__global__ void __launch_bounds__(Blend<TW, TH>::NT)
+__global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
     blend_bwd_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                      const float4* __restrict__ recA, const float4* __restrict__ recB,
                      const float4* __restrict__ recC, const uint32_t* __restrict__ egid, uint32_t ng,
