@@ -136,10 +136,19 @@ __global__ void __launch_bounds__(kPreBlock)
 // [c E, (c + 1) E) of the depth-ordered list (CTAs stride over the chunks). Gaussians with pairs are at the
 // front of the depth order (a Gaussian without tiles has the largest key), so
 // their offsets increase strictly and a chunk of E pairs involves at most
-// E + 1 of them: their offsets are loaded into shared memory and each pair
-// finds its Gaussian by binary search there. Pair q of Gaussian j covers tile
-// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j]. The
+// E + 1 of them: their offsets are loaded into shared memory. Each thread
+// emits a run of E / 256 consecutive pairs: one binary search finds the
+// Gaussian of the run's first pair, later pairs step through its rectangle
+// and on into the next Gaussian. Pair q of Gaussian j covers tile
+// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j]. The runs are
+// staged in shared memory (slots swizzled so that neither the run-wise writes
+// nor the pair-wise reads meet bank conflicts) and written out coalesced. The
 // Gaussian holding the chunk's first pair comes from depth_offsets_kernel.
+constexpr int kEmitRun = kEmitChunk / kPreBlock;  // consecutive pairs per thread
+static_assert(kEmitChunk % kPreBlock == 0 && kEmitRun == 8, "the slot swizzle assumes runs of 8");
+
+__device__ __forceinline__ uint32_t emit_slot(uint32_t i) { return i ^ ((i >> 5) & 7u); }
+
 __global__ void __launch_bounds__(kPreBlock)
     emit_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect,
                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
@@ -148,6 +157,8 @@ __global__ void __launch_bounds__(kPreBlock)
   griddep_wait();
   griddep_launch_dependents();
   __shared__ uint32_t s_off[kEmitChunk + 1];
+  __shared__ uint32_t s_key[kEmitChunk];
+  __shared__ uint32_t s_gid[kEmitChunk];
   const uint32_t K = hdr->key_count;
   // grid-stride over the output chunks: the grid is sized for the device,
   // the chunk count is only known here
@@ -157,26 +168,53 @@ __global__ void __launch_bounds__(kPreBlock)
     // window of items: up to the item holding the next chunk's first pair
     const int jhi = (q0 + kEmitChunk < K) ? static_cast<int>(chunk_start[c + 1]) : n - 1;
     const int m = min(kEmitChunk + 1, min(jhi, n - 1) - jlo + 1);
-    __syncthreads();  // the previous chunk is done with s_off
+    __syncthreads();  // the previous chunk is done with the shared arrays
     for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
     __syncthreads();
     const uint32_t qend = min(K, q0 + kEmitChunk);
-    for (uint32_t q = q0 + threadIdx.x; q < qend; q += kPreBlock) {
-      int lo = 0, hi = m - 1;  // last i with s_off[i] <= q
+    const uint32_t qa = q0 + threadIdx.x * kEmitRun;
+    if (qa < qend) {
+      int lo = 0, hi = m - 1;  // last i with s_off[i] <= qa
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= q) lo = mid;
+        if (s_off[mid] <= qa) lo = mid;
         else hi = mid - 1;
       }
-      const int j = jlo + lo;
-      const uint32_t local = q - s_off[lo];
-      const uint4 r = srect[j];  // rect, the view's first tile id and tiles_x
-      const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16, x1 = r.y & 0xffffu;
-      const uint32_t w = x1 - x0;
-      const uint32_t ty = y0 + local / w, tx = x0 + local % w;
-      tkeys[q] = r.z + ty * r.w + tx;
-      egid[q] = order[j];
-      if (ident) ident[q] = q;  // a single-tile image has no tile sort to generate the values
+      uint4 r = srect[jlo + lo];  // rect, the view's first tile id and tiles_x
+      uint32_t g = order[jlo + lo];
+      uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
+      uint32_t ly = (qa - s_off[lo]) / w, lx = (qa - s_off[lo]) - ly * w;
+      uint32_t next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+#pragma unroll
+      for (int u = 0; u < kEmitRun; ++u) {
+        const uint32_t q = qa + u;
+        if (q >= qend) break;
+        if (q >= next) {  // the run enters the next Gaussian (past any without pairs)
+          do {
+            ++lo;
+            next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+          } while (q >= next);
+          r = srect[jlo + lo];
+          g = order[jlo + lo];
+          w = (r.y & 0xffffu) - (r.x & 0xffffu);
+          ly = (q - s_off[lo]) / w;
+          lx = (q - s_off[lo]) - ly * w;
+        }
+        const uint32_t slot = emit_slot(q - q0);
+        s_key[slot] = r.z + ((r.x >> 16) + ly) * r.w + (r.x & 0xffffu) + lx;
+        s_gid[slot] = g;
+        if (++lx == w) {
+          lx = 0;
+          ++ly;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; q0 + i < qend; i += kPreBlock) {
+      const uint32_t slot = emit_slot(i);
+      tkeys[q0 + i] = s_key[slot];
+      egid[q0 + i] = s_gid[slot];
+      if (ident) ident[q0 + i] = q0 + i;  // a single-tile image has no tile sort to generate the values
     }
   }
 }
