@@ -178,6 +178,9 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.rect = o;     o = align_up(o + sizeof(uint2) * m);
   L.touched = o;  o = align_up(o + sizeof(uint32_t) * m);
   L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * td);
+  // the depth sort's scratch right after the difference array: one memset at
+  // the start of a render clears both, and the sort needs no clearing kernel
+  L.onesweep = o; o = align_up(o + onesweep_scratch_bytes(m, 32));
   L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * m);
   L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * m);
   L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * m);
@@ -201,7 +204,6 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);
   // the two sorts' scratch apart: the tile sort's is cleared and filled with
   // its histograms on a side stream while the depth sort runs
-  L.onesweep = o; o = align_up(o + onesweep_scratch_bytes(m, 32));
   L.tsort = o;    o = align_up(o + onesweep_scratch_bytes(cap, tb));
   // multi-view backward: the visible items and their partial gradients (96 B each)
   const int64_t mi = nviews > 1 ? m : 0;
@@ -270,7 +272,8 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, sizeof(uint32_t) * L.tdiff_words, s);
+  if (e == cudaSuccess)  // the difference array and the depth sort's scratch
+    e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, L.onesweep + onesweep_scratch_bytes(L.m, 32) - L.tdiff, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const bool has = L.n > 0;
   const int dpasses = 32 / kSortRadixBits;
@@ -311,10 +314,11 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   int which = 0;
   if (has) {
     // depth order of the items: stable sort of the depth bits, values = item index
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 2 + dpasses);  // clear, histogram, passes
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);  // histogram, passes (cleared with the difference array)
     e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
                         at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
-                        nullptr, static_cast<uint32_t>(L.m), L.m, 32, at<void>(frame, L.onesweep), err, s, &which);
+                        nullptr, static_cast<uint32_t>(L.m), L.m, 32, at<void>(frame, L.onesweep), err, s, &which,
+                        false, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
   }
   const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
