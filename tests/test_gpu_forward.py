@@ -208,3 +208,46 @@ def test_full_size_frame_sampled_pixels(r4g):
     assert amb.mean() < 0.02
     assert err[~amb].max() <= MAX_ABS, err[~amb].max()
     assert (ref["rgb"].numpy().sum(1) > 0).mean() > 0.5
+
+
+def _rectangles_check(ex, tiles_x):
+    """Every Gaussian's pairs cover a full rectangle of tiles once, and each
+    tile's range holds exactly its pairs."""
+    keys = ex["keys"].cpu().numpy().view(np.uint64)
+    vals = ex["values"].cpu().numpy().view(np.uint32).astype(np.int64)
+    ranges = ex["ranges"].cpu().numpy()
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    tx, ty = tiles % tiles_x, tiles // tiles_x
+    o = np.lexsort((tiles, vals))
+    g, tx, ty, tl = vals[o], tx[o], ty[o], tiles[o]
+    assert np.all((np.diff(g) > 0) | (np.diff(tl) > 0))  # no (Gaussian, tile) pair twice
+    start = np.flatnonzero(np.r_[True, np.diff(g) > 0])
+    cnt = np.diff(np.r_[start, len(g)])
+    w = np.maximum.reduceat(tx, start) - np.minimum.reduceat(tx, start) + 1
+    h = np.maximum.reduceat(ty, start) - np.minimum.reduceat(ty, start) + 1
+    assert np.array_equal(cnt, w * h)
+    per_tile = np.bincount(tiles, minlength=len(ranges))
+    assert np.array_equal(ranges[:, 1] - ranges[:, 0], per_tile)
+    assert ranges[:, 0].min() == 0 and ranges[:, 1].max() == len(keys)
+    return cnt
+
+
+def test_emission_covers_full_rectangles(r4g):
+    """Small scene: pairs of Gaussians covering up to the whole 8x8-tile image."""
+    g, cam, t = synth.small_scene(seed=4)
+    rend, res = _render(r4g, g, cam, t)
+    cnt = _rectangles_check(rend.export(res), (cam.width + 15) // 16)
+    assert cnt.max() > 8  # runs of eight pairs cross Gaussians and rectangle rows
+
+
+def test_emission_full_size_frame(r4g):
+    """300k Gaussians at 1352x1014 (sweep frame 37): ~3M pairs over ~1500
+    emission chunks, the rectangles and the ranges checked for every pair."""
+    g = synth.fwd300k_scene()
+    cam, t = synth.orbit_camera(37, 300, 8.0, 1352, 1014)
+    rend = r4g.Renderer()
+    res = rend.render(to_device(g), cam, t)
+    ex = rend.export(res)
+    assert ex["key_count"] > 2_000_000
+    cnt = _rectangles_check(ex, (1352 + 15) // 16)
+    assert cnt.min() >= 1 and (cnt == 1).any() and cnt.max() > 64
