@@ -323,7 +323,7 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   }
   const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
   {
-    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? 4 : 0);
+    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? (L.nblocks <= kSelfScanBlocks ? 3 : 4) : 0);
     if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
   }
   const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;

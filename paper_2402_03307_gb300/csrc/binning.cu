@@ -92,17 +92,27 @@ __global__ void __launch_bounds__(kScanThreads)
 // depth_blocksum_kernel; blockoff holds the scanned block totals).
 constexpr int kEmitChunk = 2048;
 
+// kSelfScan (a call with at most kSelfScanBlocks blocks): blockoff holds the
+// unscanned block totals, and each block sums those before it itself (the
+// one-CTA scan launch is skipped); the last block writes the pair count and
+// the overflow flag into the frame header, as scan_blocksums_kernel does.
+
+template <bool kSelfScan>
 __global__ void __launch_bounds__(kPreBlock)
     depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
                          const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect,
                          const ViewDev* __restrict__ views, uint32_t ng, int m, uint32_t* __restrict__ offs,
                          uint32_t* __restrict__ ioffs, uint4* __restrict__ srect, uint32_t* __restrict__ chunk_start,
-                         uint32_t nchunks) {
+                         uint32_t nchunks, FrameHeader* hdr, uint32_t cap) {
   griddep_wait();
   griddep_launch_dependents();
   __shared__ uint32_t s_warp[kPreBlock / 32];
+  __shared__ uint32_t s_pre[kPreBlock / 32];
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t pre = 0;  // kSelfScan: this thread's share of the blocks before this one
+  if constexpr (kSelfScan)
+    for (int b = threadIdx.x; b < static_cast<int>(blockIdx.x); b += kPreBlock) pre += blockoff[b];
   const uint32_t item = j < m ? order[j] : 0u;
   const uint32_t cnt = j < m ? touched[item] : 0u;
   uint32_t x = cnt;
@@ -112,8 +122,27 @@ __global__ void __launch_bounds__(kPreBlock)
     if (lane >= o) x += y;
   }
   if (lane == 31) s_warp[warp] = x;
+  if constexpr (kSelfScan) {
+    pre = __reduce_add_sync(0xffffffffu, pre);
+    if (lane == 0) s_pre[warp] = pre;
+  }
   __syncthreads();
-  uint32_t base = blockoff[blockIdx.x];
+  uint32_t base;
+  if constexpr (kSelfScan) {
+    base = 0;
+#pragma unroll
+    for (int w = 0; w < kPreBlock / 32; ++w) base += s_pre[w];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // the pair count of the call
+      uint32_t total = base;
+#pragma unroll
+      for (int w = 0; w < kPreBlock / 32; ++w) total += s_warp[w];
+      hdr->key_needed = total;
+      hdr->key_count = total < cap ? total : cap;
+      if (total > cap) atomicOr(&hdr->status, 1u);
+    }
+  } else {
+    base = blockoff[blockIdx.x];
+  }
   for (int w = 0; w < warp; ++w) base += s_warp[w];
   if (j < m) {
     const uint32_t o = base + x - cnt;
@@ -351,13 +380,15 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   uint32_t* cstart = at<uint32_t>(frame, L.chunks);
   const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
   cudaError_t e = launch_pdl(depth_blocksum_kernel, L.nblocks, kPreBlock, 0, s, touched, order, m, bs);
-  if (e == cudaSuccess)
+  const bool self_scan = L.nblocks <= kSelfScanBlocks;
+  if (e == cudaSuccess && !self_scan)
     e = launch_pdl(scan_blocksums_kernel, 1, kScanThreads, 0, s, bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
   if (e == cudaSuccess)
-    e = launch_pdl(depth_offsets_kernel, L.nblocks, kPreBlock, 0, s, touched, order,
-                   static_cast<const uint32_t*>(bs), static_cast<const uint2*>(at<uint2>(frame, L.rect)),
+    e = launch_pdl(self_scan ? depth_offsets_kernel<true> : depth_offsets_kernel<false>, L.nblocks, kPreBlock, 0, s,
+                   touched, order, static_cast<const uint32_t*>(bs), static_cast<const uint2*>(at<uint2>(frame, L.rect)),
                    static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)), static_cast<uint32_t>(L.n), m, offs,
-                   at<uint32_t>(frame, L.ioffs), srect, cstart, static_cast<uint32_t>(chunks));
+                   at<uint32_t>(frame, L.ioffs), srect, cstart, static_cast<uint32_t>(chunks), hdr,
+                   static_cast<uint32_t>(L.cap));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -93,6 +93,7 @@ struct FrameLayout {
 
 constexpr int kPreBlock = 256;     // items per preprocess-order / key-build block
 constexpr int kPreFwdBlock = 128;  // Gaussians per preprocess (forward) block
+constexpr int kSelfScanBlocks = 2048;  // up to this many blocks, the depth-order offsets scan themselves
 constexpr int kMaxTiles = 51200;   // tiles per view (the tile-count kernel keeps them in shared memory)
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;        // items per thread per tile
