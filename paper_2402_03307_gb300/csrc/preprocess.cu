@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
 // partial gradient (96 B), (3) one thread per Gaussian sums its items'
 // partials in view order (deterministic) and runs the Sigma4 -> rotor and
 // scale backward once.
-constexpr int kPartFloats = 24;  // d Sigma4 (10), d mean (4), d opacity, dir (3), d rgb (3), statistics (3)
+// float4s per partial: d Sigma4 (10), d mean (4), d opacity, dir (3), d rgb (3), statistics (3)
+constexpr int kPartVec = 6;
 
 __global__ void __launch_bounds__(1024)
     list_items_kernel(const uint32_t* __restrict__ touched, uint32_t m, uint32_t* __restrict__ ilist,
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc) && mine;
   if (mine && !got) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* dz = ipart + 6 * static_cast<size_t>(item);
+    float4* dz = ipart + kPartVec * static_cast<size_t>(item);
     dz[0] = dz[1] = dz[2] = dz[3] = dz[4] = dz[5] = z;
   }
   const uint32_t b = __ballot_sync(0xffffffffu, got);
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   ga = s_g[0][threadIdx.x];
   gb = s_g[1][threadIdx.x];
   gc = s_g[2][threadIdx.x];
-  float4* d = ipart + 6 * static_cast<size_t>(item);
+  float4* d = ipart + kPartVec * static_cast<size_t>(item);
   const int v = static_cast<int>(item / static_cast<uint32_t>(g.n));
   const int i = static_cast<int>(item - static_cast<uint32_t>(v) * static_cast<uint32_t>(g.n));
   Sig4<float> Q;
@@ -505,7 +506,7 @@ __global__ void __launch_bounds__(kBwdBlock)
     const uint32_t tcur = tnext;
     if (v + 1 < nviews) tnext = touched[static_cast<size_t>(v + 1) * g.n + i];
     if (tcur == 0u) continue;
-    const float4* p = ipart + 6 * (static_cast<size_t>(v) * g.n + i);
+    const float4* p = ipart + kPartVec * (static_cast<size_t>(v) * g.n + i);
     const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4], f = p[5];
     G4s[0] += a.x; G4s[1] += a.y; G4s[2] += a.z; G4s[3] += a.w;
     G4s[4] += b.x; G4s[5] += b.y; G4s[6] += b.z; G4s[7] += b.w;
