@@ -231,7 +231,9 @@ def run_ours(args, rank, world, local):
         render_frame(frames[i % len(frames)])
     torch.cuda.synchronize()
     abi.r4g_stage_times(rend.ctx, reset=True)
-    abi.r4g_set_timing(rend.ctx, True)
+    # the timed frames run without per-stage events (an event between two
+    # kernels ends their programmatic launch overlap); the stage times come
+    # from a second pass over the same frames below
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
     clocks = ClockSampler(local)
     clocks.start()
@@ -247,8 +249,15 @@ def run_ours(args, rank, world, local):
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    _, stage_launch = abi.r4g_stage_times(rend.ctx, reset=True)
+    # per-stage device times: the same frames again, stage events on
+    abi.r4g_set_timing(rend.ctx, True)
+    for k in frames:
+        flush.zero_()
+        render_frame(k)
+    torch.cuda.synchronize()
     abi.r4g_set_timing(rend.ctx, False)
-    stage_ms, stage_launch = abi.r4g_stage_times(rend.ctx, reset=True)
+    stage_ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
     for k in frames[-3:]:
         if rend.status(render_frame(k))[0] != abi.R4G_OK:
             raise RuntimeError("key buffer overflow during the timed region")
@@ -614,9 +623,10 @@ def inside_sweep_bench(params, dev, stream, flush, radius: float = 4.0, stride: 
         one()
     torch.cuda.synchronize()
     it["k"] = 0
+    ms = _timed(one, len(cams), stream, flush)  # no per-stage events in the timed frames
     abi.r4g_stage_times(rend.ctx, reset=True)
     abi.r4g_set_timing(rend.ctx, True)
-    ms = _timed(one, len(cams), stream, flush)
+    _timed(one, len(cams), stream, flush)
     abi.r4g_set_timing(rend.ctx, False)
     stage_ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
     keys = 0
