@@ -172,15 +172,16 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   const int cnt_ctas = L.sort_ctas > L.depth_ctas ? L.sort_ctas : L.depth_ctas;
   const size_t npix = static_cast<size_t>(pix);
   size_t o = 0;
+  // the header, the tile-count difference array and the depth sort's scratch
+  // first: one memset at the start of a render clears all three, and the sort
+  // needs no clearing kernel
   L.header = o;   o = align_up(o + sizeof(FrameHeader));
+  L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * td);
+  L.onesweep = o; o = align_up(o + onesweep_scratch_bytes(m, 32));
   L.views = o;    o = align_up(o + sizeof(ViewDev) * nviews);
   L.rec = o;      o = align_up(o + 3 * sizeof(float4) * m);
   L.rect = o;     o = align_up(o + sizeof(uint2) * m);
   L.touched = o;  o = align_up(o + sizeof(uint32_t) * m);
-  L.tdiff = o;    o = align_up(o + sizeof(uint32_t) * td);
-  // the depth sort's scratch right after the difference array: one memset at
-  // the start of a render clears both, and the sort needs no clearing kernel
-  L.onesweep = o; o = align_up(o + onesweep_scratch_bytes(m, 32));
   L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * m);
   L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * m);
   L.ord0 = o;     o = align_up(o + sizeof(uint32_t) * m);
@@ -271,9 +272,9 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
     return st;
   if (frame_bytes < L.total) return fail(ctx, R4G_EWORKSPACE, "frame smaller than r4g_frame_bytes");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0, sizeof(FrameHeader), s);
-  if (e == cudaSuccess)  // the difference array and the depth sort's scratch
-    e = cudaMemsetAsync(at<char>(frame, L.tdiff), 0, L.onesweep + onesweep_scratch_bytes(L.m, 32) - L.tdiff, s);
+  // the header, the difference array and the depth sort's scratch (adjacent)
+  cudaError_t e = cudaMemsetAsync(at<char>(frame, L.header), 0,
+                                  L.onesweep + onesweep_scratch_bytes(L.m, 32) - L.header, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "memset");
   const bool has = L.n > 0;
   const int dpasses = 32 / kSortRadixBits;
