@@ -200,6 +200,7 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.gbuf = o;     o = align_up(o + 12 * sizeof(float) * cap);
   L.reach = o;    o = align_up(o + static_cast<size_t>(cap));  // 1 when a pair's gradient slot holds a value
   L.ranges = o;   o = align_up(o + sizeof(uint2) * L.ntiles);
+  L.torder = o;   o = align_up(o + sizeof(uint32_t) * L.ntiles);  // the blends' tile order
   L.tfinal = o;   o = align_up(o + sizeof(float) * npix);
   L.last = o;     o = align_up(o + sizeof(uint32_t) * npix);
   L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);

@@ -19,6 +19,7 @@ namespace r4g {
 
 constexpr int kScanThreads = 1024;
 constexpr int kTileCountsMaxSmem = kMaxTiles * 4;
+constexpr int kTileClasses = 64;  // list-length classes of the blend's tile order
 
 // blocksum[b] = sum of touched[order[j]] over the block's depth positions.
 __global__ void __launch_bounds__(kPreBlock)
@@ -266,7 +267,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 __global__ void __launch_bounds__(1024)
     tile_counts_kernel(const uint32_t* __restrict__ tdiff, const ViewDev* __restrict__ views, uint32_t cap,
                        const FrameHeader* hdr, uint2* __restrict__ ranges, uint32_t* __restrict__ hist,
-                       int passes) {
+                       int passes, uint32_t* __restrict__ torder) {
   extern __shared__ uint32_t s_c[];  // tiles_y x tiles_x counts of this CTA's view
   __shared__ uint32_t s_h[4][kSortRadix];
   __shared__ uint32_t s_warp[32];
@@ -345,6 +346,35 @@ __global__ void __launch_bounds__(1024)
   for (int p = 0; p < passes; ++p)
     for (int d = threadIdx.x; d < kSortRadix; d += blockDim.x)
       if (s_h[p][d]) atomicAdd(&hist[p * kSortRadix + d], s_h[p][d]);
+  // The order in which the persistent blends take this view's tiles: longest
+  // list first (64 classes of the list length, a counting sort), so that the
+  // last tiles handed out are short and the SMs finish together. Any order
+  // gives the same images: tiles are independent.
+  __shared__ uint32_t s_cls[kTileClasses];
+  __shared__ uint32_t s_max;
+  if (threadIdx.x == 0) s_max = 0;
+  for (int k = threadIdx.x; k < kTileClasses; k += blockDim.x) s_cls[k] = 0;
+  __syncthreads();
+  uint32_t mx = 0;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) mx = max(mx, s_c[t]);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) atomicMax(&s_max, mx);
+  __syncthreads();
+  const uint64_t top = static_cast<uint64_t>(s_max) + 1;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)  // class 0: the longest lists
+    atomicAdd(&s_cls[kTileClasses - 1 - static_cast<int>(s_c[t] * static_cast<uint64_t>(kTileClasses) / top)], 1u);
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the class sizes (kTileClasses = 64: two per lane)
+    const uint32_t a = s_cls[2 * lane], b = s_cls[2 * lane + 1];
+    const uint32_t x = warp_incl_scan(a + b, lane);
+    s_cls[2 * lane] = x - a - b;
+    s_cls[2 * lane + 1] = x - b;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int c = kTileClasses - 1 - static_cast<int>(s_c[t] * static_cast<uint64_t>(kTileClasses) / top);
+    torder[toff + atomicAdd(&s_cls[c], 1u)] = toff + static_cast<uint32_t>(t);
+  }
 }
 
 // The sort carries each pair's emission index e; egid[e] is its Gaussian.
@@ -409,7 +439,8 @@ cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist
   cudaFuncSetAttribute(tile_counts_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileCountsMaxSmem);
   tile_counts_kernel<<<L.nviews, 1024, smem, s>>>(at<uint32_t>(frame, L.tdiff), at<ViewDev>(frame, L.views),
                                                   static_cast<uint32_t>(L.cap), at<FrameHeader>(frame, L.header),
-                                                  at<uint2>(frame, L.ranges), hist, passes);
+                                                  at<uint2>(frame, L.ranges), hist, passes,
+                                                  at<uint32_t>(frame, L.torder));
   return cudaGetLastError();
 }
 

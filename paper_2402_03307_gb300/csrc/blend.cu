@@ -396,14 +396,17 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
                      uint32_t cap, const ViewDev* __restrict__ views, int nviews, int ntiles, FrameHeader* hdr,
                      float bg0, float bg1, float bg2, float* __restrict__ out_rgb, float* __restrict__ out_T,
                      uint32_t* __restrict__ out_stop, uint32_t* __restrict__ out_last,
-                     unsigned long long* __restrict__ pair_count) {
+                     unsigned long long* __restrict__ pair_count, const uint32_t* __restrict__ torder) {
   griddep_wait();
   griddep_launch_dependents();
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ int s_tile;
   for (;;) {
     __syncthreads();  // the previous tile is done with s_tile and sg
-    if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->next_tile, 1u));
+    if (threadIdx.x == 0) {  // the next tile in the frame's tile order (longest lists first)
+      const uint32_t k = atomicAdd(&hdr->next_tile, 1u);
+      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder[k]) : ntiles;
+    }
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
                      uint32_t cap, const ViewDev* __restrict__ views, int nviews, int ntiles, FrameHeader* hdr,
                      float bg0, float bg1, float bg2, const float* __restrict__ Tfinal,
                      const uint32_t* __restrict__ stoppos, const float* __restrict__ grad_rgb,
-                     float4* __restrict__ gbuf, uint8_t* __restrict__ reach) {
+                     float4* __restrict__ gbuf, uint8_t* __restrict__ reach, const uint32_t* __restrict__ torder) {
   griddep_wait();
   griddep_launch_dependents();
   // the multi-view preprocess backward that follows lists its items anew
@@ -706,7 +709,10 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
   extern __shared__ __align__(16) float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
   for (;;) {
     __syncthreads();  // the previous tile is done with the shared buffers
-    if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->next_tile_bwd, 1u));
+    if (threadIdx.x == 0) {  // the next tile in the frame's tile order (longest lists first)
+      const uint32_t k = atomicAdd(&hdr->next_tile_bwd, 1u);
+      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder[k]) : ntiles;
+    }
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
@@ -739,12 +745,13 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   uint32_t* stop = at<uint32_t>(frame, L.last);
   const ViewDev* views = at<ViewDev>(frame, L.views);
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
+  const uint32_t* torder = at<uint32_t>(frame, L.torder);
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                          \
   e = launch_pdl(blend_fwd_kernel<TW_, TH_, LAST_>,                                                         \
                  persistent_ctas(blend_fwd_kernel<TW_, TH_, LAST_>, Blend<TW_, TH_>::NT, 0, L.ntiles),        \
                  Blend<TW_, TH_>::NT, 0, s, ranges, vals, recA, recB, recC, egid, static_cast<uint32_t>(L.m),    \
                  static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, bg[0], bg[1], bg[2], out_rgb, T,   \
-                 stop, out_last, pairs)
+                 stop, out_last, pairs, torder)
   const uint32_t* egid = at<uint32_t>(frame, L.egid);
   // the instrumented variant serves both the last-contributor output and the pair count
   const bool lst = out_last != nullptr || count;
@@ -778,6 +785,7 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   float4* gbuf = at<float4>(frame, L.gbuf);
   uint8_t* reach = at<uint8_t>(frame, L.reach);
+  const uint32_t* torder = at<uint32_t>(frame, L.torder);
   // the backward's work counter (the render zeroed the forward's)
   cudaMemsetAsync(&hdr->next_tile_bwd, 0, sizeof(uint32_t), s);
 #define R4G_BLEND_BWD(TW_, TH_)                                                                           \
@@ -789,7 +797,7 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
                    persistent_ctas(blend_bwd_kernel<TW_, TH_>, Blend<TW_, TH_>::NT, slab, L.ntiles),      \
                    Blend<TW_, TH_>::NT, slab, s, ranges, vals, recA, recB, recC, egid,                    \
                    static_cast<uint32_t>(L.m), static_cast<uint32_t>(L.cap), views, L.nviews, L.ntiles, hdr, \
-                   bg[0], bg[1], bg[2], T, stop, grad_rgb, gbuf, reach);                                  \
+                   bg[0], bg[1], bg[2], T, stop, grad_rgb, gbuf, reach, torder);                          \
   }
   cudaError_t e = cudaSuccess;
   if (L.tile_w == 16 && L.tile_h == 16) R4G_BLEND_BWD(16, 16)
