@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(1024)
   // The order in which the persistent blends take this view's tiles: longest
   // list first (64 classes of the list length, a counting sort), so that the
   // last tiles handed out are short and the SMs finish together. Any order
-  // gives the same images: tiles are independent.
+  // gives the same images: tiles are independent. (torder null: index order.)
+  if (!torder) return;
   __shared__ uint32_t s_cls[kTileClasses];
   __shared__ uint32_t s_max;
   if (threadIdx.x == 0) s_max = 0;
@@ -440,7 +441,7 @@ cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist
   tile_counts_kernel<<<L.nviews, 1024, smem, s>>>(at<uint32_t>(frame, L.tdiff), at<ViewDev>(frame, L.views),
                                                   static_cast<uint32_t>(L.cap), at<FrameHeader>(frame, L.header),
                                                   at<uint2>(frame, L.ranges), hist, passes,
-                                                  at<uint32_t>(frame, L.torder));
+                                                  const_cast<uint32_t*>(tile_order(L, frame)));
   return cudaGetLastError();
 }
 

@@ -403,9 +403,9 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
   __shared__ int s_tile;
   for (;;) {
     __syncthreads();  // the previous tile is done with s_tile and sg
-    if (threadIdx.x == 0) {  // the next tile in the frame's tile order (longest lists first)
+    if (threadIdx.x == 0) {  // the next tile: in the frame's tile order when there is one
       const uint32_t k = atomicAdd(&hdr->next_tile, 1u);
-      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder[k]) : ntiles;
+      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder ? torder[k] : k) : ntiles;
     }
     __syncthreads();
     const int tile = s_tile;
@@ -709,9 +709,9 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
   extern __shared__ __align__(16) float s_slab[];  // [NW][BS][9] per-warp sums of the batch's entries
   for (;;) {
     __syncthreads();  // the previous tile is done with the shared buffers
-    if (threadIdx.x == 0) {  // the next tile in the frame's tile order (longest lists first)
+    if (threadIdx.x == 0) {  // the next tile: in the frame's tile order when there is one
       const uint32_t k = atomicAdd(&hdr->next_tile_bwd, 1u);
-      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder[k]) : ntiles;
+      s_tile = k < static_cast<uint32_t>(ntiles) ? static_cast<int>(torder ? torder[k] : k) : ntiles;
     }
     __syncthreads();
     const int tile = s_tile;
@@ -745,7 +745,7 @@ cudaError_t launch_blend_fwd(const FrameLayout& L, void* frame, const uint32_t* 
   uint32_t* stop = at<uint32_t>(frame, L.last);
   const ViewDev* views = at<ViewDev>(frame, L.views);
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
-  const uint32_t* torder = at<uint32_t>(frame, L.torder);
+  const uint32_t* torder = tile_order(L, frame);
 #define R4G_BLEND(TW_, TH_, LAST_)                                                                          \
   e = launch_pdl(blend_fwd_kernel<TW_, TH_, LAST_>,                                                         \
                  persistent_ctas(blend_fwd_kernel<TW_, TH_, LAST_>, Blend<TW_, TH_>::NT, 0, L.ntiles),        \
@@ -785,7 +785,7 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
   float4* gbuf = at<float4>(frame, L.gbuf);
   uint8_t* reach = at<uint8_t>(frame, L.reach);
-  const uint32_t* torder = at<uint32_t>(frame, L.torder);
+  const uint32_t* torder = tile_order(L, frame);
   // the backward's work counter (the render zeroed the forward's)
   cudaMemsetAsync(&hdr->next_tile_bwd, 0, sizeof(uint32_t), s);
 #define R4G_BLEND_BWD(TW_, TH_)                                                                           \

@@ -94,6 +94,10 @@ struct FrameLayout {
 constexpr int kPreBlock = 256;     // items per preprocess-order / key-build block
 constexpr int kPreFwdBlock = 128;  // Gaussians per preprocess (forward) block
 constexpr int kSelfScanBlocks = 2048;  // up to this many blocks, the depth-order offsets scan themselves
+// The blends take tiles longest list first when the call's screen records fit
+// well within L2 (the tiles then share them wherever they lie); beyond that,
+// in index order, where neighbouring tiles in flight together reuse records.
+constexpr int64_t kTileOrderMaxRecordBytes = int64_t(64) << 20;
 constexpr int kMaxTiles = 51200;   // tiles per view (the tile-count kernel keeps them in shared memory)
 constexpr int kSortThreads = 256;
 constexpr int kSortIPT = 8;        // items per thread per tile
@@ -153,6 +157,12 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 template <typename T>
 inline T* at(void* base, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+// The blends' tile order for the frame (written by the tile counts kernel), or
+// nullptr for index order.
+inline const uint32_t* tile_order(const FrameLayout& L, void* frame) {
+  return 48 * L.m <= kTileOrderMaxRecordBytes ? at<uint32_t>(frame, L.torder) : nullptr;
 }
 
 // ---- launchers (return cudaGetLastError() after enqueueing) -----------------
