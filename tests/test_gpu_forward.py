@@ -251,3 +251,23 @@ def test_emission_full_size_frame(r4g):
     assert ex["key_count"] > 2_000_000
     cnt = _rectangles_check(ex, (1352 + 15) // 16)
     assert cnt.min() >= 1 and (cnt == 1).any() and cnt.max() > 64
+
+
+def test_inside_the_cloud_sampled_pixels(r4g):
+    """The heavier tile load of the same sweep at orbit radius 4 (the camera
+    inside the cube of Gaussians, longer lists per tile): 1000 sampled pixels
+    of frame 120 against the oracle."""
+    g = synth.fwd300k_scene()
+    cam, t = synth.orbit_camera(120, 300, 4.0, 1352, 1014)
+    rend = r4g.Renderer()
+    res = rend.render(to_device(g), cam, t)
+    img = res.image.cpu().numpy()
+    assert np.isfinite(img).all() and img.min() >= 0
+    assert rend.export(res)["key_count"] > 3_000_000
+    pix = synth.random_pixels(6, 1352, 1014, 1000)
+    ref = oracle.render_pixels(oracle.to_f64(g), cam, t, pix)
+    amb = ambiguous(ref, image=True)
+    got = img[:, pix[:, 1], pix[:, 0]].T
+    err = np.abs(got - ref["rgb"].numpy())
+    assert amb.mean() < 0.02
+    assert err[~amb].max() <= MAX_ABS, err[~amb].max()
