@@ -2,7 +2,12 @@
 analytic single-Gaussian footprints (Jacobian of the projection by automatic
 differentiation, slice by textbook conditioning, rotation from closed forms),
 two-layer closed form, the transmittance stop, the spatial/temporal
-separability of Sec. 3.2.1, cull neutrality and finite-difference gradients."""
+separability of Sec. 3.2.1, cull neutrality and finite-difference gradients.
+Both clamps are pinned: alpha <= 0.99 (closed form 0.99 rgb + 0.01 bg and a
+zero gradient on the clamped core) and the Jacobian of the projection taken at
+the point clamped to 1.3 tan(fov/2) (footprint with the Jacobian of the
+clamped point by automatic differentiation; central differences with both
+clamps active)."""
 import math
 import os
 
@@ -12,7 +17,7 @@ import torch
 
 import oracle
 import synth
-from oracle.render import PARAM_NAMES, depth_order
+from oracle.render import PARAM_NAMES, _inclusion, depth_order
 
 special = pytest.importorskip("scipy.special")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -36,8 +41,19 @@ def _real_sh_l1(d):
     return np.array(out)
 
 
-def expected_single(mean4, Rm, s, logit, sh, cam, t, bg=np.zeros(3)):
-    """Independent footprint of one Gaussian: image [3,H,W], T [H,W]."""
+def _frustum_limits(cam):
+    """1.3 tan(fov/2) on each axis of the image plane (tan(fov_x/2) = W / 2fx)."""
+    return 1.3 * cam.width / (2.0 * cam.fx), 1.3 * cam.height / (2.0 * cam.fy)
+
+
+def expected_single(mean4, Rm, s, logit, sh, cam, t, bg=np.zeros(3), jclamp=False, out_alpha=None):
+    """Independent footprint of one Gaussian: image [3,H,W], T [H,W].
+
+    The 2D covariance uses the Jacobian of the pinhole projection obtained by
+    automatic differentiation. With ``jclamp`` that Jacobian is taken at the
+    camera-space point whose x/z and y/z are clamped to the frustum limits
+    (the mean itself still projects unclamped). ``out_alpha``, when a list,
+    receives the unclamped o_t e^power map (zero outside the 3-sigma cutoff)."""
     S4 = Rm @ np.diag(s ** 2) @ Rm.T
     dt = t - mean4[3]
     mu3 = mean4[:3] + S4[:3, 3] / S4[3, 3] * dt
@@ -50,7 +66,17 @@ def expected_single(mean4, Rm, s, logit, sh, cam, t, bg=np.zeros(3)):
         return torch.stack([cam.fx * pc[0] / pc[2] + cam.cx, cam.fy * pc[1] / pc[2] + cam.cy])
 
     x0 = torch.as_tensor(mu3)
-    J = torch.autograd.functional.jacobian(pi, x0).numpy()
+    if jclamp:
+        pc = w2c[:, :3] @ mu3 + w2c[:, 3]
+        lx, ly = _frustum_limits(cam)
+        pcc = np.array([np.clip(pc[0] / pc[2], -lx, lx) * pc[2], np.clip(pc[1] / pc[2], -ly, ly) * pc[2], pc[2]])
+
+        def pi_c(p):
+            return torch.stack([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy])
+
+        J = torch.autograd.functional.jacobian(pi_c, torch.as_tensor(pcc)).numpy() @ w2c[:, :3]
+    else:
+        J = torch.autograd.functional.jacobian(pi, x0).numpy()
     m2 = pi(x0).numpy()
     cov = J @ S3 @ J.T + 0.3 * np.eye(2)
     inv = np.linalg.inv(cov)
@@ -62,18 +88,22 @@ def expected_single(mean4, Rm, s, logit, sh, cam, t, bg=np.zeros(3)):
     H, W = cam.height, cam.width
     img = np.zeros((3, H, W))
     T = np.ones((H, W))
+    araw = np.zeros((H, W))
     for j in range(H):
         for i in range(W):
             dd = np.array([i + 0.5, j + 0.5]) - m2
             power = -0.5 * dd @ inv @ dd
             if power > 0 or power < -4.5:
                 continue
+            araw[j, i] = o * math.exp(power)
             a = min(0.99, o * math.exp(power))
             if a < 1 / 255:
                 continue
             img[:, j, i] = rgb * a
             T[j, i] = 1 - a
     img += T[None] * bg[:, None, None]
+    if out_alpha is not None:
+        out_alpha.append(araw)
     return img, T, m2
 
 
@@ -288,3 +318,183 @@ def test_gradient_matches_central_differences():
     # every parameter group receives gradient
     for name in ("mean", "rotor", "logscale", "logit", "sh"):
         assert grads[name].abs().max() > 0
+
+
+# ---------------------------------------------------------------------------
+# The two clamps: alpha <= 0.99 (Sec. 3.1 Eq. 3, with the compositing rules of
+# the 3D Gaussian Splatting rasteriser that the paper follows) and the
+# Jacobian of the projection taken at a point clamped to 1.3 tan(fov/2) (the
+# EWA convention of the same rasteriser, to which Sec. 3.1 defers).
+
+C0 = 0.5 / math.sqrt(math.pi)  # real Y_00
+
+
+def _opaque_scene():
+    """One large Gaussian of opacity 1 - 1e-3 (logit ln 999), centred on the
+    optical axis at its temporal centre, DC-only colour."""
+    rotor, Rm = _golden_rotors()[3]
+    mean4 = np.array([0.05, -0.03, 0.1, 0.5])
+    ls = np.log(np.array([1.9, 1.4, 1.6, 0.6]))
+    sh = np.zeros((16, 3))
+    sh[0] = [0.3, -0.2, 0.6]
+    logit = math.log(999.0)
+    return rotor, Rm, mean4, ls, sh, logit
+
+
+def test_alpha_clamp_closed_form():
+    """Where o_t e^power exceeds 0.99 the pixel is 0.99 rgb + 0.01 bg, for any
+    opacity: the clamp applies to the product, after the exponential, and its
+    value is 0.99. Elsewhere the footprint is o_t e^power."""
+    rotor, Rm, mean4, ls, sh, logit = _opaque_scene()
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 48, 48)
+    bg = np.array([0.2, 0.4, 0.8])
+    t = 0.5
+    araw = []
+    img_ref, T_ref, _ = expected_single(mean4, Rm, np.exp(ls), logit, sh, cam, t, bg, out_alpha=araw)
+    araw = araw[0]
+    out = oracle.render(_one(mean4, rotor, ls, logit, sh), cam, t, bg=tuple(bg))
+    img = out["image"].numpy()
+    rgb = 0.5 + C0 * sh[0]
+    closed = (0.99 * rgb + 0.01 * bg)[:, None, None]
+    clamped = araw > 0.99
+    assert clamped.sum() >= 8  # several pixels sit inside the clamped core
+    assert (araw[clamped] < 0.999).all()  # ... with o_t e^power strictly between 0.99 and o_t
+    np.testing.assert_allclose(img[:, clamped], np.broadcast_to(closed, img.shape)[:, clamped], atol=1e-14)
+    np.testing.assert_allclose(out["T"].numpy()[clamped], 0.01, atol=1e-15)
+    # unclamped pixels of the footprint: alpha = o_t e^power exactly
+    ring = (araw >= 1 / 255) & ~clamped
+    assert ring.sum() > 100
+    a = araw[ring]
+    np.testing.assert_allclose(img[:, ring], rgb[:, None] * a[None] + bg[:, None] * (1 - a)[None], atol=1e-13)
+    np.testing.assert_allclose(img, img_ref, atol=1e-13)
+
+
+def test_alpha_clamp_has_zero_gradient():
+    """On pixels where alpha is clamped, the image depends on neither the
+    opacity nor the footprint's shape or position: the gradient of those pixels
+    w.r.t. the logit, log-scales, rotor and mean is zero (the colour is
+    DC-only, so it does not depend on the view direction either), and
+    d/d sh_00 = 0.99 C0 per clamped pixel."""
+    rotor, Rm, mean4, ls, sh, logit = _opaque_scene()
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 48, 48)
+    t = 0.5
+    araw = []
+    expected_single(mean4, Rm, np.exp(ls), logit, sh, cam, t, out_alpha=araw)
+    clamped = araw[0] > 0.99
+    w = np.zeros((3, 48, 48))
+    w[:, clamped] = 1.0
+    gr = oracle.render_grad(_one(mean4, rotor, ls, logit, sh), cam, t, w)
+    for k in ("logit", "logscale", "rotor", "mean"):
+        assert gr[k].abs().max().item() < 1e-12, (k, gr[k])
+    np.testing.assert_allclose(gr["sh"][0, 0].numpy(), 0.99 * C0 * clamped.sum(), rtol=1e-12)
+    # the same image weights on the unclamped ring do move the logit
+    w2 = np.zeros((3, 48, 48))
+    w2[:, (araw[0] >= 1 / 255) & ~clamped] = 1.0
+    assert abs(oracle.render_grad(_one(mean4, rotor, ls, logit, sh), cam, t, w2)["logit"].item()) > 1e-3
+
+
+@pytest.mark.parametrize("off", [(0.9, 0.0), (-0.95, 0.1), (0.1, 0.7), (-0.85, -0.68)])
+def test_jacobian_clamp_outside_the_frustum(off):
+    """A Gaussian whose camera-space x/z or y/z lies beyond 1.3 tan(fov/2) but
+    whose footprint still reaches the image: its 2D covariance uses the
+    Jacobian at the clamped point, while its centre projects unclamped."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 64, 48)
+    lx, ly = _frustum_limits(cam)
+    assert abs(off[0]) > lx or abs(off[1]) > ly
+    # camera axes of this look-at: x_c = -x, y_c = -y, z_c = z + 4
+    zc = 4.0
+    mean4 = np.array([-off[0] * zc, -off[1] * zc, 0.0, 0.5])
+    rotor, Rm = _golden_rotors()[5]
+    ls = np.log(np.array([1.0, 0.7, 0.8, 0.5]))
+    sh = np.zeros((16, 3))
+    sh[:4] = np.random.default_rng(3).normal(0, 0.4, (4, 3))
+    logit = 2.0
+    bg = np.array([0.1, 0.2, 0.3])
+    ref_c, T_c, m2 = expected_single(mean4, Rm, np.exp(ls), logit, sh, cam, 0.5, bg, jclamp=True)
+    ref_u, _, _ = expected_single(mean4, Rm, np.exp(ls), logit, sh, cam, 0.5, bg, jclamp=False)
+    assert not (0 <= m2[0] <= cam.width and 0 <= m2[1] <= cam.height)  # centre off the image
+    covered = T_c < 1
+    assert covered.sum() > 30  # the footprint reaches into the image
+    assert np.abs(ref_c - ref_u).max() > 1e-3  # the clamp changes the image (compared at 1e-12 below)
+    out = oracle.render(_one(mean4, rotor, ls, logit, sh), cam, 0.5, bg=tuple(bg))
+    np.testing.assert_allclose(out["image"].numpy(), ref_c, atol=1e-12)
+    np.testing.assert_allclose(out["T"].numpy(), T_c, atol=1e-12)
+
+
+def _clamp_flags(sc, cam, t):
+    """Which Gaussians have their Jacobian clamped (x/z or y/z beyond the limits)."""
+    rec = oracle.preprocess(sc, cam, t)
+    pc = rec["pc"].detach()
+    lx, ly = _frustum_limits(cam)
+    return ((pc[:, 0] / pc[:, 2]).abs() > lx) | ((pc[:, 1] / pc[:, 2]).abs() > ly)
+
+
+def _clamp_scene():
+    """Eight Gaussians on a 32x32 view: two opaque ones whose centres clamp
+    alpha, two beyond the frustum limits whose footprints reach the image
+    (clamped Jacobian), four ordinary ones."""
+    g = synth.gaussians(8, 31, ls_xyz=(-1.4, 0.2), ls_t=(-0.5, 0.2))
+    g["mean"][:, 3] = 0.5 + 0.05 * g["mean"][:, 3]
+    g["logit"][:2] = [7.0, 6.0]
+    g["logscale"][:2, :3] = np.log(2.0)
+    g["mean"][:2, :3] = [[0.1, 0.05, 0.3], [-0.2, -0.1, -0.2]]
+    # camera at (0,0,-4) looking at the origin: x_c = -x, z_c = z + 4
+    g["mean"][2, :3] = [-0.95 * 4.2, 0.1, 0.2]
+    g["mean"][3, :3] = [0.3, 0.85 * 3.8, -0.2]
+    g["logscale"][2:4, :3] = np.log(1.0)
+    g["logit"][2:4] = 2.0
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 32, 32)
+    return g, cam, 0.5
+
+
+def test_gradient_with_active_clamps_matches_central_differences():
+    """Central differences (FP64, h = 1e-6 max(1, |x|)) of every parameter of
+    a scene where both clamps are active, against the analytic gradient: the
+    clamps are differentiated as the piecewise functions they are (zero
+    derivative through an active clamp)."""
+    g, cam, t = _clamp_scene()
+    sc = oracle.to_f64(g)
+    jflag = _clamp_flags(sc, cam, t)
+    assert bool(jflag[2]) and bool(jflag[3]) and not bool(jflag[:2].any())
+    base_img = oracle.render(sc, cam, t)
+    n_clamped_alpha = 0
+    rec = base_img["rec"]
+    order = depth_order(rec)
+    for k in range(2):  # both opaque Gaussians clamp alpha somewhere
+        _, _, alpha_raw, *_ = _inclusion(
+            rec["mean2d"][[k]].detach(), rec["conic"][[k]].detach(), rec["opacity_t"][[k]].detach(),
+            torch.arange(32).repeat(32).double() + 0.5, torch.arange(32).repeat_interleave(32).double() + 0.5)
+        n_clamped_alpha += int((alpha_raw > 0.99).sum())
+    assert n_clamped_alpha >= 4 and order.numel() == 8
+    rng = np.random.default_rng(13)
+    wimg = rng.normal(0, 1, (3, 32, 32))
+    grads = oracle.render_grad(sc, cam, t, wimg)
+    W = torch.as_tensor(wimg)
+
+    def L(s):
+        return float((oracle.render(s, cam, t)["image"] * W).sum())
+
+    base = _decisions(sc, cam, t) + (jflag.numpy().tobytes(),)
+    checked = 0
+    for name in PARAM_NAMES:
+        flat = sc[name].reshape(-1)
+        for k in range(flat.numel()):
+            x = flat[k].item()
+            h = 1e-6 * max(1.0, abs(x))
+            vals = []
+            for sgn in (1, -1):
+                s2 = {kk: vv.clone() for kk, vv in sc.items()}
+                s2[name].reshape(-1)[k] = x + sgn * h
+                if _decisions(s2, cam, t) + (_clamp_flags(s2, cam, t).numpy().tobytes(),) != base:
+                    break
+                vals.append(L(s2))
+            if len(vals) < 2:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grads[name].reshape(-1)[k].item()
+            scale = grads[name].abs().max().item()
+            assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-3 * scale) + 1e-9, (name, int(k), fd, an)
+            checked += 1
+    assert checked >= 480
+    # the off-frustum Gaussians receive gradient through their visible footprint
+    assert grads["mean"][2:4].abs().max() > 0 and grads["logscale"][2:4].abs().max() > 0
