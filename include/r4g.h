@@ -450,6 +450,34 @@ r4g_status r4g_sort_pairs(const uint64_t* keys_in, const uint32_t* values_in,
                           int32_t begin_bit, int32_t end_bit,
                           void* scratch, size_t scratch_bytes, void* stream);
 
+/* ---- the render's own sort ----------------------------------------------------
+ * Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
+ * [0, bits), 1 <= bits <= 32, in 8-bit passes of one kernel each with a
+ * decoupled look-back between 2048-item tiles: the kernels that sort the
+ * render's depth keys and tile ids (the key-sort step of the tile rasteriser,
+ * Sec. 3.1), as an entry point of their own. values_in may be NULL (then the
+ * values are the input positions 0..n-1). keys_out/values_out must not alias
+ * the inputs; n < 2^30. scratch (device, 256-byte aligned) must hold
+ * r4g_sort32_scratch_bytes(n, bits) bytes; its first word is the call's
+ * status, which r4g_sort32_status reads (it synchronises the stream):
+ * R4G_ETIMEOUT there means a look-back wait gave up after its iteration
+ * limit and the result is invalid. Bit-exact and deterministic. */
+r4g_status r4g_sort32_scratch_bytes(int64_t n, int32_t bits, size_t* bytes /* host out */);
+r4g_status r4g_sort32(const uint32_t* keys_in, const uint32_t* values_in, uint32_t* keys_out,
+                      uint32_t* values_out, int64_t n, int32_t bits, void* scratch,
+                      size_t scratch_bytes, void* stream);
+r4g_status r4g_sort32_status(const void* scratch, void* stream);
+/* Test hook of the failure path of the look-back wait: as r4g_sort32, but the
+ * tile whose ticket is withheld_tile never publishes its counts, and every
+ * wait gives up after spin_limit (1..65536) rounds without progress instead
+ * of 2^22. The call then completes with R4G_ETIMEOUT in its status word and
+ * an invalid result; nothing hangs or faults, and the next call on the same
+ * scratch is unaffected. */
+r4g_status r4g_sort32_wait_test(const uint32_t* keys_in, const uint32_t* values_in,
+                                uint32_t* keys_out, uint32_t* values_out, int64_t n, int32_t bits,
+                                void* scratch, size_t scratch_bytes, void* stream,
+                                uint32_t withheld_tile, uint32_t spin_limit);
+
 /* ---- sort without allocation -------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory and therefore cannot pass the scratch buffer
@@ -463,7 +491,10 @@ r4g_status r4g_sort_pairs(const uint64_t* keys_in, const uint32_t* values_in,
  * contents, so calls that may overlap on the GPU (unordered streams) race and
  * corrupt each other; order them on one stream or with events. The first call
  * on each device looks up the array's device address with that device current
- * and caches it; make that first call before starting any stream capture.
+ * and caches it; make that first call before starting any stream capture. The
+ * cached address belongs to the device's primary context: after
+ * cudaDeviceReset (or any teardown of that context) it is stale, so do not
+ * call this entry point again in a process that has reset the device.
  * Error messages are returned by r4g_last_error(NULL). */
 #define R4G_SORT_NOALLOC_MAX_PAIRS 1048576
 #define R4G_SORT_NOALLOC_SCRATCH_BYTES 12894208

@@ -27,5 +27,5 @@ from .sh import sh_basis, sh_color  # noqa: F401
 from .projection import camera_tensors, project  # noqa: F401
 from .render import (  # noqa: F401
     ALPHA_MAX, ALPHA_MIN, NEAR, POWER_CUT, T_MIN, TEMPORAL_CUT, DILATION,
-    preprocess, render, render_pixels, render_grad, to_f64,
+    preprocess, render, render_pixels, render_grad, render_grad_pixels, pixel_alternatives, to_f64,
 )

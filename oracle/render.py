@@ -118,6 +118,7 @@ def _composite(m2, con, o, col, z, px, py, bg):
     img = C + T_final[:, None] * bg[None, :]
     last_pos = torch.where(included, pos[None, :], torch.full_like(pos[None, :], -1)).amax(dim=1) \
         if G > 0 else torch.full((px.shape[0],), -1, dtype=torch.long)
+    n_comp = included.sum(dim=1) if G > 0 else torch.zeros(px.shape[0], dtype=torch.long)
     # Decision margins over the Gaussians the pixel reaches (T before >= 1e-4).
     # m_thr / m_dep cover every decision; m_thr_img / m_dep_img only those
     # whose flip could move the pixel colour by IMPACT_MIN or more (a flip of
@@ -126,7 +127,7 @@ def _composite(m2, con, o, col, z, px, py, bg):
         P = px.shape[0]
         inf_row = torch.full((P,), math.inf, dtype=torch.float64)
         if G == 0:
-            return img, T_final, last_pos, inf_row, inf_row, inf_row, inf_row
+            return img, T_final, last_pos, inf_row, inf_row, inf_row, inf_row, n_comp
         Tb = T_before.detach()
         pw = power.detach()
         ar = alpha_raw.detach()
@@ -141,8 +142,10 @@ def _composite(m2, con, o, col, z, px, py, bg):
         a_cut = torch.clamp(o.detach() * math.exp(POWER_CUT), max=ALPHA_MAX)[None, :]
         imp_cut = a_cut * Tb * cmax
         imp_alpha = ALPHA_MIN * Tb * cmax
-        m_img = torch.minimum(torch.where(imp_cut >= IMPACT_MIN, m_cut, inf),
-                              torch.where(imp_alpha >= IMPACT_MIN, m_alpha, inf)).amin(dim=1)
+        imp_T = al * Tb * cmax  # a flipped stop adds or removes this Gaussian's term
+        m_img = torch.minimum(torch.minimum(torch.where(imp_cut >= IMPACT_MIN, m_cut, inf),
+                                            torch.where(imp_alpha >= IMPACT_MIN, m_alpha, inf)),
+                              torch.where(imp_T >= IMPACT_MIN, m_T, inf)).amin(dim=1)
         # depth order of consecutive contributing Gaussians
         vr = valid & reached
         posm = torch.where(vr, pos[None, :].expand_as(pw), torch.full_like(pos[None, :].expand_as(pw), -1))
@@ -155,7 +158,7 @@ def _composite(m2, con, o, col, z, px, py, bg):
         imp_dep = al * al.gather(1, pi) * Tb.gather(1, pi) * cmax
         m_dep = gap.amin(dim=1)
         m_dep_img = torch.where(imp_dep >= IMPACT_MIN, gap, inf).amin(dim=1)
-    return img, T_final, last_pos, m_thr, m_dep, m_img, m_dep_img
+    return img, T_final, last_pos, m_thr, m_dep, m_img, m_dep_img, n_comp
 
 
 def _pixel_grid(width: int, height: int):
@@ -181,8 +184,9 @@ def _chunked(rec, order, cols, rows, bg, budget=4_000_000):
     T = torch.cat([x[1] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64)
     lp = torch.cat([x[2] for x in outs]) if outs else torch.zeros(0, dtype=torch.long)
     extra = [torch.cat([x[k] for x in outs]) if outs else torch.zeros(0, dtype=torch.float64) for k in (3, 4, 5, 6)]
+    ncomp = torch.cat([x[7] for x in outs]) if outs else torch.zeros(0, dtype=torch.long)
     last = torch.where(lp >= 0, order[lp.clamp(min=0)] if G > 0 else lp, torch.full_like(lp, -1))
-    return (img, T, last, *extra)
+    return (img, T, last, *extra, ncomp)
 
 
 def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool = True,
@@ -201,7 +205,7 @@ def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool =
     W, H = cam["width"], cam["height"]
     cols, rows = _pixel_grid(W, H)
     bg_t = torch.as_tensor(bg, dtype=torch.float64)
-    img, T, last, mt, md, mi, mdi = _chunked(rec, order, cols, rows, bg_t)
+    img, T, last, mt, md, mi, mdi, _ = _chunked(rec, order, cols, rows, bg_t)
     return {
         "image": img.T.reshape(3, H, W), "T": T.reshape(H, W), "last": last.reshape(H, W),
         "margin": mt.reshape(H, W), "margin_depth": md.reshape(H, W),
@@ -211,16 +215,119 @@ def render(scene: dict, cam, t: float, bg=(0.0, 0.0, 0.0), cull_temporal: bool =
 
 def render_pixels(scene: dict, cam, t: float, pixels, bg=(0.0, 0.0, 0.0), rec: dict | None = None,
                   budget: int = 4_000_000) -> dict:
-    """Render only the listed pixels (int [P,2] as (column, row))."""
+    """Render only the listed pixels (int [P,2] as (column, row)). Also
+    returns ``n_composited``, the number of Gaussians each pixel composited."""
     cam = _cam(cam)
     if rec is None:
         rec = preprocess(scene, cam, t)
     order = depth_order(rec)
     pix = torch.as_tensor(np.asarray(pixels), dtype=torch.long)
     bg_t = torch.as_tensor(bg, dtype=torch.float64)
-    img, T, last, mt, md, mi, mdi = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
+    img, T, last, mt, md, mi, mdi, nc = _chunked(rec, order, pix[:, 0], pix[:, 1], bg_t, budget)
     return {"rgb": img, "T": T, "last": last, "margin": mt, "margin_depth": md, "margin_img": mi,
-            "margin_depth_img": mdi}
+            "margin_depth_img": mdi, "n_composited": nc}
+
+
+def pixel_alternatives(rec: dict, pixel, rel_margin: float, rel_gap: float, bg=(0.0, 0.0, 0.0)) -> list:
+    """The colours one pixel takes under every result that the rounding of its
+    threshold decisions and depth order leaves open (Eq. 3 with the per-pixel
+    rules of this module): the colour in the global depth order with every
+    decision as computed, then one colour per open decision with that decision
+    taken the other way, and one with all of them taken the other way.
+
+    Open decisions, over the Gaussians the pixel reaches (T before >= 1e-4):
+      cutoff   |power + 4.5| / 4.5 < rel_margin         (skip <-> keep)
+      alpha    |o_t e^power - 1/255| / (1/255) < rel_margin (skip <-> keep)
+      stop     |T' - 1e-4| / 1e-4 < rel_margin           (stop <-> composite)
+      depth    consecutive contributors whose depths differ by less than
+               rel_gap (relative)                         (order swapped)
+    Returns a list of float64 [3] tensors, the computed colour first."""
+    order = depth_order(rec)
+    bg_t = torch.as_tensor(bg, dtype=torch.float64)
+    px = torch.tensor([float(pixel[0]) + 0.5], dtype=torch.float64)
+    py = torch.tensor([float(pixel[1]) + 0.5], dtype=torch.float64)
+    with torch.no_grad():
+        m2 = rec["mean2d"].detach()[order]
+        con = rec["conic"].detach()[order]
+        o = rec["opacity_t"].detach()[order]
+        col = rec["rgb"].detach()[order]
+        z = rec["z"].detach()[order]
+        G = int(order.numel())
+        if G == 0:
+            return [bg_t.clone()]
+        power, in_cut, alpha_raw, alpha, valid = [x[0] for x in _inclusion(m2, con, o, px, py)[:5]]
+
+        def walk(valid_mask, perm, stop_flips):
+            """Front-to-back compositing of one pixel over the positions in
+            ``perm`` with the given validity; ``stop_flips`` holds the
+            positions whose stop decision is taken the other way. Returns the
+            colour and the open decisions met: (kind, position)."""
+            C = torch.zeros(3, dtype=torch.float64)
+            T = 1.0
+            opened = []
+            for p in perm:
+                if T < T_MIN:
+                    break
+                if abs(float(power[p]) - POWER_CUT) / abs(POWER_CUT) < rel_margin:
+                    opened.append(("cut", p))
+                if bool(in_cut[p]) and abs(float(alpha_raw[p]) - ALPHA_MIN) / ALPHA_MIN < rel_margin:
+                    opened.append(("alpha", p))
+                if not bool(valid_mask[p]):
+                    continue
+                a = float(alpha[p])
+                Tn = T * (1.0 - a)
+                stop = Tn < T_MIN
+                if abs(Tn - T_MIN) / T_MIN < rel_margin:
+                    opened.append(("stop", p))
+                if p in stop_flips:
+                    stop = not stop
+                if stop:
+                    break
+                C = C + col[p] * (a * T)
+                T = Tn
+            return C + T * bg_t, opened
+
+        # candidates: positions inside the cutoff or within the margin of it
+        near = (power <= 0.0) & (power >= POWER_CUT * (1.0 + 2.0 * rel_margin))
+        perm = torch.nonzero(near).flatten().tolist()
+        base, opened = walk(valid, perm, set())
+        out = [base]
+        flips_v, flips_s = [], set()
+        for kind, p in opened:
+            v = valid.clone()
+            if kind == "stop":
+                out.append(walk(v, perm, {p})[0])
+                flips_s.add(p)
+            else:
+                v[p] = ~v[p]
+                out.append(walk(v, perm, set())[0])
+                flips_v.append(p)
+        # depth ties between consecutive contributors (composited in the base walk)
+        contrib = []  # indices into perm
+        T = 1.0
+        for i, p in enumerate(perm):
+            if not bool(valid[p]):
+                continue
+            Tn = T * (1.0 - float(alpha[p]))
+            if Tn < T_MIN:
+                break
+            contrib.append(i)
+            T = Tn
+        close = [(a, b) for a, b in zip(contrib[:-1], contrib[1:])
+                 if (z[perm[b]] - z[perm[a]]) / z[perm[b]] < rel_gap]
+        for a, b in close:
+            p2 = list(perm)
+            p2[a], p2[b] = perm[b], perm[a]
+            out.append(walk(valid, p2, set())[0])
+        if len(opened) + len(close) > 1:
+            v = valid.clone()
+            for p in flips_v:
+                v[p] = ~v[p]
+            p2 = list(perm)
+            for a, b in close:
+                p2[a], p2[b] = perm[b], perm[a]
+            out.append(walk(v, p2, flips_s)[0])
+    return out
 
 
 def composited_counts(scene: dict, cam, t: float, rec: dict | None = None, budget: int = 4_000_000) -> torch.Tensor:
@@ -260,23 +367,45 @@ def render_grad(scene: dict, cam, t: float, grad_image, bg=(0.0, 0.0, 0.0), sh_d
     pulled back through ``preprocess``. Returns the parameter gradients under
     the parameter names and the record gradients under ``rec_<name>``."""
     cam = _cam(cam)
+    W, H = cam["width"], cam["height"]
+    cols, rows = _pixel_grid(W, H)
+    gi = torch.as_tensor(np.asarray(grad_image), dtype=torch.float64).reshape(3, H * W).T
+    return _grad_over(scene, cam, t, cols, rows, gi, bg, sh_degree, None, 2_000_000)
+
+
+def render_grad_pixels(scene: dict, cam, t: float, pixels, grad_rgb, bg=(0.0, 0.0, 0.0), keep=None,
+                       sh_degree: int = 3, budget: int = 2_000_000) -> dict:
+    """Gradient of L = sum over the listed pixels (int [P,2] as (column, row))
+    of grad_rgb [P,3] * rgb, the same function as ``render_grad`` restricted to
+    those pixels. ``keep`` (bool [N]) optionally limits the compositing to a
+    subset of the Gaussians, kept in the global depth order; callers pass the
+    Gaussians whose 3-sigma box meets the pixels, which changes no listed pixel
+    since every other Gaussian fails the power >= -4.5 cutoff there."""
+    cam = _cam(cam)
+    pix = torch.as_tensor(np.asarray(pixels), dtype=torch.long)
+    gi = torch.as_tensor(np.asarray(grad_rgb), dtype=torch.float64).reshape(-1, 3)
+    return _grad_over(scene, cam, t, pix[:, 0], pix[:, 1], gi, bg, sh_degree, keep, budget)
+
+
+def _grad_over(scene, cam, t, cols, rows, gi, bg, sh_degree, keep, budget):
     leaves = {k: v.detach().clone().requires_grad_(True) for k, v in scene.items()}
     rec = preprocess(leaves, cam, t, True, sh_degree)
     recd = {k: (rec[k].detach().clone().requires_grad_(True) if k in REC_GRAD_KEYS else rec[k])
             for k in rec}
     order = depth_order(recd)
-    W, H = cam["width"], cam["height"]
-    cols, rows = _pixel_grid(W, H)
-    gi = torch.as_tensor(np.asarray(grad_image), dtype=torch.float64).reshape(3, H * W).T
+    if keep is not None:
+        keep_t = torch.as_tensor(np.asarray(keep), dtype=torch.bool)
+        order = order[keep_t[order]]
     bg_t = torch.as_tensor(bg, dtype=torch.float64)
     G = max(int(order.numel()), 1)
-    step = max(1, 2_000_000 // G)
+    step = max(1, budget // G)
     m2 = recd["mean2d"][order]
     con = recd["conic"][order]
     o = recd["opacity_t"][order]
     col = recd["rgb"][order]
     z = recd["z"].detach()[order]
-    for s in range(0, H * W, step):
+    P = int(cols.numel())
+    for s in range(0, P, step):
         px = cols[s:s + step].to(torch.float64) + 0.5
         py = rows[s:s + step].to(torch.float64) + 0.5
         img = _composite(m2, con, o, col, z, px, py, bg_t)[0]

@@ -9,7 +9,7 @@ from . import abi  # noqa: F401
 from .render import (  # noqa: F401
     PARAM_NAMES, BatchGraph, BatchResult, Render4DBatchFunction, Render4DFunction, Renderer, RenderResult,
     camera_struct, densify, densify_config, density_stats, gaussians_struct, image_loss, knn4d, opacity_reset,
-    regularizers, render, render_batch, render_flow, sort_pairs, view_struct, views_tensor,
+    regularizers, render, render_batch, render_flow, sort32, sort_pairs, view_struct, views_tensor,
 )
 
 abi.lib()  # fail loudly here if libr4g.so is missing

@@ -125,6 +125,12 @@ SIGNATURES = [
                                  C.c_int32, C.c_int32, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("r4g_sort_pairs_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                          C.c_int32, C.c_int32, C.c_void_p]),
+    ("r4g_sort32_scratch_bytes", C.c_int, [C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("r4g_sort32", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                             C.c_void_p, C.c_size_t, C.c_void_p]),
+    ("r4g_sort32_status", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("r4g_sort32_wait_test", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                       C.c_void_p, C.c_size_t, C.c_void_p, C.c_uint32, C.c_uint32]),
 ]
 
 
@@ -360,6 +366,16 @@ def r4g_sort_scratch_bytes(n: int) -> int:
     out = C.c_size_t()
     check(lib().r4g_sort_scratch_bytes(n, C.byref(out)))
     return out.value
+
+
+def r4g_sort32_scratch_bytes(n: int, bits: int) -> int:
+    out = C.c_size_t()
+    check(lib().r4g_sort32_scratch_bytes(n, bits, C.byref(out)))
+    return out.value
+
+
+def r4g_sort32(keys_in, values_in, keys_out, values_out, n, bits, scratch, scratch_bytes, stream) -> None:
+    check(lib().r4g_sort32(keys_in, values_in, keys_out, values_out, n, bits, scratch, scratch_bytes, stream))
 
 
 def r4g_sort_pairs(keys_in, values_in, keys_out, values_out, n, begin_bit, end_bit, scratch,

@@ -469,7 +469,7 @@ r4g_status r4g_frame_bytes(const r4g_ctx* ctx, int64_t n, int32_t width, int32_t
   if (!ctx || !bytes) return fail(c, R4G_EINVAL, "NULL argument");
   if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, R4G_EINVAL, "n out of range");
   if (width <= 0 || height <= 0 || width > 32768 || height > 32768) return fail(c, R4G_EINVAL, "bad image size");
-  if (key_capacity < 0 || key_capacity > int64_t(0xffffffffu)) return fail(c, R4G_EINVAL, "key_capacity out of range");
+  if (key_capacity < 0 || key_capacity >= int64_t(1) << 30) return fail(c, R4G_EINVAL, "key_capacity out of range (< 2^30)");
   *bytes = make_layout1(n, width, height, key_capacity, ctx->cfg.tile_w, ctx->cfg.tile_h).total;
   return R4G_OK;
 }

@@ -23,6 +23,7 @@
 // for the key capacity has more CTAs than tiles; the surplus leaves at once.
 #include <cuda_runtime.h>
 
+#include "r4g.h"
 #include "r4g_internal.cuh"
 
 namespace r4g {
@@ -94,7 +95,8 @@ __global__ void __launch_bounds__(kSortThreads)
     onesweep_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* count_dev,
                          uint32_t count_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
-                         uint32_t* status, uint32_t* ticket, uint32_t* err) {
+                         uint32_t* status, uint32_t* ticket, uint32_t* err, uint32_t withheld_tile,
+                         uint32_t spin_limit) {
   constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_dstart[kSortRadix];   // global start of each digit + tile prefix
@@ -171,8 +173,11 @@ __global__ void __launch_bounds__(kSortThreads)
   // status and no look-back: its count is zero in every tile)
   const uint32_t h = hist[dd];
   const bool live = h != 0u;
+  // withheld_tile (a test of the bounded wait only; otherwise no tile): that
+  // tile never publishes, so its successors' waits run out
+  const bool publish = t != withheld_tile;
   uint32_t* st = status + static_cast<size_t>(t) * kSortRadix;
-  if (live) store_relaxed(st + dd, (t == 0 ? kFlagPrefix : kFlagAgg) | cnt);
+  if (live && publish) store_relaxed(st + dd, (t == 0 ? kFlagPrefix : kFlagAgg) | cnt);
   // Look-back, kOsWin predecessors per round (their statuses are read in
   // parallel): add published counts newest first until a published prefix;
   // a round that makes no progress counts against the spin limit.
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kSortThreads)
       }
       kt -= used;
       if (used == 0) {
-        if (++idle >= kSpinLimit) {  // gave up: record it and go on
+        if (++idle >= spin_limit) {  // gave up: record it and go on
           atomicOr(err, 2u);
           break;
         }
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads)
         nap = nap < 256u ? 2u * nap : 256u;
       }
     }
-    store_relaxed(st + dd, kFlagPrefix | (excl + cnt));
+    if (publish) store_relaxed(st + dd, kFlagPrefix | (excl + cnt));
   }
   // global digit start: exclusive scan of this pass's histogram (+ tile prefix)
   {
@@ -296,7 +301,8 @@ cudaError_t prepare_onesweep(void* scratch, int64_t cap, int bits, bool hist_rea
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf, bool hist_ready, bool prepared) {
+                            int* result_in_buf, bool hist_ready, bool prepared, uint32_t withheld_tile,
+                            uint32_t spin_limit) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   *result_in_buf = 0;
   if (passes == 0 || cap == 0) return cudaSuccess;
@@ -331,7 +337,8 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
     const cudaError_t e =
         launch_pdl(onesweep_pass_kernel, static_cast<unsigned>(tiles), kSortThreads, 0, s, ki, vi, ko, vo, count_dev,
                    count_host, shift, (1u << nb) - 1u, static_cast<const uint32_t*>(hist + p * kSortRadix),
-                   status + static_cast<size_t>(p) * pass_words, tickets + p, err);
+                   status + static_cast<size_t>(p) * pass_words, tickets + p, err, withheld_tile,
+                   spin_limit ? spin_limit : kSpinLimit);
     if (e != cudaSuccess) return e;
     ki = ko;
     vi = vo;
@@ -342,3 +349,80 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
 }
 
 }  // namespace r4g
+
+// ---- r4g_sort32: the render's sort as an entry point of its own ----------------
+// scratch: [error word | pad to 256 B][keys n][values n][onesweep scratch]
+namespace {
+constexpr size_t kS32Align = 256;
+size_t s32_al(size_t x) { return (x + kS32Align - 1) / kS32Align * kS32Align; }
+size_t s32_bytes(int64_t n, int bits) {
+  return kS32Align + 2 * s32_al(sizeof(uint32_t) * static_cast<size_t>(n)) + r4g::onesweep_scratch_bytes(n, bits);
+}
+r4g_status s32_fail(r4g_status st, const char* msg) {
+  r4g::set_last_error(msg);
+  return st;
+}
+r4g_status s32_run(const uint32_t* keys_in, const uint32_t* values_in, uint32_t* keys_out, uint32_t* values_out,
+                   int64_t n, int32_t bits, void* scratch, size_t scratch_bytes, void* stream,
+                   uint32_t withheld_tile, uint32_t spin_limit) {
+  if (n < 0 || n >= (int64_t(1) << 30)) return s32_fail(R4G_EINVAL, "r4g_sort32: n out of range (< 2^30)");
+  if (bits < 1 || bits > 32) return s32_fail(R4G_EINVAL, "r4g_sort32: bits must be in [1, 32]");
+  if (!scratch || scratch_bytes < s32_bytes(n, bits)) return s32_fail(R4G_EWORKSPACE, "r4g_sort32: scratch too small");
+  if (reinterpret_cast<uintptr_t>(scratch) % kS32Align) return s32_fail(R4G_EINVAL, "r4g_sort32: scratch not 256-byte aligned");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t* err = static_cast<uint32_t*>(scratch);
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return s32_fail(R4G_ECUDA, cudaGetErrorString(e));
+  if (n == 0) return R4G_OK;
+  if (!keys_in || !keys_out || !values_out) return s32_fail(R4G_EINVAL, "r4g_sort32: NULL buffer");
+  if (keys_in == keys_out || (values_in && values_in == values_out))
+    return s32_fail(R4G_EINVAL, "r4g_sort32: outputs alias inputs");
+  char* base = static_cast<char*>(scratch) + kS32Align;
+  uint32_t* tk = reinterpret_cast<uint32_t*>(base);
+  uint32_t* tv = reinterpret_cast<uint32_t*>(base + s32_al(sizeof(uint32_t) * n));
+  void* os = base + 2 * s32_al(sizeof(uint32_t) * n);
+  // pass p writes buffer 1 when p is even: an odd pass count ends in buffer 1
+  const int passes = (bits + r4g::kSortRadixBits - 1) / r4g::kSortRadixBits;
+  const bool odd = passes % 2 == 1;
+  int which = 0;
+  e = r4g::launch_onesweep(keys_in, values_in, odd ? keys_out : tk, odd ? values_out : tv, odd ? tk : keys_out,
+                           odd ? tv : values_out, nullptr, static_cast<uint32_t>(n), n, bits, os, err, s, &which,
+                           false, false, withheld_tile, spin_limit);
+  if (e != cudaSuccess) return s32_fail(R4G_ECUDA, cudaGetErrorString(e));
+  return R4G_OK;
+}
+}  // namespace
+
+extern "C" r4g_status r4g_sort32_scratch_bytes(int64_t n, int32_t bits, size_t* bytes) {
+  if (!bytes) return s32_fail(R4G_EINVAL, "r4g_sort32_scratch_bytes: NULL output");
+  if (n < 0 || n >= (int64_t(1) << 30) || bits < 1 || bits > 32)
+    return s32_fail(R4G_EINVAL, "r4g_sort32_scratch_bytes: n or bits out of range");
+  *bytes = s32_bytes(n, bits);
+  return R4G_OK;
+}
+
+extern "C" r4g_status r4g_sort32(const uint32_t* keys_in, const uint32_t* values_in, uint32_t* keys_out,
+                                 uint32_t* values_out, int64_t n, int32_t bits, void* scratch, size_t scratch_bytes,
+                                 void* stream) {
+  return s32_run(keys_in, values_in, keys_out, values_out, n, bits, scratch, scratch_bytes, stream, 0xffffffffu, 0u);
+}
+
+extern "C" r4g_status r4g_sort32_wait_test(const uint32_t* keys_in, const uint32_t* values_in, uint32_t* keys_out,
+                                           uint32_t* values_out, int64_t n, int32_t bits, void* scratch,
+                                           size_t scratch_bytes, void* stream, uint32_t withheld_tile,
+                                           uint32_t spin_limit) {
+  if (spin_limit == 0 || spin_limit > (1u << 16))
+    return s32_fail(R4G_EINVAL, "r4g_sort32_wait_test: spin_limit must be in [1, 65536]");
+  return s32_run(keys_in, values_in, keys_out, values_out, n, bits, scratch, scratch_bytes, stream, withheld_tile,
+                 spin_limit);
+}
+
+extern "C" r4g_status r4g_sort32_status(const void* scratch, void* stream) {
+  if (!scratch) return s32_fail(R4G_EINVAL, "r4g_sort32_status: NULL scratch");
+  uint32_t w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, scratch, sizeof(w), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return s32_fail(R4G_ECUDA, cudaGetErrorString(e));
+  if (w & 2u) return s32_fail(R4G_ETIMEOUT, "r4g_sort32: a look-back wait ran out (the result is invalid)");
+  return R4G_OK;
+}

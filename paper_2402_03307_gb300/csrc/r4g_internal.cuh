@@ -187,7 +187,8 @@ size_t onesweep_scratch_bytes(int64_t cap, int bits);
 cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* kbuf1, uint32_t* vbuf1,
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
-                            int* result_in_buf, bool hist_ready = false, bool prepared = false);
+                            int* result_in_buf, bool hist_ready = false, bool prepared = false,
+                            uint32_t withheld_tile = 0xffffffffu, uint32_t spin_limit = 0u);
 // What launch_onesweep clears before its passes (tickets, statuses and, unless
 // hist_ready, the histograms), enqueued separately so it can run early on
 // another stream; then call launch_onesweep with prepared = true.

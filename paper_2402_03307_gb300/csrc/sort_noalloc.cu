@@ -19,7 +19,8 @@
 //    count and every buffer element it later reads;
 //  * the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current and caches it; make
-//    that first call before any stream capture is started.
+//    that first call before any stream capture is started. The cache belongs
+//    to the device's primary context and does not survive cudaDeviceReset.
 #include <cuda_runtime.h>
 
 #include <cstdio>

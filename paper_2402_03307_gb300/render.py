@@ -623,6 +623,23 @@ def sort_pairs(keys: torch.Tensor, values: torch.Tensor, begin_bit: int = 0, end
     return ko, vo
 
 
+def sort32(keys: torch.Tensor, values: torch.Tensor | None = None, bits: int = 32):
+    """Stable radix sort of (int32 key as uint32 bits, int32 value) pairs on
+    key bits [0, bits) with the render's own sort kernels (r4g_sort32);
+    ``values`` None sorts the positions 0..n-1. Returns new tensors; raises
+    R4GError if a look-back wait gave up (r4g_sort32_status)."""
+    n = int(keys.numel())
+    ko = torch.empty_like(keys)
+    vo = torch.empty(n, dtype=torch.int32, device=keys.device)
+    nb = abi.r4g_sort32_scratch_bytes(n, bits)
+    scratch = torch.empty(nb, dtype=torch.uint8, device=keys.device)
+    s = torch.cuda.current_stream(keys.device).cuda_stream
+    abi.r4g_sort32(keys.data_ptr(), values.data_ptr() if values is not None else None, ko.data_ptr(), vo.data_ptr(),
+                   n, bits, scratch.data_ptr(), nb, s)
+    abi.check(abi.lib().r4g_sort32_status(scratch.data_ptr(), s))
+    return ko, vo
+
+
 def densify_config(grad_threshold: float = 2e-4, dense_scale: float = 0.06, split_divisor: float = 1.6,
                    min_opacity: float = 0.005, max_scale: float = 0.0,
                    max_screen_radius: float = 0.0) -> abi.r4g_densify_config:

@@ -69,8 +69,10 @@ def gaussians(n: int, seed: int, mean_lo: float = -1.0, mean_hi: float = 1.0,
               ls_xyz: tuple[float, float] = (-3.0, 0.5),
               ls_t: tuple[float, float] = (-2.0, 0.5),
               sh_dc: tuple[float, float] = (0.5, 0.2),
-              sh_rest_std: float = 0.05) -> dict[str, np.ndarray]:
-    """Draw N Gaussians; draw order mean, logscale, rotor, logit, SH."""
+              sh_rest_std: float = 0.05,
+              logit_dist: tuple[float, float] = (0.0, 1.0)) -> dict[str, np.ndarray]:
+    """Draw N Gaussians; draw order mean, logscale, rotor, logit, SH. The
+    opacity logit is N(logit_dist); N(4, 1) gives mostly opaque Gaussians."""
     rng = np.random.default_rng(seed)
     mean = np.empty((n, 4), np.float64)
     mean[:, :3] = rng.uniform(mean_lo, mean_hi, (n, 3))
@@ -79,7 +81,7 @@ def gaussians(n: int, seed: int, mean_lo: float = -1.0, mean_hi: float = 1.0,
     logscale[:, :3] = rng.normal(ls_xyz[0], ls_xyz[1], (n, 3))
     logscale[:, 3] = rng.normal(ls_t[0], ls_t[1], n)
     rotor = rng.normal(0.0, 1.0, (n, 8))
-    logit = rng.normal(0.0, 1.0, n)
+    logit = rng.normal(logit_dist[0], logit_dist[1], n)
     sh = np.empty((n, 16, 3), np.float64)
     sh[:, 0, :] = rng.normal(sh_dc[0], sh_dc[1], (n, 3))
     sh[:, 1:, :] = rng.normal(0.0, sh_rest_std, (n, 15, 3))

@@ -11,10 +11,9 @@ import torch
 
 import oracle
 import synth
-from gpu_util import ambiguous, to_device
+from gpu_util import NAMES, compare_grads, gpu_grads, grad_weights, to_device
 
 pytestmark = pytest.mark.gpu
-NAMES = ("mean", "rotor", "logscale", "logit", "sh")
 
 
 @pytest.fixture(scope="module")
@@ -25,34 +24,9 @@ def r4g():
     return m
 
 
-def _weights(g, cam, t, seed, bg=(0.0, 0.0, 0.0)):
-    ref = oracle.render(oracle.to_f64(g), cam, t, bg=bg)
-    amb = ambiguous(ref, image=False)
-    w = np.random.default_rng(seed).normal(0, 1, (3, cam.height, cam.width))
-    w[:, amb] = 0.0
-    return w.astype(np.float32)
-
-
-def _gpu_grads(r4g, g, cam, t, w, **kw):
-    rend = r4g.Renderer(**kw)
-    p = to_device(g)
-    res = rend.render(p, cam, t)
-    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in p.items()}
-    rend.backward(p, cam, t, res, torch.as_tensor(w).cuda(), grads)
-    torch.cuda.synchronize()
-    return {k: v.double().cpu().numpy() for k, v in grads.items()}
-
-
-def _compare(got, ref, tag):
-    for k in NAMES:
-        a = got[k].reshape(-1)
-        b = ref[k].numpy().reshape(-1)
-        nb = np.linalg.norm(b)
-        assert nb > 0, (tag, k)
-        rel = np.linalg.norm(a - b) / nb
-        assert rel <= 1e-2, (tag, k, rel)
-        bad = np.abs(a - b) > 1e-2 * (np.abs(b) + 1e-3 * np.abs(b).max())
-        assert bad.mean() <= 1e-3, (tag, k, bad.mean(), int(bad.sum()))
+_weights = grad_weights
+_gpu_grads = gpu_grads
+_compare = compare_grads
 
 
 def test_backward_fd_workload(r4g):

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import MAX_ABS, MIN_PSNR, ambiguous, gpu_last_ids, image_report, to_device
+from gpu_util import MAX_ABS, MIN_PSNR, ambiguous, gpu_last_ids, image_report, sampled_report, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -28,10 +28,11 @@ def _render(r4g, g, cam, t, **kw):
     return rend, res
 
 
-def _check_image(img, ref, tag=""):
-    rep = image_report(img, ref)
+def _check_image(img, ref, tag="", bg=(0.0, 0.0, 0.0)):
+    rep = image_report(img, ref, bg)
     assert rep["ambiguous"] < 1e-4 or rep["ambiguous"] * img.shape[1] * img.shape[2] <= 2, (tag, rep["ambiguous"])
     assert rep["max_abs"] <= MAX_ABS, (tag, rep["max_abs"])
+    assert rep["unresolved"] == 0, (tag, rep["unresolved"], rep["max_abs_ambiguous"])
     assert rep["psnr"] > MIN_PSNR, (tag, rep["psnr"])
     return rep
 
@@ -132,7 +133,7 @@ def test_background_and_sh_degree(r4g):
         bg = (0.25, 0.5, 1.0)
         _, res = _render(r4g, g, cam, t, bg=bg, sh_degree=deg)
         ref = oracle.render(oracle.to_f64(g), cam, t, bg=bg, sh_degree=deg)
-        _check_image(res.image.cpu().numpy(), ref, f"deg{deg}")
+        _check_image(res.image.cpu().numpy(), ref, f"deg{deg}", bg)
 
 
 def test_empty_and_fully_culled_scenes(r4g):
@@ -201,12 +202,17 @@ def test_full_size_frame_sampled_pixels(r4g):
     img = res.image.cpu().numpy()
     assert np.isfinite(img).all() and img.min() >= 0
     pix = synth.random_pixels(5, 1352, 1014, 1500)
-    ref = oracle.render_pixels(oracle.to_f64(g), cam, t, pix)
-    amb = ambiguous(ref, image=True)
+    sc = oracle.to_f64(g)
+    rec = oracle.preprocess(sc, cam, t)
+    ref = oracle.render_pixels(sc, cam, t, pix, rec=rec)
     got = img[:, pix[:, 1], pix[:, 0]].T
-    err = np.abs(got - ref["rgb"].numpy())
-    assert amb.mean() < 0.02
-    assert err[~amb].max() <= MAX_ABS, err[~amb].max()
+    rep = sampled_report(got, ref, rec, pix)
+    print(f"fwd300k frame 37: {rep['n_ambiguous']} of {len(pix)} sampled pixels ambiguous "
+          f"({rep['ambiguous']:.2e}), max abs {rep['max_abs']:.2e}, ambiguous vs alternatives "
+          f"{rep['max_abs_ambiguous']:.2e}")
+    assert rep["max_abs"] <= MAX_ABS, rep
+    assert rep["unresolved"] == 0, rep
+    assert rep["ambiguous"] < 0.01, rep  # depth ties of FP32 depths; each checked against both orders
     assert (ref["rgb"].numpy().sum(1) > 0).mean() > 0.5
 
 
@@ -265,9 +271,14 @@ def test_inside_the_cloud_sampled_pixels(r4g):
     assert np.isfinite(img).all() and img.min() >= 0
     assert rend.export(res)["key_count"] > 3_000_000
     pix = synth.random_pixels(6, 1352, 1014, 1000)
-    ref = oracle.render_pixels(oracle.to_f64(g), cam, t, pix)
-    amb = ambiguous(ref, image=True)
+    sc = oracle.to_f64(g)
+    rec = oracle.preprocess(sc, cam, t)
+    ref = oracle.render_pixels(sc, cam, t, pix, rec=rec)
     got = img[:, pix[:, 1], pix[:, 0]].T
-    err = np.abs(got - ref["rgb"].numpy())
-    assert amb.mean() < 0.02
-    assert err[~amb].max() <= MAX_ABS, err[~amb].max()
+    rep = sampled_report(got, ref, rec, pix)
+    print(f"fwd300k radius 4 frame 120: {rep['n_ambiguous']} of {len(pix)} sampled pixels ambiguous, "
+          f"max abs {rep['max_abs']:.2e}; composited per pixel: mean "
+          f"{float(ref['n_composited'].double().mean()):.1f}")
+    assert rep["max_abs"] <= MAX_ABS, rep
+    assert rep["unresolved"] == 0, rep
+    assert rep["ambiguous"] < 0.01, rep

@@ -498,3 +498,72 @@ def test_gradient_with_active_clamps_matches_central_differences():
     assert checked >= 480
     # the off-frustum Gaussians receive gradient through their visible footprint
     assert grads["mean"][2:4].abs().max() > 0 and grads["logscale"][2:4].abs().max() > 0
+
+
+def test_pixel_gradient_restricted_to_a_block():
+    """The gradient over a listed block of pixels, compositing only the
+    Gaussians whose 3-sigma box meets the block, equals the full-image
+    gradient with the upstream gradient zero outside the block."""
+    from gpu_util import block_pixels, box_keep
+    g, cam, t = synth.small_scene(seed=33, n=400, width=48, height=40)
+    sc = oracle.to_f64(g)
+    x0, y0, w, h = 13, 9, 20, 16
+    rng = np.random.default_rng(4)
+    gimg = np.zeros((3, 40, 48))
+    gimg[:, y0:y0 + h, x0:x0 + w] = rng.normal(0, 1, (3, h, w))
+    full = oracle.render_grad(sc, cam, t, gimg)
+    rec = oracle.preprocess(sc, cam, t)
+    keep = box_keep(rec, x0, y0, w, h)
+    assert 0 < keep.sum() < rec["visible"].sum()  # the restriction drops Gaussians
+    pix = block_pixels(x0, y0, w, h)
+    part = oracle.render_grad_pixels(sc, cam, t, pix, gimg[:, pix[:, 1], pix[:, 0]].T, keep=keep)
+    for k in PARAM_NAMES:
+        np.testing.assert_allclose(part[k].numpy(), full[k].numpy(), atol=1e-12, rtol=1e-9)
+    out = oracle.render_pixels(sc, cam, t, pix)
+    ref = oracle.render(sc, cam, t)
+    assert torch.equal(out["last"], ref["last"][y0:y0 + h, x0:x0 + w].reshape(-1))
+    # composited count: consistent with the final transmittance (no Gaussian -> T = 1)
+    assert ((out["n_composited"] == 0) == (out["T"] == 1.0)).all()
+
+
+def test_alternatives_closed_forms():
+    """Alternatives of one pixel (Eq. 3 under each open decision):
+    two Gaussians whose depths differ by 1e-9 relative give the two
+    compositing orders c1 a1 + c2 a2 (1 - a1) and c2 a2 + c1 a1 (1 - a2);
+    two clamped layers give T' = (1 - 0.99)^2, at the 1e-4 stop threshold, so
+    both 0.99 c1 + 0.0099 c2 (composited) and 0.99 c1 (stopped) are open;
+    a pixel with no open decision has one colour."""
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 33, 33)
+    ident = np.zeros(8)
+    ident[0] = 1
+
+    def scene(specs):
+        parts = []
+        for dz, c, logit in specs:
+            sh = np.zeros((16, 3))
+            sh[0] = c
+            parts.append(_one((0.0, 0.0, dz, 0.5), ident, np.log([0.3, 0.3, 0.3, 1.0]), logit, sh))
+        return oracle.preprocess({k: torch.cat([p[k] for p in parts]) for k in parts[0]}, cam, 0.5)
+
+    c = [0.5 + C0 * 0.4, 0.5 + C0 * -0.3]
+    rec = scene(((0.0, 0.4, 0.5), (4e-9, -0.3, 1.5)))
+    alts = oracle.pixel_alternatives(rec, (16, 16), 1e-5, 1e-7)
+    assert len(alts) == 2
+    a = [1 / (1 + math.exp(-0.5)), 1 / (1 + math.exp(-1.5))]  # centre pixel: power = 0
+    first = c[0] * a[0] + c[1] * a[1] * (1 - a[0])  # index 0 nearer (smaller z)
+    second = c[1] * a[1] + c[0] * a[0] * (1 - a[1])
+    assert abs(alts[0][0].item() - first) < 1e-12 and abs(alts[1][0].item() - second) < 1e-12
+    assert len(oracle.pixel_alternatives(rec, (16, 16), 1e-5, 1e-10)) == 1  # gap above the bound
+    # two opaque layers 0.5 apart: alpha clamps to 0.99 on both
+    rec = scene(((0.0, 0.4, 9.0), (0.5, -0.3, 9.0)))
+    alts = oracle.pixel_alternatives(rec, (16, 16), 1e-5, 1e-7)
+    got = sorted(float(x[0]) for x in alts)
+    want = sorted([0.99 * c[0] + 0.99 * 0.01 * c[1], 0.99 * c[0]])
+    assert len(alts) == 2 and max(abs(g - w) for g, w in zip(got, want)) < 1e-12
+    ref = oracle.render_pixels(None, cam, 0.5, np.array([[16, 16]]), rec=rec)
+    assert abs(float(alts[0][0]) - float(ref["rgb"][0, 0])) < 1e-15  # the computed colour comes first
+    # a pixel away from every threshold: one colour, equal to the render's
+    rec = scene(((0.0, 0.4, 0.5), (0.5, -0.3, 1.5)))
+    alts = oracle.pixel_alternatives(rec, (15, 17), 1e-5, 1e-7)
+    ref = oracle.render_pixels(None, cam, 0.5, np.array([[15, 17]]), rec=rec)
+    assert len(alts) == 1 and torch.allclose(alts[0], ref["rgb"][0], atol=1e-15, rtol=0)

@@ -46,6 +46,39 @@ def test_matches_the_allocating_sort_twice_in_a_row(r4g, cases):
         torch.cuda.synchronize()
         assert torch.equal(ko, rk) and torch.equal(vo, rv), (n, b0, b1)
         assert torch.equal(kd.cpu(), torch.as_tensor(keys.view(np.int64)))  # inputs untouched
+        # and against a CPU stable sort on the same key bits
+        mask = np.uint64((1 << (b1 - b0)) - 1) if b1 - b0 < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+        order = np.argsort((keys >> np.uint64(b0)) & mask, kind="stable")
+        assert np.array_equal(ko.cpu().numpy().view(np.uint64), keys[order]), (n, b0, b1)
+        assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order]), (n, b0, b1)
+
+
+def test_allocates_no_device_memory(r4g):
+    """After a warm call, further calls change neither the device's free
+    memory nor what PyTorch's allocator holds."""
+    from paper_2402_03307_gb300 import abi
+    lib = abi.lib()
+    keys, vals = synth.random_keys(seed=77, n=500_000, high_bits=13)
+    kd = torch.as_tensor(keys.view(np.int64)).cuda()
+    vd = torch.as_tensor(vals.view(np.int32)).cuda()
+    ko = torch.empty_like(kd)
+    vo = torch.empty_like(vd)
+    s = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        st = lib.r4g_sort_pairs_noalloc(kd.data_ptr(), vd.data_ptr(), ko.data_ptr(), vo.data_ptr(),
+                                        kd.numel(), 0, 45, s)
+        assert st == 0, lib.r4g_last_error(None)
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    held0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == held0
 
 
 def test_rejects_sizes_beyond_the_limit(r4g):
