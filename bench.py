@@ -264,6 +264,7 @@ def run_ours(args, rank, world, local):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = max_over_ranks(sum(step_ms), dev)
     fps = world * len(frames) / (total_ms / 1e3)
+    median_ms = statistics.median(step_ms)
 
     # per-frame work of the timed frames, counted in an untimed instrumented pass
     counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
@@ -307,9 +308,12 @@ def run_ours(args, rank, world, local):
 
     out = {"metric": METRIC, "value": round(fps, 2), "unit": "frames/s", "n_gpus": world,
            "steps": len(frames), "warmup": args.warmup, "ms_per_step": round(total_ms / len(frames), 4),
+           "ms_per_step_median": round(median_ms, 4), "fps_at_median": round(1e3 / median_ms, 2),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded 4D Gaussians; stands in for Plenoptic Video at its resolution)",
-           "config": dict(CONFIG, parallelism=f"replicas x{world}"),
+           "config": dict(CONFIG, parallelism=f"replicas x{world}",
+                          workload=CONFIG["workload"] + f"; {len(frames)} of the {FRAMES} sweep frames timed "
+                                                        f"per rank (k = 7 i mod {FRAMES})"),
            "gpu_launches": int(sum(stage_launch.values())),
            "wall_s": round(wall, 3), "clocks": clk, "roofline": roofline}
 
@@ -361,62 +365,176 @@ def _packed_target(views, seed, dev):
     return torch.as_tensor(np.concatenate(parts)).to(dev)
 
 
-def train_bench(args, rend, params, dev, stream, flush):
-    """Training step of 4 views at seeded (t, angle), 1352x1014, L1 loss
-    against a seeded smooth target: (a) through the autograd function of the
-    batched render (one batched call), (b) the plain path, one single-view
-    render + backward per view, (c) the batched step captured in a CUDA graph."""
-    import torch
-    import synth
-    import paper_2402_03307_gb300 as r4g
+# FP32 operations per composited (pixel, Gaussian) pair of the backward of
+# Eq. 3 (an FMA counts once): the forward's evaluation again, d (2),
+# -1/2 d^T conic d (9), alpha (1), the clamp (1); the transmittance recovered
+# back to front, 1 - alpha (1), T_i = T_{i+1} / (1 - alpha) (1, with the
+# reciprocal on the MUFU unit); w = alpha T_i (1); g . c (3);
+# dL/dalpha = (g . c T_i - U) / (1 - alpha) (2); U += (g . c) w (1);
+# dq = dL/dalpha alpha (1); the moments of dq over the pixel, dq dx, dq dx^2
+# and their three sums (5); the colour gradient g w, summed (6).
+BWD_FP32_OPS_PER_PAIR = 34
 
-    views = synth.train_views(seed=33, views=TRAIN_VIEWS)
-    target = _packed_target([(c, t) for c, t in views], 34, dev)
+
+def train_views_for_step(k: int):
+    """The 4 views of training step k: seeded (t ~ U[0,1], angle ~ U[0, 2 pi))."""
+    import synth
+    return synth.train_views(seed=1000 + k, views=TRAIN_VIEWS)
+
+
+def train_bench(args, rend, params, dev, stream, flush):
+    """Training step of 4 views at fresh seeded (t, angle) each step, 1352x1014,
+    L1 loss against a seeded smooth target (one per view slot): (a) through the
+    autograd function of the batched render (one batched call), (b) the plain
+    path, one single-view render + backward per view, (c) the batched step
+    captured in a CUDA graph, the step's views copied into its device view
+    table before each replay. Per-stage times come from a second pass with the
+    library's stage events on; the composited pairs from an untimed counting
+    pass over the same views."""
+    import torch
+    import paper_2402_03307_gb300 as r4g
+    from paper_2402_03307_gb300 import abi
+
+    nsteps = args.train_steps
+    warm = 3
+    step_views = [train_views_for_step(k) for k in range(warm + nsteps)]
+    target = _packed_target(step_views[0], 34, dev)
     npix = target.numel()
+    inv = 1.0 / npix
     leaves = {k: v.clone().requires_grad_(True) for k, v in params.items()}
+    cap_b = rend.reserve_batch(params, step_views)  # untimed: no step overflows its key buffer
+    # the plain path: one frame per view slot, sized for the largest view of any step
+    need = 0
+    for views in step_views:
+        for cam, t in views:
+            need = max(need, rend.status(rend.render(params, cam, t))[1])
+    cap_p = int(need * 1.1) + 1024
+    frames = [rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap_p, dev) for _ in range(TRAIN_VIEWS)]
+    imgs = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev) for _ in range(TRAIN_VIEWS)]
+    tviews = [target[k * 3 * WIDTH * HEIGHT:(k + 1) * 3 * WIDTH * HEIGHT].view(3, HEIGHT, WIDTH)
+              for k in range(TRAIN_VIEWS)]
+    gimg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+    graph = r4g.BatchGraph(rend, params, step_views[0], key_capacity=cap_b,
+                           grad_fn=lambda img: torch.sign(img - target) * inv)
+    tables = [graph.views_table(v) for v in step_views]
+    it = {"a": 0, "p": 0, "g": 0}
 
     def step_autograd():
+        views = step_views[it["a"] % len(step_views)]
+        it["a"] += 1
         for v in leaves.values():
             v.grad = None
         img = r4g.render_batch(leaves, views, renderer=rend)
         loss = (img - target).abs().mean()
         loss.backward()
 
-    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
-    res0 = [rend.render(params, cam, t) for cam, t in views]
-    caps = [int(rend.status(r)[1] * 1.1) + 1024 for r in res0]
-    frames = [rend.new_frame(N_GAUSS, WIDTH, HEIGHT, c, dev) for c in caps]
-    imgs = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev) for _ in views]
-    tviews = [target[k * 3 * WIDTH * HEIGHT:(k + 1) * 3 * WIDTH * HEIGHT].view(3, HEIGHT, WIDTH)
-              for k in range(len(views))]
-    gimg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
-    inv = 1.0 / npix
-
     def step_plain():
+        views = step_views[it["p"] % len(step_views)]
+        it["p"] += 1
         for v in grads.values():
             v.zero_()
-        for (cam, t), fr, im, c, tv in zip(views, frames, imgs, caps, tviews):
-            res = rend.render(params, cam, t, frame=fr, key_capacity=c, out=im, check=False)
+        for (cam, t), fr, im, tv in zip(views, frames, imgs, tviews):
+            res = rend.render(params, cam, t, frame=fr, key_capacity=cap_p, out=im, check=False)
             torch.sign(im - tv, out=gimg)
             gimg.mul_(inv)
             rend.backward(params, cam, t, res, gimg, grads)
 
-    graph = r4g.BatchGraph(rend, params, views, grad_fn=lambda img: torch.sign(img - target) * inv)
-    for _ in range(3):
+    def step_graph():
+        graph.replay(table=tables[it["g"] % len(tables)])
+        it["g"] += 1
+
+    for _ in range(warm):
         step_autograd()
         step_plain()
-        graph.replay()
-    ms_a = _timed(step_autograd, args.train_steps, stream, flush)
-    ms_p = _timed(step_plain, args.train_steps, stream, flush)
-    ms_g = _timed(graph.replay, args.train_steps, stream, flush)
-    return {"value": round(1000.0 / ms_a, 3), "unit": "it/s", "ms_per_it": round(ms_a, 3), "views": TRAIN_VIEWS,
-            "steps": args.train_steps,
+        step_graph()
+    for k in it:  # the timed steps take views warm .. warm + nsteps - 1
+        it[k] = warm
+    ms_a = _timed_all(step_autograd, nsteps, stream, flush)
+    ms_p = _timed_all(step_plain, nsteps, stream, flush)
+    ms_g = _timed_all(step_graph, nsteps, stream, flush)
+    if graph.status()[0] != abi.R4G_OK:
+        raise RuntimeError("the graph's last replay reports an error")
+    # stage times of the autograd step (library stage events on), same views
+    it["a"] = warm
+    abi.r4g_set_timing(rend.ctx, True)
+    abi.r4g_stage_times(rend.ctx, reset=True)
+    for _ in range(nsteps):
+        flush.zero_()
+        step_autograd()
+    torch.cuda.synchronize()
+    abi.r4g_set_timing(rend.ctx, False)
+    stage_ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
+    per_stage = {k: v / nsteps for k, v in stage_ms.items() if v > 0}
+    # work of the timed steps' views (untimed counting pass)
+    counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
+    pairs = keys = vis = 0
+    for views in step_views[warm:warm + nsteps]:
+        r = counter.render_batch(params, views, key_capacity=cap_b)
+        st_ = counter.stats(r)
+        pairs += st_["composited_pairs"]
+        keys += st_["key_count"]
+        vis += st_["n_visible"]
+    pairs, keys, vis = pairs / nsteps, keys / nsteps, vis / nsteps
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = {}
+    if "blend_bwd" in per_stage:
+        ach = pairs * BWD_FP32_OPS_PER_PAIR / (per_stage["blend_bwd"] / 1e3) / 1e12
+        roof["blend_bwd"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                             "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
+                             "fp32_ops_per_pair": BWD_FP32_OPS_PER_PAIR, "traffic": DRAM_TRAFFIC.get("blend_bwd")}
+    if "blend" in per_stage:
+        ach = pairs * FP32_OPS_PER_PAIR / (per_stage["blend"] / 1e3) / 1e12
+        roof["blend"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4)}
+    if "preprocess_bwd" in per_stage:
+        b = preprocess_bwd_bytes(N_GAUSS, vis, keys)
+        ach = b / (per_stage["preprocess_bwd"] / 1e3) / 1e9
+        roof["preprocess_bwd"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": round(ach / hbm_peak, 4), "bytes": round(b)}
+    top = max(("blend_bwd", "blend", "preprocess_bwd"), key=lambda k: per_stage.get(k, 0.0))
+    return {"value": round(1000.0 / ms_a["mean"], 3), "unit": "it/s", "ms_per_it": round(ms_a["mean"], 3),
+            "ms_per_it_median": round(ms_a["median"], 3), "views": TRAIN_VIEWS, "steps": nsteps,
+            "views_per_step": "fresh seeded (t ~ U[0,1], angle ~ U[0, 2 pi)) each step",
             "path": "autograd.Function over the batched render (one call for the 4 views), L1 loss in torch",
-            "plain_path": {"value": round(1000.0 / ms_p, 3), "ms_per_it": round(ms_p, 3),
+            "plain_path": {"value": round(1000.0 / ms_p["mean"], 3), "ms_per_it": round(ms_p["mean"], 3),
                            "path": "per view: r4g_render + r4g_render_backward (FP32, 16x16)"},
-            "graph": {"value": round(1000.0 / ms_g, 3), "ms_per_it": round(ms_g, 3),
-                      "path": "batched render + L1 sign gradient + batched backward in one CUDA graph"},
+            "graph": {"value": round(1000.0 / ms_g["mean"], 3), "ms_per_it": round(ms_g["mean"], 3),
+                      "path": "batched render + L1 sign gradient + batched backward in one CUDA graph, the "
+                              "step's views copied into the graph's device view table"},
+            "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
+            "work_per_step": {"composited_pairs": round(pairs), "keys": round(keys), "visible": round(vis)},
+            "roofline": dict(roof.get(top, {}), kernel=top), "stages": roof,
             "l2": "flushed between steps"}
+
+
+def preprocess_bwd_bytes(n: int, n_vis: float, keys: float) -> float:
+    """Algorithmic bytes of the preprocess backward of one multi-view call:
+    the parameters (68 B per Gaussian) and the SH rows of the visible items
+    (192 B), each pair's 48-byte gradient slot and its one-byte flag, the
+    96-byte per-item partial written and read, and the 65-float gradient
+    read and written (520 B per Gaussian)."""
+    return 68.0 * n + 192.0 * n_vis + 49.0 * keys + 192.0 * n_vis + 520.0 * n
+
+
+def _timed_all(fn, steps: int, stream, flush=None) -> dict:
+    """Mean and median ms of fn() over `steps` calls (CUDA events on `stream`
+    around each call; the L2 flush, when given, between calls outside them)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return {"mean": sum(ms) / steps, "median": statistics.median(ms)}
 
 
 def batch_bench(args, dev, stream, flush):
@@ -441,14 +559,16 @@ def batch_bench(args, dev, stream, flush):
     alt = [[(c2, t2) for (c2, t2) in a] for a in alt]
     sizes = [(c.width, c.height) for c, _ in views]
     alt = [a for a in alt if [(c.width, c.height) for c, _ in a] == sizes] or [views]
+    tab_f = [gf.views_table(a) for a in alt]  # device view tables, copied on the stream at replay
+    tab_t = [gt.views_table(a) for a in alt]
     it = {"k": 0}
 
     def fwd():
-        gf.replay(alt[it["k"] % len(alt)])
+        gf.replay(table=tab_f[it["k"] % len(alt)])
         it["k"] += 1
 
     def train():
-        gt.replay(alt[it["k"] % len(alt)])
+        gt.replay(table=tab_t[it["k"] % len(alt)])
         it["k"] += 1
 
     plain = r4g.Renderer()
@@ -527,13 +647,34 @@ def large_bench(args, dev, stream, flush):
         imgs[name] = gt.packed.clone()
         out[name] = {"ms_per_step": round(ms, 2), "it_per_s": round(1000.0 / ms, 3),
                      "param_bytes": int(sum(v.numel() * v.element_size() for v in p.values())),
-                     "keys": int(gt.status()[1])}
+                     "keys": int(gt.status()[1]), "stage_ms": large_stage_ms(rend, p, views, gt.cap, target, inv,
+                                                                             flush)}
         del gt
     d = (imgs["bf16"] - imgs["fp32"]).abs()
     mse = float((d.double() ** 2).mean())
     out["bf16_vs_fp32"] = {"max_abs": float(d.max()), "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-30)), 2),
                            "speedup": round(out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"], 3)}
     return out
+
+
+def large_stage_ms(rend, p, views, cap, target, inv, flush) -> dict:
+    """Per-stage device time of the large training step (the same batched
+    render and backward, eager, with the library's stage events on), ms per
+    step over 3 steps."""
+    import torch
+    from paper_2402_03307_gb300 import abi
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=v.device) for k, v in p.items()}
+    res = rend.render_batch(p, views, key_capacity=cap, check=False)
+    abi.r4g_set_timing(rend.ctx, True)
+    abi.r4g_stage_times(rend.ctx, reset=True)
+    for _ in range(3):
+        flush.zero_()
+        res = rend.render_batch(p, views, frame=res.frame, key_capacity=cap, out=res.packed, check=False)
+        rend.backward_batch(p, res, torch.sign(res.packed - target) * inv, grads)
+    torch.cuda.synchronize()
+    abi.r4g_set_timing(rend.ctx, False)
+    ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
+    return {k: round(v / 3, 3) for k, v in ms.items() if v > 0}
 
 
 def extras_bench(args, params, dev, stream, flush, frames, cap):

@@ -235,6 +235,26 @@ class Renderer:
         res = self.render_batch(params, vs, check=False, stream=st)
         return res, PendingStatus(res, st, key)
 
+    def reserve_batch(self, params: dict, view_sets) -> int:
+        """Render each list of views of ``view_sets`` once (untimed, waiting
+        for each status) and keep 10 % above the largest key count any of them
+        needed as the key capacity of batched calls of those sizes, so that
+        deferred renders of these views never overflow. Returns the capacity."""
+        n = int(params["mean"].shape[0])
+        need, key = 0, None
+        for views in view_sets:
+            vs = self.view_structs(views)
+            k = (n, tuple((v.cam.width, v.cam.height) for v in vs), self.tile)
+            if key is not None and k != key:
+                raise ValueError("every view set must have the same image sizes")
+            key = k
+            res = self.render_batch(params, vs)
+            need = max(need, self.status_of(res)[1])
+        cap = int(need * 1.1) + 1024
+        if key is not None:
+            self._cap_hint[key] = max(cap, self._cap_hint.get(key, 0))
+        return cap
+
     def settle(self, pending: "PendingStatus | None", res) -> None:
         """Raise if a deferred render's frame reports an error."""
         if pending is None:
@@ -463,7 +483,6 @@ class BatchGraph:
         first = renderer.render_batch(params, self.structs, key_capacity=key_capacity)  # sizes the key buffer
         self.cap = first.key_capacity if key_capacity else int(renderer.status_of(first)[1] * 1.2) + 4096
         self.views_dev = views_tensor(self.structs, dev)
-        self.pinned = torch.empty(self.views_dev.numel(), dtype=torch.uint8).pin_memory()
         self.frame = torch.empty(renderer.batch_frame_bytes(first.n, self.structs, self.cap), dtype=torch.uint8,
                                  device=dev)
         self.packed = torch.empty_like(first.packed)
@@ -491,14 +510,22 @@ class BatchGraph:
             gp = self.grad_fn(self.packed)
             self.r.backward_batch(self.params, res, gp, self.grads, stream=stream)
 
-    def replay(self, views=None) -> None:
-        """Run the graph, with new (camera, t) views of the same sizes if given."""
+    def views_table(self, views) -> torch.Tensor:
+        """Device copy of new (camera, t) views of the captured sizes, for
+        :meth:`replay` (build these ahead of a timed loop)."""
+        structs = self.r.view_structs(views)
+        if [(v.cam.width, v.cam.height) for v in structs] != [(v.cam.width, v.cam.height) for v in self.structs]:
+            raise ValueError("replayed views must keep the captured image sizes")
+        return views_tensor(structs, self.views_dev.device)
+
+    def replay(self, views=None, table: torch.Tensor | None = None) -> None:
+        """Run the graph, with new (camera, t) views of the same sizes if given
+        (``views``, copied from host memory, or a device ``table`` from
+        :meth:`views_table`, copied on the stream)."""
         if views is not None:
-            structs = self.r.view_structs(views)
-            if [(v.cam.width, v.cam.height) for v in structs] != [(v.cam.width, v.cam.height) for v in self.structs]:
-                raise ValueError("replayed views must keep the captured image sizes")
-            self.pinned.copy_(torch.frombuffer(bytearray(bytes(abi.view_array(structs))), dtype=torch.uint8))
-            self.views_dev.copy_(self.pinned, non_blocking=True)
+            table = self.views_table(views)
+        if table is not None:
+            self.views_dev.copy_(table)
         self.graph.replay()
 
     def status(self) -> tuple[int, int]:

@@ -74,7 +74,7 @@ def sampled_report(got: np.ndarray, ref: dict, rec: dict, pixels: np.ndarray, bg
     amb = ambiguous(ref, image=True)
     r = ref["rgb"].numpy()
     err = np.abs(got.astype(np.float64) - r)
-    alt = resolve_ambiguous(got.astype(np.float64), rec, pixels[amb], bg) if amb.any() else np.zeros(0)
+    alt = resolve_ambiguous(got[amb].astype(np.float64), rec, pixels[amb], bg) if amb.any() else np.zeros(0)
     return {
         "max_abs": float(err[~amb].max()) if (~amb).any() else 0.0,
         "max_abs_all": float(err.max()) if len(err) else 0.0,
