@@ -724,7 +724,7 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
     ms_loss = _timed(run_loss, 20, stream, flush)
     dens = densify_bench(params, dev, stream, flush)
     inside = inside_sweep_bench(params, dev, stream, flush)
-    return {"densify": dens, "inside_sweep": inside,
+    return {"densify": dens, "inside_sweep": inside, "small": small_bench(dev, stream),
             "image_loss": {"ms": round(ms_loss, 3), "what": "0.8 L1 + 0.2 (1 - SSIM) and its gradient, 3x1014x1352",
                            "note": "includes scratch allocation by the Python wrapper"},
             "flow": {"value": round(1000.0 / ms_flow, 1), "unit": "frames/s",
@@ -733,6 +733,45 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
                       "note": "includes scratch allocation by the Python wrapper"},
             "regularizers": {"ms": round(ms_reg, 3), "n": N_GAUSS,
                              "what": "entropy + 4D consistency losses and their gradients"}}
+
+
+def small_bench(dev, stream) -> dict:
+    """The small configuration: 1,000 Gaussians, 128x128, one camera at
+    distance 4, t = 0.5, FP32; frames/s of the plain single-view path (its
+    inputs stay in L2, so no flush) and of the same render captured in a CUDA
+    graph (launch-bound at this size)."""
+    import torch
+    import paper_2402_03307_gb300 as r4g
+    import synth
+    g, cam, t = synth.small_scene(seed=1)
+    p = {k: torch.as_tensor(v).to(dev).contiguous() for k, v in g.items()}
+    rend = r4g.Renderer()
+    cap = int(rend.status(rend.render(p, cam, t))[1] * 1.1) + 1024
+    frame = rend.new_frame(1000, cam.width, cam.height, cap, dev)
+    img = torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=dev)
+
+    def one():
+        rend.render(p, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
+
+    for _ in range(10):
+        one()
+    ms = _timed(one, 200, stream)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            one()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        one()
+    for _ in range(10):
+        graph.replay()
+    ms_g = _timed(graph.replay, 200, stream)
+    return {"value": round(1000.0 / ms, 1), "unit": "frames/s", "ms": round(ms, 4),
+            "graph": {"value": round(1000.0 / ms_g, 1), "ms": round(ms_g, 4)},
+            "workload": "1k 4D Gaussians, 128x128, camera at distance 4, t = 0.5, FP32, 1 view/launch"}
 
 
 def inside_sweep_bench(params, dev, stream, flush, radius: float = 4.0, stride: int = 3):
@@ -916,7 +955,13 @@ def cpu_baseline(budget_s: float = 15.0) -> dict:
         done += len(pix)
         seed += 1
     per_frame = t_pre + t_pix * (WIDTH * HEIGHT / done)
+    # the small configuration (1k Gaussians, 128x128), a whole frame
+    gs, cam_s, t_s = synth.small_scene(seed=1)
+    t0 = time.perf_counter()
+    oracle.render(oracle.to_f64(gs), cam_s, t_s)
+    t_small = time.perf_counter() - t0
     return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "small_frame_s": round(t_small, 3),
             "sample": f"FP64 oracle: preprocess of all 300k Gaussians ({t_pre:.2f} s) + {done} random pixels of "
                       f"frame 37 brute-forced over all visible Gaussians ({t_pix:.1f} s), scaled to "
                       f"{WIDTH * HEIGHT} pixels"}

@@ -165,9 +165,7 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   int tb = 0;
   while ((int64_t(1) << tb) < L.ntiles) ++tb;
   L.tile_bits = tb;
-  const int dpasses = 32 / kSortRadixBits;
   const int tpasses = (tb + kSortRadixBits - 1) / kSortRadixBits;
-  L.order_in_1 = dpasses % 2 == 1;
   L.keys_in_1 = tpasses % 2 == 1;
   const int cnt_ctas = L.sort_ctas > L.depth_ctas ? L.sort_ctas : L.depth_ctas;
   const size_t npix = static_cast<size_t>(pix);
@@ -316,17 +314,18 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
   int which = 0;
   if (has) {
     // depth order of the items: stable sort of the depth bits, values = item index
-    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);  // histogram, passes (cleared with the difference array)
-    e = launch_onesweep(at<uint32_t>(frame, L.dkey0), nullptr, at<uint32_t>(frame, L.dkey1),
-                        at<uint32_t>(frame, L.ord1), at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0),
-                        nullptr, static_cast<uint32_t>(L.m), L.m, 32, at<void>(frame, L.onesweep), err, s, &which,
-                        false, true);
+    // (items without tiles dropped by the first pass; as many passes as the
+    // frame's depth-key range needs, the others exit at once; the scratch is
+    // cleared with the difference array)
+    StageScope sc(ctx, R4G_STAGE_SORT, s, 1 + dpasses);
+    e = launch_depth_sort(at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.dkey1), at<uint32_t>(frame, L.ord1),
+                          at<uint32_t>(frame, L.dkey0), at<uint32_t>(frame, L.ord0), L.m,
+                          at<FrameHeader>(frame, L.header), at<void>(frame, L.onesweep), err, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
   }
-  const uint32_t* order = at<uint32_t>(frame, L.order_in_1 ? L.ord1 : L.ord0);
   {
     StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? (L.nblocks <= kSelfScanBlocks ? 3 : 4) : 0);
-    if ((e = launch_binning(L, frame, order, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
+    if ((e = launch_binning(L, frame, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
   }
   const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
   // join: the tile sort and the blend need the side stream's work

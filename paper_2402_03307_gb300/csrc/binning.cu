@@ -22,14 +22,23 @@ constexpr int kTileCountsMaxSmem = kMaxTiles * 4;
 constexpr int kTileClasses = 64;  // list-length classes of the blend's tile order
 
 // blocksum[b] = sum of touched[order[j]] over the block's depth positions.
+// The depth order holds the hdr->n_visible items with tiles; it ends in
+// ord_odd when the depth sort ran an odd number of passes, else in ord_even.
+__device__ __forceinline__ const uint32_t* depth_order(const uint32_t* ord_odd, const uint32_t* ord_even,
+                                                       const FrameHeader* hdr) {
+  return (depth_passes(hdr) & 1) ? ord_odd : ord_even;
+}
+
 __global__ void __launch_bounds__(kPreBlock)
-    depth_blocksum_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order, int n,
-                          uint32_t* __restrict__ blocksum) {
+    depth_blocksum_kernel(const uint32_t* __restrict__ touched, const uint32_t* ord_odd, const uint32_t* ord_even,
+                          const FrameHeader* hdr, uint32_t* __restrict__ blocksum) {
   griddep_wait();
   griddep_launch_dependents();
   __shared__ uint32_t s_sum[kPreBlock / 32];
+  const uint32_t* __restrict__ order = depth_order(ord_odd, ord_even, hdr);
+  const int nk = static_cast<int>(hdr->n_visible);
   const int j = blockIdx.x * kPreBlock + threadIdx.x;
-  const uint32_t c = j < n ? touched[order[j]] : 0u;
+  const uint32_t c = j < nk ? touched[order[j]] : 0u;
   const uint32_t ws = __reduce_add_sync(0xffffffffu, c);
   if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = ws;
   __syncthreads();
@@ -100,7 +109,7 @@ constexpr int kEmitChunk = 2048;
 
 template <bool kSelfScan>
 __global__ void __launch_bounds__(kPreBlock)
-    depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
+    depth_offsets_kernel(const uint32_t* __restrict__ touched, const uint32_t* ord_odd, const uint32_t* ord_even,
                          const uint32_t* __restrict__ blockoff, const uint2* __restrict__ rect,
                          const ViewDev* __restrict__ views, uint32_t ng, int m, uint32_t* __restrict__ offs,
                          uint32_t* __restrict__ ioffs, uint4* __restrict__ srect, uint32_t* __restrict__ chunk_start,
@@ -114,8 +123,10 @@ __global__ void __launch_bounds__(kPreBlock)
   uint32_t pre = 0;  // kSelfScan: this thread's share of the blocks before this one
   if constexpr (kSelfScan)
     for (int b = threadIdx.x; b < static_cast<int>(blockIdx.x); b += kPreBlock) pre += blockoff[b];
-  const uint32_t item = j < m ? order[j] : 0u;
-  const uint32_t cnt = j < m ? touched[item] : 0u;
+  const uint32_t* __restrict__ order = depth_order(ord_odd, ord_even, hdr);
+  const int nk = static_cast<int>(hdr->n_visible);  // the depth order's length (<= m)
+  const uint32_t item = j < nk ? order[j] : 0u;
+  const uint32_t cnt = j < nk ? touched[item] : 0u;
   uint32_t x = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -181,11 +192,12 @@ __device__ __forceinline__ uint32_t emit_slot(uint32_t i) { return i ^ ((i >> 5)
 
 __global__ void __launch_bounds__(kPreBlock)
     emit_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect,
-                const uint32_t* __restrict__ order, const uint32_t* __restrict__ chunk_start, int n,
+                const uint32_t* ord_odd, const uint32_t* ord_even, const uint32_t* __restrict__ chunk_start, int n,
                 const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
                 uint32_t* __restrict__ ident) {
   griddep_wait();
   griddep_launch_dependents();
+  const uint32_t* __restrict__ order = depth_order(ord_odd, ord_even, hdr);
   __shared__ uint32_t s_off[kEmitChunk + 1];
   __shared__ uint32_t s_key[kEmitChunk];
   __shared__ uint32_t s_gid[kEmitChunk];
@@ -400,9 +412,11 @@ __global__ void export_values_kernel(const uint32_t* __restrict__ vals, const ui
 }
 
 
-cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s) {
+cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s) {
   if (L.n == 0) return cudaSuccess;
   FrameHeader* hdr = at<FrameHeader>(frame, L.header);
+  const uint32_t* ord_odd = at<uint32_t>(frame, L.ord1);   // where the depth sort's odd pass counts end
+  const uint32_t* ord_even = at<uint32_t>(frame, L.ord0);
   uint32_t* bs = at<uint32_t>(frame, L.blocksum);
   const uint32_t* touched = at<uint32_t>(frame, L.touched);
   const int m = static_cast<int>(L.m);
@@ -410,13 +424,15 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   uint4* srect = at<uint4>(frame, L.srect);
   uint32_t* cstart = at<uint32_t>(frame, L.chunks);
   const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
-  cudaError_t e = launch_pdl(depth_blocksum_kernel, L.nblocks, kPreBlock, 0, s, touched, order, m, bs);
+  cudaError_t e = launch_pdl(depth_blocksum_kernel, L.nblocks, kPreBlock, 0, s, touched, ord_odd, ord_even,
+                             static_cast<const FrameHeader*>(hdr), bs);
   const bool self_scan = L.nblocks <= kSelfScanBlocks;
   if (e == cudaSuccess && !self_scan)
     e = launch_pdl(scan_blocksums_kernel, 1, kScanThreads, 0, s, bs, L.nblocks, hdr, static_cast<uint32_t>(L.cap));
   if (e == cudaSuccess)
     e = launch_pdl(self_scan ? depth_offsets_kernel<true> : depth_offsets_kernel<false>, L.nblocks, kPreBlock, 0, s,
-                   touched, order, static_cast<const uint32_t*>(bs), static_cast<const uint2*>(at<uint2>(frame, L.rect)),
+                   touched, ord_odd, ord_even, static_cast<const uint32_t*>(bs),
+                   static_cast<const uint2*>(at<uint2>(frame, L.rect)),
                    static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)), static_cast<uint32_t>(L.n), m, offs,
                    at<uint32_t>(frame, L.ioffs), srect, cstart, static_cast<uint32_t>(chunks), hdr,
                    static_cast<uint32_t>(L.cap));
@@ -427,7 +443,7 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* or
   const int64_t egrid = chunks < 8LL * sms ? chunks : 8LL * sms;  // eight 256-thread CTAs per SM
   if (chunks > 0)
     e = launch_pdl(emit_kernel, static_cast<unsigned>(egrid), kPreBlock, 0, s, static_cast<const uint32_t*>(offs),
-                   static_cast<const uint4*>(srect), order, static_cast<const uint32_t*>(cstart), m,
+                   static_cast<const uint4*>(srect), ord_odd, ord_even, static_cast<const uint32_t*>(cstart), m,
                    static_cast<const FrameHeader*>(hdr), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.egid),
                    L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0) : nullptr);
   return e != cudaSuccess ? e : cudaGetLastError();

@@ -51,9 +51,11 @@ __device__ __forceinline__ void store_relaxed(uint32_t* p, uint32_t v) {
 // [8 p, 8 p + 8) of the keys, limited to `bits` bits in total (at most four
 // passes). Shared-memory atomics into one sub-histogram per pair of warps,
 // eight loads in flight per thread.
+// kRel (the depth sort): digits of key - kmin, keys 0xffffffff not counted.
+template <bool kRel>
 __global__ void __launch_bounds__(kSortThreads)
     onesweep_hist_kernel(const uint32_t* __restrict__ keys, const uint32_t* count_dev, uint32_t count_host,
-                         int passes, int bits, uint32_t* __restrict__ hist) {
+                         int passes, int bits, uint32_t* __restrict__ hist, const FrameHeader* hdr) {
   griddep_wait();
   griddep_launch_dependents();
   constexpr int NS = kSortThreads / 64;  // sub-histograms
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kSortThreads)
   for (int k = threadIdx.x; k < NS * 4 * kSortRadix; k += kSortThreads) (&s_h[0][0][0])[k] = 0;
   __syncthreads();
   const uint32_t n = count_dev ? *count_dev : count_host;
+  const uint32_t kmin = kRel ? ~hdr->dkey_minc : 0u;
   const int sub = threadIdx.x / 64;
   constexpr int ILP = 8;
   for (uint32_t base = blockIdx.x * kSortThreads * ILP; base < n; base += gridDim.x * kSortThreads * ILP) {
@@ -72,11 +75,12 @@ __global__ void __launch_bounds__(kSortThreads)
     }
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      if (base + u * kSortThreads + threadIdx.x < n) {
+      if (base + u * kSortThreads + threadIdx.x < n && (!kRel || key[u] != 0xffffffffu)) {
+        const uint32_t r = key[u] - kmin;
         for (int p = 0; p < passes; ++p) {
           const int sh = p * kSortRadixBits;
           const int nb = min(kSortRadixBits, bits - sh);
-          atomicAdd(&s_h[sub][p][(key[u] >> sh) & ((1u << nb) - 1u)], 1u);
+          atomicAdd(&s_h[sub][p][(r >> sh) & ((1u << nb) - 1u)], 1u);
         }
       }
     }
@@ -91,14 +95,19 @@ __global__ void __launch_bounds__(kSortThreads)
     }
 }
 
+// kRel (the depth sort, pass `pass`): digits of key - kmin; the first pass
+// drops keys 0xffffffff (its output holds the n_visible others, which the
+// later passes sort); a pass beyond depth_passes(hdr) exits at once.
+template <bool kRel>
 __global__ void __launch_bounds__(kSortThreads)
     onesweep_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* count_dev,
                          uint32_t count_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                          uint32_t* status, uint32_t* ticket, uint32_t* err, uint32_t withheld_tile,
-                         uint32_t spin_limit) {
+                         uint32_t spin_limit, const FrameHeader* hdr, int pass) {
   constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tot;
   __shared__ uint32_t s_dstart[kSortRadix];   // global start of each digit + tile prefix
   __shared__ uint32_t s_tstart[kSortRadix];   // tile-local start of each digit
   __shared__ uint32_t s_whist[NW][kSortRadix];
@@ -109,15 +118,17 @@ __global__ void __launch_bounds__(kSortThreads)
   griddep_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  {
-    const uint32_t nn = count_dev ? *count_dev : count_host;
-    if (static_cast<uint64_t>(blockIdx.x) * kOsTile >= nn) return;  // more CTAs than tiles: leave at once
+  uint32_t kmin = 0u;
+  if constexpr (kRel) {
+    if (pass >= depth_passes(hdr)) return;  // the key range is narrower: nothing left to sort
+    kmin = ~hdr->dkey_minc;
   }
+  const uint32_t n = kRel ? (pass == 0 ? count_host : hdr->n_visible) : (count_dev ? *count_dev : count_host);
+  if (static_cast<uint64_t>(blockIdx.x) * kOsTile >= n) return;  // more CTAs than tiles: leave at once
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   for (int k = threadIdx.x; k < NW * kSortRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
   __syncthreads();
   const uint32_t t = s_tile;
-  const uint32_t n = count_dev ? *count_dev : count_host;
   const uint64_t tb64 = static_cast<uint64_t>(t) * kOsTile;
   if (tb64 >= n) return;  // grid sized for the capacity; CTA-uniform exit
   const uint32_t tb = static_cast<uint32_t>(tb64);
@@ -131,7 +142,7 @@ __global__ void __launch_bounds__(kSortThreads)
     if (li < tn) {
       k[j] = kin[tb + li];
       v[j] = vin ? vin[tb + li] : tb + li;
-      d[j] = (k[j] >> shift) & mask;
+      d[j] = (kRel && k[j] == 0xffffffffu) ? 0xffffffffu : ((k[j] - kmin) >> shift) & mask;
     } else {
       k[j] = 0;
       v[j] = 0;
@@ -239,6 +250,7 @@ __global__ void __launch_bounds__(kSortThreads)
     pre = 0;
     for (int w = 0; w < warp; ++w) pre += s_scan[w];
     s_tstart[dd] = pre + x - cnt;
+    if (dd == kSortRadix - 1) s_tot = pre + x;  // items of the tile this pass keeps
   }
   __syncthreads();
   // ---- stage in digit order, then write each digit's run contiguously
@@ -251,9 +263,10 @@ __global__ void __launch_bounds__(kSortThreads)
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < tn; i += kSortThreads) {
+  const uint32_t tk = s_tot;
+  for (uint32_t i = threadIdx.x; i < tk; i += kSortThreads) {
     const uint32_t key = s_k[i];
-    const uint32_t dg = (key >> shift) & mask;
+    const uint32_t dg = ((key - kmin) >> shift) & mask;
     const uint32_t o = s_dstart[dg] + i - s_tstart[dg];
     if (o < n) {  // only false after a key-capacity overflow, whose result is discarded
       kout[o] = key;
@@ -279,6 +292,33 @@ __global__ void onesweep_zero_kernel(uint32_t* __restrict__ hist, int hist_words
     for (size_t i = i0; i < words; i += stride) status[p * pass_words + i] = 0u;
   if (i0 < 32) tickets[i0] = 0u;
   for (size_t i = i0; i < static_cast<size_t>(hist_words); i += stride) hist[i] = 0u;
+}
+
+cudaError_t launch_depth_sort(const uint32_t* kin, uint32_t* kbuf1, uint32_t* vbuf1, uint32_t* kbuf2, uint32_t* vbuf2,
+                              int64_t m, const FrameHeader* hdr, void* scratch, uint32_t* err, cudaStream_t s) {
+  constexpr int passes = 32 / kSortRadixBits;
+  if (m == 0) return cudaSuccess;
+  const int64_t tiles = (m + kOsTile - 1) / kOsTile;
+  uint32_t* hist = static_cast<uint32_t*>(scratch);
+  uint32_t* tickets = hist + passes * kSortRadix;
+  uint32_t* status = tickets + 32;
+  const size_t pass_words = static_cast<size_t>(tiles) * kSortRadix;
+  const int hist_ctas = static_cast<int>(tiles < kOsHistCtas ? tiles : kOsHistCtas);
+  cudaError_t e = launch_pdl(onesweep_hist_kernel<true>, hist_ctas, kSortThreads, 0, s, kin,
+                             static_cast<const uint32_t*>(nullptr), static_cast<uint32_t>(m), passes, 32, hist, hdr);
+  const uint32_t* ki = kin;
+  const uint32_t* vi = nullptr;
+  for (int p = 0; p < passes && e == cudaSuccess; ++p) {
+    uint32_t* ko = (p % 2 == 0) ? kbuf1 : kbuf2;
+    uint32_t* vo = (p % 2 == 0) ? vbuf1 : vbuf2;
+    e = launch_pdl(onesweep_pass_kernel<true>, static_cast<unsigned>(tiles), kSortThreads, 0, s, ki, vi, ko, vo,
+                   static_cast<const uint32_t*>(nullptr), static_cast<uint32_t>(m), p * kSortRadixBits,
+                   (1u << kSortRadixBits) - 1u, static_cast<const uint32_t*>(hist + p * kSortRadix),
+                   status + static_cast<size_t>(p) * pass_words, tickets + p, err, 0xffffffffu, kSpinLimit, hdr, p);
+    ki = ko;
+    vi = vo;
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 size_t onesweep_scratch_bytes(int64_t cap, int bits) {
@@ -322,8 +362,8 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
   }
   if (!hist_ready) {
     const int hist_ctas = static_cast<int>(tiles < kOsHistCtas ? tiles : kOsHistCtas);
-    const cudaError_t e = launch_pdl(onesweep_hist_kernel, hist_ctas, kSortThreads, 0, s, kin, count_dev, count_host,
-                                     passes, bits, hist);
+    const cudaError_t e = launch_pdl(onesweep_hist_kernel<false>, hist_ctas, kSortThreads, 0, s, kin, count_dev,
+                                     count_host, passes, bits, hist, static_cast<const FrameHeader*>(nullptr));
     if (e != cudaSuccess) return e;
   }
   const uint32_t* ki = kin;
@@ -335,10 +375,10 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
     uint32_t* ko = (which == 1) ? kbuf2 : kbuf1;
     uint32_t* vo = (which == 1) ? vbuf2 : vbuf1;
     const cudaError_t e =
-        launch_pdl(onesweep_pass_kernel, static_cast<unsigned>(tiles), kSortThreads, 0, s, ki, vi, ko, vo, count_dev,
-                   count_host, shift, (1u << nb) - 1u, static_cast<const uint32_t*>(hist + p * kSortRadix),
+        launch_pdl(onesweep_pass_kernel<false>, static_cast<unsigned>(tiles), kSortThreads, 0, s, ki, vi, ko, vo,
+                   count_dev, count_host, shift, (1u << nb) - 1u, static_cast<const uint32_t*>(hist + p * kSortRadix),
                    status + static_cast<size_t>(p) * pass_words, tickets + p, err, withheld_tile,
-                   spin_limit ? spin_limit : kSpinLimit);
+                   spin_limit ? spin_limit : kSpinLimit, static_cast<const FrameHeader*>(nullptr), p);
     if (e != cudaSuccess) return e;
     ki = ko;
     vi = vo;

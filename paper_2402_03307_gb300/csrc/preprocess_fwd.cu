@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kPreFwdBlock)
   if constexpr (!kMulti) nviews = 1;
   __shared__ uint32_t s_pairs[kMaxViews];
   __shared__ uint32_t s_wcnt[kPreFwdBlock / 32];
-  __shared__ uint32_t s_vis, s_base;
+  __shared__ uint32_t s_vis, s_base, s_kminc, s_kmax;
   __shared__ __align__(16) ViewDev s_views[kMaxViews];  // the view table (copied as 16-byte words)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v = threadIdx.x; v < kMaxViews; v += kPreFwdBlock) s_pairs[v] = 0;
@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(kPreFwdBlock)
     s_views[0] = d;
     if (blockIdx.x == 0) views[0] = d;
   }
-  if (threadIdx.x == 0) s_vis = 0;
+  if (threadIdx.x == 0) s_vis = s_kminc = s_kmax = 0;
   __syncthreads();
   uint32_t nvis = 0;
+  uint32_t kminc = 0, kmax = 0;  // range of this thread's depth keys (complemented minimum)
   const size_t M = static_cast<size_t>(g.n) * nviews;
   for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
     uint32_t ntiles = 0;
@@ -166,7 +167,12 @@ __global__ void __launch_bounds__(kPreFwdBlock)
         out.rect[item] = make_uint2(0u, 0u);
       }
       out.touched[item] = ntiles;
-      out.dkey[item] = ntiles ? __float_as_uint(f.pc[2]) : 0xffffffffu;
+      const uint32_t key = __float_as_uint(f.pc[2]);
+      out.dkey[item] = ntiles ? key : 0xffffffffu;
+      if (ntiles) {
+        kminc = max(kminc, ~key);
+        kmax = max(kmax, key);
+      }
     }
     const uint32_t ws = __reduce_add_sync(0xffffffffu, ntiles);
     if (lane == 0 && ws) atomicAdd(&s_pairs[v], ws);
@@ -176,9 +182,15 @@ __global__ void __launch_bounds__(kPreFwdBlock)
   // view (appended per block, in index order within the block)
   const uint32_t wv = __reduce_add_sync(0xffffffffu, nvis);
   const uint32_t lm = __ballot_sync(0xffffffffu, nvis > 0);
+  kminc = __reduce_max_sync(0xffffffffu, kminc);
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
   if (lane == 0) {
     s_wcnt[warp] = __popc(lm);
-    if (wv) atomicAdd(&s_vis, wv);
+    if (wv) {
+      atomicAdd(&s_vis, wv);
+      atomicMax(&s_kminc, kminc);
+      atomicMax(&s_kmax, kmax);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -190,7 +202,11 @@ __global__ void __launch_bounds__(kPreFwdBlock)
       tot += c;
     }
     s_base = tot ? atomicAdd(&out.header->n_glist, tot) : 0u;
-    if (s_vis) atomicAdd(&out.header->n_visible, s_vis);
+    if (s_vis) {
+      atomicAdd(&out.header->n_visible, s_vis);
+      atomicMax(&out.header->dkey_minc, s_kminc);
+      atomicMax(&out.header->dkey_max, s_kmax);
+    }
   }
   for (int v = threadIdx.x; v < nviews; v += kPreFwdBlock)
     if (s_pairs[v]) atomicAdd(&out.header->view_pairs[v], s_pairs[v]);

@@ -63,7 +63,9 @@ struct FrameHeader {
   uint32_t next_tile;     // work counter of the persistent blend
   uint32_t next_tile_bwd; // work counter of the persistent blend backward
   uint32_t n_ilist;       // visible (view, Gaussian) items listed for a multi-view backward
-  uint32_t pad[54];
+  uint32_t dkey_minc;     // ~(smallest depth key of the items with tiles), by atomicMax from 0
+  uint32_t dkey_max;      // largest depth key of the items with tiles
+  uint32_t pad[52];
   uint32_t view_pairs[kMaxViews];  // (tile, Gaussian) pairs per view
 };
 static_assert(sizeof(FrameHeader) == 512, "frame header size");
@@ -87,7 +89,6 @@ struct FrameLayout {
   int sort_ctas;     // CTAs of each radix pass over the keys
   int depth_ctas;    // CTAs of each radix pass over the depth keys of the items
   int tile_bits;     // ceil(log2(ntiles)): bits of the tile sort
-  bool order_in_1;   // the depth order ends in ord1 (else ord0)
   bool keys_in_1;    // the tile-sorted values end in vals1 (else vals0)
 };
 
@@ -175,7 +176,7 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
                                   uint32_t flags, const r4g_view* views_host, const r4g_view* views_dev,
                                   cudaStream_t s);
 // scan of the tile counts in depth order and key emission (tile key, index)
-cudaError_t launch_binning(const FrameLayout& L, void* frame, const uint32_t* order, cudaStream_t s);
+cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s);
 cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf1,
                         uint32_t* vbuf1, uint64_t* kbuf2, uint32_t* vbuf2,
                         const uint32_t* count_dev, uint32_t count_host, int64_t cap,
@@ -189,6 +190,20 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
                             int* result_in_buf, bool hist_ready = false, bool prepared = false,
                             uint32_t withheld_tile = 0xffffffffu, uint32_t spin_limit = 0u);
+// The render's depth sort: a stable sort of the items' depth keys (float bits,
+// 0xffffffff for an item without tiles, which the first pass drops), the
+// values being the item indices. Digits are taken from key - kmin (kmin the
+// smallest key of the items with tiles, from the frame header), so the passes
+// beyond the width of the frame's key range exit at once; the order ends in
+// buffer 1 when the pass count depth_passes(hdr) is odd, else in buffer 2.
+// The scratch must be zero (the render's first memset clears it).
+cudaError_t launch_depth_sort(const uint32_t* kin, uint32_t* kbuf1, uint32_t* vbuf1, uint32_t* kbuf2, uint32_t* vbuf2,
+                              int64_t m, const FrameHeader* hdr, void* scratch, uint32_t* err, cudaStream_t s);
+__device__ __forceinline__ int depth_passes(const FrameHeader* hdr) {
+  const uint32_t n = hdr->n_visible;
+  const uint32_t range = hdr->dkey_max - ~hdr->dkey_minc;
+  return n == 0 ? 1 : range < (1u << 8) ? 1 : range < (1u << 16) ? 2 : range < (1u << 24) ? 3 : 4;
+}
 // What launch_onesweep clears before its passes (tickets, statuses and, unless
 // hist_ready, the histograms), enqueued separately so it can run early on
 // another stream; then call launch_onesweep with prepared = true.
