@@ -324,19 +324,27 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
     if (e != cudaSuccess) return cuda_fail(ctx, e, "depth sort");
   }
   {
-    StageScope sc(ctx, R4G_STAGE_BINNING, s, has ? (L.nblocks <= kSelfScanBlocks ? 3 : 4) : 0);
+    // depth-order offsets (and, for a one-tile image, the pair emission)
+    StageScope sc(ctx, R4G_STAGE_BINNING, s,
+                  has ? (L.nblocks <= kSelfScanBlocks ? 2 : 3) + (tpasses == 0 ? 1 : 0) : 0);
     if ((e = launch_binning(L, frame, s)) != cudaSuccess) return cuda_fail(ctx, e, "binning");
   }
   const uint32_t* count = &at<FrameHeader>(frame, L.header)->key_count;
   // join: the tile sort and the blend need the side stream's work
   if ((e = cudaStreamWaitEvent(s, ctx->join, 0)) != cudaSuccess) return cuda_fail(ctx, e, "join");
   if (has && tpasses > 0) {
-    // stable sort of the depth-ordered pairs by tile id
+    // stable sort of the depth-ordered pairs by tile id: the first pass runs in
+    // the pair emission (values: the emission index of each pair), the others
+    // here
     StageScope sc(ctx, R4G_STAGE_SORT, s, tpasses);
-    // values: the emission index of each pair, generated by the first pass
-    e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
-                        at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
-                        count, 0, L.cap, L.tile_bits, at<void>(frame, L.tsort), err, s, &which, true, true);
+    void* ts = at<void>(frame, L.tsort);
+    e = launch_emit_sort(L, frame, at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1),
+                         static_cast<const uint32_t*>(ts), onesweep_status(ts, L.tile_bits),
+                         onesweep_tickets(ts, L.tile_bits), s);
+    if (e == cudaSuccess)
+      e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
+                          at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
+                          count, 0, L.cap, L.tile_bits, ts, err, s, &which, true, true, 0xffffffffu, 0u, 1);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile sort");
   }
   const uint32_t* vals = sorted_vals(L, frame);

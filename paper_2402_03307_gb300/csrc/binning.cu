@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "r4g_internal.cuh"
+#include "onesweep.cuh"
 
 namespace r4g {
 
@@ -261,6 +262,123 @@ __global__ void __launch_bounds__(kPreBlock)
   }
 }
 
+// The emission fused with the tile sort's first radix pass: CTAs take the
+// emission chunks by ticket (chunk c, pairs [c E, (c + 1) E) of the
+// depth-ordered list, is tile c of the pass), build the chunk's (tile id,
+// item) pairs in shared memory exactly as emit_kernel does, write each pair's
+// item, and rank and scatter the tile ids by their low digit with the
+// emission indices as values (the pass of onesweep.cu, on keys that never go
+// through global memory; the digit histogram comes ready from the tile
+// counts). A CTA takes its next chunk only after publishing the previous
+// one's prefix, so every chunk it waits on belongs to a running CTA.
+static_assert(kEmitChunk == kOsTile && kPreBlock == kSortThreads, "an emission chunk is one sort tile");
+
+__global__ void __launch_bounds__(kPreBlock)
+    emit_sort_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect, const uint32_t* ord_odd,
+                     const uint32_t* ord_even, const uint32_t* __restrict__ chunk_start, int n, FrameHeader* hdr,
+                     uint32_t* __restrict__ egid, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                     const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* ticket, uint32_t mask) {
+  griddep_wait();
+  griddep_launch_dependents();
+  __shared__ uint32_t s_off[kEmitChunk + 1];
+  __shared__ uint32_t s_key[kEmitChunk];  // the chunk's tile ids, then the pass's staging of keys
+  __shared__ uint32_t s_gid[kEmitChunk];  // the chunk's items, then the pass's staging of values
+  __shared__ OsShared S;
+  __shared__ uint32_t s_c;
+  const uint32_t* __restrict__ order = depth_order(ord_odd, ord_even, hdr);
+  const uint32_t K = hdr->key_count;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    __syncthreads();  // the previous chunk is done with the shared arrays
+    if (threadIdx.x == 0) s_c = atomicAdd(ticket, 1u);
+    os_clear(S);
+    __syncthreads();
+    const uint32_t c = s_c;
+    if (static_cast<uint64_t>(c) * kEmitChunk >= K) break;
+    const uint32_t q0 = c * kEmitChunk;
+    const int jlo = static_cast<int>(chunk_start[c]);
+    const int jhi = (q0 + kEmitChunk < K) ? static_cast<int>(chunk_start[c + 1]) : n - 1;
+    const int m = min(kEmitChunk + 1, min(jhi, n - 1) - jlo + 1);
+    for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
+    __syncthreads();
+    const uint32_t qend = min(K, q0 + kEmitChunk);
+    const uint32_t qa = q0 + threadIdx.x * kEmitRun;
+    if (qa < qend) {
+      int lo = 0, hi = m - 1;  // last i with s_off[i] <= qa
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= qa) lo = mid;
+        else hi = mid - 1;
+      }
+      uint4 r = srect[jlo + lo];
+      uint32_t g = order[jlo + lo];
+      uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
+      uint32_t ly = (qa - s_off[lo]) / w, lx = (qa - s_off[lo]) - ly * w;
+      uint32_t next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+#pragma unroll
+      for (int u = 0; u < kEmitRun; ++u) {
+        const uint32_t q = qa + u;
+        if (q >= qend) break;
+        if (q >= next) {
+          do {
+            ++lo;
+            next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+          } while (q >= next);
+          r = srect[jlo + lo];
+          g = order[jlo + lo];
+          w = (r.y & 0xffffu) - (r.x & 0xffffu);
+          ly = (q - s_off[lo]) / w;
+          lx = (q - s_off[lo]) - ly * w;
+        }
+        const uint32_t slot = emit_slot(q - q0);
+        s_key[slot] = r.z + ((r.x >> 16) + ly) * r.w + (r.x & 0xffffu) + lx;
+        s_gid[slot] = g;
+        if (++lx == w) {
+          lx = 0;
+          ++ly;
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t tn = qend - q0;
+    for (uint32_t i = threadIdx.x; i < tn; i += kPreBlock) egid[q0 + i] = s_gid[emit_slot(i)];
+    uint32_t k[kOsIPT], v[kOsIPT], d[kOsIPT];
+#pragma unroll
+    for (int j = 0; j < kOsIPT; ++j) {
+      const uint32_t li = warp * (32 * kOsIPT) + j * 32 + lane;
+      k[j] = li < tn ? s_key[emit_slot(li)] : 0u;
+      v[j] = q0 + li;
+      d[j] = li < tn ? (k[j] & mask) : 0xffffffffu;
+    }
+    // (os_rank_scatter synchronises the CTA before it stages into s_key / s_gid)
+    os_rank_scatter(k, v, d, c, K, 0u, 0, mask, hist, status, &hdr->status, 0xffffffffu, kSpinLimit, S, s_key,
+                    s_gid, kout, vout);
+  }
+}
+
+cudaError_t launch_emit_sort(const FrameLayout& L, void* frame, uint32_t* kout, uint32_t* vout, const uint32_t* hist,
+                             uint32_t* status, uint32_t* ticket, cudaStream_t s) {
+  if (L.n == 0) return cudaSuccess;
+  const int64_t chunks = (L.cap + kEmitChunk - 1) / kEmitChunk;
+  if (chunks == 0) return cudaSuccess;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, emit_sort_kernel, kPreBlock, 0);
+  const int64_t resident = static_cast<int64_t>(per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+  const int64_t grid = chunks < resident ? chunks : resident;
+  const int nb = L.tile_bits < kSortRadixBits ? L.tile_bits : kSortRadixBits;
+  cudaError_t e = launch_pdl(emit_sort_kernel, static_cast<unsigned>(grid), kPreBlock, 0, s,
+                             static_cast<const uint32_t*>(at<uint32_t>(frame, L.offs)),
+                             static_cast<const uint4*>(at<uint4>(frame, L.srect)),
+                             static_cast<const uint32_t*>(at<uint32_t>(frame, L.ord1)),
+                             static_cast<const uint32_t*>(at<uint32_t>(frame, L.ord0)),
+                             static_cast<const uint32_t*>(at<uint32_t>(frame, L.chunks)), static_cast<int>(L.m),
+                             at<FrameHeader>(frame, L.header), at<uint32_t>(frame, L.egid), kout, vout, hist, status,
+                             ticket, (1u << nb) - 1u);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // Per-tile pair counts from the 2D difference array the preprocess filled
 // (prefix sums along x, then along y, in shared memory with warp scans), their
 // exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
@@ -441,7 +559,8 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t egrid = chunks < 8LL * sms ? chunks : 8LL * sms;  // eight 256-thread CTAs per SM
-  if (chunks > 0)
+  // with a tile sort, the emission runs with its first pass (launch_emit_sort)
+  if (chunks > 0 && L.tile_bits == 0)
     e = launch_pdl(emit_kernel, static_cast<unsigned>(egrid), kPreBlock, 0, s, static_cast<const uint32_t*>(offs),
                    static_cast<const uint4*>(srect), ord_odd, ord_even, static_cast<const uint32_t*>(cstart), m,
                    static_cast<const FrameHeader*>(hdr), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.egid),

@@ -25,27 +25,11 @@
 
 #include "r4g.h"
 #include "r4g_internal.cuh"
+#include "onesweep.cuh"
 
 namespace r4g {
 
-constexpr uint32_t kFlagAgg = 1u << 30;     // tile count published
-constexpr uint32_t kFlagPrefix = 2u << 30;  // inclusive prefix published
-constexpr uint32_t kValMask = (1u << 30) - 1u;
-constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr int kOsIPT = 8;                           // items per thread
-constexpr int kOsTile = kSortThreads * kOsIPT;      // 2048 items per tile
-constexpr int kOsWin = 4;                           // predecessors read per look-back round
 constexpr int kOsHistCtas = 2 * 152;
-
-__device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void store_relaxed(uint32_t* p, uint32_t v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Digit histograms of every pass: hist[p * 256 + d] for digits of bits
 // [8 p, 8 p + 8) of the keys, limited to `bits` bits in total (at most four
@@ -99,25 +83,19 @@ __global__ void __launch_bounds__(kSortThreads)
 // drops keys 0xffffffff (its output holds the n_visible others, which the
 // later passes sort); a pass beyond depth_passes(hdr) exits at once.
 template <bool kRel>
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 5)
     onesweep_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                          uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* count_dev,
                          uint32_t count_host, int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                          uint32_t* status, uint32_t* ticket, uint32_t* err, uint32_t withheld_tile,
                          uint32_t spin_limit, const FrameHeader* hdr, int pass) {
-  constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_tot;
-  __shared__ uint32_t s_dstart[kSortRadix];   // global start of each digit + tile prefix
-  __shared__ uint32_t s_tstart[kSortRadix];   // tile-local start of each digit
-  __shared__ uint32_t s_whist[NW][kSortRadix];
-  __shared__ uint32_t s_scan[NW];
+  __shared__ OsShared S;
   __shared__ uint32_t s_k[kOsTile];
   __shared__ uint32_t s_v[kOsTile];
   griddep_wait();
   griddep_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   uint32_t kmin = 0u;
   if constexpr (kRel) {
     if (pass >= depth_passes(hdr)) return;  // the key range is narrower: nothing left to sort
@@ -126,7 +104,7 @@ __global__ void __launch_bounds__(kSortThreads)
   const uint32_t n = kRel ? (pass == 0 ? count_host : hdr->n_visible) : (count_dev ? *count_dev : count_host);
   if (static_cast<uint64_t>(blockIdx.x) * kOsTile >= n) return;  // more CTAs than tiles: leave at once
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
-  for (int k = threadIdx.x; k < NW * kSortRadix; k += kSortThreads) (&s_whist[0][0])[k] = 0;
+  os_clear(S);
   __syncthreads();
   const uint32_t t = s_tile;
   const uint64_t tb64 = static_cast<uint64_t>(t) * kOsTile;
@@ -135,7 +113,7 @@ __global__ void __launch_bounds__(kSortThreads)
   const uint32_t tn = min(static_cast<uint32_t>(kOsTile), n - tb);
 
   // ---- load and rank the tile (stable: warp w holds items [w*256, w*256+256))
-  uint32_t k[kOsIPT], v[kOsIPT], d[kOsIPT], rk[kOsIPT];
+  uint32_t k[kOsIPT], v[kOsIPT], d[kOsIPT];
 #pragma unroll
   for (int j = 0; j < kOsIPT; ++j) {
     const uint32_t li = warp * (32 * kOsIPT) + j * 32 + lane;
@@ -149,130 +127,8 @@ __global__ void __launch_bounds__(kSortThreads)
       d[j] = 0xffffffffu;
     }
   }
-#pragma unroll
-  for (int j = 0; j < kOsIPT; ++j) {
-    const bool ok = d[j] != 0xffffffffu;
-    const uint32_t act = __ballot_sync(0xffffffffu, ok);
-    rk[j] = 0;
-    uint32_t peers = act;
-#pragma unroll
-    for (int b = 0; b < kSortRadixBits; ++b) {
-      const uint32_t bit = (d[j] >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-      peers &= bit ? bal : ~bal;
-    }
-    if (ok) {
-      const uint32_t base = s_whist[warp][d[j]];
-      __syncwarp(act);
-      if (lane == __ffs(peers) - 1) s_whist[warp][d[j]] = base + __popc(peers);
-      rk[j] = base + __popc(peers & lt_mask);
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-  // per digit (thread = digit): exclusive over warps, tile count
-  const int dd = threadIdx.x;
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const uint32_t c = s_whist[w][dd];
-    s_whist[w][dd] = cnt;
-    cnt += c;
-  }
-  // ---- publish the tile's count, then look back for its exclusive prefix
-  // (a digit no item of the pass has -- the histogram says so -- needs no
-  // status and no look-back: its count is zero in every tile)
-  const uint32_t h = hist[dd];
-  const bool live = h != 0u;
-  // withheld_tile (a test of the bounded wait only; otherwise no tile): that
-  // tile never publishes, so its successors' waits run out
-  const bool publish = t != withheld_tile;
-  uint32_t* st = status + static_cast<size_t>(t) * kSortRadix;
-  if (live && publish) store_relaxed(st + dd, (t == 0 ? kFlagPrefix : kFlagAgg) | cnt);
-  // Look-back, kOsWin predecessors per round (their statuses are read in
-  // parallel): add published counts newest first until a published prefix;
-  // a round that makes no progress counts against the spin limit.
-  uint32_t excl = 0;
-  if (t > 0 && live) {
-    constexpr int WIN = kOsWin;
-    int64_t kt = static_cast<int64_t>(t) - 1;
-    uint32_t idle = 0, nap = 32u;
-    bool found = false;
-    while (!found && kt >= 0) {
-      uint32_t sv[WIN];
-#pragma unroll
-      for (int w = 0; w < WIN; ++w)
-        sv[w] = (kt - w >= 0) ? load_volatile(status + static_cast<size_t>(kt - w) * kSortRadix + dd) : kFlagPrefix;
-      int used = 0;
-#pragma unroll
-      for (int w = 0; w < WIN; ++w) {
-        if (found || used < w) continue;           // stopped earlier in this window
-        if ((sv[w] & ~kValMask) == 0u) continue;   // not ready: retry from here
-        if (kt - w >= 0) excl += sv[w] & kValMask;
-        ++used;
-        if (sv[w] & kFlagPrefix) found = true;
-      }
-      kt -= used;
-      if (used == 0) {
-        if (++idle >= spin_limit) {  // gave up: record it and go on
-          atomicOr(err, 2u);
-          break;
-        }
-        __nanosleep(nap);
-        nap = nap < 256u ? 2u * nap : 256u;
-      }
-    }
-    if (publish) store_relaxed(st + dd, kFlagPrefix | (excl + cnt));
-  }
-  // global digit start: exclusive scan of this pass's histogram (+ tile prefix)
-  {
-    uint32_t x = h;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_scan[warp] = x;
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_scan[w];
-    s_dstart[dd] = pre + x - h + excl;
-    __syncthreads();
-    // tile-local digit starts: exclusive scan of the tile counts
-    x = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_scan[warp] = x;
-    __syncthreads();
-    pre = 0;
-    for (int w = 0; w < warp; ++w) pre += s_scan[w];
-    s_tstart[dd] = pre + x - cnt;
-    if (dd == kSortRadix - 1) s_tot = pre + x;  // items of the tile this pass keeps
-  }
-  __syncthreads();
-  // ---- stage in digit order, then write each digit's run contiguously
-#pragma unroll
-  for (int j = 0; j < kOsIPT; ++j) {
-    if (d[j] != 0xffffffffu) {
-      const uint32_t pos = s_tstart[d[j]] + s_whist[warp][d[j]] + rk[j];
-      s_k[pos] = k[j];
-      s_v[pos] = v[j];
-    }
-  }
-  __syncthreads();
-  const uint32_t tk = s_tot;
-  for (uint32_t i = threadIdx.x; i < tk; i += kSortThreads) {
-    const uint32_t key = s_k[i];
-    const uint32_t dg = ((key - kmin) >> shift) & mask;
-    const uint32_t o = s_dstart[dg] + i - s_tstart[dg];
-    if (o < n) {  // only false after a key-capacity overflow, whose result is discarded
-      kout[o] = key;
-      vout[o] = s_v[i];
-    }
-  }
+  os_rank_scatter(k, v, d, t, n, kmin, shift, mask, hist, status, err, withheld_tile, spin_limit, S, s_k, s_v,
+                  kout, vout);
 }
 
 // Clears what the passes expect at zero (instead of a memset, so that the
@@ -321,6 +177,13 @@ cudaError_t launch_depth_sort(const uint32_t* kin, uint32_t* kbuf1, uint32_t* vb
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+uint32_t* onesweep_tickets(void* scratch, int bits) {
+  const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
+  return static_cast<uint32_t*>(scratch) + passes * kSortRadix;
+}
+
+uint32_t* onesweep_status(void* scratch, int bits) { return onesweep_tickets(scratch, bits) + 32; }
+
 size_t onesweep_scratch_bytes(int64_t cap, int bits) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   const int64_t tiles = (cap + kOsTile - 1) / kOsTile;
@@ -342,7 +205,7 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
                             int* result_in_buf, bool hist_ready, bool prepared, uint32_t withheld_tile,
-                            uint32_t spin_limit) {
+                            uint32_t spin_limit, int first_pass) {
   const int passes = (bits + kSortRadixBits - 1) / kSortRadixBits;
   *result_in_buf = 0;
   if (passes == 0 || cap == 0) return cudaSuccess;
@@ -366,10 +229,12 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
                                      count_host, passes, bits, hist, static_cast<const FrameHeader*>(nullptr));
     if (e != cudaSuccess) return e;
   }
-  const uint32_t* ki = kin;
-  const uint32_t* vi = vin;
-  int which = 0;
-  for (int p = 0; p < passes; ++p) {
+  // passes before first_pass ran elsewhere (the emission runs the tile sort's
+  // first): pass p writes buffer 1 when p is even, buffer 2 when odd
+  int which = first_pass == 0 ? 0 : ((first_pass - 1) % 2 == 0 ? 1 : 2);
+  const uint32_t* ki = which == 1 ? kbuf1 : which == 2 ? kbuf2 : kin;
+  const uint32_t* vi = which == 1 ? vbuf1 : which == 2 ? vbuf2 : vin;
+  for (int p = first_pass; p < passes; ++p) {
     const int shift = p * kSortRadixBits;
     const int nb = min(kSortRadixBits, bits - shift);
     uint32_t* ko = (which == 1) ? kbuf2 : kbuf1;

@@ -177,6 +177,10 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
                                   cudaStream_t s);
 // scan of the tile counts in depth order and key emission (tile key, index)
 cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s);
+// the pair emission fused with the tile sort's first radix pass (tile_bits > 0;
+// hist: the tile sort's histograms, status / ticket: its first pass's)
+cudaError_t launch_emit_sort(const FrameLayout& L, void* frame, uint32_t* kout, uint32_t* vout, const uint32_t* hist,
+                             uint32_t* status, uint32_t* ticket, cudaStream_t s);
 cudaError_t launch_sort(const uint64_t* kin, const uint32_t* vin, uint64_t* kbuf1,
                         uint32_t* vbuf1, uint64_t* kbuf2, uint32_t* vbuf2,
                         const uint32_t* count_dev, uint32_t count_host, int64_t cap,
@@ -189,7 +193,11 @@ cudaError_t launch_onesweep(const uint32_t* kin, const uint32_t* vin, uint32_t* 
                             uint32_t* kbuf2, uint32_t* vbuf2, const uint32_t* count_dev, uint32_t count_host,
                             int64_t cap, int bits, void* scratch, uint32_t* err, cudaStream_t s,
                             int* result_in_buf, bool hist_ready = false, bool prepared = false,
-                            uint32_t withheld_tile = 0xffffffffu, uint32_t spin_limit = 0u);
+                            uint32_t withheld_tile = 0xffffffffu, uint32_t spin_limit = 0u, int first_pass = 0);
+// The scratch of launch_onesweep: histograms [passes][256], tickets [32], then
+// each pass's look-back statuses ([tiles][256] words per pass).
+uint32_t* onesweep_tickets(void* scratch, int bits);
+uint32_t* onesweep_status(void* scratch, int bits);
 // The render's depth sort: a stable sort of the items' depth keys (float bits,
 // 0xffffffff for an item without tiles, which the first pass drops), the
 // values being the item indices. Digits are taken from key - kmin (kmin the
