@@ -468,14 +468,18 @@ def train_bench(args, rend, params, dev, stream, flush):
     per_stage = {k: v / nsteps for k, v in stage_ms.items() if v > 0}
     # work of the timed steps' views (untimed counting pass)
     counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
-    pairs = keys = vis = 0
+    pairs = keys = vis = reached = vis_g = 0
     for views in step_views[warm:warm + nsteps]:
         r = counter.render_batch(params, views, key_capacity=cap_b)
+        counter.backward_batch(params, r, torch.sign(r.packed - target) * inv, grads)
         st_ = counter.stats(r)
         pairs += st_["composited_pairs"]
         keys += st_["key_count"]
         vis += st_["n_visible"]
+        reached += st_["reached_pairs"]
+        vis_g += st_["visible_gaussians"]
     pairs, keys, vis = pairs / nsteps, keys / nsteps, vis / nsteps
+    reached, vis_g = reached / nsteps, vis_g / nsteps
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12
@@ -491,7 +495,7 @@ def train_bench(args, rend, params, dev, stream, flush):
         roof["blend"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
                          "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4)}
     if "preprocess_bwd" in per_stage:
-        b = preprocess_bwd_bytes(N_GAUSS, vis, keys)
+        b = preprocess_bwd_bytes(vis_g, vis, keys, reached)
         ach = b / (per_stage["preprocess_bwd"] / 1e3) / 1e9
         roof["preprocess_bwd"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                                   "frac": round(ach / hbm_peak, 4), "bytes": round(b)}
@@ -506,18 +510,19 @@ def train_bench(args, rend, params, dev, stream, flush):
                       "path": "batched render + L1 sign gradient + batched backward in one CUDA graph, the "
                               "step's views copied into the graph's device view table"},
             "stage_ms": {k: round(v, 4) for k, v in per_stage.items()},
-            "work_per_step": {"composited_pairs": round(pairs), "keys": round(keys), "visible": round(vis)},
+            "work_per_step": {"composited_pairs": round(pairs), "keys": round(keys), "visible_items": round(vis),
+                              "pairs_with_gradient": round(reached), "visible_gaussians": round(vis_g)},
             "roofline": dict(roof.get(top, {}), kernel=top), "stages": roof,
             "l2": "flushed between steps"}
 
 
-def preprocess_bwd_bytes(n: int, n_vis: float, keys: float) -> float:
-    """Algorithmic bytes of the preprocess backward of one multi-view call:
-    the parameters (68 B per Gaussian) and the SH rows of the visible items
-    (192 B), each pair's 48-byte gradient slot and its one-byte flag, the
-    96-byte per-item partial written and read, and the 65-float gradient
-    read and written (520 B per Gaussian)."""
-    return 68.0 * n + 192.0 * n_vis + 49.0 * keys + 192.0 * n_vis + 520.0 * n
+def preprocess_bwd_bytes(n_gauss: float, n_items: float, keys: float, reached: float) -> float:
+    """Algorithmic bytes of the preprocess backward of one multi-view call, per
+    Gaussian visible in some view: its parameters (68 B) and SH row (192 B)
+    read once, its 65-float gradient read and written (520 B); per visible
+    (view, Gaussian) item: the 96-byte partial written and read; per pair: the
+    one-byte flag, and the 48-byte gradient slot of the pairs that have one."""
+    return (68.0 + 192.0 + 520.0) * n_gauss + 192.0 * n_items + 1.0 * keys + 48.0 * reached
 
 
 def _timed_all(fn, steps: int, stream, flush=None) -> dict:

@@ -191,6 +191,9 @@ typedef struct r4g_frame_info {
                                 has R4G_FLAG_COUNT_PAIRS */
   int32_t status;            /* R4G_OK, R4G_EOVERFLOW, R4G_ETIMEOUT or R4G_EDEVICE */
   int32_t reserved;
+  int64_t reached_pairs;     /* (tile, Gaussian) pairs that got a gradient slot in the last
+                                backward on this frame (a pixel of the tile composited them) */
+  int64_t visible_gaussians; /* Gaussians visible in at least one view of the call */
 } r4g_frame_info;
 r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, r4g_frame_info* out,
                            void* stream);

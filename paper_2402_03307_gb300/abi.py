@@ -53,7 +53,8 @@ class r4g_params_out(C.Structure):
 
 class r4g_frame_info(C.Structure):
     _fields_ = [("n_visible", C.c_int64), ("key_count", C.c_int64), ("key_needed", C.c_int64),
-                ("composited_pairs", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("composited_pairs", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("reached_pairs", C.c_int64), ("visible_gaussians", C.c_int64)]
 
 
 class r4g_view(C.Structure):

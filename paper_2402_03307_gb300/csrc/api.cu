@@ -536,6 +536,8 @@ r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, 
                 : (h.status & 4u) ? R4G_EDEVICE
                                   : R4G_OK;
   out->reserved = 0;
+  out->reached_pairs = h.n_reached;
+  out->visible_gaussians = h.n_glist;
   return R4G_OK;
 }
 

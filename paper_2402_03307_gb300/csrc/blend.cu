@@ -551,7 +551,7 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
                                                int nviews, float bg0, float bg1, float bg2,
                                                const float* __restrict__ Tfinal, const uint32_t* __restrict__ stoppos,
                                                const float* __restrict__ grad_rgb, float4* __restrict__ gbuf,
-                                               uint8_t* __restrict__ reach) {
+                                               uint8_t* __restrict__ reach, uint32_t* n_reached) {
   using B = Blend<TW, TH>;
   constexpr int BS = B::NT, Q = B::Q;
   const TileLoc loc = locate_tile(views, nviews, tile);
@@ -635,6 +635,10 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
       }
     }
     __syncthreads();
+    {  // pairs of the batch that get a gradient slot (a statistic of the frame)
+      const uint32_t tk = __ballot_sync(0xffffffffu, idx < n && sE[threadIdx.x] < cap && sTook[threadIdx.x] != 0u);
+      if (lane == 0 && tk) atomicAdd(n_reached, static_cast<uint32_t>(__popc(tk)));
+    }
     // each entry of the batch: sum over the warps (fixed order), convert, one write
     if (idx < n) {
       float acc[9];
@@ -699,7 +703,8 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
                      float4* __restrict__ gbuf, uint8_t* __restrict__ reach, const uint32_t* __restrict__ torder) {
   griddep_wait();
   griddep_launch_dependents();
-  // the multi-view preprocess backward that follows lists its items anew
+  // the multi-view preprocess backward that follows lists its items anew;
+  // the count of pairs with a gradient starts again
   if (blockIdx.x == 0 && threadIdx.x == 0) hdr->n_ilist = 0u;
   __shared__ StagedG sg[Blend<TW, TH>::NT];
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
@@ -717,7 +722,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
     const int tile = s_tile;
     if (tile >= ntiles) break;
     blend_bwd_tile<TW, TH>(tile, sg, sE, sTook, s_max, s_slab, ranges, vals, recA, recB, recC, egid, ng, cap, views,
-                           nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf, reach);
+                           nviews, bg0, bg1, bg2, Tfinal, stoppos, grad_rgb, gbuf, reach, &hdr->n_reached);
   }
 }
 
@@ -786,8 +791,10 @@ cudaError_t launch_blend_bwd(const FrameLayout& L, void* frame, const uint32_t* 
   float4* gbuf = at<float4>(frame, L.gbuf);
   uint8_t* reach = at<uint8_t>(frame, L.reach);
   const uint32_t* torder = tile_order(L, frame);
-  // the backward's work counter (the render zeroed the forward's)
-  cudaMemsetAsync(&hdr->next_tile_bwd, 0, sizeof(uint32_t), s);
+  // the backward's work counter and its count of pairs with a gradient (the
+  // render zeroed the forward's counter)
+  static_assert(offsetof(FrameHeader, n_reached) == offsetof(FrameHeader, next_tile_bwd) + 4, "adjacent counters");
+  cudaMemsetAsync(&hdr->next_tile_bwd, 0, 2 * sizeof(uint32_t), s);
 #define R4G_BLEND_BWD(TW_, TH_)                                                                           \
   {                                                                                                       \
     const size_t slab = sizeof(float) * 9 * Blend<TW_, TH_>::NW * Blend<TW_, TH_>::NT;                   \

@@ -62,10 +62,11 @@ struct FrameHeader {
   uint32_t n_glist;       // Gaussians visible in at least one view (the backward's work list)
   uint32_t next_tile;     // work counter of the persistent blend
   uint32_t next_tile_bwd; // work counter of the persistent blend backward
+  uint32_t n_reached;     // pairs whose gradient slot the last backward wrote (cleared with next_tile_bwd)
   uint32_t n_ilist;       // visible (view, Gaussian) items listed for a multi-view backward
   uint32_t dkey_minc;     // ~(smallest depth key of the items with tiles), by atomicMax from 0
   uint32_t dkey_max;      // largest depth key of the items with tiles
-  uint32_t pad[52];
+  uint32_t pad[51];
   uint32_t view_pairs[kMaxViews];  // (tile, Gaussian) pairs per view
 };
 static_assert(sizeof(FrameHeader) == 512, "frame header size");

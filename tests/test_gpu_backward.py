@@ -92,3 +92,24 @@ def test_backward_fp64_slice_path(r4g):
     got = _gpu_grads(r4g, g, cam, t, w, flags=abi.R4G_FLAG_FP64_SLICE)
     ref = oracle.render_grad(oracle.to_f64(g), cam, t, w)
     _compare(got, ref, "fp64")
+
+
+def test_backward_counts_pairs_with_gradient(r4g):
+    """The frame statistics after a backward: the pairs that got a gradient
+    slot are those whose tile composited them (at least one per pixel that
+    composited something, at most every pair), and a second backward on the
+    same render counts them again from zero."""
+    g, cam, t = synth.small_scene(seed=26)
+    rend = r4g.Renderer(flags=r4g.abi.R4G_FLAG_COUNT_PAIRS)
+    p = to_device(g)
+    res = rend.render(p, cam, t)
+    grads = {k: torch.zeros(v.shape, dtype=torch.float32, device="cuda") for k, v in p.items()}
+    gimg = torch.ones((3, cam.height, cam.width), device="cuda")
+    rend.backward(p, cam, t, res, gimg, grads)
+    a = rend.stats(res)
+    rend.backward(p, cam, t, res, gimg, grads)
+    b = rend.stats(res)
+    assert 0 < a["reached_pairs"] <= a["key_count"]
+    assert a["reached_pairs"] == b["reached_pairs"]
+    assert a["composited_pairs"] >= a["reached_pairs"]  # each such pair composites into a pixel
+    assert 0 < a["visible_gaussians"] <= len(g["logit"])
