@@ -965,8 +965,14 @@ def cpu_baseline(budget_s: float = 15.0) -> dict:
     t0 = time.perf_counter()
     oracle.render(oracle.to_f64(gs), cam_s, t_s)
     t_small = time.perf_counter() - t0
+    # the analytic FP64 gradient at the finite-difference size (64 Gaussians, 32x32)
+    gf = synth.gaussians(64, 11, ls_xyz=(-1.6, 0.3), ls_t=(-0.7, 0.3))
+    cam_f = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 32, 32)
+    t0 = time.perf_counter()
+    oracle.render_grad(oracle.to_f64(gf), cam_f, 0.5, np.ones((3, 32, 32)))
+    t_grad = time.perf_counter() - t0
     return {"value": 1.0 / per_frame, "unit": "frames/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "small_frame_s": round(t_small, 3),
+            "small_frame_s": round(t_small, 3), "fd_size_gradient_s": round(t_grad, 3),
             "sample": f"FP64 oracle: preprocess of all 300k Gaussians ({t_pre:.2f} s) + {done} random pixels of "
                       f"frame 37 brute-forced over all visible Gaussians ({t_pix:.1f} s), scaled to "
                       f"{WIDTH * HEIGHT} pixels"}
