@@ -203,51 +203,74 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 }
 
 // Sum of an item's per-pair gradients (pairs [o, o + cnt) of the gradient
-// buffer) for each lane's item: the warp walks its lanes' items in turn,
-// lane l adding pairs l, l + 32, ... (coalesced), then a butterfly sum; a
-// single pair is read by its owner. Only pairs whose reach flag is set hold
-// a gradient (a pixel of their tile composited them); the others count as
-// zero and are not read. gc.w counts the tiles in which a pixel composited
-// the item (summed only with kStats). Returns whether any pair of the lane's
-// item holds a gradient (if none, the item's gradient is zero).
-template <bool kStats>
+// buffer) for each lane's item: the warp takes its lanes' items four at a
+// time (their loads in flight together), lane l adding pairs l, l + 32, ...
+// of each (coalesced), then a butterfly sum per item; a single pair is read
+// by its owner. Only pairs whose reach flag is set hold a gradient (a pixel of
+// their tile composited them); the others count as zero and are not read.
+// gc.w counts the tiles in which a pixel composited the item (summed only
+// with kStats). Returns whether any pair of the lane's item holds a gradient
+// (if none, the item's gradient is zero). The sums are in a fixed order.
+template <bool kStats, int U>
 __device__ __forceinline__ bool gather_pairs(uint32_t cnt, uint32_t o, int lane, const float4* __restrict__ gbuf,
                                              const uint8_t* __restrict__ reach, float4& ga, float4& gb,
                                              float4& gc) {
+  // U: items in flight per round
   ga = make_float4(0.f, 0.f, 0.f, 0.f);
   gb = ga;
   gc = ga;
   bool got = false;
-  for (int q = 0; q < 32; ++q) {
-    const uint32_t qc = __shfl_sync(0xffffffffu, cnt, q);
-    if (qc < 2) continue;  // warp-uniform; a single pair is read by its owner below
-    const uint32_t qo = __shfl_sync(0xffffffffu, o, q);
-    float v9[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool found = false;
-    for (uint32_t k = lane; k < qc; k += 32) {
-      if (!reach[qo + k]) continue;
-      found = true;
-      const float4* pr = gbuf + 3 * static_cast<size_t>(qo + k);
-      const float4 x = pr[0], y = pr[1], z = pr[2];
-      v9[0] += x.x; v9[1] += x.y; v9[2] += x.z; v9[3] += x.w;
-      v9[4] += y.x; v9[5] += y.y;
-      v9[6] += z.x; v9[7] += z.y; v9[8] += z.z; v9[9] += z.w;
-    }
-    if (!__any_sync(0xffffffffu, found)) continue;  // no pair of item q holds a gradient
-    if (lane == q) got = true;
+  for (int q0 = 0; q0 < 32; q0 += U) {
+    uint32_t qc[U], qo[U], kmax = 0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-#pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) v9[k] += __shfl_xor_sync(0xffffffffu, v9[k], sh);
+    for (int u = 0; u < U; ++u) {
+      qc[u] = __shfl_sync(0xffffffffu, cnt, q0 + u);
+      qo[u] = __shfl_sync(0xffffffffu, o, q0 + u);
+      if (qc[u] < 2) qc[u] = 0;  // a single pair is read by its owner below
+      kmax = max(kmax, qc[u]);
     }
-    if constexpr (kStats) {
+    if (kmax == 0) continue;  // warp-uniform
+    float v[U][10];
+    bool found[U];
 #pragma unroll
-      for (int sh = 16; sh > 0; sh >>= 1) v9[9] += __shfl_xor_sync(0xffffffffu, v9[9], sh);
+    for (int u = 0; u < U; ++u) {
+      found[u] = false;
+#pragma unroll
+      for (int k = 0; k < 10; ++k) v[u][k] = 0.f;
     }
-    if (lane == q) {
-      ga = make_float4(v9[0], v9[1], v9[2], v9[3]);
-      gb = make_float4(v9[4], v9[5], 0.f, 0.f);
-      gc = make_float4(v9[6], v9[7], v9[8], v9[9]);
+    for (uint32_t k = lane; k < kmax; k += 32) {
+      bool f[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) f[u] = k < qc[u] && reach[qo[u] + k];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!f[u]) continue;
+        found[u] = true;
+        const float4* pr = gbuf + 3 * static_cast<size_t>(qo[u] + k);
+        const float4 x = pr[0], y = pr[1], z = pr[2];
+        v[u][0] += x.x; v[u][1] += x.y; v[u][2] += x.z; v[u][3] += x.w;
+        v[u][4] += y.x; v[u][5] += y.y;
+        v[u][6] += z.x; v[u][7] += z.y; v[u][8] += z.z; v[u][9] += z.w;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!__any_sync(0xffffffffu, found[u])) continue;  // no pair of this item holds a gradient
+      if (lane == q0 + u) got = true;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v[u][k] += __shfl_xor_sync(0xffffffffu, v[u][k], sh);
+      }
+      if constexpr (kStats) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v[u][9] += __shfl_xor_sync(0xffffffffu, v[u][9], sh);
+      }
+      if (lane == q0 + u) {
+        ga = make_float4(v[u][0], v[u][1], v[u][2], v[u][3]);
+        gb = make_float4(v[u][4], v[u][5], 0.f, 0.f);
+        gc = make_float4(v[u][6], v[u][7], v[u][8], v[u][9]);
+      }
     }
   }
   if (cnt == 1 && reach[o]) {
@@ -298,7 +321,7 @@ __global__ void __launch_bounds__(kBwdBlock, kMulti ? 3 : 4)
     if (__ballot_sync(0xffffffffu, cnt != 0u) == 0u) continue;
     const uint32_t o = cnt ? ioffs[item] : 0u;
     float4 ga, gb, gc;
-    const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc);
+    const bool got = gather_pairs<kStats, 2>(cnt, o, lane, gbuf, reach, ga, gb, gc);
     if (got) {  // an item no pixel composited has a zero gradient
       float radius;
       view_backward<S, kShBF16>(g, i, Q, views[v].cam, views[v].t, sh_degree, temporal_cull, ga, gb, gc, out.sh,
@@ -395,19 +418,57 @@ __global__ void __launch_bounds__(1024)
   if (vis) ilist[s_base + s_warp[warp] + __popc(b & ((1u << lane) - 1u))] = k;
 }
 
+// First pass of the multi-view backward: each listed item's per-pair
+// gradients summed (gather_pairs), written into the first three vectors of its
+// partial slot (ga, gb with gb.z = 1 marking an item with a gradient, gc); an
+// item without one gets its whole partial zeroed. A kernel of its own, lean
+// in registers, so that many warps keep the gather's loads in flight.
+constexpr int kGatherBlock = 256;
+constexpr int kGatherItems = 2;  // items in flight per round of the gather
+
+template <bool kStats>
+__global__ void __launch_bounds__(kGatherBlock)
+    preprocess_bwd_gather_kernel(const uint32_t* __restrict__ ilist, const uint32_t* __restrict__ ioffs,
+                                 const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
+                                 const uint8_t* __restrict__ reach, const FrameHeader* hdr,
+                                 float4* __restrict__ ipart) {
+  griddep_wait();
+  griddep_launch_dependents();
+  const int j = blockIdx.x * kGatherBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int nlist = static_cast<int>(hdr->n_ilist);
+  if ((hdr->status & 1u) || (j - lane) >= nlist) return;  // warp-uniform
+  const bool mine = j < nlist;
+  const uint32_t item = mine ? ilist[j] : 0u;
+  const uint32_t cnt = mine ? touched[item] : 0u;
+  const uint32_t o = cnt ? ioffs[item] : 0u;
+  float4 ga, gb, gc;
+  const bool got = gather_pairs<kStats, kGatherItems>(cnt, o, lane, gbuf, reach, ga, gb, gc) && mine;
+  if (!mine) return;
+  float4* d = ipart + kPartVec * static_cast<size_t>(item);
+  if (got) {
+    gb.z = 1.0f;
+    d[0] = ga;
+    d[1] = gb;
+    d[2] = gc;
+  } else {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    d[0] = d[1] = d[2] = d[3] = d[4] = d[5] = z;
+  }
+}
+
 template <bool kScaleBF16, bool kShBF16, bool kStats>
 __global__ void __launch_bounds__(kBwdBlock, 4)
     preprocess_bwd_items_kernel(r4g_gaussians g, const ViewDev* __restrict__ views,
-                                const uint32_t* __restrict__ ilist, const uint32_t* __restrict__ ioffs,
-                                const uint32_t* __restrict__ touched, const float4* __restrict__ gbuf,
-                                const uint8_t* __restrict__ reach, const FrameHeader* hdr, int sh_degree,
+                                const uint32_t* __restrict__ ilist, const FrameHeader* hdr, int sh_degree,
                                 bool temporal_cull, float4* __restrict__ ipart) {
   griddep_wait();
   griddep_launch_dependents();
-  // Items without a gradient (no pixel composited them) only get a zero
-  // partial; the others are packed to the front of the CTA (their summed
-  // pair gradients through shared memory) so the chain rule runs on full
-  // warps: in a scene whose pixels saturate early most items have none.
+  // Items without a gradient (no pixel composited them) have a zero partial
+  // already (the gather pass); the others are packed to the front of the CTA
+  // (their summed pair gradients through shared memory) so the chain rule
+  // runs on full warps: in a scene whose pixels saturate early most items
+  // have none.
   __shared__ float4 s_g[3][kBwdBlock];
   __shared__ uint32_t s_item[kBwdBlock];
   __shared__ uint32_t s_wcnt[kBwdBlock / 32];
@@ -417,15 +478,16 @@ __global__ void __launch_bounds__(kBwdBlock, 4)
   if ((hdr->status & 1u) || static_cast<int>(blockIdx.x) * kBwdBlock >= nlist) return;  // CTA-uniform
   const bool mine = j < nlist;
   uint32_t item = mine ? ilist[j] : 0u;
-  const uint32_t cnt = mine ? touched[item] : 0u;
-  const uint32_t o = cnt ? ioffs[item] : 0u;
-  float4 ga, gb, gc;
-  const bool got = gather_pairs<kStats>(cnt, o, lane, gbuf, reach, ga, gb, gc) && mine;
-  if (mine && !got) {
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* dz = ipart + kPartVec * static_cast<size_t>(item);
-    dz[0] = dz[1] = dz[2] = dz[3] = dz[4] = dz[5] = z;
+  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+  if (mine) {
+    const float4* src = ipart + kPartVec * static_cast<size_t>(item);
+    gb = src[1];
+    if (gb.z != 0.0f) {
+      ga = src[0];
+      gc = src[2];
+    }
   }
+  const bool got = mine && gb.z != 0.0f;
   const uint32_t b = __ballot_sync(0xffffffffu, got);
   if (lane == 0) s_wcnt[warp] = __popc(b);
   __syncthreads();
@@ -582,13 +644,17 @@ static void launch_pre_bwd_t(const r4g_gaussians& g, const FrameLayout& L, void*
       // (the blend backward zeroed the item counter)
       const int nbm = static_cast<int>((L.m + 1023) / 1024);
       launch_pdl(list_items_kernel, nbm, 1024, 0, s, touched, static_cast<uint32_t>(L.m), ilist, hdr);
+      const int nbg = static_cast<int>((L.m + kGatherBlock - 1) / kGatherBlock);
+      auto kgt = stats ? preprocess_bwd_gather_kernel<true> : preprocess_bwd_gather_kernel<false>;
+      launch_pdl(kgt, nbg, kGatherBlock, 0, s, static_cast<const uint32_t*>(ilist),
+                 static_cast<const uint32_t*>(at<uint32_t>(frame, L.ioffs)), touched,
+                 static_cast<const float4*>(at<float4>(frame, L.gbuf)),
+                 static_cast<const uint8_t*>(at<uint8_t>(frame, L.reach)), static_cast<const FrameHeader*>(hdr),
+                 ipart);
       const int nbi = static_cast<int>((L.m + kBwdBlock - 1) / kBwdBlock);
       auto ki = stats ? preprocess_bwd_items_kernel<A, B, true> : preprocess_bwd_items_kernel<A, B, false>;
       launch_pdl(ki, nbi, kBwdBlock, 0, s, g, static_cast<const ViewDev*>(at<ViewDev>(frame, L.views)),
-                 static_cast<const uint32_t*>(ilist), static_cast<const uint32_t*>(at<uint32_t>(frame, L.ioffs)),
-                 touched, static_cast<const float4*>(at<float4>(frame, L.gbuf)),
-                 static_cast<const uint8_t*>(at<uint8_t>(frame, L.reach)), static_cast<const FrameHeader*>(hdr),
-                 sh_degree, tc, ipart);
+                 static_cast<const uint32_t*>(ilist), static_cast<const FrameHeader*>(hdr), sh_degree, tc, ipart);
       auto kg = stats ? preprocess_bwd_gauss_kernel<A, true> : preprocess_bwd_gauss_kernel<A, false>;
       launch_pdl(kg, nb, kBwdBlock, 0, s, g, L.nviews, static_cast<const uint32_t*>(at<uint32_t>(frame, L.glist)),
                  touched, static_cast<const float4*>(ipart), static_cast<const FrameHeader*>(hdr), sh_degree, out);
