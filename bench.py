@@ -402,7 +402,11 @@ def train_bench(args, rend, params, dev, stream, flush):
     npix = target.numel()
     inv = 1.0 / npix
     leaves = {k: v.clone().requires_grad_(True) for k, v in params.items()}
-    cap_b = rend.reserve_batch(params, step_views)  # untimed: no step overflows its key buffer
+    # the batched paths take the tile shape the library's autotuner picks for
+    # these views (untimed); the plain per-view path keeps 16x16
+    rb = r4g.Renderer()
+    tune = rb.autotune(params, step_views[0], backward=True, reps=3)
+    cap_b = rb.reserve_batch(params, step_views)  # untimed: no step overflows its key buffer
     # the plain path: one frame per view slot, sized for the largest view of any step
     need = 0
     for views in step_views:
@@ -415,7 +419,7 @@ def train_bench(args, rend, params, dev, stream, flush):
               for k in range(TRAIN_VIEWS)]
     gimg = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
     grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
-    graph = r4g.BatchGraph(rend, params, step_views[0], key_capacity=cap_b,
+    graph = r4g.BatchGraph(rb, params, step_views[0], key_capacity=cap_b,
                            grad_fn=lambda img: torch.sign(img - target) * inv)
     tables = [graph.views_table(v) for v in step_views]
     it = {"a": 0, "p": 0, "g": 0}
@@ -425,7 +429,7 @@ def train_bench(args, rend, params, dev, stream, flush):
         it["a"] += 1
         for v in leaves.values():
             v.grad = None
-        img = r4g.render_batch(leaves, views, renderer=rend)
+        img = r4g.render_batch(leaves, views, renderer=rb)
         loss = (img - target).abs().mean()
         loss.backward()
 
@@ -457,17 +461,17 @@ def train_bench(args, rend, params, dev, stream, flush):
         raise RuntimeError("the graph's last replay reports an error")
     # stage times of the autograd step (library stage events on), same views
     it["a"] = warm
-    abi.r4g_set_timing(rend.ctx, True)
-    abi.r4g_stage_times(rend.ctx, reset=True)
+    abi.r4g_set_timing(rb.ctx, True)
+    abi.r4g_stage_times(rb.ctx, reset=True)
     for _ in range(nsteps):
         flush.zero_()
         step_autograd()
     torch.cuda.synchronize()
-    abi.r4g_set_timing(rend.ctx, False)
-    stage_ms, _ = abi.r4g_stage_times(rend.ctx, reset=True)
+    abi.r4g_set_timing(rb.ctx, False)
+    stage_ms, _ = abi.r4g_stage_times(rb.ctx, reset=True)
     per_stage = {k: v / nsteps for k, v in stage_ms.items() if v > 0}
     # work of the timed steps' views (untimed counting pass)
-    counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
+    counter = r4g.Renderer(tile=rb.tile, flags=abi.R4G_FLAG_COUNT_PAIRS)
     pairs = keys = vis = reached = vis_g = 0
     for views in step_views[warm:warm + nsteps]:
         r = counter.render_batch(params, views, key_capacity=cap_b)
@@ -502,8 +506,10 @@ def train_bench(args, rend, params, dev, stream, flush):
     top = max(("blend_bwd", "blend", "preprocess_bwd"), key=lambda k: per_stage.get(k, 0.0))
     return {"value": round(1000.0 / ms_a["mean"], 3), "unit": "it/s", "ms_per_it": round(ms_a["mean"], 3),
             "ms_per_it_median": round(ms_a["median"], 3), "views": TRAIN_VIEWS, "steps": nsteps,
+            "tile": f"{rb.tile[0]}x{rb.tile[1]}", "autotune_ms": tune["ms"],
             "views_per_step": "fresh seeded (t ~ U[0,1], angle ~ U[0, 2 pi)) each step",
-            "path": "autograd.Function over the batched render (one call for the 4 views), L1 loss in torch",
+            "path": "autograd.Function over the batched render (one call for the 4 views, tile shape from the "
+                    "autotuner), L1 loss in torch",
             "plain_path": {"value": round(1000.0 / ms_p["mean"], 3), "ms_per_it": round(ms_p["mean"], 3),
                            "path": "per view: r4g_render + r4g_render_backward (FP32, 16x16)"},
             "graph": {"value": round(1000.0 / ms_g["mean"], 3), "ms_per_it": round(ms_g["mean"], 3),

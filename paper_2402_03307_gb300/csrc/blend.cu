@@ -453,6 +453,7 @@ __device__ __forceinline__ bool bwd_entry(BwdState<Q>& S, const StagedG& gs, uin
   }
   if (!__any_sync(0xffffffffu, any)) return false;
   const float4 p3 = gs.p3, p4 = gs.p4;
+  float2 sdq, st, sqq, scr, scg, scb;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const bool a0 = a[2 * q], a1 = a[2 * q + 1];
@@ -477,22 +478,23 @@ __device__ __forceinline__ bool bwd_entry(BwdState<Q>& S, const StagedG& gs, uin
     const float2 t = __fmul2_rn(dq, ev.dx[q]);
     const float2 qq = __fmul2_rn(t, ev.dx[q]);
     const float2 cr = __fmul2_rn(S.gr[q], w), cg = __fmul2_rn(S.gg[q], w), cb = __fmul2_rn(S.gb[q], w);
-    if (q == 0) {
-      v[0] = dq.x + dq.y;
-      v[1] = t.x + t.y;
-      v[3] = qq.x + qq.y;
-      v[6] = cr.x + cr.y;
-      v[7] = cg.x + cg.y;
-      v[8] = cb.x + cb.y;
+    if (q == 0) {  // packed sums over the thread's pairs, halves added at the end
+      sdq = dq; st = t; sqq = qq; scr = cr; scg = cg; scb = cb;
     } else {
-      v[0] += dq.x + dq.y;
-      v[1] += t.x + t.y;
-      v[3] += qq.x + qq.y;
-      v[6] += cr.x + cr.y;
-      v[7] += cg.x + cg.y;
-      v[8] += cb.x + cb.y;
+      sdq = __fadd2_rn(sdq, dq);
+      st = __fadd2_rn(st, t);
+      sqq = __fadd2_rn(sqq, qq);
+      scr = __fadd2_rn(scr, cr);
+      scg = __fadd2_rn(scg, cg);
+      scb = __fadd2_rn(scb, cb);
     }
   }
+  v[0] = sdq.x + sdq.y;
+  v[1] = st.x + st.y;
+  v[3] = sqq.x + sqq.y;
+  v[6] = scr.x + scr.y;
+  v[7] = scg.x + scg.y;
+  v[8] = scb.x + scb.y;
   v[2] = ev.dy * v[0];
   v[4] = ev.dy * v[1];
   v[5] = ev.dy * v[2];
