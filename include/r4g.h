@@ -203,7 +203,7 @@ r4g_status r4g_frame_stats(r4g_ctx* ctx, const void* frame, size_t frame_bytes, 
  * entries, key = tile_id << 32 | float_bits(depth)), per-tile ranges
  * (uint32 [tiles][2], [begin, end)), and the per-Gaussian screen records
  * (float [n][12] = mean2d.x, mean2d.y, conic a, b, c, opacity_t, depth,
- * unused, r, g, b, unused; conic is the inverse 2D covariance, exponent
+ * log2(255 opacity_t), r, g, b, max(log2 opacity_t, -126); conic is the inverse 2D covariance, exponent
  * -1/2 (a dx^2 + 2 b dx dy + c dy^2); culled Gaussians have opacity_t = 0).
  * Any output pointer may be NULL. For tests and tools. */
 r4g_status r4g_frame_export(r4g_ctx* ctx, const void* frame, size_t frame_bytes, int64_t n,

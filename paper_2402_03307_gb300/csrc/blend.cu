@@ -76,25 +76,24 @@ struct __align__(128) StagedG {
 // Can the Gaussian's contributing region {q <= min(9, 2 ln(255 o))}, q = d^T conic d,
 // contain a pixel centre of the rectangle [x0, x1] x [y0, y1]? Exact minimum of
 // q over the rectangle (inside, or on one of the four edges), compared with a
-// relative and an absolute slack so the answer is conservative under FP32.
-__device__ __forceinline__ bool ellipse_meets_rect(const float4 A, float c, float o, float x0, float x1,
-                                                   float y0, float y1) {
+// threshold thr that carries a relative and an absolute slack so the answer is
+// conservative under FP32; boc = b / c and boa = b / a.
+__device__ __forceinline__ bool ellipse_meets_rect(const float4 A, float c, float thr, float boc, float boa,
+                                                   float x0, float x1, float y0, float y1) {
   const float mx = A.x, my = A.y, a = A.z, b = A.w;
   if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-  const float k2 = fminf(9.0f, 2.0f * __logf(255.0f * o));
-  const float thr = k2 * 1.001f + 1e-3f;
   float qmin = 3.4e38f;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {  // vertical edges: minimise over dy
     const float dx = (e ? x1 : x0) - mx;
-    float dy = -b * dx / c;
+    float dy = -boc * dx;
     dy = fminf(fmaxf(dy, y0 - my), y1 - my);
     qmin = fminf(qmin, a * dx * dx + 2.0f * b * dx * dy + c * dy * dy);
   }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {  // horizontal edges: minimise over dx
     const float dy = (e ? y1 : y0) - my;
-    float dx = -b * dy / a;
+    float dx = -boa * dy;
     dx = fminf(fmaxf(dx, x0 - mx), x1 - mx);
     qmin = fminf(qmin, a * dx * dx + 2.0f * b * dx * dy + c * dy * dy);
   }
@@ -113,16 +112,20 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
   }
   const float4 A = recA[gid], Bv = recB[gid], C = recC[gid];
   const float Ap = -0.5f * kLog2e * A.z, Bp = -kLog2e * A.w, Cp = -0.5f * kLog2e * Bv.x, o = Bv.y;
-  const float pmin = fmaxf(kCut2, -log2f(255.0f * o));
+  // the record carries log2(255 o) and max(log2 o, -126) (the preprocess's)
+  const float l255 = Bv.w, lo = C.w;
+  const float pmin = fmaxf(kCut2, -l255);
   const float mid = 0.5f * pmin, half = fmaxf(-0.5f * pmin, 1e-6f);
-  const float lo = fmaxf(log2f(o), -126.0f);
   const float ih = 1.0f / half, nm = -(mid + lo) * ih;
   uint32_t m = o > kAlphaMax ? kClampBit : 0u;
+  // the contributing ellipse q <= min(9, 2 ln(255 o)), with slack
+  const float thr = fminf(9.0f, 2.0f * kLn2 * l255) * 1.001f + 1e-3f;
+  const float boc = A.w / Bv.x, boa = A.w / A.z;
 #pragma unroll
   for (int w = 0; w < B::NW; ++w) {  // pixel centres of warp w's block
     const float x0 = B::px0(tx, w) + 0.5f, x1 = x0 + static_cast<float>(B::BW - 1);
     const float y0 = B::py0(ty, w) + 0.5f, y1 = y0 + 7.0f;
-    if (ellipse_meets_rect(A, Bv.x, o, x0, x1, y0, y1)) m |= 1u << w;
+    if (ellipse_meets_rect(A, Bv.x, thr, boc, boa, x0, x1, y0, y1)) m |= 1u << w;
   }
   sg->p0 = make_float4(-A.x, -A.x, -A.y, -A.y);
   sg->p1 = make_float4(Ap, Ap, Bp, Bp);
@@ -178,27 +181,29 @@ __device__ __forceinline__ float& lane_of(float2& v, int h) { return h ? v.y : v
 // Gaussian's opacity_t exceeds 0.99 so alpha is clamped; kLast: track the
 // last composited position. Returns true when every pixel of the warp has
 // stopped.
+// Returns kApplyDone when every pixel of the warp has stopped, and
+// kApplyStopped when some pixel of the warp stopped at this Gaussian.
+constexpr int kApplyDone = 1, kApplyStopped = 2;
+
 template <bool kClamp, bool kLast, int Q>
-__device__ __forceinline__ bool fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const StagedG& g, uint32_t pos) {
+__device__ __forceinline__ int fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const StagedG& g, uint32_t pos) {
   float2 a[Q], Tn[Q];
-  bool st[2 * Q], any = false;
+  float tmin = 3.0e38f;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     a[q] = make_float2(ev.v[2 * q] ? ev.araw[q].x : 0.0f, ev.v[2 * q + 1] ? ev.araw[q].y : 0.0f);
     if constexpr (kClamp) a[q] = make_float2(fminf(a[q].x, kAlphaMax), fminf(a[q].y, kAlphaMax));
     Tn[q] = __ffma2_rn(make_float2(-S.T[q].x, -S.T[q].y), a[q], S.T[q]);  // T (1 - alpha)
-    st[2 * q] = Tn[q].x < kTMin;  // only a taken Gaussian can stop
-    st[2 * q + 1] = Tn[q].y < kTMin;
-    any = any || st[2 * q] || st[2 * q + 1];
+    tmin = fminf(tmin, fminf(Tn[q].x, Tn[q].y));  // only a taken Gaussian can take T below 1e-4
   }
-  bool wdone = false;
-  if (__any_sync(0xffffffffu, any)) {
+  int ret = 0;
+  if (__any_sync(0xffffffffu, tmin < kTMin)) {
     // stop before this Gaussian: it is not composited; the pixel is done
     bool all = true;
 #pragma unroll
     for (int j = 0; j < 2 * Q; ++j) {
       const int q = j >> 1, h = j & 1;
-      if (st[j]) {
+      if (lane_of(Tn[q], h) < kTMin) {
         lane_of(a[q], h) = 0.0f;
         lane_of(Tn[q], h) = lane_of(S.T[q], h);
         lane_of(S.PX[q], h) = kFar;
@@ -208,7 +213,7 @@ __device__ __forceinline__ bool fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const
       }
       all = all && S.done[j];
     }
-    wdone = __all_sync(0xffffffffu, all);
+    ret = kApplyStopped | (__all_sync(0xffffffffu, all) ? kApplyDone : 0);
   }
   const float4 p3 = g.p3, p4 = g.p4;
 #pragma unroll
@@ -226,7 +231,7 @@ __device__ __forceinline__ bool fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const
       S.pairs += ev.v[j] ? 1u : 0u;
     }
   }
-  return wdone;
+  return ret;
 }
 
 // Walk the set bits of one 32-entry group, two Gaussians per iteration: the
@@ -249,20 +254,22 @@ __device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StagedG* grp, ui
       eval_pairs<Q>(grp[j0], S.PX, PY, e0);
       eval_pairs<Q>(grp[j1], S.PX, PY, e1);
       const bool c0 = kClamp && ((cbits >> j0) & 1u), c1 = kClamp && ((cbits >> j1) & 1u);
-      if (c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
-             : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0))
-        return true;
+      const int r0 = c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
+                        : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0);
+      if (r0 & kApplyDone) return true;
+      if (r0 & kApplyStopped) {  // (warp-uniform) a pixel stopped: the second result is void there
 #pragma unroll
-      for (int j = 0; j < 2 * Q; ++j) e1.v[j] = e1.v[j] && !S.done[j];
-      if (c1 ? fwd_apply<true, kLast, Q>(S, e1, grp[j1], pos0 + j1)
-             : fwd_apply<false, kLast, Q>(S, e1, grp[j1], pos0 + j1))
+        for (int j = 0; j < 2 * Q; ++j) e1.v[j] = e1.v[j] && !S.done[j];
+      }
+      if ((c1 ? fwd_apply<true, kLast, Q>(S, e1, grp[j1], pos0 + j1)
+              : fwd_apply<false, kLast, Q>(S, e1, grp[j1], pos0 + j1)) & kApplyDone)
         return true;
     } else {
       PairEval<Q> e0;
       eval_pairs<Q>(grp[j0], S.PX, PY, e0);
       const bool c0 = kClamp && ((cbits >> j0) & 1u);
-      if (c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
-             : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0))
+      if ((c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
+              : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0)) & kApplyDone)
         return true;
     }
   }

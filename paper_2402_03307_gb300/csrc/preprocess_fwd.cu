@@ -149,8 +149,9 @@ __global__ void __launch_bounds__(kPreFwdBlock)
         const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
         ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
         out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
-        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], 0.0f);
-        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], 0.0f);
+        // with the opacity's logarithms the blends' staging needs
+        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], log2f(255.0f * f.o_t));
+        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], fmaxf(log2f(f.o_t), -126.0f));
         out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                     static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
         // +1 on every tile of the rectangle, as four corner updates
