@@ -179,6 +179,7 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.views = o;    o = align_up(o + sizeof(ViewDev) * nviews);
   L.rec = o;      o = align_up(o + 3 * sizeof(float4) * m);
   L.rect = o;     o = align_up(o + sizeof(uint2) * m);
+  L.spans = o;    o = align_up(o + 2 * sizeof(uint4) * m);  // per item: 16 tile rows' (offset, width) bytes
   L.touched = o;  o = align_up(o + sizeof(uint32_t) * m);
   L.dkey0 = o;    o = align_up(o + sizeof(uint32_t) * m);
   L.dkey1 = o;    o = align_up(o + sizeof(uint32_t) * m);

@@ -15,6 +15,7 @@
 
 #include "r4g_internal.cuh"
 #include "onesweep.cuh"
+#include "tile_rows.cuh"
 
 namespace r4g {
 
@@ -180,9 +181,10 @@ __global__ void __launch_bounds__(kPreBlock)
 // their offsets increase strictly and a chunk of E pairs involves at most
 // E + 1 of them: their offsets are loaded into shared memory. Each thread
 // emits a run of E / 256 consecutive pairs: one binary search finds the
-// Gaussian of the run's first pair, later pairs step through its rectangle
-// and on into the next Gaussian. Pair q of Gaussian j covers tile
-// (x0 + l mod w, y0 + l div w) of its rectangle, l = q - offs[j]. The runs are
+// Gaussian of the run's first pair, later pairs step through its tiles and on
+// into the next Gaussian. Pair q of Gaussian j is its l-th tile, l = q -
+// offs[j], counting the intervals of its tile rows top to bottom (emit_run).
+// The runs are
 // staged in shared memory (slots swizzled so that neither the run-wise writes
 // nor the pair-wise reads meet bank conflicts) and written out coalesced. The
 // Gaussian holding the chunk's first pair comes from depth_offsets_kernel.
@@ -191,11 +193,143 @@ static_assert(kEmitChunk % kPreBlock == 0 && kEmitRun == 8, "the slot swizzle as
 
 __device__ __forceinline__ uint32_t emit_slot(uint32_t i) { return i ^ ((i >> 5) & 7u); }
 
+// A Gaussian's pairs in emission order: tile rows top to bottom, in each the
+// interval of columns its contributing ellipse meets, as the preprocess
+// stored them (tile_rows.cuh; every column of the row for a rectangle too
+// large to store spans for).
+struct EmitG {
+  uint32_t tile_off, tiles_x, gid;
+  int x0, x1, y0, y1;
+  bool span;
+  uint4 s0, s1;  // 16 rows x (first column - x0, width) bytes
+  int k, c1, col;  // current row (relative to y0), its last column, the current column
+};
+
+__device__ __forceinline__ uint32_t span_word(const EmitG& G, int w) {
+  switch (w) {
+    case 0: return G.s0.x;
+    case 1: return G.s0.y;
+    case 2: return G.s0.z;
+    case 3: return G.s0.w;
+    case 4: return G.s1.x;
+    case 5: return G.s1.y;
+    case 6: return G.s1.z;
+    default: return G.s1.w;
+  }
+}
+
+// First column and width of row k.
+__device__ __forceinline__ void span_row(const EmitG& G, int k, int& c0, int& w) {
+  if (!G.span) {
+    c0 = G.x0;
+    w = G.x1 - G.x0;
+    return;
+  }
+  const uint32_t h = span_word(G, k >> 1) >> (16 * (k & 1));
+  c0 = G.x0 + static_cast<int>(h & 0xffu);
+  w = static_cast<int>((h >> 8) & 0xffu);
+}
+
+__device__ __forceinline__ void emit_load(EmitG& G, uint4 r, uint32_t gid, const uint4* __restrict__ spans) {
+  G.tile_off = r.z;
+  G.tiles_x = r.w;
+  G.gid = gid;
+  G.x0 = static_cast<int>(r.x & 0xffffu);
+  G.x1 = static_cast<int>(r.y & 0xffffu);
+  G.y0 = static_cast<int>(r.x >> 16);
+  G.y1 = static_cast<int>(r.y >> 16);
+  G.span = span_mode(G.x0, G.x1, G.y0, G.y1);
+  if (G.span) {
+    G.s0 = spans[2 * static_cast<size_t>(gid)];
+    G.s1 = spans[2 * static_cast<size_t>(gid) + 1];
+  }
+}
+
+// Place G on its pair l.
+__device__ __forceinline__ void emit_locate(EmitG& G, uint32_t l) {
+  const int rows = G.y1 - G.y0;
+  if (!G.span) {
+    const uint32_t w = static_cast<uint32_t>(G.x1 - G.x0);
+    G.k = static_cast<int>(l / w);
+    G.col = G.x0 + static_cast<int>(l - static_cast<uint32_t>(G.k) * w);
+    G.c1 = G.x1 - 1;
+    return;
+  }
+  for (G.k = 0; G.k < rows; ++G.k) {
+    int c0, w;
+    span_row(G, G.k, c0, w);
+    if (l < static_cast<uint32_t>(w)) {
+      G.col = c0 + static_cast<int>(l);
+      G.c1 = c0 + w - 1;
+      return;
+    }
+    l -= static_cast<uint32_t>(w);
+  }
+  G.k = rows - 1;  // unreachable when the counts agree; stays inside the rectangle
+  G.col = G.c1 = G.x0;
+}
+
+// The next pair of G (rows with tiles are consecutive).
+__device__ __forceinline__ void emit_step(EmitG& G) {
+  if (++G.col <= G.c1) return;
+  const int rows = G.y1 - G.y0;
+  while (++G.k < rows) {
+    int c0, w;
+    span_row(G, G.k, c0, w);
+    if (w > 0) {
+      G.col = c0;
+      G.c1 = c0 + w - 1;
+      return;
+    }
+  }
+  G.k = rows - 1;  // past the Gaussian's last pair: the caller moves to the next one
+  G.col = G.c1;
+}
+
+// The thread's run of kEmitRun pairs qa, qa + 1, ... (< qend) of an
+// emission chunk starting at q0: one binary search for the run's first
+// Gaussian among the chunk's window of items (offsets s_off, m of them),
+// then a step through its row intervals and on into the next Gaussian;
+// tile ids and items staged in swizzled slots.
+__device__ __forceinline__ void emit_run(uint32_t qa, uint32_t qend, uint32_t q0, int jlo, int m,
+                                         const uint32_t* s_off, const uint4* __restrict__ srect,
+                                         const uint32_t* __restrict__ order, const uint4* __restrict__ spans,
+                                         uint32_t* s_key, uint32_t* s_gid) {
+  if (qa >= qend) return;
+  int lo = 0, hi = m - 1;  // last i with s_off[i] <= qa
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_off[mid] <= qa) lo = mid;
+    else hi = mid - 1;
+  }
+  EmitG G;
+  emit_load(G, srect[jlo + lo], order[jlo + lo], spans);
+  emit_locate(G, qa - s_off[lo]);
+  uint32_t next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+#pragma unroll 1
+  for (int u = 0; u < kEmitRun; ++u) {
+    const uint32_t q = qa + u;
+    if (q >= qend) break;
+    if (q >= next) {  // the run enters the next Gaussian (past any without pairs)
+      do {
+        ++lo;
+        next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
+      } while (q >= next);
+      emit_load(G, srect[jlo + lo], order[jlo + lo], spans);
+      emit_locate(G, q - s_off[lo]);
+    }
+    const uint32_t slot = emit_slot(q - q0);
+    s_key[slot] = G.tile_off + static_cast<uint32_t>(G.y0 + G.k) * G.tiles_x + static_cast<uint32_t>(G.col);
+    s_gid[slot] = G.gid;
+    emit_step(G);
+  }
+}
+
 __global__ void __launch_bounds__(kPreBlock)
     emit_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect,
                 const uint32_t* ord_odd, const uint32_t* ord_even, const uint32_t* __restrict__ chunk_start, int n,
-                const FrameHeader* hdr, uint32_t* __restrict__ tkeys, uint32_t* __restrict__ egid,
-                uint32_t* __restrict__ ident) {
+                const FrameHeader* hdr, const uint4* __restrict__ spans, uint32_t* __restrict__ tkeys,
+                uint32_t* __restrict__ egid, uint32_t* __restrict__ ident) {
   griddep_wait();
   griddep_launch_dependents();
   const uint32_t* __restrict__ order = depth_order(ord_odd, ord_even, hdr);
@@ -215,43 +349,7 @@ __global__ void __launch_bounds__(kPreBlock)
     for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
     __syncthreads();
     const uint32_t qend = min(K, q0 + kEmitChunk);
-    const uint32_t qa = q0 + threadIdx.x * kEmitRun;
-    if (qa < qend) {
-      int lo = 0, hi = m - 1;  // last i with s_off[i] <= qa
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= qa) lo = mid;
-        else hi = mid - 1;
-      }
-      uint4 r = srect[jlo + lo];  // rect, the view's first tile id and tiles_x
-      uint32_t g = order[jlo + lo];
-      uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
-      uint32_t ly = (qa - s_off[lo]) / w, lx = (qa - s_off[lo]) - ly * w;
-      uint32_t next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
-#pragma unroll
-      for (int u = 0; u < kEmitRun; ++u) {
-        const uint32_t q = qa + u;
-        if (q >= qend) break;
-        if (q >= next) {  // the run enters the next Gaussian (past any without pairs)
-          do {
-            ++lo;
-            next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
-          } while (q >= next);
-          r = srect[jlo + lo];
-          g = order[jlo + lo];
-          w = (r.y & 0xffffu) - (r.x & 0xffffu);
-          ly = (q - s_off[lo]) / w;
-          lx = (q - s_off[lo]) - ly * w;
-        }
-        const uint32_t slot = emit_slot(q - q0);
-        s_key[slot] = r.z + ((r.x >> 16) + ly) * r.w + (r.x & 0xffffu) + lx;
-        s_gid[slot] = g;
-        if (++lx == w) {
-          lx = 0;
-          ++ly;
-        }
-      }
-    }
+    emit_run(q0 + threadIdx.x * kEmitRun, qend, q0, jlo, m, s_off, srect, order, spans, s_key, s_gid);
     __syncthreads();
     for (uint32_t i = threadIdx.x; q0 + i < qend; i += kPreBlock) {
       const uint32_t slot = emit_slot(i);
@@ -273,10 +371,10 @@ __global__ void __launch_bounds__(kPreBlock)
 // one's prefix, so every chunk it waits on belongs to a running CTA.
 static_assert(kEmitChunk == kOsTile && kPreBlock == kSortThreads, "an emission chunk is one sort tile");
 
-__global__ void __launch_bounds__(kPreBlock)
+__global__ void __launch_bounds__(kPreBlock, 5)
     emit_sort_kernel(const uint32_t* __restrict__ offs, const uint4* __restrict__ srect, const uint32_t* ord_odd,
                      const uint32_t* ord_even, const uint32_t* __restrict__ chunk_start, int n, FrameHeader* hdr,
-                     uint32_t* __restrict__ egid, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                     const uint4* __restrict__ spans, uint32_t* __restrict__ egid, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                      const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* ticket, uint32_t mask) {
   griddep_wait();
   griddep_launch_dependents();
@@ -302,43 +400,7 @@ __global__ void __launch_bounds__(kPreBlock)
     for (int i = threadIdx.x; i < m; i += kPreBlock) s_off[i] = offs[jlo + i];
     __syncthreads();
     const uint32_t qend = min(K, q0 + kEmitChunk);
-    const uint32_t qa = q0 + threadIdx.x * kEmitRun;
-    if (qa < qend) {
-      int lo = 0, hi = m - 1;  // last i with s_off[i] <= qa
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= qa) lo = mid;
-        else hi = mid - 1;
-      }
-      uint4 r = srect[jlo + lo];
-      uint32_t g = order[jlo + lo];
-      uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
-      uint32_t ly = (qa - s_off[lo]) / w, lx = (qa - s_off[lo]) - ly * w;
-      uint32_t next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
-#pragma unroll
-      for (int u = 0; u < kEmitRun; ++u) {
-        const uint32_t q = qa + u;
-        if (q >= qend) break;
-        if (q >= next) {
-          do {
-            ++lo;
-            next = lo + 1 < m ? s_off[lo + 1] : 0xffffffffu;
-          } while (q >= next);
-          r = srect[jlo + lo];
-          g = order[jlo + lo];
-          w = (r.y & 0xffffu) - (r.x & 0xffffu);
-          ly = (q - s_off[lo]) / w;
-          lx = (q - s_off[lo]) - ly * w;
-        }
-        const uint32_t slot = emit_slot(q - q0);
-        s_key[slot] = r.z + ((r.x >> 16) + ly) * r.w + (r.x & 0xffffu) + lx;
-        s_gid[slot] = g;
-        if (++lx == w) {
-          lx = 0;
-          ++ly;
-        }
-      }
-    }
+    emit_run(q0 + threadIdx.x * kEmitRun, qend, q0, jlo, m, s_off, srect, order, spans, s_key, s_gid);
     __syncthreads();
     const uint32_t tn = qend - q0;
     for (uint32_t i = threadIdx.x; i < tn; i += kPreBlock) egid[q0 + i] = s_gid[emit_slot(i)];
@@ -374,13 +436,14 @@ cudaError_t launch_emit_sort(const FrameLayout& L, void* frame, uint32_t* kout, 
                              static_cast<const uint32_t*>(at<uint32_t>(frame, L.ord1)),
                              static_cast<const uint32_t*>(at<uint32_t>(frame, L.ord0)),
                              static_cast<const uint32_t*>(at<uint32_t>(frame, L.chunks)), static_cast<int>(L.m),
-                             at<FrameHeader>(frame, L.header), at<uint32_t>(frame, L.egid), kout, vout, hist, status,
-                             ticket, (1u << nb) - 1u);
+                             at<FrameHeader>(frame, L.header), static_cast<const uint4*>(at<uint4>(frame, L.spans)),
+                             at<uint32_t>(frame, L.egid), kout, vout, hist, status, ticket, (1u << nb) - 1u);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Per-tile pair counts from the 2D difference array the preprocess filled
-// (prefix sums along x, then along y, in shared memory with warp scans), their
+// Per-tile pair counts from the per-row difference arrays the preprocess
+// filled (+1 at the first tile of a Gaussian's interval in a tile row, -1
+// after its last: prefix sums along x, in shared memory with warp scans), their
 // exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
 // list, and the digit histograms of the tile sort's radix passes. One CTA per
 // view; the difference array is copied into dynamic shared memory. Needs only
@@ -430,17 +493,6 @@ __global__ void __launch_bounds__(1024)
       const uint32_t val = x < tiles_x ? s_c[y * tiles_x + x] : 0u;
       const uint32_t inc = warp_incl_scan(val, lane) + carry;
       if (x < tiles_x) s_c[y * tiles_x + x] = inc;
-      carry = __shfl_sync(0xffffffffu, inc, 31);
-    }
-  }
-  __syncthreads();
-  for (int x = warp; x < tiles_x; x += nwarp) {  // each warp: running sums down its columns
-    uint32_t carry = 0;
-    for (int y0 = 0; y0 < tiles_y; y0 += 32) {
-      const int y = y0 + lane;
-      const uint32_t val = y < tiles_y ? s_c[y * tiles_x + x] : 0u;
-      const uint32_t inc = warp_incl_scan(val, lane) + carry;
-      if (y < tiles_y) s_c[y * tiles_x + x] = inc;
       carry = __shfl_sync(0xffffffffu, inc, 31);
     }
   }
@@ -563,7 +615,8 @@ cudaError_t launch_binning(const FrameLayout& L, void* frame, cudaStream_t s) {
   if (chunks > 0 && L.tile_bits == 0)
     e = launch_pdl(emit_kernel, static_cast<unsigned>(egrid), kPreBlock, 0, s, static_cast<const uint32_t*>(offs),
                    static_cast<const uint4*>(srect), ord_odd, ord_even, static_cast<const uint32_t*>(cstart), m,
-                   static_cast<const FrameHeader*>(hdr), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.egid),
+                   static_cast<const FrameHeader*>(hdr), static_cast<const uint4*>(at<uint4>(frame, L.spans)),
+                   at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.egid),
                    L.tile_bits == 0 ? at<uint32_t>(frame, L.vals0) : nullptr);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

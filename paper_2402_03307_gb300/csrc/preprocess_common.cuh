@@ -15,14 +15,16 @@ namespace r4g {
 // Per-item outputs (item = view * N + Gaussian).
 struct PreOut {
   float4* recA;  // [3][M] records: (mean2d.x, mean2d.y, conic a, conic b),
-                 // (conic c, opacity_t, depth, 0), (r, g, b, 0)
+                 // (conic c, opacity_t, depth, log2(255 o_t)), (r, g, b, max(log2 o_t, -126))
   uint2* rect;   // tile rect: (x0 | y0 << 16, x1 | y1 << 16), [x0, x1) x [y0, y1)
+  uint4* spans;  // [2 per item] the tile rows' column spans (tile_rows.cuh)
   uint32_t* touched;
   uint32_t* dkey;  // float bits of the depth for items with tiles, else 0xffffffff
-  uint32_t* tdiff; // per view, 2D difference array of the tile counts, (tiles_y + 1) x (tiles_x + 1)
+  uint32_t* tdiff; // per view, per-row difference arrays of the tile counts, (tiles_y + 1) x (tiles_x + 1)
   uint32_t* glist; // Gaussians visible in some view
   FrameHeader* header;
   int tile_w, tile_h;
+  int tws, ths;  // log2 of the tile width and height
 };
 
 // Everything the forward computes for one Gaussian, kept so the backward can

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "preprocess_common.cuh"
+#include "tile_rows.cuh"
 
 namespace r4g {
 
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kPreFwdBlock)
   __shared__ uint32_t s_pairs[kMaxViews];
   __shared__ uint32_t s_wcnt[kPreFwdBlock / 32];
   __shared__ uint32_t s_vis, s_base, s_kminc, s_kmax;
+  __shared__ uint32_t s_cnt[kPreFwdBlock];  // each thread's pair count in the current view
   __shared__ __align__(16) ViewDev s_views[kMaxViews];  // the view table (copied as 16-byte words)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int v = threadIdx.x; v < kMaxViews; v += kPreFwdBlock) s_pairs[v] = 0;
@@ -130,45 +132,116 @@ __global__ void __launch_bounds__(kPreFwdBlock)
   const size_t M = static_cast<size_t>(g.n) * nviews;
   for (int v = 0; v < (kMulti ? nviews : 1); ++v) {
     uint32_t ntiles = 0;
+    const ViewDev& V = s_views[v];
+    const size_t item = static_cast<size_t>(v) * g.n + i;
+    bool vis = false;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    TileEllipse E{};
+    uint32_t key = 0xffffffffu;
     if (live) {
-      const ViewDev& V = s_views[v];
       const CamDev& cam = V.cam;
-      const size_t item = static_cast<size_t>(v) * g.n + i;
       Fwd f;
       S invW, dt;
       view_geometry<S>(G, cam, V.t, temporal_cull, f, invW, dt);
       int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
-      const bool vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
+      vis = f.visible && pixel_box(f, cam, i0, i1, j0, j1);
+      key = __float_as_uint(f.pc[2]);
       if (vis) {
         if (flow) {  // the colour slot carries d(mean2d)/dt (channel 2 zero)
           image_velocity<S>(G, invW, cam, f);
         } else {
           forward_color<kShBF16>(g, i, cam, sh_degree, f);
         }
-        const int x0 = i0 / out.tile_w, x1 = i1 / out.tile_w + 1;
-        const int y0 = j0 / out.tile_h, y1 = j1 / out.tile_h + 1;
-        ntiles = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
-        out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
+        x0 = i0 / out.tile_w;
+        x1 = i1 / out.tile_w + 1;
+        y0 = j0 / out.tile_h;
+        y1 = j1 / out.tile_h + 1;
         // with the opacity's logarithms the blends' staging needs
-        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], log2f(255.0f * f.o_t));
+        const float l255 = log2f(255.0f * f.o_t);
+        out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
+        out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], l255);
         out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], fmaxf(log2f(f.o_t), -126.0f));
         out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                     static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
-        // +1 on every tile of the rectangle, as four corner updates
-        uint32_t* td = out.tdiff + V.tdiff_off;
-        const int st = V.tiles_x + 1;
-        atomicAdd(td + y0 * st + x0, 1u);
-        atomicAdd(td + y0 * st + x1, 0xffffffffu);
-        atomicAdd(td + y1 * st + x0, 0xffffffffu);
-        atomicAdd(td + y1 * st + x1, 1u);
+        if (span_mode(x0, x1, y0, y1))
+          E = tile_ellipse(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1], f.conic[2], l255);
       } else {
         out.recA[item] = make_float4(0.f, 0.f, 0.f, 0.f);
         out.recA[M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
         out.recA[2 * M + item] = make_float4(0.f, 0.f, 0.f, 0.f);
         out.rect[item] = make_uint2(0u, 0u);
       }
+    }
+    {
+      // The tiles of each tile row the contributing ellipse meets (an
+      // interval; every tile of the row for a rectangle too large to store
+      // spans for), +1 on each as two updates of the row's difference array,
+      // the spans kept for the pair emission. The warp shares the rows of its
+      // lanes' Gaussians out 32 at a time (lanes' row counts differ widely).
+      {
+        const int R = vis ? y1 - y0 : 0;
+        int pre = R;  // inclusive scan of the row counts over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, pre, o);
+          if (lane >= o) pre += y;
+        }
+        const int excl = pre - R;
+        const int total = __shfl_sync(0xffffffffu, pre, 31);
+        s_cnt[threadIdx.x] = 0u;
+        __syncwarp();
+        uint32_t* td = out.tdiff + V.tdiff_off;
+        const int st = V.tiles_x + 1;
+        uint16_t* sp16 = reinterpret_cast<uint16_t*>(out.spans);
+        for (int f0 = 0; f0 < total; f0 += 32) {
+          const int fi = f0 + lane;
+          int j = 0;  // the lane whose rows hold flattened row fi: the last with excl <= fi
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = j + step;
+            const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+            if (cand < 32 && ec <= fi) j = cand;
+          }
+          TileEllipse Ej;
+          Ej.mx = __shfl_sync(0xffffffffu, E.mx, j);
+          Ej.my = __shfl_sync(0xffffffffu, E.my, j);
+          Ej.a = __shfl_sync(0xffffffffu, E.a, j);
+          Ej.b = __shfl_sync(0xffffffffu, E.b, j);
+          Ej.c = __shfl_sync(0xffffffffu, E.c, j);
+          Ej.thr = __shfl_sync(0xffffffffu, E.thr, j);
+          Ej.det = __shfl_sync(0xffffffffu, E.det, j);
+          Ej.ia = __shfl_sync(0xffffffffu, E.ia, j);
+          Ej.rx = __shfl_sync(0xffffffffu, E.rx, j);
+          Ej.ry = __shfl_sync(0xffffffffu, E.ry, j);
+          Ej.dyl = __shfl_sync(0xffffffffu, E.dyl, j);
+          Ej.dyr = __shfl_sync(0xffffffffu, E.dyr, j);
+          Ej.exact = __shfl_sync(0xffffffffu, E.exact ? 1 : 0, j) != 0;
+          const int jx0 = __shfl_sync(0xffffffffu, x0, j), jx1 = __shfl_sync(0xffffffffu, x1, j);
+          const int jy0 = __shfl_sync(0xffffffffu, y0, j), jy1 = __shfl_sync(0xffffffffu, y1, j);
+          const int jex = __shfl_sync(0xffffffffu, excl, j);
+          if (fi >= total) continue;
+          const int k = fi - jex, ty = jy0 + k;
+          const bool spanned = span_mode(jx0, jx1, jy0, jy1);
+          int c0 = jx0, c1 = jx1 - 1;
+          const bool ok = spanned ? tile_row_span(Ej, ty, out.tws, out.ths, jx0, jx1, c0, c1) : true;
+          uint32_t w = 0;
+          if (ok) {
+            atomicAdd(td + ty * st + c0, 1u);
+            atomicAdd(td + ty * st + c1 + 1, 0xffffffffu);
+            w = static_cast<uint32_t>(c1 - c0 + 1);
+            atomicAdd(&s_cnt[(threadIdx.x & ~31) + j], w);
+          }
+          if (spanned) {
+            const size_t jitem = static_cast<size_t>(v) * g.n + (i - lane + j);
+            sp16[jitem * kSpanRows + k] = static_cast<uint16_t>(ok ? (static_cast<uint32_t>(c0 - jx0) | (w << 8)) : 0u);
+          }
+        }
+        __syncwarp();
+        ntiles = s_cnt[threadIdx.x];
+      }
+    }
+    if (live) {
       out.touched[item] = ntiles;
-      const uint32_t key = __float_as_uint(f.pc[2]);
       out.dkey[item] = ntiles ? key : 0xffffffffu;
       if (ntiles) {
         kminc = max(kminc, ~key);
@@ -245,6 +318,7 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
   PreOut o;
   o.recA = at<float4>(frame, L.rec);
   o.rect = at<uint2>(frame, L.rect);
+  o.spans = at<uint4>(frame, L.spans);
   o.touched = at<uint32_t>(frame, L.touched);
   o.dkey = at<uint32_t>(frame, L.dkey0);
   o.tdiff = at<uint32_t>(frame, L.tdiff);
@@ -252,6 +326,8 @@ cudaError_t launch_preprocess_fwd(const r4g_gaussians& g, const FrameLayout& L, 
   o.header = at<FrameHeader>(frame, L.header);
   o.tile_w = L.tile_w;
   o.tile_h = L.tile_h;
+  o.tws = log2_pow2(L.tile_w);
+  o.ths = log2_pow2(L.tile_h);
   ViewDev* views = at<ViewDev>(frame, L.views);
   const bool tc = !(flags & R4G_FLAG_NO_TEMPORAL_CULL);
   const bool fl = (flags & R4G_FLAG_FLOW) != 0;

@@ -73,7 +73,7 @@ static_assert(sizeof(FrameHeader) == 512, "frame header size");
 
 // Byte offsets of the regions of a frame; computed on the host.
 struct FrameLayout {
-  size_t header, views, rec, rect, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, ioffs, srect, chunks,
+  size_t header, views, rec, rect, spans, touched, tdiff, dkey0, dkey1, ord0, ord1, offs, ioffs, srect, chunks,
       blocksum, glist, keys0, vals0, keys1, vals1, egid, gbuf, reach, ranges, torder, tfinal, last, sortcnt,
       onesweep, tsort, ilist, ipart, total;
   int64_t n, cap;

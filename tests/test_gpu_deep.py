@@ -11,8 +11,8 @@ deep (about a hundred composited Gaussians per pixel):
 * the render's own radix sorts, bit for bit: the exported (tile | depth) keys
   and Gaussian indices must equal their own stable order (np.lexsort by key,
   then by index), each key's depth bits must be its Gaussian's depth, every
-  Gaussian's pairs must form one full tile rectangle and each tile's range
-  must hold exactly its pairs."""
+  Gaussian's pairs must form one interval of columns in each of consecutive
+  tile rows and each tile's range must hold exactly its pairs."""
 import numpy as np
 import pytest
 import torch
@@ -93,7 +93,7 @@ def test_render_sort_bit_exact_full_size(r4g, scene, rho, frame):
     keys = ex["keys"].cpu().numpy().view(np.uint64)
     vals = ex["values"].cpu().numpy().view(np.uint32)
     rec = ex["records"].cpu().numpy()
-    assert ex["key_count"] > 2_000_000
+    assert ex["key_count"] > 1_500_000
     order = np.lexsort((vals, keys))  # by key, ties by Gaussian index
     assert np.array_equal(keys[order], keys)
     assert np.array_equal(vals[order], vals)

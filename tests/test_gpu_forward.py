@@ -217,44 +217,118 @@ def test_full_size_frame_sampled_pixels(r4g):
 
 
 def _rectangles_check(ex, tiles_x):
-    """Every Gaussian's pairs cover a full rectangle of tiles once, and each
-    tile's range holds exactly its pairs."""
+    """Every Gaussian's pairs cover, in each of consecutive tile rows, one
+    interval of columns (the tiles its contributing ellipse meets), each
+    (Gaussian, tile) pair once, and each tile's range holds exactly its pairs.
+    Returns the pair count of each Gaussian."""
     keys = ex["keys"].cpu().numpy().view(np.uint64)
     vals = ex["values"].cpu().numpy().view(np.uint32).astype(np.int64)
     ranges = ex["ranges"].cpu().numpy()
     tiles = (keys >> np.uint64(32)).astype(np.int64)
     tx, ty = tiles % tiles_x, tiles // tiles_x
-    o = np.lexsort((tiles, vals))
-    g, tx, ty, tl = vals[o], tx[o], ty[o], tiles[o]
-    assert np.all((np.diff(g) > 0) | (np.diff(tl) > 0))  # no (Gaussian, tile) pair twice
-    start = np.flatnonzero(np.r_[True, np.diff(g) > 0])
+    o = np.lexsort((tx, ty, vals))  # by Gaussian, then tile row, then column
+    g, tx, ty = vals[o], tx[o], ty[o]
+    same_g = g[1:] == g[:-1]
+    same_row = same_g & (ty[1:] == ty[:-1])
+    assert np.all(tx[1:][same_row] == tx[:-1][same_row] + 1)  # one interval per row, no pair twice
+    new_row = same_g & (ty[1:] != ty[:-1])
+    assert np.all(ty[1:][new_row] == ty[:-1][new_row] + 1)  # consecutive rows
+    start = np.flatnonzero(np.r_[True, ~same_g])
     cnt = np.diff(np.r_[start, len(g)])
-    w = np.maximum.reduceat(tx, start) - np.minimum.reduceat(tx, start) + 1
-    h = np.maximum.reduceat(ty, start) - np.minimum.reduceat(ty, start) + 1
-    assert np.array_equal(cnt, w * h)
     per_tile = np.bincount(tiles, minlength=len(ranges))
     assert np.array_equal(ranges[:, 1] - ranges[:, 0], per_tile)
     assert ranges[:, 0].min() == 0 and ranges[:, 1].max() == len(keys)
     return cnt
 
 
-def test_emission_covers_full_rectangles(r4g):
-    """Small scene: pairs of Gaussians covering up to the whole 8x8-tile image."""
-    g, cam, t = synth.small_scene(seed=4)
+def _tile_qmin(m, con, x0, x1, y0, y1):
+    """FP64 minimum of q = d^T conic d over the rectangles [x0, x1] x [y0, y1]
+    (one per row of the arrays): 0 inside, else the least of the four edges'
+    minima."""
+    a, b, c = con[:, 0], con[:, 1], con[:, 2]
+    mx, my = m[:, 0], m[:, 1]
+    inside = (mx >= x0) & (mx <= x1) & (my >= y0) & (my <= y1)
+    q = np.full(len(m), np.inf)
+    for xe in (x0, x1):
+        dx = xe - mx
+        dy = np.clip(-b * dx / c, y0 - my, y1 - my)
+        q = np.minimum(q, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    for ye in (y0, y1):
+        dy = ye - my
+        dx = np.clip(-b * dy / a, x0 - mx, x1 - mx)
+        q = np.minimum(q, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    return np.where(inside, 0.0, q)
+
+
+def _tile_qmin_centres(m, con, tx, ty, tw, th):
+    """FP64 minimum of q over the pixel centres of tile (tx, ty): per pixel row,
+    the two centres around the row's minimiser x* = mx - b dy / a (clamped to
+    the tile), the least over the rows."""
+    a, b, c = con[:, 0], con[:, 1], con[:, 2]
+    q = np.full(len(m), np.inf)
+    for r in range(th):
+        dy = ty * th + r + 0.5 - m[:, 1]
+        xs = m[:, 0] - b * dy / a - 0.5  # the minimiser as a pixel index
+        for i in (np.floor(xs), np.floor(xs) + 1):
+            i = np.clip(i, tx * tw, tx * tw + tw - 1)
+            dx = i + 0.5 - m[:, 0]
+            q = np.minimum(q, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    return q
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 32)])
+def test_emitted_tiles_are_those_the_ellipse_meets(r4g, tile):
+    """Each Gaussian's tiles, against an FP64 test of its contributing ellipse
+    q <= min(9, 2 ln(255 o_t)) (the 3-sigma cutoff and the alpha >= 1/255 rule):
+    every tile with a pixel centre inside the ellipse (margin 1e-4) is listed,
+    and every listed tile's rectangle of pixel centres meets the ellipse
+    within the emission's 2% slack."""
+    g, cam, t = synth.small_scene(seed=12, n=1500)
+    rend, res = _render(r4g, g, cam, t, tile=tile)
+    ex = rend.export(res)
+    tw, th = tile
+    tiles_x, tiles_y = (cam.width + tw - 1) // tw, (cam.height + th - 1) // th
+    keys = ex["keys"].cpu().numpy().view(np.uint64)
+    vals = ex["values"].cpu().numpy().view(np.uint32).astype(np.int64)
+    rec = ex["records"].cpu().numpy().astype(np.float64)
+    listed = set(zip(vals.tolist(), (keys >> np.uint64(32)).astype(np.int64).tolist()))
+    vis = np.nonzero(rec[:, 5] > 0)[0]
+    gi, ti = np.meshgrid(vis, np.arange(tiles_x * tiles_y), indexing="ij")
+    gi, ti = gi.ravel(), ti.ravel()
+    tx, ty = ti % tiles_x, ti // tiles_x
+    q = _tile_qmin(rec[gi, 0:2], rec[gi][:, [2, 3, 4]], tx * tw + 0.5, tx * tw + tw - 0.5, ty * th + 0.5,
+                   ty * th + th - 0.5)
+    qc = _tile_qmin_centres(rec[gi, 0:2], rec[gi][:, [2, 3, 4]], tx, ty, tw, th)
+    k2 = np.minimum(9.0, 2.0 * np.log(255.0 * rec[gi, 5]))
+    must = qc <= k2 * (1 - 1e-4) - 1e-4
+    may = q <= k2 * 1.02 + 0.02
+    got = np.array([(int(a), int(b)) in listed for a, b in zip(gi, ti)])
+    assert must.sum() > 1000
+    assert np.all(got[must]), int((must & ~got).sum())
+    assert np.all(may[got]), int((got & ~may).sum())
+    assert got.sum() == len(listed)  # no pair outside the visible Gaussians' tiles
+
+
+def test_emission_covers_row_intervals(r4g):
+    """Small scene with larger Gaussians: pairs of Gaussians covering up to the
+    whole 8x8-tile image."""
+    g = synth.gaussians(1000, 4, ls_xyz=(-2.3, 0.5))
+    cam = synth.look_at((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 128, 128)
+    t = synth._f32(0.5)
     rend, res = _render(r4g, g, cam, t)
     cnt = _rectangles_check(rend.export(res), (cam.width + 15) // 16)
     assert cnt.max() > 8  # runs of eight pairs cross Gaussians and rectangle rows
 
 
 def test_emission_full_size_frame(r4g):
-    """300k Gaussians at 1352x1014 (sweep frame 37): ~3M pairs over ~1500
-    emission chunks, the rectangles and the ranges checked for every pair."""
+    """300k Gaussians at 1352x1014 (sweep frame 37): ~2M pairs over ~1000
+    emission chunks, the row intervals and the ranges checked for every pair."""
     g = synth.fwd300k_scene()
     cam, t = synth.orbit_camera(37, 300, 8.0, 1352, 1014)
     rend = r4g.Renderer()
     res = rend.render(to_device(g), cam, t)
     ex = rend.export(res)
-    assert ex["key_count"] > 2_000_000
+    assert ex["key_count"] > 1_500_000
     cnt = _rectangles_check(ex, (1352 + 15) // 16)
     assert cnt.min() >= 1 and (cnt == 1).any() and cnt.max() > 64
 
@@ -269,7 +343,7 @@ def test_inside_the_cloud_sampled_pixels(r4g):
     res = rend.render(to_device(g), cam, t)
     img = res.image.cpu().numpy()
     assert np.isfinite(img).all() and img.min() >= 0
-    assert rend.export(res)["key_count"] > 3_000_000
+    assert rend.export(res)["key_count"] > 2_500_000
     pix = synth.random_pixels(6, 1352, 1014, 1000)
     sc = oracle.to_f64(g)
     rec = oracle.preprocess(sc, cam, t)
