@@ -152,7 +152,7 @@ DRAM_TRAFFIC = {"blend": 23_762_688}
 # the workload both arms report (the reference arm times the oracle on a
 # bounded sample of it: frame 37, random pixels)
 CONFIG = {"workload": "300k 4D Gaussians, 1352x1014, 300-frame orbit sweep r=8, FP32, 1 view/launch",
-          "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile": "16x16",
+          "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile": "from the autotuner (plain path 16x16)",
           "l2": "flushed between steps (512 MB write)"}
 
 
@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     if args.train_only:
-        return {"train": train_bench(args, rend, params, dev, stream, flush)}
+        return {"train": train_bench(args, r4g.Renderer(), params, dev, stream, flush)}
     if args.backward_only:
         cam, t = frame_camera(37)
         grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
@@ -211,6 +211,13 @@ def run_ours(args, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
+    frames = frames_for_rank(rank, args.steps)
+    # the tile shape: the library's autotuner on the first frame (untimed);
+    # the plain 16x16 path is timed on the same frames below
+    rend16 = rend
+    rend = r4g.Renderer()
+    cam0, t0 = frame_camera(frames[0])
+    tune = rend.autotune(params, [(cam0, t0)], backward=False, reps=3)
     # size the key buffer once over the whole sweep (not timed): 10 % above the
     # largest (tile, Gaussian) pair count of any frame
     need_max = 0
@@ -221,22 +228,25 @@ def run_ours(args, rank, world, local):
     cap = int(need_max * 1.1) + 1024
     frame = rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
     img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
-    frames = frames_for_rank(rank, args.steps)
 
     def render_frame(k):
         cam, t = frame_camera(k)
         return rend.render(params, cam, t, frame=frame, key_capacity=cap, out=img, check=False)
 
-    for i in range(args.warmup):
+    # the clock sampler's process starts during the warm-up frames (its
+    # start-up otherwise lands on the first timed one)
+    clocks = ClockSampler(local)
+    clocks.start()
+    for i in range(max(args.warmup, 3)):
         render_frame(frames[i % len(frames)])
+    for k in frames[:min(len(frames), 8)]:
+        render_frame(k)
     torch.cuda.synchronize()
     abi.r4g_stage_times(rend.ctx, reset=True)
     # the timed frames run without per-stage events (an event between two
     # kernels ends their programmatic launch overlap); the stage times come
     # from a second pass over the same frames below
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
@@ -267,7 +277,7 @@ def run_ours(args, rank, world, local):
     median_ms = statistics.median(step_ms)
 
     # per-frame work of the timed frames, counted in an untimed instrumented pass
-    counter = r4g.Renderer(flags=abi.R4G_FLAG_COUNT_PAIRS)
+    counter = r4g.Renderer(tile=rend.tile, flags=abi.R4G_FLAG_COUNT_PAIRS)
     cframe = counter.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
     work = {"keys": 0, "n_visible": 0, "pairs": 0}
     for k in frames:
@@ -309,6 +319,8 @@ def run_ours(args, rank, world, local):
     out = {"metric": METRIC, "value": round(fps, 2), "unit": "frames/s", "n_gpus": world,
            "steps": len(frames), "warmup": args.warmup, "ms_per_step": round(total_ms / len(frames), 4),
            "ms_per_step_median": round(median_ms, 4), "fps_at_median": round(1e3 / median_ms, 2),
+           "ms_per_step_min_max": [round(min(step_ms), 4), round(max(step_ms), 4)],
+           "ms_per_frame": {str(k): round(x, 4) for k, x in zip(frames, step_ms)},
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded 4D Gaussians; stands in for Plenoptic Video at its resolution)",
            "config": dict(CONFIG, parallelism=f"replicas x{world}",
@@ -316,17 +328,20 @@ def run_ours(args, rank, world, local):
                                                         f"per rank (k = 7 i mod {FRAMES})"),
            "gpu_launches": int(sum(stage_launch.values())),
            "wall_s": round(wall, 3), "clocks": clk, "roofline": roofline}
+    out["config"]["tile"] = f"{rend.tile[0]}x{rend.tile[1]} (from the autotuner; plain path 16x16)"
+    out["autotune_ms"] = tune["ms"]
+    out["plain_path"], cap16 = plain_sweep_bench(rend16, params, dev, stream, flush, frames)
 
     # ---- training step: 4 views forward + L1 + backward --------------------------
     if not args.no_train and not args.frames_only:
-        out["train"] = train_bench(args, rend, params, dev, stream, flush)
+        out["train"] = train_bench(args, rend16, params, dev, stream, flush)
     # ---- batched views (autotuned tile, CUDA graph) and the large BF16 scene ---------
     if not args.no_batch and not args.frames_only:
         out["batched"] = batch_bench(args, dev, stream, flush)
     if not args.no_large and not args.frames_only:
         out["large"] = large_bench(args, dev, stream, flush)
     if not args.no_extras and not args.frames_only:
-        out["extras"] = extras_bench(args, params, dev, stream, flush, frames, cap)
+        out["extras"] = extras_bench(args, params, dev, stream, flush, frames, cap16)
     # ---- end to end through host buffers ---------------------------------------------
     if not args.no_e2e and not args.frames_only:
         out["e2e"] = e2e_bench(args, rend, g, dev, stream, frames, cap)
@@ -744,6 +759,34 @@ def extras_bench(args, params, dev, stream, flush, frames, cap):
                       "note": "includes scratch allocation by the Python wrapper"},
             "regularizers": {"ms": round(ms_reg, 3), "n": N_GAUSS,
                              "what": "entropy + 4D consistency losses and their gradients"}}
+
+
+def plain_sweep_bench(rend16, params, dev, stream, flush, frames) -> tuple[dict, int]:
+    """The plain path of the sweep: the same timed frames, FP32, one view per
+    call, 16x16 tiles (key buffer sized over the whole sweep, untimed).
+    Returns its record and its key capacity."""
+    import torch
+    need = 0
+    for k in range(FRAMES):
+        c, tt = frame_camera(k)
+        need = max(need, rend16.status(rend16.render(params, c, tt))[1])
+    cap = int(need * 1.1) + 1024
+    frame = rend16.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev)
+    img = torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev)
+    it = {"k": 0}
+
+    def one():
+        c, tt = frame_camera(frames[it["k"] % len(frames)])
+        it["k"] += 1
+        rend16.render(params, c, tt, frame=frame, key_capacity=cap, out=img, check=False)
+
+    for _ in range(3):
+        one()
+    it["k"] = 0
+    r = _timed_all(one, len(frames), stream, flush)
+    return ({"value": round(1000.0 / r["mean"], 2), "unit": "frames/s", "ms_per_step": round(r["mean"], 4),
+             "ms_per_step_median": round(r["median"], 4), "tile": "16x16",
+             "path": "FP32, one view per r4g_render call, 16x16 tiles"}, cap)
 
 
 def small_bench(dev, stream) -> dict:
