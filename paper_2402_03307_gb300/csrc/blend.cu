@@ -61,16 +61,43 @@ struct Blend {
   __device__ static int py0(int ty, int warp) { return ty * TH + (warp / WX) * 8; }
 };
 
-// A staged Gaussian (128-byte slot), operands duplicated for the packed pairs:
+// A staged Gaussian, operands duplicated for the packed pairs:
 //   p0 = (-mx, -mx, -my, -my)     p1 = (A', A', B', B')
 //   p2 = (C', C', lo, lo)         p3 = (r, r, g, g)
-//   p4 = (b, b, ih, ih)           p5 = (nm, nm, mask bits, o)
+//   p4 = (b, b, ih, ih)           p5 = (nm, nm)
 // with power' = A' dx^2 + B' dx dy + C' dy^2, lo = log2 o (the opacity enters
 // the exponent: alpha = 2^(power' + lo)), ih = 1 / half, nm = -(mid + lo) / half
-// (the window on power' shifted by lo).
-struct __align__(128) StagedG {
-  float4 p0, p1, p2, p3, p4, p5;
-  float4 pad0, pad1;  // 128-byte stride: the entry address is a shift
+// (the window on power' shifted by lo); m: the warp-block bits and the clamp
+// bit; o: opacity_t. StagedG is an entry in registers; a batch is staged as
+// a StageSet, one array per operand group: the lanes of a warp write
+// consecutive entries of each array and read the lanes' consecutive mask
+// words without bank conflicts, and a warp that evaluates an entry reads it
+// as a broadcast.
+struct StagedG {
+  float4 p0, p1, p2, p3, p4;
+  float2 p5;
+  uint32_t m;
+  float o;
+};
+
+template <int N>
+struct StageSet {
+  float4 p0[N], p1[N], p2[N], p3[N], p4[N];
+  float2 p5[N];
+  uint32_t mask[N];
+  float o[N];
+  __device__ __forceinline__ StagedG get(int j) const {
+    StagedG g;
+    g.p0 = p0[j];
+    g.p1 = p1[j];
+    g.p2 = p2[j];
+    g.p3 = p3[j];
+    g.p4 = p4[j];
+    g.p5 = p5[j];
+    g.m = mask[j];
+    g.o = o[j];
+    return g;
+  }
 };
 
 // Can the Gaussian's contributing region {q <= min(9, 2 ln(255 o))}, q = d^T conic d,
@@ -104,10 +131,11 @@ __device__ __forceinline__ bool ellipse_meets_rect(const float4 A, float c, floa
 template <int TW, int TH>
 __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, const float4* __restrict__ recB,
                                             const float4* __restrict__ recC, uint32_t gid, uint32_t ng, int tx,
-                                            int ty, StagedG* sg) {
+                                            int ty, StageSet<Blend<TW, TH>::NT>& sg, int i) {
   using B = Blend<TW, TH>;
   if (gid >= ng) {  // defensive: an entry that reaches no pixel
-    sg->p5 = make_float4(0.0f, 0.0f, __uint_as_float(0u), 0.0f);
+    sg.mask[i] = 0u;
+    sg.o[i] = 0.0f;
     return;
   }
   const float4 A = recA[gid], Bv = recB[gid], C = recC[gid];
@@ -127,12 +155,14 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ recA, con
     const float y0 = B::py0(ty, w) + 0.5f, y1 = y0 + 7.0f;
     if (ellipse_meets_rect(A, Bv.x, thr, boc, boa, x0, x1, y0, y1)) m |= 1u << w;
   }
-  sg->p0 = make_float4(-A.x, -A.x, -A.y, -A.y);
-  sg->p1 = make_float4(Ap, Ap, Bp, Bp);
-  sg->p2 = make_float4(Cp, Cp, lo, lo);
-  sg->p3 = make_float4(C.x, C.x, C.y, C.y);
-  sg->p4 = make_float4(C.z, C.z, ih, ih);
-  sg->p5 = make_float4(nm, nm, __uint_as_float(m), o);
+  sg.p0[i] = make_float4(-A.x, -A.x, -A.y, -A.y);
+  sg.p1[i] = make_float4(Ap, Ap, Bp, Bp);
+  sg.p2[i] = make_float4(Cp, Cp, lo, lo);
+  sg.p3[i] = make_float4(C.x, C.x, C.y, C.y);
+  sg.p4[i] = make_float4(C.z, C.z, ih, ih);
+  sg.p5[i] = make_float2(nm, nm);
+  sg.mask[i] = m;
+  sg.o[i] = o;
 }
 
 // Evaluation of one staged Gaussian at the thread's Q pixel pairs (PX[q],
@@ -149,7 +179,8 @@ struct PairEval {
 
 template <int Q>
 __device__ __forceinline__ void eval_pairs(const StagedG& g, const float2 (&PX)[Q], float2 PY, PairEval<Q>& r) {
-  const float4 p0 = g.p0, p1 = g.p1, p2 = g.p2, p4 = g.p4, p5 = g.p5;
+  const float4 p0 = g.p0, p1 = g.p1, p2 = g.p2, p4 = g.p4;
+  const float2 p5 = g.p5;
   const float2 dy = __fadd2_rn(PY, make_float2(p0.z, p0.w));
   const float2 bdy = __fmul2_rn(make_float2(p1.z, p1.w), dy);
   const float2 u = __ffma2_rn(__fmul2_rn(make_float2(p2.x, p2.y), dy), dy, make_float2(p2.z, p2.w));
@@ -241,9 +272,9 @@ __device__ __forceinline__ int fwd_apply(FwdState<Q>& S, PairEval<Q>& ev, const 
 // old position, so its result is discarded for that pixel. (The backward
 // walks one entry at a time: two would cost it more in occupancy than they
 // gain in overlap.)
-template <bool kClamp, bool kLast, int Q>
-__device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StagedG* grp, uint32_t bits, uint32_t cbits,
-                                          float2 PY, uint32_t pos0) {
+template <bool kClamp, bool kLast, int Q, int N>
+__device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StageSet<N>& sg, int base, uint32_t bits,
+                                          uint32_t cbits, float2 PY, uint32_t pos0) {
   while (bits) {
     const int j0 = __ffs(bits) - 1;
     bits &= bits - 1;
@@ -251,25 +282,27 @@ __device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StagedG* grp, ui
       const int j1 = __ffs(bits) - 1;
       bits &= bits - 1;
       PairEval<Q> e0, e1;
-      eval_pairs<Q>(grp[j0], S.PX, PY, e0);
-      eval_pairs<Q>(grp[j1], S.PX, PY, e1);
+      const StagedG g0 = sg.get(base + j0), g1 = sg.get(base + j1);
+      eval_pairs<Q>(g0, S.PX, PY, e0);
+      eval_pairs<Q>(g1, S.PX, PY, e1);
       const bool c0 = kClamp && ((cbits >> j0) & 1u), c1 = kClamp && ((cbits >> j1) & 1u);
-      const int r0 = c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
-                        : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0);
+      const int r0 = c0 ? fwd_apply<true, kLast, Q>(S, e0, g0, pos0 + j0)
+                        : fwd_apply<false, kLast, Q>(S, e0, g0, pos0 + j0);
       if (r0 & kApplyDone) return true;
       if (r0 & kApplyStopped) {  // (warp-uniform) a pixel stopped: the second result is void there
 #pragma unroll
         for (int j = 0; j < 2 * Q; ++j) e1.v[j] = e1.v[j] && !S.done[j];
       }
-      if ((c1 ? fwd_apply<true, kLast, Q>(S, e1, grp[j1], pos0 + j1)
-              : fwd_apply<false, kLast, Q>(S, e1, grp[j1], pos0 + j1)) & kApplyDone)
+      if ((c1 ? fwd_apply<true, kLast, Q>(S, e1, g1, pos0 + j1)
+              : fwd_apply<false, kLast, Q>(S, e1, g1, pos0 + j1)) & kApplyDone)
         return true;
     } else {
       PairEval<Q> e0;
-      eval_pairs<Q>(grp[j0], S.PX, PY, e0);
+      const StagedG g0 = sg.get(base + j0);
+      eval_pairs<Q>(g0, S.PX, PY, e0);
       const bool c0 = kClamp && ((cbits >> j0) & 1u);
-      if ((c0 ? fwd_apply<true, kLast, Q>(S, e0, grp[j0], pos0 + j0)
-              : fwd_apply<false, kLast, Q>(S, e0, grp[j0], pos0 + j0)) & kApplyDone)
+      if ((c0 ? fwd_apply<true, kLast, Q>(S, e0, g0, pos0 + j0)
+              : fwd_apply<false, kLast, Q>(S, e0, g0, pos0 + j0)) & kApplyDone)
         return true;
     }
   }
@@ -308,7 +341,8 @@ __device__ __forceinline__ TileLoc locate_tile(const ViewDev* __restrict__ views
 
 // The tile's pixels, front to back over its list.
 template <int TW, int TH, bool kLast>
-__device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint2* __restrict__ ranges,
+__device__ __forceinline__ void blend_fwd_tile(int tile, StageSet<Blend<TW, TH>::NT>& sg,
+                                               const uint2* __restrict__ ranges,
                                                const uint32_t* __restrict__ vals, const float4* __restrict__ recA,
                                                const float4* __restrict__ recB, const float4* __restrict__ recC,
                                                const uint32_t* __restrict__ egid, uint32_t ng, uint32_t cap,
@@ -354,20 +388,19 @@ __device__ __forceinline__ void blend_fwd_tile(int tile, StagedG* sg, const uint
     const int idx = b + static_cast<int>(threadIdx.x);
     if (idx < n) {
       const uint32_t e = vals[rg.x + idx];  // emission index of the pair
-      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, &sg[threadIdx.x]);
+      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, sg, threadIdx.x);
     }
     __syncthreads();
     const int cnt = min(BS, n - b);
     bool wdone = __all_sync(0xffffffffu, all_done);
     for (int j0 = 0; j0 < cnt && !wdone; j0 += 32) {
-      const uint32_t m = (j0 + lane < cnt) ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
+      const uint32_t m = (j0 + lane < cnt) ? sg.mask[j0 + lane] : 0u;
       uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
       const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
-      const StagedG* grp = sg + j0;
       const uint32_t pos0 = static_cast<uint32_t>(b + j0);
       // no Gaussian of this group needs the alpha clamp: the common path
-      wdone = cbits == 0u ? fwd_group<false, kLast, Q>(S, grp, bits, cbits, PY, pos0)
-                          : fwd_group<true, kLast, Q>(S, grp, bits, cbits, PY, pos0);
+      wdone = cbits == 0u ? fwd_group<false, kLast, Q>(S, sg, j0, bits, cbits, PY, pos0)
+                          : fwd_group<true, kLast, Q>(S, sg, j0, bits, cbits, PY, pos0);
     }
   }
   const size_t plane = static_cast<size_t>(width) * height;
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (fwd_min_blocks<TW, TH>()))
                      unsigned long long* __restrict__ pair_count, const uint32_t* __restrict__ torder) {
   griddep_wait();
   griddep_launch_dependents();
-  __shared__ StagedG sg[Blend<TW, TH>::NT];
+  __shared__ StageSet<Blend<TW, TH>::NT> sg;
   __shared__ int s_tile;
   for (;;) {
     __syncthreads();  // the previous tile is done with s_tile and sg
@@ -551,7 +584,8 @@ __device__ __forceinline__ void warp_reduce9(float v[9], int lane) {
 // backward sums per Gaussian. No float atomics: the gradient is
 // deterministic.
 template <int TW, int TH>
-__device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* sE, uint32_t* sTook, uint32_t& s_max,
+__device__ __forceinline__ void blend_bwd_tile(int tile, StageSet<Blend<TW, TH>::NT>& sg, uint32_t* sE,
+                                               uint32_t* sTook, uint32_t& s_max,
                                                float* s_slab,
                                                const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals,
                                                const float4* __restrict__ recA, const float4* __restrict__ recB,
@@ -618,13 +652,13 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
     if (idx < n) {
       const uint32_t e = vals[rg.x + idx];
       sE[threadIdx.x] = e;
-      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, &sg[threadIdx.x]);
+      stage_entry<TW, TH>(recA, recB, recC, e < cap ? egid[e] : ng, ng, tx, ty, sg, threadIdx.x);
     }
     __syncthreads();
     const int cnt = min(BS, n - b0);
     for (int j0 = ((cnt - 1) / 32) * 32; j0 >= 0; j0 -= 32) {
       const uint32_t m = (j0 + lane < cnt && static_cast<uint32_t>(b0 + j0 + lane) < wmax)
-                             ? __float_as_uint(sg[j0 + lane].p5.z) : 0u;
+                             ? sg.mask[j0 + lane] : 0u;
       uint32_t bits = __ballot_sync(0xffffffffu, m & wbit);
       const uint32_t cbits = __ballot_sync(0xffffffffu, m & kClampBit);
       while (bits) {
@@ -632,8 +666,9 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
         bits &= ~(1u << jj);
         const uint32_t p = static_cast<uint32_t>(b0 + j0 + jj);
         float v[9];
-        const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true, Q>(S, sg[j0 + jj], p, PY, v)
-                                               : bwd_entry<false, Q>(S, sg[j0 + jj], p, PY, v);
+        const StagedG gj = sg.get(j0 + jj);
+        const bool took = ((cbits >> jj) & 1u) ? bwd_entry<true, Q>(S, gj, p, PY, v)
+                                               : bwd_entry<false, Q>(S, gj, p, PY, v);
         if (took) {
           if (lane == 0) atomicOr(&sTook[j0 + jj], wbit);
           warp_reduce9(v, lane);
@@ -666,10 +701,10 @@ __device__ __forceinline__ void blend_bwd_tile(int tile, StagedG* sg, uint32_t* 
         const bool took = sTook[threadIdx.x] != 0u;
         reach[e] = took ? 1u : 0u;
         if (took) {
-          const StagedG& gs = sg[threadIdx.x];
           // power' = A' dx^2 + B' dx dy + C' dy^2 with A' = -a/(2 ln 2), B' = -b/ln 2,
           // C' = -c/(2 ln 2) for the conic (a, b, c); d power/d mean = (a dx + b dy, b dx + c dy)
-          const float Ap = gs.p1.x, Bp = gs.p1.z, Cp = gs.p2.x, o = gs.p5.w;
+          const float4 p1 = sg.p1[threadIdx.x];
+          const float Ap = p1.x, Bp = p1.z, Cp = sg.p2[threadIdx.x].x, o = sg.o[threadIdx.x];
           float4 r0, r1, r2;
           r0.x = -(2.0f * Ap * acc[1] + Bp * acc[2]) * kLn2;  // d mean2d.x
           r0.y = -(Bp * acc[1] + 2.0f * Cp * acc[2]) * kLn2;  // d mean2d.y
@@ -715,7 +750,7 @@ __global__ void __launch_bounds__(Blend<TW, TH>::NT, (bwd_min_blocks<TW, TH>()))
   // the multi-view preprocess backward that follows lists its items anew;
   // the count of pairs with a gradient starts again
   if (blockIdx.x == 0 && threadIdx.x == 0) hdr->n_ilist = 0u;
-  __shared__ StagedG sg[Blend<TW, TH>::NT];
+  __shared__ StageSet<Blend<TW, TH>::NT> sg;
   __shared__ uint32_t sE[Blend<TW, TH>::NT];
   __shared__ uint32_t sTook[Blend<TW, TH>::NT];  // per batch entry: warps that composited it
   __shared__ uint32_t s_max;
