@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the flow / KNN / regulariser timings")
     ap.add_argument("--batch-only", action="store_true", help="batched and large workloads only (profiling)")
     ap.add_argument("--frames-only", action="store_true", help="render frames only (profiling)")
+    ap.add_argument("--tile", default=None, metavar="WxH",
+                    help="tile shape of the frame sweep (8x8, 16x16 or 16x32) instead of the autotuner's choice, "
+                         "e.g. to profile the shape a timed run chose (the autotuner times live launches)")
     ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
     ap.add_argument("--backward-only", action="store_true",
                     help="render + backward of sweep frame 37, four times (profiling the backward)")
@@ -101,7 +104,30 @@ class ClockSampler:
         except (FileNotFoundError, OSError):
             self.proc = None
 
-    def stop(self) -> dict:
+    def _rows(self) -> list:
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and line.endswith("\n"):
+                rows.append(parts)
+        return rows
+
+    def wait_ready(self, timeout: float = 10.0) -> None:
+        """Block until the sampler has written its first sample (nvidia-smi's
+        start-up then lies before the timed region, not inside it)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < timeout:
+            if self._rows():
+                return
+            time.sleep(0.02)
+
+    def mark(self) -> int:
+        """The number of samples so far (the timed region starts after them)."""
+        return len(self._rows()) if self.proc is not None else 0
+
+    def stop(self, since: int = 0) -> dict:
+        """Stop sampling; summarise the samples from the last one before mark
+        `since` (the clocks as the timed region began) to the end."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -109,11 +135,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()[max(since - 1, 0):]
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
@@ -144,10 +166,10 @@ SMS, FP32_LANES = 152, 128
 # C += c w (3); the exponential itself runs on the MUFU unit.
 FP32_OPS_PER_PAIR = 19
 
-# DRAM bytes (read + write) of one launch of the kernel, from one ncu capture
-# of the sweep (--metrics dram__bytes_read.sum,dram__bytes_write.sum); None
-# for a kernel changed since its counters were taken.
-DRAM_TRAFFIC = {"blend": 23_762_688}
+# DRAM bytes (read + write) of one launch of the kernel at a tile shape, from
+# one ncu capture of a sweep frame (dram__bytes_read.sum + dram__bytes_write.sum);
+# a kernel or shape without a capture of its current code reports None.
+DRAM_TRAFFIC = {"blend@16x32": 18_494_464}
 
 # the workload both arms report (the reference arm times the oracle on a
 # bounded sample of it: frame 37, random pixels)
@@ -195,6 +217,8 @@ def run_ours(args, rank, world, local):
     if args.train_only:
         return {"train": train_bench(args, r4g.Renderer(), params, dev, stream, flush)}
     if args.backward_only:
+        if args.tile:
+            rend.set_tile(tuple(int(x) for x in args.tile.lower().split("x")))
         cam, t = frame_camera(37)
         grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
         gimg = torch.randn((3, HEIGHT, WIDTH), device=dev, generator=torch.Generator(device=dev).manual_seed(3)) * 1e-6
@@ -202,7 +226,7 @@ def run_ours(args, rank, world, local):
             res = rend.render(params, cam, t)
             rend.backward(params, cam, t, res, gimg, grads)
         torch.cuda.synchronize()
-        return {"backward_only": "frame 37, 4 x (render + backward)"}
+        return {"backward_only": f"frame 37, 4 x (render + backward), {rend.tile[0]}x{rend.tile[1]} tiles"}
     if args.batch_only:
         return {"batched": batch_bench(args, dev, stream, flush), "large": large_bench(args, dev, stream, flush)}
 
@@ -217,7 +241,11 @@ def run_ours(args, rank, world, local):
     rend16 = rend
     rend = r4g.Renderer()
     cam0, t0 = frame_camera(frames[0])
-    tune = rend.autotune(params, [(cam0, t0)], backward=False, reps=3)
+    if args.tile:
+        rend.set_tile(tuple(int(x) for x in args.tile.lower().split("x")))
+        tune = {"ms": None, "tile": list(rend.tile)}
+    else:
+        tune = rend.autotune(params, [(cam0, t0)], backward=False, reps=3)
     # size the key buffer once over the whole sweep (not timed): 10 % above the
     # largest (tile, Gaussian) pair count of any frame
     need_max = 0
@@ -242,6 +270,7 @@ def run_ours(args, rank, world, local):
     for k in frames[:min(len(frames), 8)]:
         render_frame(k)
     torch.cuda.synchronize()
+    clocks.wait_ready()
     abi.r4g_stage_times(rend.ctx, reset=True)
     # the timed frames run without per-stage events (an event between two
     # kernels ends their programmatic launch overlap); the stage times come
@@ -249,7 +278,14 @@ def run_ours(args, rank, world, local):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
     barrier()
     torch.cuda.synchronize()
+    since = clocks.mark()
     wall0 = time.perf_counter()
+    # two untimed renders queued right before the first timed frame: coming
+    # out of the idle gap above, the device ran the first frame 20-100 %
+    # slower (0.33-0.55 ms against 0.28 ms for the same frame queued behind
+    # other work); L2 flushes alone did not bring it back
+    for k in frames[-2:]:
+        render_frame(k)
     for i, k in enumerate(frames):
         flush.zero_()  # evict L2 between frames (outside the timed events)
         evs[i][0].record(stream)
@@ -258,7 +294,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - wall0
-    clk = clocks.stop()
+    clk = clocks.stop(since)
     _, stage_launch = abi.r4g_stage_times(rend.ctx, reset=True)
     # per-stage device times: the same frames again, stage events on
     abi.r4g_set_timing(rend.ctx, True)
@@ -308,7 +344,7 @@ def run_ours(args, rank, world, local):
                 "frac": round(ach / hbm_peak, 4)}
 
     roofline = dict(stage_roof(top))
-    roofline.update({"kernel": top, "traffic": DRAM_TRAFFIC.get(top),
+    roofline.update({"kernel": top, "traffic": DRAM_TRAFFIC.get(f"{top}@{rend.tile[0]}x{rend.tile[1]}"),
                      "peak_source": (f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of "
                                      f"MEASURED_PEAKS.json)") if top == "blend" else f"{src} hbm_gbs",
                      "work_per_frame": {"composited_pairs": round(work["pairs"]), "keys": round(keys),
@@ -328,7 +364,8 @@ def run_ours(args, rank, world, local):
                                                         f"per rank (k = 7 i mod {FRAMES})"),
            "gpu_launches": int(sum(stage_launch.values())),
            "wall_s": round(wall, 3), "clocks": clk, "roofline": roofline}
-    out["config"]["tile"] = f"{rend.tile[0]}x{rend.tile[1]} (from the autotuner; plain path 16x16)"
+    out["config"]["tile"] = (f"{rend.tile[0]}x{rend.tile[1]} "
+                             f"({'--tile' if args.tile else 'from the autotuner'}; plain path 16x16)")
     out["autotune_ms"] = tune["ms"]
     out["plain_path"], cap16 = plain_sweep_bench(rend16, params, dev, stream, flush, frames)
 
@@ -508,7 +545,8 @@ def train_bench(args, rend, params, dev, stream, flush):
         ach = pairs * BWD_FP32_OPS_PER_PAIR / (per_stage["blend_bwd"] / 1e3) / 1e12
         roof["blend_bwd"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
                              "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4),
-                             "fp32_ops_per_pair": BWD_FP32_OPS_PER_PAIR, "traffic": DRAM_TRAFFIC.get("blend_bwd")}
+                             "fp32_ops_per_pair": BWD_FP32_OPS_PER_PAIR,
+                             "traffic": DRAM_TRAFFIC.get(f"blend_bwd@{rb.tile[0]}x{rb.tile[1]}")}
     if "blend" in per_stage:
         ach = pairs * FP32_OPS_PER_PAIR / (per_stage["blend"] / 1e3) / 1e12
         roof["blend"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
@@ -546,12 +584,16 @@ def preprocess_bwd_bytes(n_gauss: float, n_items: float, keys: float, reached: f
     return (68.0 + 192.0 + 520.0) * n_gauss + 192.0 * n_items + 1.0 * keys + 48.0 * reached
 
 
-def _timed_all(fn, steps: int, stream, flush=None) -> dict:
+def _timed_all(fn, steps: int, stream, flush=None, warm: int = 2) -> dict:
     """Mean and median ms of fn() over `steps` calls (CUDA events on `stream`
-    around each call; the L2 flush, when given, between calls outside them)."""
+    around each call; the L2 flush, when given, between calls outside them).
+    `warm` untimed calls are queued right before the first timed one: a device
+    coming out of the idle gap of the synchronize runs its first call slower."""
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
+    for _ in range(warm):
+        fn()
     for a, b in evs:
         if flush is not None:
             flush.zero_()
