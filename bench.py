@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--train-steps", type=int, default=10)
+    ap.add_argument("--train-steps", type=int, default=50, help="timed training steps (after 5 warm-up)")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -466,7 +466,7 @@ def train_bench(args, rend, params, dev, stream, flush):
     from paper_2402_03307_gb300 import abi
 
     nsteps = args.train_steps
-    warm = 3
+    warm = 5
     step_views = [train_views_for_step(k) for k in range(warm + nsteps)]
     target = _packed_target(step_views[0], 34, dev)
     npix = target.numel()
@@ -576,7 +576,8 @@ def train_bench(args, rend, params, dev, stream, flush):
                                   "frac": round(ach / hbm_peak, 4), "bytes": round(b)}
     top = max(("blend_bwd", "blend", "preprocess_bwd"), key=lambda k: per_stage.get(k, 0.0))
     return {"value": round(1000.0 / ms_a["mean"], 3), "unit": "it/s", "ms_per_it": round(ms_a["mean"], 3),
-            "ms_per_it_median": round(ms_a["median"], 3), "views": TRAIN_VIEWS, "steps": nsteps,
+            "ms_per_it_median": round(ms_a["median"], 3), "it_per_s_at_median": round(1000.0 / ms_a["median"], 3),
+            "views": TRAIN_VIEWS, "steps": nsteps,
             "tile": f"{rb.tile[0]}x{rb.tile[1]}", "autotune_ms": tune["ms"],
             "views_per_step": "fresh seeded (t ~ U[0,1], angle ~ U[0, 2 pi)) each step",
             "path": "autograd.Function over the batched render (one call for the 4 views, tile shape from the "

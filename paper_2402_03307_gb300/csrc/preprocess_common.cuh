@@ -61,10 +61,10 @@ __device__ __forceinline__ void gauss_setup(const r4g_gaussians& g, int i, Geo<S
   load_params<kScaleBF16>(g, i, G.p);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float s = expf(G.p.ls[k]);
+    const float s = __expf(G.p.ls[k]);  // the hardware exponential: ~1e-7 relative
     G.sc2[k] = static_cast<S>(s) * static_cast<S>(s);
   }
-  G.opacity = 1.0f / (1.0f + expf(-G.p.logit));
+  G.opacity = __fdividef(1.0f, 1.0f + __expf(-G.p.logit));  // 0 once exp(-logit) overflows
   rotor_normalize<S>(G.p.rot, G.rn);
   rotor_matrix<S>(G.rn.r, G.R);
   cov4<S>(G.R, G.sc2, G.C);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void forward_color(const r4g_gaussians& g, int i, con
     float acc = 0.5f;
 #pragma unroll
     for (int k = 0; k < 16; ++k)
-      if (k < nb) acc += Y[k] * c[k][ch];
+      if (k < nb) acc = fma_s(Y[k], c[k][ch], acc);
     f.rgb_pos[ch] = acc > 0.0f;
     f.rgb[ch] = fmaxf(acc, 0.0f);
   }
@@ -224,7 +224,7 @@ __device__ __forceinline__ void image_velocity(const Sig4<S>& Q, S invW, const C
 // applies the exact tests, so the image does not depend on the tile shape.
 __device__ __forceinline__ bool pixel_box(const Fwd& f, const CamDev& cam, int& i0, int& i1,
                                           int& j0, int& j1) {
-  const float k2 = 1.01f * fminf(9.0f, 2.0f * logf(255.0f * f.o_t));
+  const float k2 = 1.01f * fminf(9.0f, 2.0f * __logf(255.0f * f.o_t));
   const float hx = sqrtf(k2 * f.cov[0]) + 0.5f;
   const float hy = sqrtf(k2 * f.cov[2]) + 0.5f;
   const float lim = 1e7f;

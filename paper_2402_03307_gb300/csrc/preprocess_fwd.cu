@@ -98,7 +98,7 @@ struct OneView {
 };
 
 template <typename S, bool kScaleBF16, bool kShBF16, bool kMulti>
-__global__ void __launch_bounds__(kPreFwdBlock)
+__global__ void __launch_bounds__(kPreFwdBlock, kMulti ? 4 : 7)
     preprocess_fwd_kernel(r4g_gaussians g, ViewDev* __restrict__ views, int nviews, OneView one, PreOut out,
                           int sh_degree, bool temporal_cull, bool flow) {
   // the next kernel of the render (the depth sort's) may launch now and wait
@@ -157,10 +157,10 @@ __global__ void __launch_bounds__(kPreFwdBlock)
         y0 = j0 / out.tile_h;
         y1 = j1 / out.tile_h + 1;
         // with the opacity's logarithms the blends' staging needs
-        const float l255 = log2f(255.0f * f.o_t);
+        const float l255 = __log2f(255.0f * f.o_t);
         out.recA[item] = make_float4(f.mean2d[0], f.mean2d[1], f.conic[0], f.conic[1]);
         out.recA[M + item] = make_float4(f.conic[2], f.o_t, f.pc[2], l255);
-        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], fmaxf(log2f(f.o_t), -126.0f));
+        out.recA[2 * M + item] = make_float4(f.rgb[0], f.rgb[1], f.rgb[2], fmaxf(__log2f(f.o_t), -126.0f));
         out.rect[item] = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                     static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
         if (span_mode(x0, x1, y0, y1))

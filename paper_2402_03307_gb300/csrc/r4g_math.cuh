@@ -152,41 +152,68 @@ __device__ __forceinline__ void rotor_normalize(const float in[8], RotorNorm<S>&
   }
 }
 
-// R (row-major 4x4) from a normalised rotor, the closed forms of appendix A.2.
+// a b + c rounded once, in the slice precision, whatever the translation
+// unit's contraction flags: the forward preprocess (compiled without
+// contraction, so that one-view and multi-view renders agree bit for bit) and
+// the backward's recomputation take the same fused steps.
+__device__ __forceinline__ float fma_s(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_s(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// a0 b0 + a1 b1 + a2 b2 + a3 b3 as one product and three fused steps.
+template <typename S>
+__device__ __forceinline__ S dot4(S a0, S b0, S a1, S b1, S a2, S b2, S a3, S b3) {
+  return fma_s(a3, b3, fma_s(a2, b2, fma_s(a1, b1, a0 * b0)));
+}
+
+// R (row-major 4x4) from a normalised rotor, the closed forms of appendix A.2
+// (each diagonal entry a signed sum of the eight squares, each off-diagonal
+// entry twice a signed sum of four products).
 template <typename S>
 __device__ __forceinline__ void rotor_matrix(const S r[8], S R[16]) {
   const S s = r[0], b01 = r[1], b02 = r[2], b12 = r[3], b03 = r[4], b13 = r[5], b23 = r[6], p = r[7];
-  const S s2 = s * s, p2 = p * p, a01 = b01 * b01, a02 = b02 * b02, a12 = b12 * b12,
-          a03 = b03 * b03, a13 = b13 * b13, a23 = b23 * b23;
-  R[0] = -a01 - a02 - a03 + a12 + a13 + a23 - p2 + s2;
-  R[1] = S(2) * (b01 * s - b02 * b12 - b03 * b13 + b23 * p);
-  R[2] = S(2) * (b01 * b12 + b02 * s - b03 * b23 - b13 * p);
-  R[3] = S(2) * (b01 * b13 + b02 * b23 + b03 * s + b12 * p);
-  R[4] = S(2) * (-b01 * s - b02 * b12 - b03 * b13 - b23 * p);
-  R[5] = -a01 + a02 + a03 - a12 - a13 + a23 - p2 + s2;
-  R[6] = S(2) * (-b01 * b02 + b03 * p + b12 * s - b13 * b23);
-  R[7] = S(2) * (-b01 * b03 - b02 * p + b12 * b23 + b13 * s);
-  R[8] = S(2) * (b01 * b12 - b02 * s - b03 * b23 + b13 * p);
-  R[9] = S(2) * (-b01 * b02 - b03 * p - b12 * s - b13 * b23);
-  R[10] = a01 - a02 + a03 - a12 + a13 - a23 - p2 + s2;
-  R[11] = S(2) * (b01 * p - b02 * b03 - b12 * b13 + b23 * s);
-  R[12] = S(2) * (b01 * b13 + b02 * b23 - b03 * s - b12 * p);
-  R[13] = S(2) * (-b01 * b03 + b02 * p + b12 * b23 - b13 * s);
-  R[14] = S(2) * (-b01 * p - b02 * b03 - b12 * b13 - b23 * s);
-  R[15] = a01 + a02 - a03 + a12 - a13 - a23 - p2 + s2;
+  // sum of s^2 - p^2 and the squares of the bivector parts with the given signs
+  auto diag = [&](S e01, S e02, S e03, S e12, S e13, S e23) {
+    S x = fma_s(-p, p, s * s);
+    x = fma_s(e01 * b01, b01, x);
+    x = fma_s(e02 * b02, b02, x);
+    x = fma_s(e03 * b03, b03, x);
+    x = fma_s(e12 * b12, b12, x);
+    x = fma_s(e13 * b13, b13, x);
+    return fma_s(e23 * b23, b23, x);
+  };
+  const S one = S(1);
+  R[0] = diag(-one, -one, -one, one, one, one);
+  R[5] = diag(-one, one, one, -one, -one, one);
+  R[10] = diag(one, -one, one, -one, one, -one);
+  R[15] = diag(one, one, -one, one, -one, -one);
+  R[1] = S(2) * dot4(b01, s, -b02, b12, -b03, b13, b23, p);
+  R[2] = S(2) * dot4(b01, b12, b02, s, -b03, b23, -b13, p);
+  R[3] = S(2) * dot4(b01, b13, b02, b23, b03, s, b12, p);
+  R[4] = S(2) * dot4(-b01, s, -b02, b12, -b03, b13, -b23, p);
+  R[6] = S(2) * dot4(-b01, b02, b03, p, b12, s, -b13, b23);
+  R[7] = S(2) * dot4(-b01, b03, -b02, p, b12, b23, b13, s);
+  R[8] = S(2) * dot4(b01, b12, -b02, s, -b03, b23, b13, p);
+  R[9] = S(2) * dot4(-b01, b02, -b03, p, -b12, s, -b13, b23);
+  R[11] = S(2) * dot4(b01, p, -b02, b03, -b12, b13, b23, s);
+  R[12] = S(2) * dot4(b01, b13, b02, b23, -b03, s, -b12, p);
+  R[13] = S(2) * dot4(-b01, b03, b02, p, b12, b23, -b13, s);
+  R[14] = S(2) * dot4(-b01, p, -b02, b03, -b12, b13, -b23, s);
 }
 
 // Sigma4 = R diag(s^2) R^T; returned as its 10 unique entries
 // (00, 01, 02, 03, 11, 12, 13, 22, 23, 33).
 template <typename S>
 __device__ __forceinline__ void cov4(const S R[16], const S sc2[4], S C[10]) {
+  S Rs[16];  // R diag(s^2)
+#pragma unroll
+  for (int i = 0; i < 16; ++i) Rs[i] = R[i] * sc2[i & 3];
   int k = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
 #pragma unroll
     for (int j = i; j < 4; ++j) {
-      C[k++] = R[4 * i + 0] * sc2[0] * R[4 * j + 0] + R[4 * i + 1] * sc2[1] * R[4 * j + 1] +
-               R[4 * i + 2] * sc2[2] * R[4 * j + 2] + R[4 * i + 3] * sc2[3] * R[4 * j + 3];
+      C[k++] = dot4(Rs[4 * i + 0], R[4 * j + 0], Rs[4 * i + 1], R[4 * j + 1], Rs[4 * i + 2], R[4 * j + 2],
+                    Rs[4 * i + 3], R[4 * j + 3]);
     }
   }
 }
