@@ -311,7 +311,7 @@ __device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StageSet<N>& sg,
 
 template <int TW, int TH>
 constexpr int fwd_min_blocks() {
-  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 12 : Blend<TW, TH>::NT <= 128 ? 6 : 3;
+  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 12 : Blend<TW, TH>::NT <= 128 ? 7 : 3;
 }
 
 // Where a global tile id lies: its view (binary search over the views'
