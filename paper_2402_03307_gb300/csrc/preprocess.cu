@@ -203,30 +203,97 @@ __device__ __forceinline__ void view_backward(const r4g_gaussians& g, int i, con
 }
 
 // Sum of an item's per-pair gradients (pairs [o, o + cnt) of the gradient
-// buffer) for each lane's item: the warp takes its lanes' items four at a
-// time (their loads in flight together), lane l adding pairs l, l + 32, ...
-// of each (coalesced), then a butterfly sum per item; a single pair is read
-// by its owner. Only pairs whose reach flag is set hold a gradient (a pixel of
-// their tile composited them); the others count as zero and are not read.
-// gc.w counts the tiles in which a pixel composited the item (summed only
-// with kStats). Returns whether any pair of the lane's item holds a gradient
-// (if none, the item's gradient is zero). The sums are in a fixed order.
+// buffer) for each lane's item. Only pairs whose reach flag is set hold a
+// gradient (a pixel of their tile composited them); the others count as zero
+// and are not read. Items of 2 .. kGroupPairs pairs (nearly all of them) are
+// taken by groups of kGroupLanes lanes, 32 / kGroupLanes items per round: each
+// lane reads up to kGroupPairs / kGroupLanes of its item's pairs (all loads
+// issued together), the group sums them by a butterfly, and each item's owner
+// takes its group's sums with one shuffle per value. Larger items are taken by
+// the whole warp, U at a time (lane l adding pairs l, l + 32, ..., then a
+// butterfly over the warp); a single pair is read by its owner. gc.w counts the
+// tiles in which a pixel composited the item (summed only with kStats).
+// Returns whether any pair of the lane's item holds a gradient (if none, the
+// item's gradient is zero). The sums are in a fixed order.
+constexpr int kGroupLanes = 8;
+constexpr uint32_t kGroupPairs = 32;
+
 template <bool kStats, int U>
 __device__ __forceinline__ bool gather_pairs(uint32_t cnt, uint32_t o, int lane, const float4* __restrict__ gbuf,
                                              const uint8_t* __restrict__ reach, float4& ga, float4& gb,
                                              float4& gc) {
-  // U: items in flight per round
+  constexpr int G = kGroupLanes, NG = 32 / G, PPL = kGroupPairs / G;  // pairs per lane
+  constexpr int NV = kStats ? 10 : 9;
   ga = make_float4(0.f, 0.f, 0.f, 0.f);
   gb = ga;
   gc = ga;
   bool got = false;
+  // ---- items of 2 .. kGroupPairs pairs: a group of G lanes each
+  const bool grouped = cnt >= 2u && cnt <= kGroupPairs;
+  const uint32_t gmask = __ballot_sync(0xffffffffu, grouped);
+  const int grp = lane / G, gl = lane % G;
+  for (int r0 = 0; r0 < 32 && (gmask >> r0); r0 += NG) {
+    if (((gmask >> r0) & ((1u << NG) - 1u)) == 0u) continue;  // warp-uniform
+    const uint32_t qc = __shfl_sync(0xffffffffu, grouped ? cnt : 0u, r0 + grp);
+    const uint32_t qo = __shfl_sync(0xffffffffu, o, r0 + grp);
+    bool f[PPL];
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+      const uint32_t k = static_cast<uint32_t>(gl + i * G);
+      f[i] = k < qc && reach[qo + k];
+    }
+    float v[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = 0.f;
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) {
+      if (!f[i]) continue;
+      const float4* pr = gbuf + 3 * static_cast<size_t>(qo + static_cast<uint32_t>(gl + i * G));
+      const float4 x = pr[0], y = pr[1], z = pr[2];
+      v[0] += x.x; v[1] += x.y; v[2] += x.z; v[3] += x.w;
+      v[4] += y.x; v[5] += y.y;
+      v[6] += z.x; v[7] += z.y; v[8] += z.z; v[9] += z.w;
+    }
+    bool found = false;
+#pragma unroll
+    for (int i = 0; i < PPL; ++i) found = found || f[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+      for (int sh = G / 2; sh > 0; sh >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], sh);
+    }
+    const uint32_t fb = __ballot_sync(0xffffffffu, found);
+    // the owner of item r0 + g takes group g's sums (held by its first lane)
+    const int src = ((lane - r0) & (NG - 1)) * G;
+    float w[10];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = __shfl_sync(0xffffffffu, v[k], src);
+    const bool any = ((fb >> src) & ((1u << G) - 1u)) != 0u;
+    if (grouped && lane >= r0 && lane < r0 + NG && any) {
+      got = true;
+      ga = make_float4(w[0], w[1], w[2], w[3]);
+      gb = make_float4(w[4], w[5], 0.f, 0.f);
+      gc = make_float4(w[6], w[7], w[8], kStats ? w[9] : 0.f);
+    }
+  }
+  // ---- larger items: the whole warp each, U at a time
+  const uint32_t big = cnt > kGroupPairs ? cnt : 0u;
+  if (__ballot_sync(0xffffffffu, big != 0u) == 0u) {
+    if (cnt == 1 && reach[o]) {
+      const float4* pr = gbuf + 3 * static_cast<size_t>(o);
+      ga = pr[0];
+      gb = pr[1];
+      gc = pr[2];
+      got = true;
+    }
+    return got;
+  }
   for (int q0 = 0; q0 < 32; q0 += U) {
     uint32_t qc[U], qo[U], kmax = 0;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      qc[u] = __shfl_sync(0xffffffffu, cnt, q0 + u);
+      qc[u] = __shfl_sync(0xffffffffu, big, q0 + u);  // only the larger items (the others are done)
       qo[u] = __shfl_sync(0xffffffffu, o, q0 + u);
-      if (qc[u] < 2) qc[u] = 0;  // a single pair is read by its owner below
       kmax = max(kmax, qc[u]);
     }
     if (kmax == 0) continue;  // warp-uniform
