@@ -169,7 +169,7 @@ FP32_OPS_PER_PAIR = 19
 # DRAM bytes (read + write) of one launch of the kernel at a tile shape, from
 # one ncu capture of a sweep frame (dram__bytes_read.sum + dram__bytes_write.sum);
 # a kernel or shape without a capture of its current code reports None.
-DRAM_TRAFFIC = {"blend@16x32": 18_583_552}
+DRAM_TRAFFIC = {"blend@16x32": 18_583_552, "blend@16x16": 21_566_464}
 
 # the workload both arms report (the reference arm times the oracle on a
 # bounded sample of it: frame 37, random pixels)
