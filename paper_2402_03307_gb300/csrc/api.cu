@@ -388,9 +388,10 @@ r4g_status backward_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* v
       return cuda_fail(ctx, e, "blend backward");
   }
   {
-    // a multi-view FP32 call lists its items, then runs the item and Gaussian passes
+    // a multi-view FP32 call lists its items, gathers their pair gradients, then
+    // runs the item and Gaussian passes
     const bool two_pass = L.nviews > 1 && !(ctx->cfg.flags & R4G_FLAG_FP64_SLICE);
-    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, two_pass ? 3 : 1);
+    StageScope sc(ctx, R4G_STAGE_PREPROCESS_BWD, s, two_pass ? 4 : 1);
     if ((e = launch_preprocess_bwd(*g, L, frame, ctx->cfg.sh_degree, ctx->cfg.flags, *grads, s)) != cudaSuccess)
       return cuda_fail(ctx, e, "preprocess backward");
   }
