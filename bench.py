@@ -997,20 +997,33 @@ def densify_bench(params, dev, stream, flush):
 
 def e2e_bench(args, rend, g, dev, stream, frames, cap):
     """Frames/s through the public API with host buffers: every step copies
-    its inputs (all Gaussian parameters, 78 MB) from pinned host memory and
-    reads its image back (16 MB). The steps are pipelined over two buffer
+    its inputs (all Gaussian parameters, 78 MB, held in one pinned buffer) from
+    host memory and reads its image back (16 MB). The steps are pipelined over two buffer
     sets on three streams -- upload of step k + 1, render of step k, read-back
     of step k - 1 -- so the job's throughput is bounded by the slowest of the
     three, as in a serving loop; every copy of every step is inside the timed
     region."""
     import torch
 
-    host = {k: torch.as_tensor(v).pin_memory() for k, v in g.items()}
-    dparams = [{k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in host.items()} for _ in range(2)]
+    # the parameters in one pinned host buffer (each array 64-byte aligned),
+    # uploaded by one copy per step into one device buffer whose views are the
+    # parameter tensors the renderer takes (five copies measured 2.6 % slower)
+    arrays = {k: torch.as_tensor(v) for k, v in g.items()}
+    offs, total = {}, 0
+    for k, v in arrays.items():
+        offs[k] = total
+        total += (v.numel() * v.element_size() + 63) // 64 * 64
+    hbuf = torch.empty(total, dtype=torch.uint8).pin_memory()
+    for k, v in arrays.items():
+        n = v.numel() * v.element_size()
+        hbuf[offs[k]:offs[k] + n].view(v.dtype).view(v.shape).copy_(v)
+    dbuf = [torch.empty(total, dtype=torch.uint8, device=dev) for _ in range(2)]
+    dparams = [{k: d[offs[k]:offs[k] + v.numel() * v.element_size()].view(v.dtype).view(v.shape)
+                for k, v in arrays.items()} for d in dbuf]
     fr = [rend.new_frame(N_GAUSS, WIDTH, HEIGHT, cap, dev) for _ in range(2)]
     img = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32, device=dev) for _ in range(2)]
     himg = [torch.empty((3, HEIGHT, WIDTH), dtype=torch.float32).pin_memory() for _ in range(2)]
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = total
     d2h = himg[0].numel() * 4
     s_up, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev_up = [torch.cuda.Event() for _ in range(2)]
@@ -1023,8 +1036,7 @@ def e2e_bench(args, rend, g, dev, stream, frames, cap):
         b = i % 2
         with torch.cuda.stream(s_up):
             s_up.wait_event(ev_ren[b])  # the render that read this buffer set is done
-            for name, v in host.items():
-                dparams[b][name].copy_(v, non_blocking=True)
+            dbuf[b].copy_(hbuf, non_blocking=True)
             ev_up[b].record(s_up)
         stream.wait_event(ev_up[b])
         stream.wait_event(ev_out[b])  # the read-back of this image buffer is done
