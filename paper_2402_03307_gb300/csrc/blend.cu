@@ -311,7 +311,7 @@ __device__ __forceinline__ bool fwd_group(FwdState<Q>& S, const StageSet<N>& sg,
 
 template <int TW, int TH>
 constexpr int fwd_min_blocks() {
-  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 12 : Blend<TW, TH>::NT <= 128 ? 7 : 3;
+  return Blend<TW, TH>::NT <= 32 ? 16 : Blend<TW, TH>::NT <= 64 ? 14 : Blend<TW, TH>::NT <= 128 ? 7 : 3;
 }
 
 // Where a global tile id lies: its view (binary search over the views'
@@ -501,7 +501,8 @@ __device__ __forceinline__ bool bwd_entry(BwdState<Q>& S, const StagedG& gs, uin
     float2 al = ar;
     if constexpr (kClamp) al = make_float2(fminf(ar.x, kAlphaMax), fminf(ar.y, kAlphaMax));
     const float2 om = __ffma2_rn(al, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - alpha >= 0.01
-    const float2 iom = make_float2(a0 ? rcp_approx(om.x) : 1.0f, a1 ? rcp_approx(om.y) : 1.0f);
+    // a pixel that does not take the entry has alpha = 0, 1 - alpha = 1 and a reciprocal of exactly 1
+    const float2 iom = make_float2(rcp_approx(om.x), rcp_approx(om.y));
     const float2 Ti = __fmul2_rn(S.T[q], iom);
     const float2 w = __fmul2_rn(al, Ti);
     const float2 gc = __ffma2_rn(S.gb[q], make_float2(p4.x, p4.y),
