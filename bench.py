@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--train-only", action="store_true", help="training steps only (profiling)")
     ap.add_argument("--backward-only", action="store_true",
                     help="render + backward of sweep frame 37, four times (profiling the backward)")
+    ap.add_argument("--backward-views", type=int, default=1, metavar="V",
+                    help="with --backward-only and V > 1: one batched render + backward of the first training "
+                         "step's V views instead, four times (profiling the training step's backward launch)")
     return ap.parse_args()
 
 
@@ -167,9 +170,11 @@ SMS, FP32_LANES = 152, 128
 FP32_OPS_PER_PAIR = 19
 
 # DRAM bytes (read + write) of one launch of the kernel at a tile shape, from
-# one ncu capture of a sweep frame (dram__bytes_read.sum + dram__bytes_write.sum);
-# a kernel or shape without a capture of its current code reports None.
-DRAM_TRAFFIC = {"blend@16x32": 18_583_552, "blend@16x16": 21_566_464}
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum): the blend on a
+# sweep frame, the blend backward on the training step's 4-view launch (the views
+# of step 0, `--backward-only --backward-views 4`); a kernel or shape without a
+# capture of its current code reports None.
+DRAM_TRAFFIC = {"blend@16x32": 18_583_552, "blend@16x16": 21_566_464, "blend_bwd@16x32": 340_284_672}
 
 # the workload both arms report (the reference arm times the oracle on a
 # bounded sample of it: frame 37, random pixels)
@@ -219,6 +224,16 @@ def run_ours(args, rank, world, local):
     if args.backward_only:
         if args.tile:
             rend.set_tile(tuple(int(x) for x in args.tile.lower().split("x")))
+        if args.backward_views > 1:
+            views = train_views_for_step(0)[:args.backward_views]
+            grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
+            target = _packed_target(views, 34, dev)
+            for _ in range(4):
+                res = rend.render_batch(params, views)
+                rend.backward_batch(params, res, torch.sign(res.packed - target) / target.numel(), grads)
+            torch.cuda.synchronize()
+            return {"backward_only": f"training step 0's {len(views)} views, 4 x (batched render + backward), "
+                                     f"{rend.tile[0]}x{rend.tile[1]} tiles"}
         cam, t = frame_camera(37)
         grads = {k: torch.zeros(v.shape, dtype=torch.float32, device=dev) for k, v in params.items()}
         gimg = torch.randn((3, HEIGHT, WIDTH), device=dev, generator=torch.Generator(device=dev).manual_seed(3)) * 1e-6
