@@ -117,6 +117,30 @@ def test_image_does_not_depend_on_tile_shape(r4g):
     assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
 
 
+def test_tile_shape_full_size_bit_identical(r4g):
+    """Every pixel computes the same numbers whatever the tile shape (the
+    per-warp culls and the tiles' lists only decide which entries a pixel
+    skips without effect), so on the 300k-Gaussian 1352x1014 frame the 16x32
+    render's image and final transmittance equal the 16x16 render's bit for
+    bit."""
+    from paper_2402_03307_gb300 import abi
+    g = to_device(synth.fwd300k_scene())
+    cam, t = synth.orbit_camera(37, 300, 8.0, 1352, 1014)
+    s = torch.cuda.current_stream().cuda_stream
+    out = []
+    for tile in ((16, 32), (16, 16)):
+        rend = r4g.Renderer(tile=tile)
+        res = rend.render(g, cam, t)
+        T = torch.empty((cam.height, cam.width), device="cuda")
+        abi.r4g_render(rend.ctx, r4g.gaussians_struct(g), r4g.camera_struct(cam), t, res.image.data_ptr(),
+                       T.data_ptr(), None, res.frame.data_ptr(), res.frame.numel(), res.key_capacity, s)
+        torch.cuda.synchronize()
+        assert rend.status(res)[0] == abi.R4G_OK
+        out.append((res.image.clone(), T))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("size", [(37, 29), (1, 1), (200, 17), (64, 64)])
 def test_ragged_image_sizes(r4g, size):
     w, h = size
