@@ -205,7 +205,7 @@ FrameLayout make_layout(int64_t n, const int* widths, const int* heights, int nv
   L.sortcnt = o;  o = align_up(o + sizeof(uint32_t) * kSortRadix * cnt_ctas);
   // the two sorts' scratch apart: the tile sort's is cleared and filled with
   // its histograms on a side stream while the depth sort runs
-  L.tsort = o;    o = align_up(o + onesweep_scratch_bytes(cap, tb));
+  L.tsort = o;    o = align_up(o + onesweep_scratch_bytes(cap + kChainSlack, tb));
   // multi-view backward: the visible items and their partial gradients (96 B each)
   const int64_t mi = nviews > 1 ? m : 0;
   L.ilist = o;    o = align_up(o + sizeof(uint32_t) * mi);
@@ -308,7 +308,8 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
     uint32_t* hist = at<uint32_t>(frame, L.tsort);
     e = tpasses > 0 ? cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kSortRadix * tpasses, ctx->side) : cudaSuccess;
     if (e == cudaSuccess) e = launch_tile_counts(L, frame, hist, tpasses, ctx->side);
-    if (e == cudaSuccess && has && tpasses > 0) e = prepare_onesweep(hist, L.cap, L.tile_bits, true, ctx->side);
+    if (e == cudaSuccess && has && tpasses > 0)
+      e = prepare_onesweep(hist, L.cap + kChainSlack, L.tile_bits, true, ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->join, ctx->side);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tile counts");
   }
@@ -342,7 +343,10 @@ r4g_status render_impl(r4g_ctx* ctx, const r4g_gaussians* g, const r4g_view* vie
     e = launch_emit_sort(L, frame, at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1),
                          static_cast<const uint32_t*>(ts), onesweep_status(ts, L.tile_bits),
                          onesweep_tickets(ts, L.tile_bits), s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && tpasses == 2)  // the second pass, its look-back chained within low-digit groups
+      e = launch_tile_chain_pass(L, frame, at<uint32_t>(frame, L.keys1), at<uint32_t>(frame, L.vals1),
+                                 at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0), ts, s);
+    else if (e == cudaSuccess)
       e = launch_onesweep(at<uint32_t>(frame, L.keys0), nullptr, at<uint32_t>(frame, L.keys1),
                           at<uint32_t>(frame, L.vals1), at<uint32_t>(frame, L.keys0), at<uint32_t>(frame, L.vals0),
                           count, 0, L.cap, L.tile_bits, ts, err, s, &which, true, true, 0xffffffffu, 0u, 1);

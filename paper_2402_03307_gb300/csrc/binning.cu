@@ -441,13 +441,7 @@ cudaError_t launch_emit_sort(const FrameLayout& L, void* frame, uint32_t* kout, 
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// Per-tile pair counts from the per-row difference arrays the preprocess
-// filled (+1 at the first tile of a Gaussian's interval in a tile row, -1
-// after its last: prefix sums along x, in shared memory with warp scans), their
-// exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
-// list, and the digit histograms of the tile sort's radix passes. One CTA per
-// view; the difference array is copied into dynamic shared memory. Needs only
-// what the preprocess wrote.
+// Inclusive scan over the lanes of a warp.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -457,6 +451,110 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
   return x;
 }
 
+// The tile sort's second pass (tile ids of 9 to 16 bits), chunk by chunk in
+// group order. The first pass (run by the emission) leaves the list grouped
+// by the low 8 bits g of the tile id, each group in emission (depth) order;
+// group g holds the pairs of the tiles g + 256 h. The chunks of 2048 pairs
+// are numbered group after group and each is ranked and scattered by h as in a
+// onesweep pass, but its look-back stops at the first chunk of its group, and
+// digit h of group g starts at the range of tile g + 256 h, which the tile
+// counts already hold: a chunk waits on the chunks of its own group only (a
+// few) instead of on every chunk before it. The result is the onesweep pass's
+// bit for bit. The group order has at most one partial chunk per group more
+// than the list has chunks (kChainSlack pairs of status room).
+__global__ void __launch_bounds__(kSortThreads, 5)
+    tile_chain_pass_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ hist0,
+                           const uint2* __restrict__ ranges, FrameHeader* hdr, uint32_t* status, uint32_t* ticket,
+                           int hbits, int ntiles) {
+  __shared__ uint32_t s_tile;
+  __shared__ OsShared S;
+  __shared__ uint32_t s_k[kOsTile];
+  __shared__ uint32_t s_v[kOsTile];
+  __shared__ uint32_t s_cpre[kSortRadix + 1];  // first chunk of each group in group order; [256]: all chunks
+  __shared__ uint32_t s_gpre[kSortRadix];      // first pair of each group
+  __shared__ uint32_t s_sc[kOsWarps][2];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int h = threadIdx.x;  // thread h: group h in the scans, digit h in the pass
+  const uint32_t K = hdr->key_count;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  os_clear(S);
+  {  // exclusive scans of the groups' sizes and chunk counts
+    const uint32_t gn = hist0[h];
+    const uint32_t gc = (gn + kOsTile - 1) / kOsTile;
+    const uint32_t xn = warp_incl_scan(gn, lane), xc = warp_incl_scan(gc, lane);
+    if (lane == 31) {
+      s_sc[warp][0] = xn;
+      s_sc[warp][1] = xc;
+    }
+    __syncthreads();
+    uint32_t pn = 0, pc = 0;
+    for (int w = 0; w < warp; ++w) {
+      pn += s_sc[w][0];
+      pc += s_sc[w][1];
+    }
+    s_gpre[h] = pn + xn - gn;
+    s_cpre[h] = pc + xc - gc;
+    if (h == kSortRadix - 1) s_cpre[kSortRadix] = pc + xc;
+  }
+  __syncthreads();
+  const uint32_t t = s_tile;
+  if (t >= s_cpre[kSortRadix]) return;  // grid sized for the capacity; CTA-uniform exit
+  int g = 0;  // the chunk's group: the last g whose first chunk is at or before t
+#pragma unroll
+  for (int step = kSortRadix / 2; step >= 1; step >>= 1)
+    if (g + step < kSortRadix && s_cpre[g + step] <= t) g += step;
+  const uint32_t chain0 = s_cpre[g];
+  const uint32_t gb = s_gpre[g] + (t - chain0) * kOsTile;  // the chunk's first pair
+  const uint32_t ge = min(s_gpre[g] + hist0[g], K);       // after an overflow the group may run past the list
+  const uint32_t tn = gb < ge ? min(static_cast<uint32_t>(kOsTile), ge - gb) : 0u;
+  const uint32_t mask = (1u << hbits) - 1u;
+  uint32_t k[kOsIPT], v[kOsIPT], d[kOsIPT];
+#pragma unroll
+  for (int j = 0; j < kOsIPT; ++j) {
+    const uint32_t li = warp * (32 * kOsIPT) + j * 32 + lane;
+    if (li < tn) {
+      k[j] = kin[gb + li];
+      v[j] = vin[gb + li];
+      d[j] = (k[j] >> kSortRadixBits) & mask;
+    } else {
+      k[j] = 0;
+      v[j] = 0;
+      d[j] = 0xffffffffu;
+    }
+  }
+  // digit h of this group: tile g + 256 h, its range's begin; a tile without pairs needs no status
+  const int tile = g + (h << kSortRadixBits);
+  const bool exists = static_cast<uint32_t>(h) <= mask && tile < ntiles;
+  const uint2 rg = exists ? ranges[tile] : make_uint2(0u, 0u);
+  os_rank_scatter<true>(k, v, d, t, K, 0u, kSortRadixBits, mask, nullptr, status, &hdr->status, 0xffffffffu,
+                        kSpinLimit, S, s_k, s_v, kout, vout, chain0, rg.x, rg.y > rg.x);
+}
+
+cudaError_t launch_tile_chain_pass(const FrameLayout& L, void* frame, const uint32_t* kin, const uint32_t* vin,
+                                   uint32_t* kout, uint32_t* vout, void* tsort, cudaStream_t s) {
+  if (L.n == 0 || L.cap == 0) return cudaSuccess;
+  const int64_t tiles = (L.cap + kOsTile - 1) / kOsTile;
+  const int64_t grid = tiles + kSortRadix;  // at most one partial chunk per group more
+  uint32_t* status = onesweep_status(tsort, L.tile_bits) + static_cast<size_t>(tiles) * kSortRadix;  // pass 1's
+  const cudaError_t e = launch_pdl(tile_chain_pass_kernel, static_cast<unsigned>(grid), kSortThreads, 0, s, kin, vin,
+                                   kout, vout, static_cast<const uint32_t*>(tsort),
+                                   static_cast<const uint2*>(at<uint2>(frame, L.ranges)),
+                                   at<FrameHeader>(frame, L.header), status, onesweep_tickets(tsort, L.tile_bits) + 1,
+                                   L.tile_bits - kSortRadixBits, L.ntiles);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+
+// Per-tile pair counts from the per-row difference arrays the preprocess
+// filled (+1 at the first tile of a Gaussian's interval in a tile row, -1
+// after its last: prefix sums along x, in shared memory with warp scans), their
+// exclusive scan in tile order as the [begin, end) ranges of the tile-sorted
+// list, and the digit histograms of the tile sort's radix passes. One CTA per
+// view; the difference array is copied into dynamic shared memory. Needs only
+// what the preprocess wrote.
 __global__ void __launch_bounds__(1024)
     tile_counts_kernel(const uint32_t* __restrict__ tdiff, const ViewDev* __restrict__ views, uint32_t cap,
                        const FrameHeader* hdr, uint2* __restrict__ ranges, uint32_t* __restrict__ hist,

@@ -53,12 +53,19 @@ __device__ __forceinline__ void os_clear(OsShared& S) {
 // wait of the look-back is bounded by spin_limit rounds without progress,
 // after which err gets bit 2 (withheld_tile: a tile that never publishes, a
 // test of that bound). s_k, s_v: 2048-entry staging arrays.
+// kChain (the tile sort's second pass taken group by group): the look-back
+// stops at tile chain0, the first tile of its chain, which publishes its
+// count as its prefix; digit dd starts at dbase (thread dd's argument)
+// instead of the histogram's exclusive scan, and dlive says whether any tile
+// of the chain can hold it (hist is not read).
+template <bool kChain = false>
 __device__ __forceinline__ void os_rank_scatter(const uint32_t (&k)[kOsIPT], const uint32_t (&v)[kOsIPT],
                                                 const uint32_t (&d)[kOsIPT], uint32_t t, uint32_t n, uint32_t kmin,
                                                 int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                                                 uint32_t* status, uint32_t* err, uint32_t withheld_tile,
                                                 uint32_t spin_limit, OsShared& S, uint32_t* s_k, uint32_t* s_v,
-                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                uint32_t chain0 = 0u, uint32_t dbase = 0u, bool dlive = false) {
   constexpr int NW = kOsWarps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -96,33 +103,34 @@ __device__ __forceinline__ void os_rank_scatter(const uint32_t (&k)[kOsIPT], con
   // ---- publish the tile's count, then look back for its exclusive prefix
   // (a digit no item of the pass has -- the histogram says so -- needs no
   // status and no look-back: its count is zero in every tile)
-  const uint32_t h = hist[dd];
-  const bool live = h != 0u;
+  const uint32_t h = kChain ? 0u : hist[dd];
+  const bool live = kChain ? dlive : h != 0u;
   // withheld_tile (a test of the bounded wait only; otherwise no tile): that
   // tile never publishes, so its successors' waits run out
   const bool publish = t != withheld_tile;
   uint32_t* st = status + static_cast<size_t>(t) * kSortRadix;
-  if (live && publish) store_relaxed(st + dd, (t == 0 ? kFlagPrefix : kFlagAgg) | cnt);
+  if (live && publish) store_relaxed(st + dd, (t == chain0 ? kFlagPrefix : kFlagAgg) | cnt);
   // Look-back, kOsWin predecessors per round (their statuses are read in
   // parallel): add published counts newest first until a published prefix;
   // a round that makes no progress counts against the spin limit.
   uint32_t excl = 0;
-  if (t > 0 && live) {
+  if (t > chain0 && live) {
     constexpr int WIN = kOsWin;
+    const int64_t k0 = static_cast<int64_t>(chain0);
     int64_t kt = static_cast<int64_t>(t) - 1;
     uint32_t idle = 0, nap = 32u;
     bool found = false;
-    while (!found && kt >= 0) {
+    while (!found && kt >= k0) {
       uint32_t sv[WIN];
 #pragma unroll
       for (int w = 0; w < WIN; ++w)
-        sv[w] = (kt - w >= 0) ? load_volatile(status + static_cast<size_t>(kt - w) * kSortRadix + dd) : kFlagPrefix;
+        sv[w] = (kt - w >= k0) ? load_volatile(status + static_cast<size_t>(kt - w) * kSortRadix + dd) : kFlagPrefix;
       int used = 0;
 #pragma unroll
       for (int w = 0; w < WIN; ++w) {
         if (found || used < w) continue;           // stopped earlier in this window
         if ((sv[w] & ~kValMask) == 0u) continue;   // not ready: retry from here
-        if (kt - w >= 0) excl += sv[w] & kValMask;
+        if (kt - w >= k0) excl += sv[w] & kValMask;
         ++used;
         if (sv[w] & kFlagPrefix) found = true;
       }
@@ -150,7 +158,7 @@ __device__ __forceinline__ void os_rank_scatter(const uint32_t (&k)[kOsIPT], con
     __syncthreads();
     uint32_t pre = 0;
     for (int w = 0; w < warp; ++w) pre += S.scan[w];
-    S.dstart[dd] = pre + x - h + excl;
+    S.dstart[dd] = (kChain ? dbase : pre + x - h) + excl;
     __syncthreads();
     // tile-local digit starts: exclusive scan of the tile counts
     x = cnt;

@@ -220,6 +220,12 @@ cudaError_t prepare_onesweep(void* scratch, int64_t cap, int bits, bool hist_rea
 // per-tile counts -> ranges and the tile sort's digit histograms (hist[p][256],
 // zeroed by the caller)
 cudaError_t launch_tile_counts(const FrameLayout& L, void* frame, uint32_t* hist, int passes, cudaStream_t s);
+// The tile sort's second pass taken group by group (tile ids of 9 to 16
+// bits): look-back chains one low-digit group long. Its statuses need
+// kChainSlack pairs' worth of room beyond the key capacity's.
+constexpr int64_t kChainSlack = int64_t(256) * 2048;
+cudaError_t launch_tile_chain_pass(const FrameLayout& L, void* frame, const uint32_t* kin, const uint32_t* vin,
+                                   uint32_t* kout, uint32_t* vout, void* tsort, cudaStream_t s);
 // 64-bit (tile << 32 | depth bits) keys of the sorted list, for export
 cudaError_t launch_export_keys(const FrameLayout& L, void* frame, const uint32_t* tile_keys,
                                const uint32_t* vals, uint64_t* out, cudaStream_t s);
