@@ -71,6 +71,22 @@ def test_batch_full_size_mixed_resolutions(r4g):
         assert torch.equal(rend.render(p, cam, t).image, res.images[k]), k
 
 
+def test_batch_three_tile_sort_passes(r4g):
+    """Four 1352x1014 views at 8x8 tiles: 85,852 tiles, tile ids of 17 bits,
+    so the tile sort takes three radix passes (the emission's, then two
+    onesweep passes) instead of the emission's and the grouped second pass;
+    every view's image equals its single-view 16x16 render bit for bit."""
+    g = synth.gaussians(100_000, 5, mean_lo=-3.0, mean_hi=3.0)
+    p = to_device(g)
+    views = [synth.orbit_camera(k, 300, 8.0, 1352, 1014) for k in (5, 80, 150, 230)]
+    rend = r4g.Renderer(tile=(8, 8))
+    res = rend.render_batch(p, views)
+    st, need = rend.status(res)
+    assert st == 0 and need > 0
+    for k, (cam, t) in enumerate(views):
+        assert torch.equal(r4g.Renderer().render(p, cam, t).image, res.images[k]), k
+
+
 def test_batch_tile_shapes_and_autotune(r4g):
     g, _, _ = synth.small_scene(seed=42)
     p = to_device(g)
